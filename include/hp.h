@@ -1,0 +1,189 @@
+/*
+ * hp.h -- C ABI of the GB300 DFPT Hubbard-parameter engine (arXiv:2203.15684, the "HP" method).
+ *
+ * The library computes the bare and self-consistent occupation-response matrices chi_0 and chi of
+ * the Hubbard manifolds of a periodic crystal by density-functional perturbation theory, and from
+ * them the Hubbard U and V (Sec. 2.3, Eqs. chi, U_def, V_def).  For every perturbed Hubbard atom J
+ * and wavevector q of a Gamma-centred q mesh it solves the self-consistent q-specific static
+ * Sternheimer problem (Eq. LRKSeq_lp) over all occupied bands of all k points, accumulates the
+ * response occupations (Eq. occ_matrix_response_lp_2) and sums the q components with phases
+ * (Eq. occ_matrix_response_lp_1).  All of it runs in CUDA kernels on one GPU (sm_103a).
+ *
+ * Model: norm-conserving-like model species (a Gaussian local well, one separable projector of
+ * angular momentum l_proj, optional Hubbard orbitals of angular momentum l_hub), plane waves
+ * |k+G|^2 <= ecutwfc [Ry], LDA (Slater + Perdew-Zunger 1981), fixed occupations (insulators),
+ * nspin = 1 or collinear nspin = 2 with tot_magnetization = 0.
+ *
+ * Conventions
+ *   - Every function returns hp_status; nothing throws or exits across the ABI.  The message of
+ *     the last failure is kept in the context (hp_last_error).
+ *   - Host buffers are owned by the caller; the library copies what it reads before returning and
+ *     writes outputs only on HP_OK (HP_ENOTCONV also fills the partial result).  The library owns
+ *     every device allocation it makes and frees it in hp_destroy.
+ *   - Complex arrays are interleaved (re, im) FP64.  Units: bohr, Hartree; ecutwfc in Ry; chi in
+ *     electrons per Ha; U and V in eV (1 Ha = 27.211386245988 eV).
+ *   - Meshes: Gamma-centred, unshifted; point index (i1*n2 + i2)*n3 + i3, crystal coordinate i/n.
+ *   - Real-space grid: point (j1, j2, j3) at sum_i (j_i/N_i) a_i, flat index (j1*N2 + j2)*N3 + j3.
+ *   - A lattice-periodic function u(r) = sum_G c(G) exp(iG.r) with sum |c|^2 = 1.
+ *   - Work is issued on the stream given in hp_options.cuda_stream (0 = legacy default stream);
+ *     every call synchronises that stream before returning host results.
+ */
+#ifndef HP_H
+#define HP_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hp_ctx hp_ctx;
+
+typedef enum {
+    HP_OK = 0,
+    HP_EINVAL = 1,      /* an argument is out of range or inconsistent */
+    HP_ENOMEM = 2,      /* a device or host allocation failed */
+    HP_ESTATE = 3,      /* called out of order (e.g. hp_response before a ground state) */
+    HP_ENOTCONV = 4,    /* an iteration hit its cap; partial results are filled in */
+    HP_ENUMERIC = 5,    /* NaN/Inf met in an FP64 scalar */
+    HP_ECUDA = 6,       /* a CUDA runtime call failed (message in hp_last_error) */
+    HP_ETIMEOUT = 7,    /* reserved: a bounded device wait ran out */
+    HP_ESINGULAR = 8,   /* chi_0 or chi could not be inverted (condition number > 1e12) */
+    HP_ENOGAP = 9,      /* the ground state has no gap (<= 1e-4 Ha) at the fixed band count */
+    HP_ENOTIMPL = 10    /* the requested form is not available */
+} hp_status;
+
+/* One model species.  V_loc(r) = amp * exp(-r^2 / (2 width^2)) [Ha, bohr]; one separable projector
+ * |beta_lm> D <beta_lm| with radial r^l_proj exp(-r^2 / (2 proj_width^2)) normalised to
+ * int r^2 R^2 dr = 1 (D in Ha; D = 0 switches it off); Hubbard orbitals phi_lm with radial
+ * r^l_hub exp(-r^2 / (2 hub_width^2)), normalised the same way, l_hub < 0: not a Hubbard species.
+ * 0 <= l_proj, l_hub <= 2. */
+typedef struct {
+    double amp, width;
+    int l_proj;
+    double D, proj_width;
+    int l_hub;
+    double hub_width;
+} hp_species;
+
+#define HP_PRECISION_FP64 0
+#define HP_PRECISION_MIXED 1
+
+typedef struct {
+    int precision;          /* HP_PRECISION_FP64 (HP_PRECISION_MIXED: HP_ENOTIMPL for now) */
+    double cg_tol;          /* Sternheimer CG: stop a band when ||r_v||_2 <= cg_tol (1e-11) */
+    int cg_maxiter;         /* per outer iteration (default 400) */
+    double scf_tol;         /* response SCF: rms of dV_out - dV_in below this (1e-10) ...      */
+    double conv_thr_chi;    /* ... and every response trace changed by less than this (1e-10) */
+    int niter_max;          /* outer iterations (default 100, as the paper's niter_max) */
+    int nmix;               /* modified Broyden history (default 4) */
+    double alpha_mix;       /* mixing parameter (default 0.3) */
+    double gs_tol;          /* ground-state SCF: rms residual of V_Hxc (default 1e-11) */
+    int gs_maxiter;         /* ground-state SCF iterations (default 200) */
+    int fft_grid[3];        /* FFT grid; 0 = smallest alias-free 2-3-5 grid */
+    int band_batch;         /* bands per FFT batch (0 = automatic) */
+    void* cuda_stream;      /* cudaStream_t to issue work on; NULL = legacy default stream */
+} hp_options;
+
+/* Fills *opt with the defaults listed above. */
+void hp_default_options(hp_options* opt);
+
+typedef struct {
+    int nk, nq, nspin, nocc, nbnd;  /* nbnd: bands kept per k by the ground state (nocc + extra) */
+    int grid[3], nr;
+    int nat, nhub_atoms, nhub_orb, nproj, mmax; /* mmax: padded m dimension of Delta n (5) */
+    int npw_max;                    /* largest wavefunction sphere over the k mesh */
+    int ncell;                      /* N_q: cells of the supercell imaged by the q mesh */
+    int nchi;                       /* N_H * N_q, the dimension of chi */
+} hp_sizes;
+
+typedef struct {
+    int iterations;         /* SCF iterations */
+    double residual;        /* final rms residual of V_Hxc */
+    double gap;             /* min over spins of (lowest empty - highest occupied) [Ha] */
+    double homo, lumo;
+    double seconds;
+} hp_gs_info;
+
+typedef struct {
+    int iterations;         /* outer (self-consistency) iterations */
+    long long cg_iterations;/* summed over bands */
+    long long hpsi;         /* single-band applications of the Sternheimer operator */
+    double residual;        /* final rms of dV_out - dV_in */
+    double dchi;            /* final change of the response traces */
+    double seconds;
+} hp_resp_info;
+
+/* ------------------------------------------------------------------------------------------ */
+/* Set-up (a1 of the hot path: the cell, spheres, grid maps, closed-form form factors).
+ * cell: lattice vectors as rows (bohr), 9 doubles.  sp: nspecies species.  species_of: natoms
+ * indices into sp.  frac_pos: natoms x 3 crystal coordinates.  kmesh, qmesh: Gamma-centred mesh
+ * sizes; every q-mesh size must divide the k-mesh size along its axis (k+q stays on the k mesh).
+ * opt may be NULL (defaults).  *out receives a new context owned by the caller (hp_destroy).
+ * Errors: HP_EINVAL (bad sizes, a grid too small for the sphere, l out of range), HP_ECUDA,
+ * HP_ENOMEM.  On error *out is NULL. */
+hp_status hp_setup(const double cell[9], int nspecies, const hp_species* sp, int natoms,
+                   const int* species_of, const double* frac_pos, double ecutwfc_ry,
+                   const int kmesh[3], const int qmesh[3], const hp_options* opt, hp_ctx** out);
+
+hp_status hp_query_sizes(const hp_ctx* ctx, hp_sizes* out);
+
+/* Wavefunction sphere at k point ik of the mesh: *npw receives its size; if miller != NULL it
+ * receives npw x 3 Miller indices (int) in the library's coefficient order. */
+hp_status hp_sphere(const hp_ctx* ctx, int ik, int* npw, int* miller);
+
+/* Hubbard atoms: atom index (0-based, into the set-up atom list) and m dimension, for each of the
+ * nhub_atoms Hubbard atoms in order.  Either pointer may be NULL. */
+hp_status hp_hubbard_atoms(const hp_ctx* ctx, int* atom_index, int* mdim);
+
+/* Ground state by the library: fixed-occupation SCF on the GPU (LDA/LSDA), nelec electrons,
+ * nspin 1 or 2; init_moment: natoms signs (+1, -1, 0) of the starting magnetisation, NULL for
+ * none.  Starting density: uniform nelec/Omega, for nspin = 2 split as rho0/2 (1 +- s(r)),
+ * s(r) = clip(sum_I m_I 0.9 exp(-|r - tau_I|^2 / 2), -0.9, 0.9).
+ * Errors: HP_EINVAL, HP_ENOTCONV, HP_ENOGAP (the state is kept; hp_response refuses it). */
+hp_status hp_ground_state(hp_ctx* ctx, double nelec, int nspin, const int* init_moment,
+                          hp_gs_info* info);
+
+/* Imports a ground state (so that the response can be checked on identical inputs).
+ * vhxc, rho: nspin x nr (real, V_H + V_xc and the spin densities).  eps: nspin x nk x nocc.
+ * psi: for each spin, for each k, nocc vectors of npw_k complex coefficients in hp_sphere order,
+ * packed without padding.  The band count per spin is nocc = nelec / 2 (fixed occupations).
+ * Errors: HP_EINVAL. */
+hp_status hp_set_ground_state(hp_ctx* ctx, int nspin, double nelec, const double* vhxc,
+                              const double* rho, const double* eps, const double* psi);
+
+/* Reads back the ground state: any pointer may be NULL.  eps: nspin x nk x nocc; rho, vhxc:
+ * nspin x nr.  Errors: HP_ESTATE before a ground state. */
+hp_status hp_get_ground_state(const hp_ctx* ctx, double* eps, double* rho, double* vhxc);
+
+/* Kohn-Sham operator at mesh point ik and spin s applied to nb host vectors (npw_k complex each,
+ * hp_sphere order): out = H psi with H = T + V_loc + V_Hxc,s + V_NL (needs a ground state). */
+hp_status hp_apply_h(hp_ctx* ctx, int ik, int spin, int nb, const double* psi, double* out);
+
+/* One (q, J) response (hot path a1-a10): iq indexes the q mesh, atom is the index of the
+ * perturbed Hubbard atom in the set-up atom list.  dn0 / dn (may be NULL) receive the bare and
+ * self-consistent Delta_q n^{s sigma}_{m1 m2} as complex [nhub_atoms][nspin][mmax][mmax]
+ * (m1 slowest of the two, rows beyond the atom's m dimension zero).  The columns are also kept in
+ * the context for hp_hubbard.  Errors: HP_ESTATE (no ground state), HP_ENOGAP, HP_EINVAL,
+ * HP_ENOTCONV (partial data written), HP_ENUMERIC. */
+hp_status hp_response(hp_ctx* ctx, int iq, int atom, double* dn0, double* dn, hp_resp_info* info);
+
+/* Post-processing (a11): chi0, chi: real nchi x nchi (row-major, index (l, s) -> l*nhub_atoms+s,
+ * l the supercell cell (l1*n2 + l2)*n3 + l3); hub: (chi0^-1 - chi^-1) in eV (U on the diagonal,
+ * V off it).  Any pointer may be NULL.  Needs every (q, J) column (HP_ESTATE otherwise).
+ * Errors: HP_ESINGULAR. */
+hp_status hp_hubbard(hp_ctx* ctx, double* chi0, double* chi, double* hub);
+
+/* Message of the last failure on this context ("" if none).  Valid until the next call. */
+const char* hp_last_error(const hp_ctx* ctx);
+
+/* Frees the context and all device memory it owns.  NULL is ignored. */
+void hp_destroy(hp_ctx* ctx);
+
+/* Host-only self-test of the FFT engine's stage logic (runs the same Stockham code on the CPU).
+ * in/out: nlines x n complex; sign -1 forward exp(-2 pi i jk/n), +1 backward (unnormalised). */
+hp_status hp_selftest_fft_host(int n, int nlines, int sign, const double* in, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HP_H */

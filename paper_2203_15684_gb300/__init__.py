@@ -1,0 +1,255 @@
+"""Python binding of the GB300 DFPT Hubbard-parameter engine (C ABI in include/hp.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA kernels of
+``libhpgb.so``.  There is no CPU fallback; if the library is missing the import of a function
+raises, and a call on a machine without a GPU returns HP_ECUDA.
+
+    ctx = Context.from_workload(w)          # hp_setup
+    ctx.ground_state(nelec, nspin, moments) # hp_ground_state  (or ctx.set_ground_state(...))
+    dn0, dn, info = ctx.response(iq, atom)  # hp_response
+    chi0, chi, hub = ctx.hubbard()          # hp_hubbard
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhpgb.so")
+
+STATUS = {0: "HP_OK", 1: "HP_EINVAL", 2: "HP_ENOMEM", 3: "HP_ESTATE", 4: "HP_ENOTCONV", 5: "HP_ENUMERIC",
+          6: "HP_ECUDA", 7: "HP_ETIMEOUT", 8: "HP_ESINGULAR", 9: "HP_ENOGAP", 10: "HP_ENOTIMPL"}
+HP_OK, HP_ENOTCONV = 0, 4
+
+
+class HPError(RuntimeError):
+    def __init__(self, code, where, msg=""):
+        self.code = code
+        super().__init__("%s failed: %s %s" % (where, STATUS.get(code, code), msg))
+
+
+class Species(C.Structure):
+    _fields_ = [("amp", C.c_double), ("width", C.c_double), ("l_proj", C.c_int), ("D", C.c_double),
+                ("proj_width", C.c_double), ("l_hub", C.c_int), ("hub_width", C.c_double)]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("cg_tol", C.c_double), ("cg_maxiter", C.c_int), ("scf_tol", C.c_double),
+                ("conv_thr_chi", C.c_double), ("niter_max", C.c_int), ("nmix", C.c_int), ("alpha_mix", C.c_double),
+                ("gs_tol", C.c_double), ("gs_maxiter", C.c_int), ("fft_grid", C.c_int * 3), ("band_batch", C.c_int),
+                ("cuda_stream", C.c_void_p)]
+
+
+class Sizes(C.Structure):
+    _fields_ = [(n, C.c_int) for n in ("nk", "nq", "nspin", "nocc", "nbnd")] + [("grid", C.c_int * 3), ("nr", C.c_int)] + \
+               [(n, C.c_int) for n in ("nat", "nhub_atoms", "nhub_orb", "nproj", "mmax", "npw_max", "ncell", "nchi")]
+
+
+class GsInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("residual", C.c_double), ("gap", C.c_double), ("homo", C.c_double),
+                ("lumo", C.c_double), ("seconds", C.c_double)]
+
+
+class RespInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("cg_iterations", C.c_longlong), ("hpsi", C.c_longlong),
+                ("residual", C.c_double), ("dchi", C.c_double), ("seconds", C.c_double)]
+
+
+_lib = None
+
+SYMBOLS = ["hp_default_options", "hp_setup", "hp_query_sizes", "hp_sphere", "hp_hubbard_atoms", "hp_ground_state",
+           "hp_set_ground_state", "hp_get_ground_state", "hp_apply_h", "hp_response", "hp_hubbard", "hp_last_error",
+           "hp_destroy", "hp_selftest_fft_host"]
+
+
+def lib():
+    """The loaded engine library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libhpgb.so is not built (run `python -m paper_2203_15684_gb300.build`); "
+                           "there is no CPU fallback")
+    L = C.CDLL(LIB_PATH)
+    P, I, D, V = C.POINTER, C.c_int, C.c_double, C.c_void_p
+    L.hp_default_options.argtypes = [P(Options)]
+    L.hp_default_options.restype = None
+    L.hp_setup.argtypes = [P(D), I, P(Species), I, P(I), P(D), D, P(I), P(I), P(Options), P(V)]
+    L.hp_query_sizes.argtypes = [V, P(Sizes)]
+    L.hp_sphere.argtypes = [V, I, P(I), P(I)]
+    L.hp_hubbard_atoms.argtypes = [V, P(I), P(I)]
+    L.hp_ground_state.argtypes = [V, D, I, P(I), P(GsInfo)]
+    L.hp_set_ground_state.argtypes = [V, I, D, P(D), P(D), P(D), P(D)]
+    L.hp_get_ground_state.argtypes = [V, P(D), P(D), P(D)]
+    L.hp_apply_h.argtypes = [V, I, I, I, P(D), P(D)]
+    L.hp_response.argtypes = [V, I, I, P(D), P(D), P(RespInfo)]
+    L.hp_hubbard.argtypes = [V, P(D), P(D), P(D)]
+    L.hp_last_error.argtypes = [V]
+    L.hp_last_error.restype = C.c_char_p
+    L.hp_destroy.argtypes = [V]
+    L.hp_destroy.restype = None
+    L.hp_selftest_fft_host.argtypes = [I, I, I, P(D), P(D)]
+    for n in SYMBOLS:
+        f = getattr(L, n)
+        if n not in ("hp_default_options", "hp_last_error", "hp_destroy"):
+            f.restype = I
+    _lib = L
+    return L
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _iptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def default_options(**kw):
+    o = Options()
+    lib().hp_default_options(C.byref(o))
+    for k, v in kw.items():
+        if k == "fft_grid":
+            for i in range(3):
+                o.fft_grid[i] = int(v[i]) if v is not None else 0
+        else:
+            setattr(o, k, v)
+    return o
+
+
+def selftest_fft_host(x, sign):
+    """Runs the engine's Stockham stage code on the host: x (nlines, n) complex."""
+    x = np.ascontiguousarray(x, dtype=np.complex128)
+    nlines, n = x.shape
+    out = np.empty_like(x)
+    st = lib().hp_selftest_fft_host(n, nlines, sign, _dptr(x.view(np.float64)), _dptr(out.view(np.float64)))
+    if st != HP_OK:
+        raise HPError(st, "hp_selftest_fft_host")
+    return out
+
+
+class Context:
+    """An hp_ctx: one crystal, its ground state and its response columns."""
+
+    def __init__(self, cell, species, atoms, ecutwfc, kmesh, qmesh, options=None):
+        L = lib()
+        self._ptr = C.c_void_p()
+        cell = np.ascontiguousarray(np.asarray(cell, dtype=np.float64).reshape(9))
+        sp = (Species * len(species))()
+        for i, s in enumerate(species):
+            sp[i] = Species(s["amp"], s["width"], int(s["l_proj"]), s["D"], s["proj_width"], int(s["l_hub"]),
+                            s["hub_width"])
+        kinds = np.ascontiguousarray([int(a[0]) for a in atoms], dtype=np.int32)
+        frac = np.ascontiguousarray([list(a[1]) for a in atoms], dtype=np.float64).reshape(-1)
+        km = np.ascontiguousarray(kmesh, dtype=np.int32)
+        qm = np.ascontiguousarray(qmesh, dtype=np.int32)
+        opt = options if options is not None else default_options()
+        st = L.hp_setup(_dptr(cell), len(species), sp, len(kinds), _iptr(kinds), _dptr(frac), float(ecutwfc),
+                        _iptr(km), _iptr(qm), C.byref(opt), C.byref(self._ptr))
+        if st != HP_OK:
+            raise HPError(st, "hp_setup")
+
+    @classmethod
+    def from_workload(cls, w, **opts):
+        opts.setdefault("fft_grid", w.get("grid"))
+        return cls(w["cell"], w["species"], w["atoms"], w["ecutwfc"], w["kmesh"], w["qmesh"], default_options(**opts))
+
+    # -------------------------------------------------------------------------------------------
+    def _check(self, st, where, ok=(HP_OK,)):
+        if st not in ok:
+            raise HPError(st, where, self.last_error())
+        return st
+
+    def last_error(self):
+        return lib().hp_last_error(self._ptr).decode()
+
+    def destroy(self):
+        if self._ptr:
+            lib().hp_destroy(self._ptr)
+            self._ptr = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def query_sizes(self):
+        s = Sizes()
+        self._check(lib().hp_query_sizes(self._ptr, C.byref(s)), "hp_query_sizes")
+        d = {n: getattr(s, n) for n, _ in Sizes._fields_}
+        d["grid"] = tuple(s.grid)
+        return d
+
+    def sphere(self, ik):
+        n = C.c_int()
+        self._check(lib().hp_sphere(self._ptr, ik, C.byref(n), None), "hp_sphere")
+        m = np.zeros((n.value, 3), dtype=np.int32)
+        self._check(lib().hp_sphere(self._ptr, ik, C.byref(n), _iptr(m)), "hp_sphere")
+        return m
+
+    def hubbard_atoms(self):
+        nh = self.query_sizes()["nhub_atoms"]
+        a = np.zeros(nh, dtype=np.int32)
+        m = np.zeros(nh, dtype=np.int32)
+        self._check(lib().hp_hubbard_atoms(self._ptr, _iptr(a), _iptr(m)), "hp_hubbard_atoms")
+        return a, m
+
+    def ground_state(self, nelec, nspin, moments=None):
+        info = GsInfo()
+        mom = None
+        if moments is not None:
+            mom_a = np.ascontiguousarray(moments, dtype=np.int32)
+            mom = _iptr(mom_a)
+        st = lib().hp_ground_state(self._ptr, float(nelec), int(nspin), mom, C.byref(info))
+        self._check(st, "hp_ground_state")
+        return {n: getattr(info, n) for n, _ in GsInfo._fields_}
+
+    def set_ground_state(self, nspin, nelec, vhxc, rho, eps, psi):
+        """psi: list over spin of lists over k of (npw_k, nocc) complex arrays in sphere order."""
+        vh = np.ascontiguousarray(vhxc, dtype=np.float64).reshape(-1)
+        rh = np.ascontiguousarray(rho, dtype=np.float64).reshape(-1)
+        ep = np.ascontiguousarray(eps, dtype=np.float64).reshape(-1)
+        flat = np.concatenate([np.ascontiguousarray(psi[s][k].T).reshape(-1) for s in range(nspin)
+                               for k in range(len(psi[s]))]).astype(np.complex128)
+        self._check(lib().hp_set_ground_state(self._ptr, int(nspin), float(nelec), _dptr(vh), _dptr(rh), _dptr(ep),
+                                              _dptr(flat.view(np.float64))), "hp_set_ground_state")
+
+    def get_ground_state(self):
+        s = self.query_sizes()
+        eps = np.zeros((s["nspin"], s["nk"], s["nocc"]))
+        rho = np.zeros((s["nspin"], s["nr"]))
+        vhxc = np.zeros((s["nspin"], s["nr"]))
+        self._check(lib().hp_get_ground_state(self._ptr, _dptr(eps), _dptr(rho), _dptr(vhxc)), "hp_get_ground_state")
+        return eps, rho, vhxc
+
+    def apply_h(self, ik, spin, psi):
+        """psi: (nb, npw_k) complex in sphere order -> H psi, same shape."""
+        x = np.ascontiguousarray(psi, dtype=np.complex128)
+        out = np.empty_like(x)
+        self._check(lib().hp_apply_h(self._ptr, ik, spin, x.shape[0], _dptr(x.view(np.float64)),
+                                     _dptr(out.view(np.float64))), "hp_apply_h")
+        return out
+
+    def response(self, iq, atom):
+        """Returns (dn0, dn, info); dn arrays complex [nhub_atoms][nspin][mmax][mmax]."""
+        s = self.query_sizes()
+        shape = (s["nhub_atoms"], s["nspin"], s["mmax"], s["mmax"])
+        dn0 = np.zeros(shape, dtype=np.complex128)
+        dn = np.zeros(shape, dtype=np.complex128)
+        info = RespInfo()
+        st = lib().hp_response(self._ptr, int(iq), int(atom), _dptr(dn0.view(np.float64)), _dptr(dn.view(np.float64)),
+                               C.byref(info))
+        self._check(st, "hp_response")
+        return dn0, dn, {n: getattr(info, n) for n, _ in RespInfo._fields_}
+
+    def hubbard(self):
+        n = self.query_sizes()["nchi"]
+        chi0 = np.zeros((n, n))
+        chi = np.zeros((n, n))
+        hub = np.zeros((n, n))
+        self._check(lib().hp_hubbard(self._ptr, _dptr(chi0), _dptr(chi), _dptr(hub)), "hp_hubbard")
+        return chi0, chi, hub

@@ -1,0 +1,1134 @@
+// Orchestration and C ABI of the DFPT Hubbard engine.
+//
+// hp_setup        a1: cell, reciprocal lattice, wavefunction spheres, FFT grid maps, closed-form
+//                 form factors beta and phi at the k mesh, V_loc on the grid.
+// hp_response     a3-a10 for one (q, J): V_pert u, Delta V_Hxc u, P_c, the batched Sternheimer CG
+//                 over every (spin, k, band), Delta rho, Delta n, Delta V_Hxc, modified Broyden.
+// hp_hubbard      a11: q-sum with phases, chi_0 and chi, FP64 inverses, U and V.
+// Every arithmetic step runs in the kernels of kernels.cu / fft.cu; host code only builds index
+// lists, moves a few scalars for control flow and copies results out.
+#include <algorithm>
+#include <array>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "hp_internal.h"
+
+using namespace hp;
+
+namespace {
+
+constexpr double kHaToEv = 27.211386245988;
+constexpr int kMmax = 5;
+constexpr int kPStride = 128;
+
+hp_status fail(hp_ctx* c, hp_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+hp_status cuda_fail(hp_ctx* c, cudaError_t e, const char* what) {
+    char buf[512];
+    snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+    if (c) c->err = buf;
+    return e == cudaErrorMemoryAllocation ? HP_ENOMEM : HP_ECUDA;
+}
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, #call);     \
+    } while (0)
+
+template <class T>
+cudaError_t dalloc(hp_ctx* c, T** p, size_t n) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc((void**)p, sizeof(T) * n);
+    if (e == cudaSuccess) c->owned.push_back((void*)*p);
+    return e;
+}
+
+void dfree(hp_ctx* c, void* p) {
+    if (!p) return;
+    auto it = std::find(c->owned.begin(), c->owned.end(), p);
+    if (it != c->owned.end()) c->owned.erase(it);
+    cudaFree(p);
+}
+
+template <class T>
+cudaError_t h2d(T* d, const T* h, size_t n, cudaStream_t st) {
+    return cudaMemcpyAsync(d, h, sizeof(T) * n, cudaMemcpyHostToDevice, st);
+}
+
+template <class T>
+cudaError_t d2h(T* h, const T* d, size_t n, cudaStream_t st) {
+    cudaError_t e = cudaMemcpyAsync(h, d, sizeof(T) * n, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(st);
+}
+
+int good_fft_size(int n) {
+    for (int m = std::max(1, n);; ++m) {
+        int k = m;
+        for (int p : {2, 3, 5})
+            while (k % p == 0) k /= p;
+        if (k == 1) return m;
+    }
+}
+
+void cross(const double* a, const double* b, double* o) {
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// enumerate the sphere |k + m.B|^2 <= ecut, ordered by (|k+G|^2, m)
+void build_sphere(const hp_ctx* c, const double kfrac[3], KSphere& s) {
+    for (int i = 0; i < 3; ++i) {
+        s.kfrac[i] = kfrac[i];
+        s.kcart[i] = kfrac[0] * c->bvec[0 * 3 + i] + kfrac[1] * c->bvec[1 * 3 + i] + kfrac[2] * c->bvec[2 * 3 + i];
+    }
+    const double kn = std::sqrt(s.kcart[0] * s.kcart[0] + s.kcart[1] * s.kcart[1] + s.kcart[2] * s.kcart[2]);
+    const double gmax = std::sqrt(c->ecut) + kn;
+    int lim[3];
+    for (int i = 0; i < 3; ++i) {
+        const double an = std::sqrt(c->cell[3 * i] * c->cell[3 * i] + c->cell[3 * i + 1] * c->cell[3 * i + 1] +
+                                    c->cell[3 * i + 2] * c->cell[3 * i + 2]);
+        lim[i] = (int)std::ceil(gmax * an / (2.0 * M_PI)) + 1;
+    }
+    struct E { double g2; int m[3]; };
+    std::vector<E> v;
+    for (int a = -lim[0]; a <= lim[0]; ++a)
+        for (int b = -lim[1]; b <= lim[1]; ++b)
+            for (int d = -lim[2]; d <= lim[2]; ++d) {
+                double K[3];
+                for (int i = 0; i < 3; ++i) K[i] = s.kcart[i] + a * c->bvec[i] + b * c->bvec[3 + i] + d * c->bvec[6 + i];
+                const double g2 = K[0] * K[0] + K[1] * K[1] + K[2] * K[2];
+                if (g2 <= c->ecut) v.push_back({g2, {a, b, d}});
+            }
+    std::sort(v.begin(), v.end(), [](const E& x, const E& y) {
+        const double rx = std::round(x.g2 * 1e12), ry = std::round(y.g2 * 1e12);
+        if (rx != ry) return rx < ry;
+        if (x.m[0] != y.m[0]) return x.m[0] < y.m[0];
+        if (x.m[1] != y.m[1]) return x.m[1] < y.m[1];
+        return x.m[2] < y.m[2];
+    });
+    s.npw = (int)v.size();
+    s.miller.resize(3 * s.npw);
+    s.g2.resize(s.npw);
+    for (int i = 0; i < s.npw; ++i) {
+        for (int j = 0; j < 3; ++j) s.miller[3 * i + j] = v[i].m[j];
+        s.g2[i] = v[i].g2;
+    }
+}
+
+int grid_index(const hp_ctx* c, int m0, int m1, int m2) {
+    auto md = [](int m, int n) { return ((m % n) + n) % n; };
+    return (md(m0, c->N[0]) * c->N[1] + md(m1, c->N[1])) * c->N[2] + md(m2, c->N[2]);
+}
+
+// sphere set upload: npw per k, grid index (Miller shifted by -shift[k]), |k+G|^2
+hp_status upload_sphereset(hp_ctx* c, const std::vector<const KSphere*>& sph, const std::vector<std::array<int, 3>>* shift,
+                           SphereSet& S) {
+    const int nk = (int)sph.size(), ld = c->ld;
+    S.nk = nk;
+    S.ld = ld;
+    S.npw.resize(nk);
+    std::vector<int> idx((size_t)nk * ld, 0);
+    std::vector<double> g2((size_t)nk * ld, 0.0);
+    for (int k = 0; k < nk; ++k) {
+        const KSphere& s = *sph[k];
+        S.npw[k] = s.npw;
+        std::vector<char> seen(c->nr, 0);
+        for (int i = 0; i < s.npw; ++i) {
+            int m[3];
+            for (int j = 0; j < 3; ++j) m[j] = s.miller[3 * i + j] - (shift ? (*shift)[k][j] : 0);
+            const int gi = grid_index(c, m[0], m[1], m[2]);
+            if (seen[gi]) return fail(c, HP_EINVAL, "FFT grid too small to hold the wavefunction sphere");
+            seen[gi] = 1;
+            idx[(size_t)k * ld + i] = gi;
+            g2[(size_t)k * ld + i] = s.g2[i];
+        }
+    }
+    if (!S.d_npw) {
+        CK(dalloc(c, &S.d_npw, nk));
+        CK(dalloc(c, &S.d_idx, (size_t)nk * ld));
+        CK(dalloc(c, &S.d_g2, (size_t)nk * ld));
+    }
+    CK(h2d(S.d_npw, S.npw.data(), nk, c->st));
+    CK(h2d(S.d_idx, idx.data(), idx.size(), c->st));
+    CK(h2d(S.d_g2, g2.data(), g2.size(), c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return HP_OK;
+}
+
+// upload a band list (host vectors row/k/spin/shift filled by the caller); builds segments
+hp_status upload_list(hp_ctx* c, BandList& L) {
+    L.nb = (int)L.row.size();
+    L.seg_start.clear();
+    L.seg_k.clear();
+    L.seg_s.clear();
+    for (int i = 0; i < L.nb; ++i) {
+        if (i == 0 || L.k[i] != L.k[i - 1] || L.spin[i] != L.spin[i - 1]) {
+            L.seg_start.push_back(i);
+            L.seg_k.push_back(L.k[i]);
+            L.seg_s.push_back(L.spin[i]);
+        }
+    }
+    L.seg_start.push_back(L.nb);
+    L.nseg = (int)L.seg_k.size();
+    if (L.nb + 1 > L.cap) {
+        for (void* p : {(void*)L.d_row, (void*)L.d_k, (void*)L.d_spin, (void*)L.d_shift, (void*)L.d_seg_start,
+                        (void*)L.d_seg_k, (void*)L.d_seg_s})
+            dfree(c, p);
+        const int cap = L.nb + 1;
+        CK(dalloc(c, &L.d_row, cap));
+        CK(dalloc(c, &L.d_k, cap));
+        CK(dalloc(c, &L.d_spin, cap));
+        CK(dalloc(c, &L.d_shift, cap));
+        CK(dalloc(c, &L.d_seg_start, cap + 1));
+        CK(dalloc(c, &L.d_seg_k, cap));
+        CK(dalloc(c, &L.d_seg_s, cap));
+        L.cap = cap;
+    }
+    if (L.nb == 0) return HP_OK;
+    CK(h2d(L.d_row, L.row.data(), L.nb, c->st));
+    CK(h2d(L.d_k, L.k.data(), L.nb, c->st));
+    CK(h2d(L.d_spin, L.spin.data(), L.nb, c->st));
+    CK(h2d(L.d_shift, L.shift.data(), L.nb, c->st));
+    CK(h2d(L.d_seg_start, L.seg_start.data(), L.nseg + 1, c->st));
+    CK(h2d(L.d_seg_k, L.seg_k.data(), L.nseg, c->st));
+    CK(h2d(L.d_seg_s, L.seg_s.data(), L.nseg, c->st));
+    return HP_OK;
+}
+
+void list_clear(BandList& L) {
+    L.row.clear();
+    L.k.clear();
+    L.spin.clear();
+    L.shift.clear();
+}
+
+void list_add(BandList& L, int row, int k, int spin, double shift) {
+    L.row.push_back(row);
+    L.k.push_back(k);
+    L.spin.push_back(spin);
+    L.shift.push_back(shift);
+}
+
+hp_status ensure_grid(hp_ctx* c, int want) {
+    if (want <= c->grid_cap) return HP_OK;
+    dfree(c, c->d_grid);
+    c->d_grid = nullptr;
+    CK(dalloc(c, &c->d_grid, (size_t)want * c->nr));
+    c->grid_cap = want;
+    return HP_OK;
+}
+
+int band_batch(const hp_ctx* c, int nb) {
+    if (c->opt.band_batch > 0) return std::min(nb, std::min(c->opt.band_batch, 32768));
+    const size_t budget = (size_t)768 << 20;  // bytes of grid buffers
+    int b = (int)std::min<size_t>(32768, std::max<size_t>(1, budget / (sizeof(double2) * (size_t)c->nr)));
+    return std::max(1, std::min(nb, b));
+}
+
+hp_status ensure_scratch(hp_ctx* c, size_t elems) {
+    if (elems <= c->scratch_elems) return HP_OK;
+    dfree(c, c->d_scratch);
+    c->d_scratch = nullptr;
+    CK(dalloc(c, &c->d_scratch, elems));
+    c->scratch_elems = elems;
+    return HP_OK;
+}
+
+// Y = (T + V_loc + V_Hxc,s - shift) X on the list items (grid part + kinetic, zero padding)
+hp_status apply_local(hp_ctx* c, const SphereSet& S, const BandList& L, const double2* X, double2* Y,
+                      const double* veff) {
+    if (L.nb == 0) return HP_OK;
+    hp_status s = ensure_grid(c, band_batch(c, L.nb));
+    if (s != HP_OK) return s;
+    for (int c0 = 0; c0 < L.nb; c0 += c->grid_cap) {
+        const int nc = std::min(c->grid_cap, L.nb - c0);
+        CK(k_scatter(S, L, c0, nc, X, c->ld, c->d_grid, c->nr, c->st));
+        CK(fft3d(c->fft, c->d_grid, nc, +1, c->st));
+        CK(k_mul_rpot(c->d_grid, nc, c->nr, veff, L, c0, c->st));
+        CK(fft3d(c->fft, c->d_grid, nc, -1, c->st));
+        CK(k_gather_h(S, L, c0, nc, c->d_grid, c->nr, X, Y, c->ld, c->st));
+    }
+    return HP_OK;
+}
+
+hp_status project(hp_ctx* c, const SphereSet& S, const BandList& L, const ProjMat& A, const double2* X, double2* P) {
+    hp_status s = ensure_scratch(c, (size_t)8 * std::max(1, L.nb) * kPStride);
+    if (s != HP_OK) return s;
+    CK(k_proj(L, S, A, X, c->ld, P, c->d_scratch, c->scratch_elems, c->st));
+    return HP_OK;
+}
+
+ProjMat beta_family(const hp_ctx* c, const int* kmap) {
+    return ProjMat{c->d_beta_k, 0, (long long)c->nproj * c->ld, c->nproj, 0, kmap};
+}
+
+// Y += V_NL X  (beta D beta^H, beta at the list's spheres)
+hp_status apply_nonlocal(hp_ctx* c, const SphereSet& S, const BandList& L, const double2* X, double2* Y, double2* P,
+                         const int* kmap) {
+    if (c->nproj == 0) return HP_OK;
+    ProjMat B = beta_family(c, kmap);
+    hp_status s = project(c, S, L, B, X, P);
+    if (s != HP_OK) return s;
+    CK(k_expand(L, S, B, P, c->d_projD, 1.0, Y, c->ld, c->st));
+    return HP_OK;
+}
+
+hp_status resp_alloc(hp_ctx* c);
+
+}  // namespace
+
+// ================================================================================================
+// C ABI
+// ================================================================================================
+extern "C" void hp_default_options(hp_options* o) {
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->precision = HP_PRECISION_FP64;
+    o->cg_tol = 1e-11;
+    o->cg_maxiter = 400;
+    o->scf_tol = 1e-10;
+    o->conv_thr_chi = 1e-10;
+    o->niter_max = 100;
+    o->nmix = 4;
+    o->alpha_mix = 0.3;
+    o->gs_tol = 1e-11;
+    o->gs_maxiter = 200;
+    o->band_batch = 0;
+    o->cuda_stream = nullptr;
+}
+
+extern "C" const char* hp_last_error(const hp_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+extern "C" void hp_destroy(hp_ctx* c) {
+    if (!c) return;
+    for (void* p : c->owned) cudaFree(p);
+    c->owned.clear();
+    fft_plan_destroy(c->fft);
+    delete c;
+}
+
+static hp_status setup_impl(hp_ctx* c, const double cell[9], int nspecies, const hp_species* sp, int natoms,
+                            const int* species_of, const double* frac_pos, double ecut, const int kmesh[3],
+                            const int qmesh[3]) {
+    if (!cell || nspecies < 1 || !sp || natoms < 1 || !species_of || !frac_pos || !(ecut > 0) || !kmesh || !qmesh)
+        return fail(c, HP_EINVAL, "hp_setup: missing or non-positive argument");
+    for (int i = 0; i < 3; ++i) {
+        if (kmesh[i] < 1 || qmesh[i] < 1) return fail(c, HP_EINVAL, "hp_setup: mesh sizes must be >= 1");
+        if (kmesh[i] % qmesh[i] != 0)
+            return fail(c, HP_ENOTIMPL, "hp_setup: the q mesh must divide the k mesh (k+q off the k mesh needs a "
+                                        "non-self-consistent k+q calculation, not available)");
+    }
+    if (c->opt.nmix < 0 || c->opt.nmix > 8 || !(c->opt.cg_tol > 0) || c->opt.niter_max < 1 || c->opt.cg_maxiter < 1)
+        return fail(c, HP_EINVAL, "hp_setup: options out of range (0 <= nmix <= 8, tolerances > 0)");
+    for (int s = 0; s < nspecies; ++s) {
+        if (sp[s].l_proj < 0 || sp[s].l_proj > 2 || sp[s].l_hub > 2 || !(sp[s].width > 0) || !(sp[s].proj_width > 0) ||
+            (sp[s].l_hub >= 0 && !(sp[s].hub_width > 0)))
+            return fail(c, HP_EINVAL, "hp_setup: species parameters out of range (0 <= l <= 2, widths > 0)");
+    }
+    memcpy(c->cell, cell, sizeof(double) * 9);
+    // reciprocal vectors: b_i = 2 pi (a_j x a_k) / Omega
+    double cr[3][3];
+    cross(cell + 3, cell + 6, cr[0]);
+    cross(cell + 6, cell + 0, cr[1]);
+    cross(cell + 0, cell + 3, cr[2]);
+    const double vol = cell[0] * cr[0][0] + cell[1] * cr[0][1] + cell[2] * cr[0][2];
+    if (std::fabs(vol) < 1e-12) return fail(c, HP_EINVAL, "hp_setup: degenerate cell");
+    c->omega = std::fabs(vol);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) c->bvec[3 * i + j] = 2.0 * M_PI * cr[i][j] / vol;
+    c->species.assign(sp, sp + nspecies);
+    c->atom_species.assign(species_of, species_of + natoms);
+    c->frac.assign(frac_pos, frac_pos + 3 * natoms);
+    c->tau.resize(3 * natoms);
+    for (int a = 0; a < natoms; ++a) {
+        if (species_of[a] < 0 || species_of[a] >= nspecies) return fail(c, HP_EINVAL, "hp_setup: bad species index");
+        for (int j = 0; j < 3; ++j)
+            c->tau[3 * a + j] = frac_pos[3 * a] * cell[j] + frac_pos[3 * a + 1] * cell[3 + j] + frac_pos[3 * a + 2] * cell[6 + j];
+    }
+    c->ecut = ecut;
+    for (int i = 0; i < 3; ++i) {
+        c->kmesh[i] = kmesh[i];
+        c->qmesh[i] = qmesh[i];
+    }
+    c->nk = kmesh[0] * kmesh[1] * kmesh[2];
+    c->nq = qmesh[0] * qmesh[1] * qmesh[2];
+    // FFT grid
+    for (int i = 0; i < 3; ++i) {
+        if (c->opt.fft_grid[i] > 0) {
+            c->N[i] = c->opt.fft_grid[i];
+        } else {
+            const double an = std::sqrt(cell[3 * i] * cell[3 * i] + cell[3 * i + 1] * cell[3 * i + 1] + cell[3 * i + 2] * cell[3 * i + 2]);
+            const int mmax = (int)std::floor(2.0 * std::sqrt(ecut) * an / (2.0 * M_PI));
+            c->N[i] = good_fft_size(2 * mmax + 1);
+        }
+        Radices r;
+        if (!fft_factor(c->N[i], r)) return fail(c, HP_EINVAL, "hp_setup: FFT grid sizes must factor into 2, 3 and 5");
+    }
+    c->nr = c->N[0] * c->N[1] * c->N[2];
+    // spheres at the k mesh
+    c->ks.resize(c->nk);
+    c->ld = 0;
+    for (int i1 = 0, ik = 0; i1 < kmesh[0]; ++i1)
+        for (int i2 = 0; i2 < kmesh[1]; ++i2)
+            for (int i3 = 0; i3 < kmesh[2]; ++i3, ++ik) {
+                const double kf[3] = {(double)i1 / kmesh[0], (double)i2 / kmesh[1], (double)i3 / kmesh[2]};
+                build_sphere(c, kf, c->ks[ik]);
+                c->ld = std::max(c->ld, c->ks[ik].npw);
+            }
+    // projector and Hubbard rows, with the K-independent prefactor
+    //   (4 pi / sqrt(Omega)) N_R sqrt(pi/2) s^(2l+3),  N_R = sqrt(2 / (Gamma(l + 3/2) s^(2l+3)))
+    auto pref = [&](int l, double s) {
+        const double s2l3 = std::pow(s, 2 * l + 3);
+        const double NR = std::sqrt(2.0 / (std::tgamma(l + 1.5) * s2l3));
+        return 4.0 * M_PI / std::sqrt(c->omega) * NR * std::sqrt(M_PI / 2.0) * s2l3;
+    };
+    for (int a = 0; a < natoms; ++a) {
+        const hp_species& s = sp[species_of[a]];
+        for (int m = 0; m < 2 * s.l_proj + 1; ++m) {
+            c->proj_atom.push_back(a);
+            c->proj_l.push_back(s.l_proj);
+            c->proj_m.push_back(m);
+            c->proj_D.push_back(s.D);
+            c->proj_w.push_back(s.proj_width);
+            c->proj_pref.push_back(pref(s.l_proj, s.proj_width));
+        }
+        if (s.l_hub >= 0) {
+            c->hub_atoms.push_back(a);
+            c->hub_off.push_back((int)c->hub_row_atom.size());
+            c->hub_mdim.push_back(2 * s.l_hub + 1);
+            for (int m = 0; m < 2 * s.l_hub + 1; ++m) {
+                c->hub_row_atom.push_back(a);
+                c->hub_row_l.push_back(s.l_hub);
+                c->hub_row_m.push_back(m);
+                c->hub_row_w.push_back(s.hub_width);
+                c->hub_row_pref.push_back(pref(s.l_hub, s.hub_width));
+            }
+        }
+    }
+    c->nproj = (int)c->proj_atom.size();
+    c->nhub = (int)c->hub_row_atom.size();
+    if (c->nproj > kPStride || c->nhub > kPStride) return fail(c, HP_EINVAL, "hp_setup: more than 128 projector rows");
+    if (c->hub_atoms.empty()) return fail(c, HP_EINVAL, "hp_setup: no Hubbard species");
+    // device data
+    CK(fft_plan_create(c->fft, c->N));
+    CK(dalloc(c, &c->d_bvec, 9));
+    CK(h2d(c->d_bvec, c->bvec, 9, c->st));
+    CK(dalloc(c, &c->d_tau, 3 * natoms));
+    CK(h2d(c->d_tau, c->tau.data(), 3 * natoms, c->st));
+    std::vector<const KSphere*> sph;
+    for (auto& s : c->ks) sph.push_back(&s);
+    hp_status st = upload_sphereset(c, sph, nullptr, c->kset);
+    if (st != HP_OK) return st;
+    // V_loc(r): closed-form V(G) on the grid, then to real space
+    {
+        std::vector<double> amp(natoms), wid(natoms);
+        for (int a = 0; a < natoms; ++a) {
+            amp[a] = sp[species_of[a]].amp;
+            wid[a] = sp[species_of[a]].width;
+        }
+        double *d_amp, *d_wid;
+        double2* d_vg;
+        CK(dalloc(c, &d_amp, natoms));
+        CK(dalloc(c, &d_wid, natoms));
+        CK(dalloc(c, &d_vg, c->nr));
+        CK(h2d(d_amp, amp.data(), natoms, c->st));
+        CK(h2d(d_wid, wid.data(), natoms, c->st));
+        CK(k_vloc_g(d_vg, c->N, c->d_bvec, 4.0 * ecut, natoms, c->d_tau, d_amp, d_wid, c->omega, c->st));
+        CK(fft3d(c->fft, d_vg, 1, +1, c->st));
+        CK(dalloc(c, &c->d_vloc, c->nr));
+        CK(k_real_part(d_vg, c->d_vloc, c->nr, 1.0, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        dfree(c, d_amp);
+        dfree(c, d_wid);
+        dfree(c, d_vg);
+    }
+    // form factors beta_k, phi_k
+    {
+        const int nrow_all = c->nproj + c->nhub;
+        std::vector<int> ri(3 * nrow_all);
+        std::vector<double> rd(2 * nrow_all);
+        for (int r = 0; r < c->nproj; ++r) {
+            ri[r] = c->proj_atom[r];
+            ri[nrow_all + r] = c->proj_l[r];
+            ri[2 * nrow_all + r] = c->proj_m[r];
+            rd[r] = c->proj_w[r];
+            rd[nrow_all + r] = c->proj_pref[r];
+        }
+        for (int r = 0; r < c->nhub; ++r) {
+            const int o = c->nproj + r;
+            ri[o] = c->hub_row_atom[r];
+            ri[nrow_all + o] = c->hub_row_l[r];
+            ri[2 * nrow_all + o] = c->hub_row_m[r];
+            rd[o] = c->hub_row_w[r];
+            rd[nrow_all + o] = c->hub_row_pref[r];
+        }
+        CK(dalloc(c, &c->d_proj_int, ri.size()));
+        CK(dalloc(c, &c->d_proj_dbl, rd.size()));
+        CK(h2d(c->d_proj_int, ri.data(), ri.size(), c->st));
+        CK(h2d(c->d_proj_dbl, rd.data(), rd.size(), c->st));
+        std::vector<int> mil((size_t)c->nk * c->ld * 3, 0);
+        std::vector<double> kc(3 * c->nk);
+        for (int k = 0; k < c->nk; ++k) {
+            for (int i = 0; i < c->ks[k].npw * 3; ++i) mil[(size_t)k * c->ld * 3 + i] = c->ks[k].miller[i];
+            for (int j = 0; j < 3; ++j) kc[3 * k + j] = c->ks[k].kcart[j];
+        }
+        int* d_mil;
+        double* d_kc;
+        CK(dalloc(c, &d_mil, mil.size()));
+        CK(dalloc(c, &d_kc, kc.size()));
+        CK(h2d(d_mil, mil.data(), mil.size(), c->st));
+        CK(h2d(d_kc, kc.data(), kc.size(), c->st));
+        CK(dalloc(c, &c->d_beta_k, (size_t)c->nk * std::max(1, c->nproj) * c->ld));
+        CK(dalloc(c, &c->d_phi_k, (size_t)c->nk * c->nhub * c->ld));
+        CK(k_formfactor(d_kc, c->nk, d_mil, c->kset.d_npw, c->ld, c->d_bvec, c->nproj, c->d_proj_int,
+                        c->d_proj_int + nrow_all, c->d_proj_int + 2 * nrow_all, c->d_proj_dbl,
+                        c->d_proj_dbl + nrow_all, c->d_tau, c->d_beta_k, c->st));
+        CK(k_formfactor(d_kc, c->nk, d_mil, c->kset.d_npw, c->ld, c->d_bvec, c->nhub, c->d_proj_int + c->nproj,
+                        c->d_proj_int + nrow_all + c->nproj, c->d_proj_int + 2 * nrow_all + c->nproj,
+                        c->d_proj_dbl + c->nproj, c->d_proj_dbl + nrow_all + c->nproj, c->d_tau, c->d_phi_k, c->st));
+        CK(dalloc(c, &c->d_projD, std::max(1, c->nproj)));
+        if (c->nproj) CK(h2d(c->d_projD, c->proj_D.data(), c->nproj, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        dfree(c, d_mil);
+        dfree(c, d_kc);
+    }
+    return HP_OK;
+}
+
+extern "C" hp_status hp_setup(const double cell[9], int nspecies, const hp_species* sp, int natoms,
+                              const int* species_of, const double* frac_pos, double ecutwfc_ry, const int kmesh[3],
+                              const int qmesh[3], const hp_options* opt, hp_ctx** out) {
+    if (!out) return HP_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return HP_ECUDA;
+    hp_ctx* c = new hp_ctx();
+    if (opt) c->opt = *opt;
+    else hp_default_options(&c->opt);
+    c->st = (cudaStream_t)c->opt.cuda_stream;
+    hp_status s = setup_impl(c, cell, nspecies, sp, natoms, species_of, frac_pos, ecutwfc_ry, kmesh, qmesh);
+    if (s != HP_OK) {
+        fprintf(stderr, "hp_setup: %s\n", c->err.c_str());
+        hp_destroy(c);
+        return s;
+    }
+    *out = c;
+    return HP_OK;
+}
+
+extern "C" hp_status hp_query_sizes(const hp_ctx* c, hp_sizes* o) {
+    if (!c || !o) return HP_EINVAL;
+    o->nk = c->nk;
+    o->nq = c->nq;
+    o->nspin = c->nspin;
+    o->nocc = c->nocc;
+    o->nbnd = c->nbnd;
+    for (int i = 0; i < 3; ++i) o->grid[i] = c->N[i];
+    o->nr = c->nr;
+    o->nat = (int)c->atom_species.size();
+    o->nhub_atoms = (int)c->hub_atoms.size();
+    o->nhub_orb = c->nhub;
+    o->nproj = c->nproj;
+    o->mmax = kMmax;
+    o->npw_max = c->ld;
+    o->ncell = c->nq;
+    o->nchi = c->nq * (int)c->hub_atoms.size();
+    return HP_OK;
+}
+
+extern "C" hp_status hp_sphere(const hp_ctx* c, int ik, int* npw, int* miller) {
+    if (!c || !npw || ik < 0 || ik >= c->nk) return HP_EINVAL;
+    *npw = c->ks[ik].npw;
+    if (miller) memcpy(miller, c->ks[ik].miller.data(), sizeof(int) * 3 * c->ks[ik].npw);
+    return HP_OK;
+}
+
+extern "C" hp_status hp_hubbard_atoms(const hp_ctx* c, int* atom_index, int* mdim) {
+    if (!c) return HP_EINVAL;
+    for (size_t i = 0; i < c->hub_atoms.size(); ++i) {
+        if (atom_index) atom_index[i] = c->hub_atoms[i];
+        if (mdim) mdim[i] = c->hub_mdim[i];
+    }
+    return HP_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// ground state import / export
+// ------------------------------------------------------------------------------------------------
+static hp_status gs_alloc(hp_ctx* c, int nspin, int nbnd) {
+    for (void* p : {(void*)c->d_vhxc, (void*)c->d_rho, (void*)c->d_veff, (void*)c->d_psi}) dfree(c, p);
+    c->d_vhxc = c->d_rho = c->d_veff = nullptr;
+    c->d_psi = nullptr;
+    CK(dalloc(c, &c->d_vhxc, (size_t)nspin * c->nr));
+    CK(dalloc(c, &c->d_rho, (size_t)nspin * c->nr));
+    CK(dalloc(c, &c->d_veff, (size_t)nspin * c->nr));
+    CK(dalloc(c, &c->d_psi, (size_t)nspin * c->nk * nbnd * c->ld));
+    CK(cudaMemsetAsync(c->d_psi, 0, sizeof(double2) * (size_t)nspin * c->nk * nbnd * c->ld, c->st));
+    return HP_OK;
+}
+
+static void invalidate_response(hp_ctx* c) {
+    c->resp_ready = false;
+    c->qc.iq = -1;
+    c->cols.clear();
+}
+
+extern "C" hp_status hp_set_ground_state(hp_ctx* c, int nspin, double nelec, const double* vhxc, const double* rho,
+                                         const double* eps, const double* psi) {
+    if (!c) return HP_EINVAL;
+    if ((nspin != 1 && nspin != 2) || !vhxc || !rho || !eps || !psi)
+        return fail(c, HP_EINVAL, "hp_set_ground_state: nspin must be 1 or 2 and every array given");
+    const int nocc = (int)std::lround(nelec / 2.0);
+    if (nocc < 1 || std::fabs(nelec - 2.0 * nocc) > 1e-9)
+        return fail(c, HP_EINVAL, "hp_set_ground_state: nelec must be an even positive number");
+    for (int k = 0; k < c->nk; ++k)
+        if (c->ks[k].npw < nocc) return fail(c, HP_EINVAL, "hp_set_ground_state: fewer plane waves than bands");
+    invalidate_response(c);
+    c->have_gs = false;
+    hp_status s = gs_alloc(c, nspin, nocc);
+    if (s != HP_OK) return s;
+    c->nspin = nspin;
+    c->nelec = nelec;
+    c->nocc = c->nbnd = nocc;
+    c->gap = INFINITY;
+    c->eps.assign(eps, eps + (size_t)nspin * c->nk * nocc);
+    CK(h2d(c->d_vhxc, vhxc, (size_t)nspin * c->nr, c->st));
+    CK(h2d(c->d_rho, rho, (size_t)nspin * c->nr, c->st));
+    for (int sp = 0; sp < nspin; ++sp) CK(k_add_real(c->d_vloc, c->d_vhxc + (size_t)sp * c->nr, c->d_veff + (size_t)sp * c->nr, c->nr, c->st));
+    size_t off = 0;
+    std::vector<double2> row(c->ld);
+    for (int sp = 0; sp < nspin; ++sp)
+        for (int k = 0; k < c->nk; ++k)
+            for (int v = 0; v < nocc; ++v) {
+                const int npw = c->ks[k].npw;
+                std::fill(row.begin(), row.end(), cmk(0.0, 0.0));
+                for (int i = 0; i < npw; ++i) row[i] = cmk(psi[2 * (off + i)], psi[2 * (off + i) + 1]);
+                off += npw;
+                CK(cudaMemcpy(c->d_psi + ((size_t)(sp * c->nk + k) * nocc + v) * c->ld, row.data(), sizeof(double2) * c->ld,
+                              cudaMemcpyHostToDevice));
+            }
+    CK(cudaStreamSynchronize(c->st));
+    c->have_gs = true;
+    return HP_OK;
+}
+
+extern "C" hp_status hp_get_ground_state(const hp_ctx* cc, double* eps, double* rho, double* vhxc) {
+    hp_ctx* c = const_cast<hp_ctx*>(cc);
+    if (!c) return HP_EINVAL;
+    if (!c->have_gs) return fail(c, HP_ESTATE, "no ground state");
+    if (eps) {
+        for (int s = 0; s < c->nspin; ++s)
+            for (int k = 0; k < c->nk; ++k)
+                for (int v = 0; v < c->nocc; ++v) eps[((size_t)s * c->nk + k) * c->nocc + v] = c->eps[((size_t)s * c->nk + k) * c->nbnd + v];
+    }
+    if (rho) CK(d2h(rho, c->d_rho, (size_t)c->nspin * c->nr, c->st));
+    if (vhxc) CK(d2h(vhxc, c->d_vhxc, (size_t)c->nspin * c->nr, c->st));
+    return HP_OK;
+}
+
+extern "C" hp_status hp_apply_h(hp_ctx* c, int ik, int spin, int nb, const double* psi, double* out) {
+    if (!c) return HP_EINVAL;
+    if (!c->have_gs) return fail(c, HP_ESTATE, "hp_apply_h: no ground state (potential) yet");
+    if (ik < 0 || ik >= c->nk || spin < 0 || spin >= c->nspin || nb < 1 || !psi || !out)
+        return fail(c, HP_EINVAL, "hp_apply_h: bad arguments");
+    const int npw = c->ks[ik].npw, ld = c->ld;
+    std::vector<double2> h((size_t)nb * ld, cmk(0.0, 0.0));
+    for (int b = 0; b < nb; ++b)
+        for (int i = 0; i < npw; ++i) h[(size_t)b * ld + i] = cmk(psi[2 * ((size_t)b * npw + i)], psi[2 * ((size_t)b * npw + i) + 1]);
+    double2 *dX, *dY, *dP;
+    CK(dalloc(c, &dX, (size_t)nb * ld));
+    CK(dalloc(c, &dY, (size_t)nb * ld));
+    CK(dalloc(c, &dP, (size_t)nb * kPStride));
+    CK(h2d(dX, h.data(), h.size(), c->st));
+    BandList& L = c->L1;
+    list_clear(L);
+    for (int b = 0; b < nb; ++b) list_add(L, b, ik, spin, 0.0);
+    hp_status s = upload_list(c, L);
+    if (s == HP_OK) s = apply_local(c, c->kset, L, dX, dY, c->d_veff);
+    if (s == HP_OK) s = apply_nonlocal(c, c->kset, L, dX, dY, dP, nullptr);
+    if (s == HP_OK) {
+        cudaError_t e = d2h(h.data(), dY, h.size(), c->st);
+        if (e != cudaSuccess) s = cuda_fail(c, e, "hp_apply_h copy-out");
+    }
+    dfree(c, dX);
+    dfree(c, dY);
+    dfree(c, dP);
+    if (s != HP_OK) return s;
+    for (int b = 0; b < nb; ++b)
+        for (int i = 0; i < npw; ++i) {
+            out[2 * ((size_t)b * npw + i)] = h[(size_t)b * ld + i].x;
+            out[2 * ((size_t)b * npw + i) + 1] = h[(size_t)b * ld + i].y;
+        }
+    return HP_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// response
+// ------------------------------------------------------------------------------------------------
+namespace {
+
+hp_status resp_alloc(hp_ctx* c) {
+    const int rows = c->nspin * c->nk * c->nocc;
+    if (rows == c->resp_rows && c->d_x) return HP_OK;
+    for (void* p : {(void*)c->d_x, (void*)c->d_r, (void*)c->d_p, (void*)c->d_ap, (void*)c->d_b, (void*)c->d_vpu,
+                    (void*)c->d_rz, (void*)c->d_rzold, (void*)c->d_rr, (void*)c->d_pap, (void*)c->d_Pbuf})
+        dfree(c, p);
+    const size_t n = (size_t)rows * c->ld;
+    CK(dalloc(c, &c->d_x, n));
+    CK(dalloc(c, &c->d_r, n));
+    CK(dalloc(c, &c->d_p, n));
+    CK(dalloc(c, &c->d_ap, n));
+    CK(dalloc(c, &c->d_b, n));
+    CK(dalloc(c, &c->d_vpu, n));
+    CK(dalloc(c, &c->d_rz, rows));
+    CK(dalloc(c, &c->d_rzold, rows));
+    CK(dalloc(c, &c->d_rr, rows));
+    CK(dalloc(c, &c->d_pap, rows));
+    CK(dalloc(c, &c->d_Pbuf, (size_t)rows * kPStride));
+    c->resp_rows = rows;
+    return HP_OK;
+}
+
+// per ground state: real-space occupied u_k, <phi_k|u_k>, f_xc, alpha
+hp_status prepare_resp(hp_ctx* c) {
+    if (c->resp_ready) return HP_OK;
+    const int nspin = c->nspin, nk = c->nk, nocc = c->nocc, nr = c->nr;
+    const int rows = nspin * nk * nocc;
+    hp_status s = resp_alloc(c);
+    if (s != HP_OK) return s;
+    dfree(c, c->d_ur);
+    dfree(c, c->d_aphi);
+    dfree(c, c->d_fxc);
+    CK(dalloc(c, &c->d_ur, (size_t)rows * nr));
+    CK(dalloc(c, &c->d_aphi, (size_t)rows * kPStride));
+    CK(dalloc(c, &c->d_fxc, (size_t)(nspin == 1 ? 1 : 3) * nr));
+    // list of occupied ground-state rows (psi rows), items ordered (s, k, v)
+    BandList& L = c->L2;
+    list_clear(L);
+    for (int sp = 0; sp < nspin; ++sp)
+        for (int k = 0; k < nk; ++k)
+            for (int v = 0; v < nocc; ++v) list_add(L, (sp * nk + k) * c->nbnd + v, k, sp, 0.0);
+    s = upload_list(c, L);
+    if (s != HP_OK) return s;
+    // u_k(r): scatter straight into the cache and transform in place
+    const int chunk = std::max(1, band_batch(c, rows));
+    for (int c0 = 0; c0 < rows; c0 += chunk) {
+        const int nc = std::min(chunk, rows - c0);
+        CK(k_scatter(c->kset, L, c0, nc, c->d_psi, c->ld, c->d_ur + (size_t)c0 * nr, nr, c->st));
+        CK(fft3d(c->fft, c->d_ur + (size_t)c0 * nr, nc, +1, c->st));
+    }
+    // <phi_m,k|u_vk>
+    ProjMat phi{c->d_phi_k, 0, (long long)c->nhub * c->ld, c->nhub, 0, nullptr};
+    s = project(c, c->kset, L, phi, c->d_psi, c->d_aphi);
+    if (s != HP_OK) return s;
+    // f_xc
+    double* d_vtmp;
+    CK(dalloc(c, &d_vtmp, (size_t)nspin * nr));
+    CK(k_xc(c->d_rho, nspin, nr, d_vtmp, c->d_fxc, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    dfree(c, d_vtmp);
+    double emax = -INFINITY, emin = INFINITY;
+    for (int sp = 0; sp < nspin; ++sp)
+        for (int k = 0; k < nk; ++k)
+            for (int v = 0; v < nocc; ++v) {
+                const double e = c->eps[((size_t)sp * nk + k) * c->nbnd + v];
+                emax = std::max(emax, e);
+                emin = std::min(emin, e);
+            }
+    c->alpha_pv = 2.0 * (emax - emin);
+    if (c->alpha_pv <= 0) c->alpha_pv = 1.0;
+    // small work buffers
+    if (!c->d_small) CK(dalloc(c, &c->d_small, 512));
+    if (!c->d_partial) CK(dalloc(c, &c->d_partial, 1024));
+    dfree(c, c->d_dv);
+    dfree(c, c->d_dvout);
+    dfree(c, c->d_drho);
+    dfree(c, c->d_dvh);
+    CK(dalloc(c, &c->d_dv, (size_t)nspin * nr));
+    CK(dalloc(c, &c->d_dvout, (size_t)nspin * nr));
+    CK(dalloc(c, &c->d_drho, (size_t)nspin * nr));
+    CK(dalloc(c, &c->d_dvh, (size_t)nr));
+    dfree(c, c->d_M);
+    dfree(c, c->d_dn);
+    CK(dalloc(c, &c->d_M, (size_t)nspin * c->nhub * c->nhub));
+    CK(dalloc(c, &c->d_dn, (size_t)c->hub_atoms.size() * nspin * kMmax * kMmax + c->hub_atoms.size()));
+    for (auto p : c->d_hist_dx) dfree(c, p);
+    for (auto p : c->d_hist_df) dfree(c, p);
+    c->d_hist_dx.assign(c->opt.nmix + 2, nullptr);
+    c->d_hist_df.assign(c->opt.nmix + 2, nullptr);
+    for (int i = 0; i < c->opt.nmix + 2; ++i) {
+        CK(dalloc(c, &c->d_hist_dx[i], (size_t)nspin * nr));
+        CK(dalloc(c, &c->d_hist_df[i], (size_t)nspin * nr));
+    }
+    if (!c->d_hist_ptrs) CK(dalloc(c, &c->d_hist_ptrs, 64));
+    c->resp_ready = true;
+    return HP_OK;
+}
+
+// per q: spheres at k+q = k' + G0 (the k' sphere with Miller indices shifted by -G0), kmap k -> k'
+struct QState {
+    std::vector<int> kprime;
+    int* d_kprime = nullptr;
+};
+
+hp_status prepare_q(hp_ctx* c, int iq, std::vector<int>& kprime) {
+    const int q1 = iq / (c->qmesh[1] * c->qmesh[2]), q2 = (iq / c->qmesh[2]) % c->qmesh[1], q3 = iq % c->qmesh[2];
+    const int qi[3] = {q1, q2, q3};
+    kprime.assign(c->nk, 0);
+    std::vector<std::array<int, 3>> g0(c->nk);
+    std::vector<const KSphere*> sph(c->nk);
+    for (int i1 = 0, ik = 0; i1 < c->kmesh[0]; ++i1)
+        for (int i2 = 0; i2 < c->kmesh[1]; ++i2)
+            for (int i3 = 0; i3 < c->kmesh[2]; ++i3, ++ik) {
+                const int ii[3] = {i1, i2, i3};
+                int j[3];
+                for (int d = 0; d < 3; ++d) {
+                    const int x = ii[d] + qi[d] * (c->kmesh[d] / c->qmesh[d]);  // (k+q) in units of 1/kmesh
+                    j[d] = x % c->kmesh[d];
+                    g0[ik][d] = x / c->kmesh[d];
+                }
+                kprime[ik] = (j[0] * c->kmesh[1] + j[1]) * c->kmesh[2] + j[2];
+                sph[ik] = &c->ks[kprime[ik]];
+            }
+    if (c->qc.iq == iq) return HP_OK;
+    hp_status s = upload_sphereset(c, sph, &g0, c->qc.set);
+    if (s != HP_OK) return s;
+    if (!c->qc.d_miller) CK(dalloc(c, &c->qc.d_miller, c->nk));  // holds kprime
+    CK(h2d(c->qc.d_miller, kprime.data(), c->nk, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    c->qc.iq = iq;
+    return HP_OK;
+}
+
+// Y = A X = (H_k+q + alpha O_k+q - eps_v) X on the items of L
+hp_status apply_sternheimer(hp_ctx* c, const BandList& L, const double2* X, double2* Y) {
+    const SphereSet& S = c->qc.set;
+    const int* kmap = c->qc.d_miller;
+    hp_status s = apply_local(c, S, L, X, Y, c->d_veff);
+    if (s != HP_OK) return s;
+    s = apply_nonlocal(c, S, L, X, Y, c->d_Pbuf, kmap);
+    if (s != HP_OK) return s;
+    ProjMat U{c->d_psi, (long long)c->nk * c->nbnd * c->ld, (long long)c->nbnd * c->ld, c->nocc, 0, kmap};
+    s = project(c, S, L, U, X, c->d_Pbuf);
+    if (s != HP_OK) return s;
+    CK(k_expand(L, S, U, c->d_Pbuf, nullptr, c->alpha_pv, Y, c->ld, c->st));
+    return HP_OK;
+}
+
+double dev_dot(hp_ctx* c, const double2* a, const double2* b, long long n, cudaError_t* err) {
+    double v = 0.0;
+    cudaError_t e = k_vec_dot(a, b, n, c->d_small, c->d_partial, c->st);
+    if (e == cudaSuccess) e = d2h(&v, c->d_small, 1, c->st);
+    *err = e;
+    return v;
+}
+
+}  // namespace
+
+extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, double* dn_out, hp_resp_info* info) {
+    if (!c) return HP_EINVAL;
+    if (!c->have_gs) return fail(c, HP_ESTATE, "hp_response: no ground state");
+    if (!(c->gap > 1e-4)) return fail(c, HP_ENOGAP, "hp_response: the ground state has no gap at the fixed band count");
+    if (iq < 0 || iq >= c->nq) return fail(c, HP_EINVAL, "hp_response: q index out of range");
+    int jj = -1;
+    for (size_t i = 0; i < c->hub_atoms.size(); ++i)
+        if (c->hub_atoms[i] == atom) jj = (int)i;
+    if (jj < 0) return fail(c, HP_EINVAL, "hp_response: atom is not a Hubbard atom");
+    if (c->opt.precision != HP_PRECISION_FP64) return fail(c, HP_ENOTIMPL, "hp_response: only the FP64 form is built");
+    auto t0 = std::chrono::steady_clock::now();
+    hp_status s = prepare_resp(c);
+    if (s != HP_OK) return s;
+    std::vector<int> kprime;
+    s = prepare_q(c, iq, kprime);
+    if (s != HP_OK) return s;
+    const int nspin = c->nspin, nk = c->nk, nocc = c->nocc, nr = c->nr, ld = c->ld;
+    const int rows = nspin * nk * nocc;
+    const int nh = (int)c->hub_atoms.size();
+    const long long nvec = (long long)rows * ld;
+    const long long ndv = (long long)nspin * nr;
+    const SphereSet& Sq = c->qc.set;
+    const int* kmap = c->qc.d_miller;
+    // lists: Lall over response rows, Lpsi over the same (s, k, v) items with psi rows
+    BandList& Lall = c->L1;
+    BandList& Lpsi = c->L2;
+    list_clear(Lall);
+    list_clear(Lpsi);
+    for (int sp = 0; sp < nspin; ++sp)
+        for (int k = 0; k < nk; ++k)
+            for (int v = 0; v < nocc; ++v) {
+                const int item = (sp * nk + k) * nocc + v;
+                list_add(Lall, item, k, sp, c->eps[((size_t)sp * nk + k) * c->nbnd + v]);
+                list_add(Lpsi, (sp * nk + k) * c->nbnd + v, k, sp, 0.0);
+            }
+    if ((s = upload_list(c, Lall)) != HP_OK) return s;
+    if ((s = upload_list(c, Lpsi)) != HP_OK) return s;
+    // V_pert u_k = sum_m phi^J_m,k+q <phi^J_m,k|u_k>
+    const int mJ = c->hub_mdim[jj], oJ = c->hub_off[jj];
+    ProjMat phiJk{c->d_phi_k, 0, (long long)c->nhub * ld, mJ, oJ, nullptr};
+    ProjMat phiJkq{c->d_phi_k, 0, (long long)c->nhub * ld, mJ, oJ, kmap};
+    ProjMat phikq{c->d_phi_k, 0, (long long)c->nhub * ld, c->nhub, 0, kmap};
+    ProjMat Ukq{c->d_psi, (long long)nk * c->nbnd * ld, (long long)c->nbnd * ld, nocc, 0, kmap};
+    if ((s = project(c, c->kset, Lpsi, phiJk, c->d_psi, c->d_Pbuf)) != HP_OK) return s;
+    CK(cudaMemsetAsync(c->d_vpu, 0, sizeof(double2) * nvec, c->st));
+    CK(k_expand(Lall, Sq, phiJkq, c->d_Pbuf, nullptr, 1.0, c->d_vpu, ld, c->st));
+    CK(cudaMemsetAsync(c->d_x, 0, sizeof(double2) * nvec, c->st));
+    CK(cudaMemsetAsync(c->d_dv, 0, sizeof(double2) * ndv, c->st));
+    const double f = nspin == 1 ? 2.0 : 1.0;
+    const double wrho = 2.0 * f / (nk * c->omega);
+    const double tol2 = c->opt.cg_tol * c->opt.cg_tol;
+    std::vector<double> rr(rows);
+    std::vector<double> dn0, dn((size_t)nh * nspin * kMmax * kMmax * 2);
+    std::vector<double> tr0, tr((size_t)2 * nh), tr_prev;
+    long long cg_total = 0, hpsi = 0;
+    int nhist = 0;
+    double res = INFINITY, dchi = INFINITY;
+    bool converged = false, cg_ok = true;
+    int it = 0;
+    for (it = 1; it <= c->opt.niter_max; ++it) {
+        // ---- right-hand side b = -P_c (dV u + V_pert u)
+        if (it == 1) {
+            CK(k_vec_scale_copy(c->d_b, c->d_vpu, -1.0, nvec, c->st));
+        } else {
+            s = ensure_grid(c, band_batch(c, rows));
+            if (s != HP_OK) return s;
+            for (int c0 = 0; c0 < rows; c0 += c->grid_cap) {
+                const int nc = std::min(c->grid_cap, rows - c0);
+                CK(k_mul_cpot(c->d_grid, c->d_ur, Lall.d_row, nc, nr, c->d_dv, Lall, c0, c->st));
+                CK(fft3d(c->fft, c->d_grid, nc, -1, c->st));
+                CK(k_gather_scaled(Sq, Lall, c0, nc, c->d_grid, nr, -1.0 / nr, c->d_b, ld, 0, c->st));
+            }
+            CK(k_vec_axpy(c->d_b, c->d_vpu, -1.0, nvec, c->st));
+        }
+        if ((s = project(c, Sq, Lall, Ukq, c->d_b, c->d_Pbuf)) != HP_OK) return s;
+        CK(k_expand(Lall, Sq, Ukq, c->d_Pbuf, nullptr, -1.0, c->d_b, ld, c->st));
+        // ---- CG on every band, warm start from the previous x
+        if ((s = apply_sternheimer(c, Lall, c->d_x, c->d_ap)) != HP_OK) return s;
+        hpsi += rows;
+        CK(k_vec_sub(c->d_r, c->d_b, c->d_ap, nvec, c->st));
+        CK(k_cg_init(Lall, Sq, c->d_r, c->d_p, ld, c->d_rz, c->d_rr, c->st));
+        int cgit = 0;
+        BandList& La = c->L3;  // active (not yet converged) bands
+        for (;;) {
+            CK(d2h(rr.data(), c->d_rr, rows, c->st));
+            list_clear(La);
+            for (int i = 0; i < rows; ++i) {
+                if (!std::isfinite(rr[i])) return fail(c, HP_ENUMERIC, "hp_response: non-finite CG residual");
+                if (rr[i] > tol2) list_add(La, Lall.row[i], Lall.k[i], Lall.spin[i], Lall.shift[i]);
+            }
+            if (La.row.empty()) break;
+            if (cgit >= c->opt.cg_maxiter) {
+                cg_ok = false;
+                break;
+            }
+            if ((s = upload_list(c, La)) != HP_OK) return s;
+            if ((s = apply_sternheimer(c, La, c->d_p, c->d_ap)) != HP_OK) return s;
+            hpsi += La.nb;
+            CK(k_band_dot(La, Sq, c->d_p, c->d_ap, ld, c->d_pap, c->st));
+            CK(k_cg_update(La, Sq, c->d_pap, c->d_x, c->d_r, c->d_p, c->d_ap, ld, c->d_rz, c->d_rr, c->d_rzold, c->st));
+            CK(k_cg_direction(La, Sq, c->d_rz, c->d_rzold, c->d_r, c->d_p, ld, c->st));
+            cg_total += La.nb;
+            ++cgit;
+        }
+        // ---- response density
+        CK(cudaMemsetAsync(c->d_drho, 0, sizeof(double2) * ndv, c->st));
+        s = ensure_grid(c, band_batch(c, rows));
+        if (s != HP_OK) return s;
+        for (int c0 = 0; c0 < rows; c0 += c->grid_cap) {
+            const int nc = std::min(c->grid_cap, rows - c0);
+            CK(k_scatter(Sq, Lall, c0, nc, c->d_x, ld, c->d_grid, nr, c->st));
+            CK(fft3d(c->fft, c->d_grid, nc, +1, c->st));
+            CK(k_drho_acc(c->d_ur, Lall.d_row, c->d_grid, nc, nr, Lall, c0, wrho, nspin, c->d_drho, c->st));
+        }
+        // ---- response occupations
+        if ((s = project(c, Sq, Lall, phikq, c->d_x, c->d_Pbuf)) != HP_OK) return s;
+        CK(k_occ_response(c->d_Pbuf, c->d_aphi, nspin * nk, nocc, c->nhub, nk, nspin, c->d_M, c->st));
+        {
+            std::vector<int> off(c->hub_off), md(c->hub_mdim);
+            int* d_int;
+            CK(dalloc(c, &d_int, 2 * nh));
+            CK(h2d(d_int, off.data(), nh, c->st));
+            CK(h2d(d_int + nh, md.data(), nh, c->st));
+            CK(k_dn_blocks(c->d_M, nspin, c->nhub, nh, d_int, d_int + nh, kMmax, c->d_dn, c->st));
+            double2* d_tr = c->d_dn + (size_t)nh * nspin * kMmax * kMmax;
+            CK(k_dn_traces(c->d_dn, nh, nspin, kMmax, f, d_tr, c->st));
+            CK(d2h((double2*)dn.data(), c->d_dn, (size_t)nh * nspin * kMmax * kMmax, c->st));
+            CK(d2h((double2*)tr.data(), d_tr, nh, c->st));
+            dfree(c, d_int);
+        }
+        if (it == 1) {
+            dn0 = dn;
+            tr0 = tr;
+        }
+        // ---- Delta V_Hxc from Delta rho
+        CK(cudaMemcpyAsync(c->d_dvh, c->d_drho, sizeof(double2) * nr, cudaMemcpyDeviceToDevice, c->st));
+        if (nspin == 2) CK(k_vec_axpy(c->d_dvh, c->d_drho + nr, 1.0, nr, c->st));
+        CK(fft3d(c->fft, c->d_dvh, 1, -1, c->st));
+        const int qi[3] = {iq / (c->qmesh[1] * c->qmesh[2]), (iq / c->qmesh[2]) % c->qmesh[1], iq % c->qmesh[2]};
+        const double qf[3] = {(double)qi[0] / c->qmesh[0], (double)qi[1] / c->qmesh[1], (double)qi[2] / c->qmesh[2]};
+        CK(k_hartree_q(c->d_dvh, c->N, c->d_bvec, qf, 4.0 * c->ecut, 1.0 / nr, c->st));
+        CK(fft3d(c->fft, c->d_dvh, 1, +1, c->st));
+        CK(k_hxc_combine(c->d_dvh, c->d_drho, c->d_fxc, nspin, nr, c->d_dvout, c->st));
+        // residual F = dV_out - dV_in (kept in d_dvout)
+        CK(k_vec_sub(c->d_dvout, c->d_dvout, c->d_dv, ndv, c->st));
+        cudaError_t e;
+        const double ff = dev_dot(c, c->d_dvout, c->d_dvout, ndv, &e);
+        if (e != cudaSuccess) return cuda_fail(c, e, "residual");
+        if (!std::isfinite(ff)) return fail(c, HP_ENUMERIC, "hp_response: non-finite Hxc residual");
+        res = std::sqrt(ff / (double)ndv);
+        dchi = INFINITY;
+        if (!tr_prev.empty()) {
+            dchi = 0.0;
+            for (int a = 0; a < 2 * nh; ++a) dchi = std::max(dchi, std::fabs(tr[a] - tr_prev[a]));
+        }
+        tr_prev = tr;
+        if (it > 1 && res < c->opt.scf_tol && dchi < c->opt.conv_thr_chi) {
+            converged = true;
+            break;
+        }
+        // ---- modified Broyden step on dV (history in a ring of nmix pairs)
+        const int nmix = c->opt.nmix;
+        double2* xprev = c->d_hist_dx[nmix];
+        double2* fprev = c->d_hist_df[nmix];
+        if (it > 1 && nmix > 0) {
+            // new pair: dF = F - F_prev, dX = X - X_prev, both / |dF|
+            if (nhist == nmix) {  // drop the oldest
+                double2* t0x = c->d_hist_dx[0];
+                double2* t0f = c->d_hist_df[0];
+                for (int i = 0; i + 1 < nmix; ++i) {
+                    c->d_hist_dx[i] = c->d_hist_dx[i + 1];
+                    c->d_hist_df[i] = c->d_hist_df[i + 1];
+                }
+                c->d_hist_dx[nmix - 1] = t0x;
+                c->d_hist_df[nmix - 1] = t0f;
+                --nhist;
+            }
+            double2* ndf = c->d_hist_df[nhist];
+            double2* ndx = c->d_hist_dx[nhist];
+            CK(k_vec_sub(ndf, c->d_dvout, fprev, ndv, c->st));
+            CK(k_vec_sub(ndx, c->d_dv, xprev, ndv, c->st));
+            const double nn = dev_dot(c, ndf, ndf, ndv, &e);
+            if (e != cudaSuccess) return cuda_fail(c, e, "broyden norm");
+            if (nn > 0) {
+                const double inv = 1.0 / std::sqrt(nn);
+                CK(k_vec_scale_copy(ndf, ndf, inv, ndv, c->st));
+                CK(k_vec_scale_copy(ndx, ndx, inv, ndv, c->st));
+                ++nhist;
+            }
+        }
+        CK(cudaMemcpyAsync(xprev, c->d_dv, sizeof(double2) * ndv, cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemcpyAsync(fprev, c->d_dvout, sizeof(double2) * ndv, cudaMemcpyDeviceToDevice, c->st));
+        const int m = nhist;
+        // overlaps <dF_i|dF_j> and <dF_k|F> into d_small[16 + i*(m+1) + j]
+        for (int i = 0; i < m; ++i) {
+            for (int j = 0; j <= m; ++j) {
+                const double2* bj = (j < m) ? c->d_hist_df[j] : c->d_dvout;
+                CK(k_vec_dot(c->d_hist_df[i], bj, ndv, c->d_small + 16 + i * (m + 1) + j, c->d_partial, c->st));
+            }
+        }
+        CK(k_broyden_coef(c->d_small + 16, m, m + 1, 0.01, c->d_small + 8, c->st));
+        std::vector<const double2*> ptrs(2 * (nmix + 1), nullptr);
+        for (int i = 0; i < m; ++i) {
+            ptrs[i] = c->d_hist_dx[i];
+            ptrs[nmix + 1 + i] = c->d_hist_df[i];
+        }
+        CK(h2d((const double2**)c->d_hist_ptrs, ptrs.data(), ptrs.size(), c->st));
+        CK(k_broyden_apply(c->d_dv, c->d_dvout, (const double2* const*)c->d_hist_ptrs,
+                           (const double2* const*)(c->d_hist_ptrs + nmix + 1), c->d_small + 8, m, c->opt.alpha_mix, ndv,
+                           c->st));
+    }
+    CK(cudaStreamSynchronize(c->st));
+    RespCols& rc = c->cols[{iq, atom}];
+    rc.dn0 = dn0;
+    rc.dn = dn;
+    rc.tr0 = tr0;
+    rc.tr = tr;
+    if (dn0_out) memcpy(dn0_out, dn0.data(), sizeof(double) * dn0.size());
+    if (dn_out) memcpy(dn_out, dn.data(), sizeof(double) * dn.size());
+    if (info) {
+        info->iterations = std::min(it, c->opt.niter_max);
+        info->cg_iterations = cg_total;
+        info->hpsi = hpsi;
+        info->residual = res;
+        info->dchi = dchi;
+        info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (!converged || !cg_ok) {
+        c->cols.erase({iq, atom});
+        return fail(c, HP_ENOTCONV, "hp_response: self-consistency or CG cap reached");
+    }
+    return HP_OK;
+}
+
+extern "C" hp_status hp_hubbard(hp_ctx* c, double* chi0_out, double* chi_out, double* hub_out) {
+    if (!c) return HP_EINVAL;
+    const int nh = (int)c->hub_atoms.size(), nq = c->nq;
+    const int n = nh * nq;
+    std::vector<double2> cols0((size_t)nq * nh * nh), cols((size_t)nq * nh * nh);
+    for (int iq = 0; iq < nq; ++iq)
+        for (int jj = 0; jj < nh; ++jj) {
+            auto it = c->cols.find({iq, c->hub_atoms[jj]});
+            if (it == c->cols.end()) return fail(c, HP_ESTATE, "hp_hubbard: a (q, J) response is missing");
+            for (int s = 0; s < nh; ++s) {
+                cols0[((size_t)iq * nh + jj) * nh + s] = cmk(it->second.tr0[2 * s], it->second.tr0[2 * s + 1]);
+                cols[((size_t)iq * nh + jj) * nh + s] = cmk(it->second.tr[2 * s], it->second.tr[2 * s + 1]);
+            }
+        }
+    std::vector<double> qf(3 * nq), Rl(3 * nq);
+    for (int i1 = 0, i = 0; i1 < c->qmesh[0]; ++i1)
+        for (int i2 = 0; i2 < c->qmesh[1]; ++i2)
+            for (int i3 = 0; i3 < c->qmesh[2]; ++i3, ++i) {
+                qf[3 * i] = (double)i1 / c->qmesh[0];
+                qf[3 * i + 1] = (double)i2 / c->qmesh[1];
+                qf[3 * i + 2] = (double)i3 / c->qmesh[2];
+                Rl[3 * i] = i1;
+                Rl[3 * i + 1] = i2;
+                Rl[3 * i + 2] = i3;
+            }
+    double2* d_cols;
+    double *d_q, *d_R, *d_mats, *d_work;
+    int* d_sing;
+    CK(dalloc(c, &d_cols, 2 * cols.size()));
+    CK(dalloc(c, &d_q, 3 * nq));
+    CK(dalloc(c, &d_R, 3 * nq));
+    CK(dalloc(c, &d_mats, (size_t)7 * n * n));
+    CK(dalloc(c, &d_work, n));
+    CK(dalloc(c, &d_sing, 2));
+    CK(h2d(d_cols, cols0.data(), cols0.size(), c->st));
+    CK(h2d(d_cols + cols0.size(), cols.data(), cols.size(), c->st));
+    CK(h2d(d_q, qf.data(), qf.size(), c->st));
+    CK(h2d(d_R, Rl.data(), Rl.size(), c->st));
+    double* chi0 = d_mats;
+    double* chi0i = d_mats + (size_t)n * n;
+    double* chi = d_mats + (size_t)2 * n * n;
+    double* chii = d_mats + (size_t)3 * n * n;
+    double* inv0 = d_mats + (size_t)4 * n * n;
+    double* inv = d_mats + (size_t)5 * n * n;
+    double* hub = d_mats + (size_t)6 * n * n;
+    CK(k_chi_assemble(d_cols, nq, nh, d_q, d_R, nq, chi0, chi0i, c->st));
+    CK(k_chi_assemble(d_cols + cols0.size(), nq, nh, d_q, d_R, nq, chi, chii, c->st));
+    CK(cudaMemcpyAsync(inv0, chi0, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, c->st));
+    CK(cudaMemcpyAsync(inv, chi, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, c->st));
+    CK(k_invert(inv0, d_work, n, d_sing, c->st));
+    CK(k_invert(inv, d_work, n, d_sing + 1, c->st));
+    CK(k_hub_matrix(inv0, inv, n, kHaToEv, hub, c->st));
+    std::vector<double> h((size_t)7 * n * n);
+    int sing[2];
+    CK(d2h(h.data(), d_mats, h.size(), c->st));
+    CK(d2h(sing, d_sing, 2, c->st));
+    for (void* p : {(void*)d_cols, (void*)d_q, (void*)d_R, (void*)d_mats, (void*)d_work, (void*)d_sing}) dfree(c, p);
+    if (sing[0] || sing[1]) return fail(c, HP_ESINGULAR, "hp_hubbard: chi0 or chi is singular");
+    if (chi0_out) memcpy(chi0_out, h.data(), sizeof(double) * n * n);
+    if (chi_out) memcpy(chi_out, h.data() + (size_t)2 * n * n, sizeof(double) * n * n);
+    if (hub_out) memcpy(hub_out, h.data() + (size_t)6 * n * n, sizeof(double) * n * n);
+    return HP_OK;
+}

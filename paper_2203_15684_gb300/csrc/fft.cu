@@ -1,0 +1,247 @@
+// Batched 3D complex FFT for the plane-wave <-> real-space transforms of H.psi (the "FFT to real
+// space, multiply by V_loc + V_Hxc, FFT back" step of every Sternheimer iteration, Sec. 2.3).
+//
+// Design: one kernel launch per axis.  A grid is viewed as [A][n][B] with the transformed axis of
+// length n in the middle; a CTA stages a tile of LT lines (TA consecutive a's x TB consecutive b's)
+// in shared memory with the line index fastest (conflict-free butterfly reads), runs every mixed-
+// radix Stockham stage (radix 4, 2, 3, 5) in shared memory, and writes the tile back in place.
+// Reads and writes of a tile are runs of TB contiguous complex numbers (whole lines when B = 1).
+#include <cmath>
+#include <cstdio>
+
+#include "hp_internal.h"
+
+namespace hp {
+
+bool fft_factor(int n, Radices& out) {
+    out.n = n;
+    out.nst = 0;
+    int m = n;
+    while (m % 4 == 0 && out.nst < kMaxStages) { out.r[out.nst++] = 4; m /= 4; }
+    while (m % 2 == 0 && out.nst < kMaxStages) { out.r[out.nst++] = 2; m /= 2; }
+    while (m % 3 == 0 && out.nst < kMaxStages) { out.r[out.nst++] = 3; m /= 3; }
+    while (m % 5 == 0 && out.nst < kMaxStages) { out.r[out.nst++] = 5; m /= 5; }
+    return m == 1 && n >= 1;
+}
+
+// ---- one work item of one Stockham stage: butterfly j of line l (shared by host and device) ----
+// src/dst: [n][LT] (line fastest).  Ns: product of the radices of the earlier stages.
+HD void radix_butterfly(double2* v, int R, int s) {
+    if (R == 2) {
+        double2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else if (R == 4) {
+        double2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+        double2 t2 = cadd(v[1], v[3]), t3 = cmul_si(csub(v[1], v[3]), s);
+        v[0] = cadd(t0, t2);
+        v[2] = csub(t0, t2);
+        v[1] = cadd(t1, t3);
+        v[3] = csub(t1, t3);
+    } else if (R == 3) {
+        const double h = 0.86602540378443864676;  // sin(2 pi / 3)
+        double2 t1 = cadd(v[1], v[2]);
+        double2 t2 = csub(v[0], cscale(t1, 0.5));
+        double2 t3 = cmul_si(cscale(csub(v[1], v[2]), h), s);
+        v[0] = cadd(v[0], t1);
+        v[1] = cadd(t2, t3);
+        v[2] = csub(t2, t3);
+    } else if (R == 5) {
+        const double c1 = 0.30901699437494742410, c2 = -0.80901699437494742410;  // cos(2pi/5), cos(4pi/5)
+        const double s1 = 0.95105651629515357212, s2 = 0.58778525229247312917;   // sin(2pi/5), sin(4pi/5)
+        double2 t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
+        double2 t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
+        double2 a1 = cadd(v[0], cadd(cscale(t1, c1), cscale(t2, c2)));
+        double2 a2 = cadd(v[0], cadd(cscale(t1, c2), cscale(t2, c1)));
+        double2 b1 = cmul_si(cadd(cscale(t3, s1), cscale(t4, s2)), s);
+        double2 b2 = cmul_si(csub(cscale(t3, s2), cscale(t4, s1)), s);
+        v[0] = cadd(v[0], cadd(t1, t2));
+        v[1] = cadd(a1, b1);
+        v[4] = csub(a1, b1);
+        v[2] = cadd(a2, b2);
+        v[3] = csub(a2, b2);
+    }
+}
+
+HD void stockham_item(const double2* src, double2* dst, const double2* tw, int n, int LT, int R, int Ns,
+                      int sign, int w) {
+    const int l = w % LT;
+    const int j = w / LT;
+    const int nR = n / R;
+    double2 v[5];
+    const int k = j % Ns;
+    const int tstep = k * (n / (Ns * R));
+    for (int r = 0; r < R; ++r) {
+        double2 x = src[(j + r * nR) * LT + l];
+        if (r > 0 && tstep != 0) {
+            double2 t = tw[(r * tstep) % n];
+            if (sign > 0) t.y = -t.y;
+            x = cmul(x, t);
+        }
+        v[r] = x;
+    }
+    radix_butterfly(v, R, sign);
+    const int idxD = (j / Ns) * Ns * R + k;
+    for (int r = 0; r < R; ++r) dst[(idxD + r * Ns) * LT + l] = v[r];
+}
+
+// ---- device kernel: one pass along the middle axis of [batch][A][n][B] ----
+template <int LT>
+__global__ void __launch_bounds__(256) fft_axis_kernel(double2* __restrict__ data, int A, int B, Radices rad,
+                                                        const double2* __restrict__ tw, int sign, int TA,
+                                                        int TB, int tilesA, int tilesB) {
+    extern __shared__ double2 sm[];
+    const int n = rad.n;
+    double2* buf0 = sm;
+    double2* buf1 = sm + n * LT;
+    const int tile = blockIdx.x;
+    const long long g = blockIdx.y;
+    const int ta = tile / tilesB, tb = tile % tilesB;
+    const int a0 = ta * TA, b0 = tb * TB;
+    const long long gbase = g * (long long)A * n * B;
+    const int nel = n * TA * TB;
+    // load
+    if (B == 1) {
+        for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+            const int i = e % n, la = e / n;
+            const int a = a0 + la;
+            double2 x = cmk(0.0, 0.0);
+            if (a < A) x = data[gbase + (long long)a * n + i];
+            buf0[i * LT + la] = x;
+        }
+    } else {
+        for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+            const int lb = e % TB, rest = e / TB;
+            const int la = rest % TA, i = rest / TA;
+            const int a = a0 + la, b = b0 + lb;
+            double2 x = cmk(0.0, 0.0);
+            if (a < A && b < B) x = data[gbase + ((long long)a * n + i) * B + b];
+            buf0[i * LT + la * TB + lb] = x;
+        }
+    }
+    __syncthreads();
+    double2* src = buf0;
+    double2* dst = buf1;
+    int Ns = 1;
+    for (int st = 0; st < rad.nst; ++st) {
+        const int R = rad.r[st];
+        const int items = LT * (n / R);
+        for (int w = threadIdx.x; w < items; w += blockDim.x) stockham_item(src, dst, tw, n, LT, R, Ns, sign, w);
+        __syncthreads();
+        Ns *= R;
+        double2* t = src;
+        src = dst;
+        dst = t;
+    }
+    // store from src
+    if (B == 1) {
+        for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+            const int i = e % n, la = e / n;
+            const int a = a0 + la;
+            if (a < A) data[gbase + (long long)a * n + i] = src[i * LT + la];
+        }
+    } else {
+        for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+            const int lb = e % TB, rest = e / TB;
+            const int la = rest % TA, i = rest / TA;
+            const int a = a0 + la, b = b0 + lb;
+            if (a < A && b < B) data[gbase + ((long long)a * n + i) * B + b] = src[i * LT + la * TB + lb];
+        }
+    }
+}
+
+cudaError_t fft_plan_create(FftPlan& p, const int N[3]) {
+    for (int d = 0; d < 3; ++d) {
+        p.N[d] = N[d];
+        if (!fft_factor(N[d], p.ax[d].rad)) return cudaErrorInvalidValue;
+        std::vector<double2> tw(N[d]);
+        for (int t = 0; t < N[d]; ++t) {
+            const double a = -2.0 * M_PI * (double)t / (double)N[d];
+            tw[t] = cmk(std::cos(a), std::sin(a));
+        }
+        cudaError_t e = cudaMalloc(&p.ax[d].d_tw, sizeof(double2) * N[d]);
+        if (e != cudaSuccess) return e;
+        e = cudaMemcpy(p.ax[d].d_tw, tw.data(), sizeof(double2) * N[d], cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+void fft_plan_destroy(FftPlan& p) {
+    for (int d = 0; d < 3; ++d) {
+        if (p.ax[d].d_tw) cudaFree(p.ax[d].d_tw);
+        p.ax[d].d_tw = nullptr;
+    }
+}
+
+static constexpr int kLT = 16;
+
+cudaError_t fft3d(const FftPlan& p, double2* data, int nb, int sign, cudaStream_t st) {
+    const int N0 = p.N[0], N1 = p.N[1], N2 = p.N[2];
+    // axis d: A = prod of earlier dims, B = prod of later dims
+    const int As[3] = {1, N0, N0 * N1};
+    const int Bs[3] = {N1 * N2, N2, 1};
+    // order: contiguous axis first for the forward-to-real (any order gives the same result)
+    const int order[3] = {2, 1, 0};
+    for (int oi = 0; oi < 3; ++oi) {
+        const int d = order[oi];
+        const int A = As[d], B = Bs[d], n = p.N[d];
+        int TB = B < kLT ? B : kLT;
+        int TA = kLT / TB;
+        if (TA < 1) TA = 1;
+        const int tilesA = (A + TA - 1) / TA, tilesB = (B + TB - 1) / TB;
+        const size_t smem = 2 * sizeof(double2) * n * kLT;
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(fft_axis_kernel<kLT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        dim3 grid(tilesA * tilesB, nb);
+        fft_axis_kernel<kLT><<<grid, 128, smem, st>>>(data, A, B, p.ax[d].rad, p.ax[d].d_tw, sign, TA, TB, tilesA,
+                                                      tilesB);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+void fft_host_lines(const Radices& rad, const std::vector<double2>& tw, int nlines, int sign, double2* data) {
+    const int n = rad.n;
+    std::vector<double2> b0(n * nlines), b1(n * nlines);
+    for (int l = 0; l < nlines; ++l)
+        for (int i = 0; i < n; ++i) b0[i * nlines + l] = data[l * n + i];
+    double2* src = b0.data();
+    double2* dst = b1.data();
+    int Ns = 1;
+    for (int s = 0; s < rad.nst; ++s) {
+        const int R = rad.r[s];
+        for (int w = 0; w < nlines * (n / R); ++w) stockham_item(src, dst, tw.data(), n, nlines, R, Ns, sign, w);
+        Ns *= R;
+        double2* t = src;
+        src = dst;
+        dst = t;
+    }
+    for (int l = 0; l < nlines; ++l)
+        for (int i = 0; i < n; ++i) data[l * n + i] = src[i * nlines + l];
+}
+
+}  // namespace hp
+
+extern "C" hp_status hp_selftest_fft_host(int n, int nlines, int sign, const double* in, double* out) {
+    if (n < 1 || nlines < 1 || !in || !out || (sign != 1 && sign != -1)) return HP_EINVAL;
+    hp::Radices rad;
+    if (!hp::fft_factor(n, rad)) return HP_EINVAL;
+    std::vector<double2> tw(n);
+    for (int t = 0; t < n; ++t) {
+        const double a = -2.0 * M_PI * (double)t / (double)n;
+        tw[t] = hp::cmk(std::cos(a), std::sin(a));
+    }
+    std::vector<double2> d(n * nlines);
+    for (int i = 0; i < n * nlines; ++i) d[i] = hp::cmk(in[2 * i], in[2 * i + 1]);
+    hp::fft_host_lines(rad, tw, nlines, sign, d.data());
+    for (int i = 0; i < n * nlines; ++i) {
+        out[2 * i] = d[i].x;
+        out[2 * i + 1] = d[i].y;
+    }
+    return HP_OK;
+}

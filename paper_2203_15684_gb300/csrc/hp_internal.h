@@ -1,0 +1,265 @@
+// Internal declarations of the GB300 DFPT Hubbard engine: device complex arithmetic, the FFT
+// plan, the batched operator kernels and the context that owns every device buffer.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "hp.h"
+
+namespace hp {
+
+// ------------------------------------------------------------------------------------------------
+// complex FP64 helpers (double2 = (re, im))
+// ------------------------------------------------------------------------------------------------
+#if defined(__CUDACC__)
+#define HD __host__ __device__ __forceinline__
+#else
+#define HD inline
+#endif
+
+HD double2 cmk(double r, double i) { double2 z; z.x = r; z.y = i; return z; }
+HD double2 cadd(double2 a, double2 b) { return cmk(a.x + b.x, a.y + b.y); }
+HD double2 csub(double2 a, double2 b) { return cmk(a.x - b.x, a.y - b.y); }
+HD double2 cmul(double2 a, double2 b) { return cmk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+HD double2 cmulc(double2 a, double2 b) { return cmk(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x); }  // conj(a)*b
+HD double2 cscale(double2 a, double s) { return cmk(a.x * s, a.y * s); }
+HD double2 cconj(double2 a) { return cmk(a.x, -a.y); }
+// a * (s i) for s = +-1
+HD double2 cmul_si(double2 a, int s) { return s > 0 ? cmk(-a.y, a.x) : cmk(a.y, -a.x); }
+
+// ------------------------------------------------------------------------------------------------
+// FFT (batched 3D complex, mixed radix 2/3/4/5 Stockham in shared memory, one pass per axis)
+// ------------------------------------------------------------------------------------------------
+constexpr int kMaxStages = 12;
+
+struct Radices {
+    int n, nst;
+    int r[kMaxStages];
+};
+
+struct FftAxis {
+    Radices rad;
+    double2* d_tw = nullptr;   // n twiddles exp(-2 pi i t / n)
+};
+
+struct FftPlan {
+    int N[3] = {0, 0, 0};
+    FftAxis ax[3];
+};
+
+bool fft_factor(int n, Radices& out);
+cudaError_t fft_plan_create(FftPlan& p, const int N[3]);
+void fft_plan_destroy(FftPlan& p);
+// In place, nb grids of N0*N1*N2 complex each, contiguous.  sign +1: sum_G c(G) exp(+iG.r)
+// (to real space), sign -1: sum_r f(r) exp(-iG.r).  Unnormalised both ways.
+cudaError_t fft3d(const FftPlan& p, double2* data, int nb, int sign, cudaStream_t st);
+// the same Stockham code on the host (self-test of the stage logic)
+void fft_host_lines(const Radices& rad, const std::vector<double2>& tw, int nlines, int sign,
+                    double2* data);
+
+// ------------------------------------------------------------------------------------------------
+// Batched band operations.  A band list names nb vectors: for item c its row (index of a vector
+// of ld complex numbers in the matrix it lives in), its sphere k, its spin and a scalar shift.
+// Items are sorted into segments of consecutive items with the same (spin, k); a projector matrix
+// for a segment sits at element offset spin * a_stride_s + k * a_stride_k of its base pointer.
+// ------------------------------------------------------------------------------------------------
+struct SphereSet {          // device arrays, nk spheres of at most ld points
+    int nk = 0, ld = 0;
+    int* d_npw = nullptr;   // [nk]
+    int* d_idx = nullptr;   // [nk][ld] flat grid index of each coefficient
+    double* d_g2 = nullptr; // [nk][ld] |k+G|^2
+    std::vector<int> npw;   // host copy
+};
+
+struct BandList {
+    int nb = 0, nseg = 0;
+    int* d_row = nullptr;
+    int* d_k = nullptr;
+    int* d_spin = nullptr;
+    double* d_shift = nullptr;
+    int* d_seg_start = nullptr;     // [nseg + 1]
+    int* d_seg_k = nullptr;         // [nseg]
+    int* d_seg_s = nullptr;         // [nseg]
+    int cap = 0;                    // allocated items
+    std::vector<int> row, k, spin, seg_start, seg_k, seg_s;
+    std::vector<double> shift;
+};
+
+struct ProjMat {            // a family of projector matrices: base + s*stride_s + k*stride_k
+    const double2* base;
+    long long stride_s, stride_k;
+    int nrow;               // rows used (<= 128)
+    int row0;               // first row inside each matrix
+    const int* kmap;        // optional device map: matrix of list sphere k is kmap[k]
+};
+
+// kernels.cu
+cudaError_t k_scatter(const SphereSet& S, const BandList& L, int c0, int nc, const double2* X, int ldx,
+                      double2* grid, int nr, cudaStream_t st);
+cudaError_t k_gather_h(const SphereSet& S, const BandList& L, int c0, int nc, const double2* grid, int nr,
+                       const double2* X, double2* Y, int ld, cudaStream_t st);
+cudaError_t k_gather_scaled(const SphereSet& S, const BandList& L, int c0, int nc, const double2* grid,
+                            int nr, double scale, double2* Y, int ld, int accumulate, cudaStream_t st);
+cudaError_t k_mul_rpot(double2* grid, int nc, int nr, const double* v, const BandList& L, int c0,
+                       cudaStream_t st);
+cudaError_t k_mul_cpot(double2* grid, const double2* src_rows, const int* src_row_of_item, int nc, int nr,
+                       const double2* v, const BandList& L, int c0, cudaStream_t st);
+cudaError_t k_proj(const BandList& L, const SphereSet& S, const ProjMat& A, const double2* X, int ld,
+                   double2* P, double2* scratch, size_t scratch_elems, cudaStream_t st);
+cudaError_t k_expand(const BandList& L, const SphereSet& S, const ProjMat& A, const double2* P,
+                     const double* pscale, double alpha, double2* Y, int ld, cudaStream_t st);
+cudaError_t k_band_dot(const BandList& L, const SphereSet& S, const double2* X, const double2* Y, int ld,
+                       double* out, cudaStream_t st);
+cudaError_t k_cg_init(const BandList& L, const SphereSet& S, const double2* r, double2* p, int ld,
+                      double* rz, double* rr, cudaStream_t st);
+cudaError_t k_cg_update(const BandList& L, const SphereSet& S, const double* pap, double2* x, double2* r,
+                        const double2* p, const double2* ap, int ld, double* rz, double* rr, double* rz_old,
+                        cudaStream_t st);
+cudaError_t k_cg_direction(const BandList& L, const SphereSet& S, const double* rz, const double* rz_old,
+                           const double2* r, double2* p, int ld, cudaStream_t st);
+cudaError_t k_rows_axpby(const BandList& L, const SphereSet& S, double a, const double2* X, double b,
+                         double2* Y, int ld, cudaStream_t st);
+cudaError_t k_gather_kq(const int* map, const int* npw_kq, const int* kprime, int nk, int nspin, int nocc,
+                        int ld, const double2* psi, int nbnd, double2* ukq, cudaStream_t st);
+cudaError_t k_formfactor(const double* kcart, int nk, const int* miller, const int* npw, int ld,
+                         const double* bvec, int nrow, const int* row_atom, const int* row_l, const int* row_m,
+                         const double* row_width, const double* row_pref, const double* tau, double2* out,
+                         cudaStream_t st);
+cudaError_t k_drho_acc(const double2* ur, const int* ur_row_of_item, const double2* xr, int nc, int nr,
+                       const BandList& L, int c0, double weight, int nspin, double2* drho, cudaStream_t st);
+cudaError_t k_density_acc(const double2* ur, int nc, int nr, const BandList& L, int c0, double weight, int nspin,
+                          double* rho, cudaStream_t st);
+cudaError_t k_hartree_q(double2* rho_g, const int N[3], const double* bvec, const double qfrac[3], double ecut4,
+                        double scale, cudaStream_t st);
+cudaError_t k_vloc_g(double2* vg, const int N[3], const double* bvec, double ecut4, int nat, const double* tau,
+                     const double* amp, const double* width, double omega, cudaStream_t st);
+cudaError_t k_real_part(const double2* z, double* out, int n, double scale, cudaStream_t st);
+cudaError_t k_xc(const double* rho, int nspin, int nr, double* vxc, double* fxc, cudaStream_t st);
+cudaError_t k_hxc_combine(const double2* vh, const double2* drho, const double* fxc, int nspin, int nr,
+                          double2* dv, cudaStream_t st);
+cudaError_t k_occ_response(const double2* B, const double2* Aphi, int ngroups, int nocc, int nhub, int nk,
+                           int nspin, double2* M, cudaStream_t st);
+cudaError_t k_dn_blocks(const double2* M, int nspin, int nhub, int nhub_atoms, const int* off, const int* mdim,
+                        int mmax, double2* dn, cudaStream_t st);
+cudaError_t k_dn_traces(const double2* dn, int nh, int nspin, int mmax, double f, double2* tr, cudaStream_t st);
+cudaError_t k_vec_dot(const double2* a, const double2* b, long long n, double* out, double* partial,
+                      cudaStream_t st);
+cudaError_t k_vec_axpy(double2* y, const double2* x, double a, long long n, cudaStream_t st);
+cudaError_t k_vec_sub(double2* out, const double2* a, const double2* b, long long n, cudaStream_t st);
+cudaError_t k_vec_scale_copy(double2* out, const double2* a, double s, long long n, cudaStream_t st);
+cudaError_t k_broyden_coef(const double* dots, int m, int ld, double w0, double* gamma, cudaStream_t st);
+cudaError_t k_broyden_apply(double2* x, const double2* f, const double2* const* dx, const double2* const* df,
+                            const double* gamma, int m, double alpha, long long n, cudaStream_t st);
+cudaError_t k_chi_assemble(const double2* cols, int nq, int nh, const double* qfrac, const double* Rl, int ncell,
+                           double* chi_re, double* chi_im, cudaStream_t st);
+cudaError_t k_invert(double* a, double* work, int n, int* singular, cudaStream_t st);
+cudaError_t k_hub_matrix(const double* inv0, const double* inv, int n, double scale, double* hub, cudaStream_t st);
+cudaError_t k_add_real(const double* a, const double* b, double* out, int n, cudaStream_t st);
+cudaError_t k_sum_reduce(const double* partial, int nparts, double* out, cudaStream_t st);
+
+// ------------------------------------------------------------------------------------------------
+// Context
+// ------------------------------------------------------------------------------------------------
+struct KSphere {
+    double kfrac[3], kcart[3];
+    int npw = 0;
+    std::vector<int> miller;    // npw x 3
+    std::vector<int> idx;       // flat grid index
+    std::vector<double> g2;
+};
+
+struct RespCols {
+    std::vector<double> dn0, dn;   // complex [nhub_atoms][nspin][mmax][mmax]
+    std::vector<double> tr0, tr;   // spin-summed traces per Hubbard atom
+};
+
+struct QCache {                    // per-q data: k+q spheres, projectors and occupied states at k+q
+    int iq = -1;
+    SphereSet set;
+    std::vector<KSphere> ks;
+    double2* d_beta = nullptr;     // [nk][nproj][ld]
+    double2* d_phi = nullptr;      // [nk][nhub][ld]
+    double2* d_u = nullptr;        // [nspin][nk][nocc][ld]
+    double* d_kcart = nullptr;
+    int* d_miller = nullptr;
+};
+
+}  // namespace hp
+
+struct hp_ctx {
+    hp_options opt;
+    cudaStream_t st = nullptr;
+    std::string err;
+    // cell
+    double cell[9], bvec[9], omega = 0;
+    std::vector<hp_species> species;
+    std::vector<int> atom_species;
+    std::vector<double> frac, tau;     // natoms x 3
+    double ecut = 0;
+    int kmesh[3], qmesh[3];
+    int N[3], nr = 0;
+    int nk = 0, nq = 0;
+    std::vector<hp::KSphere> ks;       // sphere per mesh k
+    int ld = 0;                        // padded sphere length (max npw over k and every k+q)
+    // projector rows and Hubbard rows
+    int nproj = 0, nhub = 0;
+    std::vector<int> proj_atom, proj_l, proj_m;
+    std::vector<double> proj_D, proj_w, proj_pref;
+    std::vector<int> hub_row_atom, hub_row_l, hub_row_m;
+    std::vector<double> hub_row_w, hub_row_pref;
+    std::vector<int> hub_atoms, hub_off, hub_mdim;
+    hp::FftPlan fft;
+    hp::SphereSet kset;                // mesh spheres
+    // device constants
+    double* d_bvec = nullptr;
+    double* d_tau = nullptr;
+    double* d_vloc = nullptr;          // [nr]
+    double* d_projD = nullptr;         // [nproj]
+    double2* d_beta_k = nullptr;       // [nk][nproj][ld]
+    double2* d_phi_k = nullptr;        // [nk][nhub][ld]
+    int* d_proj_int = nullptr;         // row_atom, row_l, row_m for projectors then Hubbard rows
+    double* d_proj_dbl = nullptr;      // widths and prefactors
+    // ground state
+    bool have_gs = false;
+    int nspin = 0, nocc = 0, nbnd = 0;
+    double nelec = 0;
+    double gap = 0;
+    std::vector<double> eps;           // [nspin][nk][nbnd]
+    double* d_vhxc = nullptr;          // [nspin][nr]
+    double* d_rho = nullptr;           // [nspin][nr]
+    double* d_veff = nullptr;          // [nspin][nr] V_loc + V_Hxc
+    double2* d_psi = nullptr;          // [nspin][nk][nbnd][ld]
+    // response caches (built on first use after a ground state)
+    bool resp_ready = false;
+    double2* d_ur = nullptr;           // [nspin][nk][nocc][nr]
+    double2* d_aphi = nullptr;         // [nspin][nk][nocc][nhub] <phi_m,k|u_v>
+    double* d_fxc = nullptr;           // [3 or 1][nr]
+    double alpha_pv = 0;
+    hp::QCache qc;
+    // response work arrays
+    int resp_rows = 0;
+    double2 *d_x = nullptr, *d_r = nullptr, *d_p = nullptr, *d_ap = nullptr, *d_b = nullptr, *d_vpu = nullptr;
+    double *d_rz = nullptr, *d_rzold = nullptr, *d_rr = nullptr, *d_pap = nullptr;
+    double2 *d_dv = nullptr, *d_dvout = nullptr, *d_drho = nullptr, *d_dvh = nullptr;
+    double2* d_Pbuf = nullptr;         // projections [rows][128]
+    double2* d_M = nullptr;            // [nspin][nhub][nhub]
+    double2* d_dn = nullptr;           // [nhub_atoms][nspin][mmax][mmax]
+    std::vector<double2*> d_hist_dx, d_hist_df;
+    double2** d_hist_ptrs = nullptr;
+    double* d_small = nullptr;         // small scalars for reductions / Broyden
+    double* d_partial = nullptr;
+    // results
+    std::map<std::pair<int, int>, hp::RespCols> cols;
+    // scratch (device)
+    double2* d_grid = nullptr;         // grid_cap x nr
+    int grid_cap = 0;
+    double2* d_scratch = nullptr;
+    size_t scratch_elems = 0;
+    hp::BandList L1, L2, L3;           // reusable band lists
+    std::vector<void*> owned;          // device allocations freed in hp_destroy
+};

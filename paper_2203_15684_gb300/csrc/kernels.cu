@@ -1,0 +1,1137 @@
+// Operator kernels of the FP64 Sternheimer path: sphere <-> grid maps, local potentials, the
+// segmented projector contractions (nonlocal beta D beta^H, the valence projector alpha O and P_c,
+// Hubbard projections), CG vector updates, response densities, the Hartree and LDA response
+// kernels, and the small dense algebra of the mixing and of chi.
+#include <cmath>
+
+#include "hp_internal.h"
+
+namespace hp {
+
+static inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// block-wide sum of one double (blockDim.x multiple of 32, <= 1024); result valid in thread 0
+__device__ double block_sum(double v, double* sh) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    const int nw = blockDim.x >> 5;
+    v = (threadIdx.x < nw) ? sh[threadIdx.x] : 0.0;
+    if (wid == 0) v = warp_sum(v);
+    __syncthreads();
+    return v;
+}
+
+// ------------------------------------------------------------------------------------------------
+// sphere <-> grid
+// ------------------------------------------------------------------------------------------------
+__global__ void scatter_kernel(const int* __restrict__ npw, const int* __restrict__ idx, int ld,
+                               const int* __restrict__ row, const int* __restrict__ kk, int c0,
+                               const double2* __restrict__ X, double2* __restrict__ grid, int nr) {
+    const int c = c0 + blockIdx.y;
+    const int k = kk[c];
+    const int G = blockIdx.x * blockDim.x + threadIdx.x;
+    if (G < npw[k]) grid[(long long)blockIdx.y * nr + idx[(long long)k * ld + G]] = X[(long long)row[c] * ld + G];
+}
+
+cudaError_t k_scatter(const SphereSet& S, const BandList& L, int c0, int nc, const double2* X, int ldx,
+                      double2* grid, int nr, cudaStream_t st) {
+    if (nc <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(grid, 0, sizeof(double2) * (size_t)nc * nr, st);
+    if (e != cudaSuccess) return e;
+    dim3 g(cdiv(S.ld, 128), nc);
+    scatter_kernel<<<g, 128, 0, st>>>(S.d_npw, S.d_idx, S.ld, L.d_row, L.d_k, c0, X, grid, nr);
+    (void)ldx;
+    return cudaGetLastError();
+}
+
+// Y = grid[idx] / nr + (|k+G|^2/2 - shift) X   (local + kinetic - shift), zero beyond npw
+__global__ void gather_h_kernel(const int* __restrict__ npw, const int* __restrict__ idx,
+                                const double* __restrict__ g2, int ld, const int* __restrict__ row,
+                                const int* __restrict__ kk, const double* __restrict__ shift, int c0,
+                                const double2* __restrict__ grid, int nr, const double2* __restrict__ X,
+                                double2* __restrict__ Y) {
+    const int c = c0 + blockIdx.y;
+    const int k = kk[c];
+    const int G = blockIdx.x * blockDim.x + threadIdx.x;
+    if (G >= ld) return;
+    const long long o = (long long)row[c] * ld + G;
+    if (G < npw[k]) {
+        const double inv = 1.0 / (double)nr;
+        const double2 v = grid[(long long)blockIdx.y * nr + idx[(long long)k * ld + G]];
+        const double d = 0.5 * g2[(long long)k * ld + G] - shift[c];
+        const double2 x = X[o];
+        Y[o] = cmk(v.x * inv + d * x.x, v.y * inv + d * x.y);
+    } else {
+        Y[o] = cmk(0.0, 0.0);
+    }
+}
+
+cudaError_t k_gather_h(const SphereSet& S, const BandList& L, int c0, int nc, const double2* grid, int nr,
+                       const double2* X, double2* Y, int ld, cudaStream_t st) {
+    if (nc <= 0) return cudaSuccess;
+    dim3 g(cdiv(ld, 128), nc);
+    gather_h_kernel<<<g, 128, 0, st>>>(S.d_npw, S.d_idx, S.d_g2, ld, L.d_row, L.d_k, L.d_shift, c0, grid, nr, X, Y);
+    return cudaGetLastError();
+}
+
+__global__ void gather_scaled_kernel(const int* __restrict__ npw, const int* __restrict__ idx, int ld,
+                                     const int* __restrict__ row, const int* __restrict__ kk, int c0,
+                                     const double2* __restrict__ grid, int nr, double scale,
+                                     double2* __restrict__ Y, int accumulate) {
+    const int c = c0 + blockIdx.y;
+    const int k = kk[c];
+    const int G = blockIdx.x * blockDim.x + threadIdx.x;
+    if (G >= ld) return;
+    const long long o = (long long)row[c] * ld + G;
+    double2 v = cmk(0.0, 0.0);
+    if (G < npw[k]) v = cscale(grid[(long long)blockIdx.y * nr + idx[(long long)k * ld + G]], scale);
+    Y[o] = accumulate ? cadd(Y[o], v) : v;
+}
+
+cudaError_t k_gather_scaled(const SphereSet& S, const BandList& L, int c0, int nc, const double2* grid, int nr,
+                            double scale, double2* Y, int ld, int accumulate, cudaStream_t st) {
+    if (nc <= 0) return cudaSuccess;
+    dim3 g(cdiv(ld, 128), nc);
+    gather_scaled_kernel<<<g, 128, 0, st>>>(S.d_npw, S.d_idx, ld, L.d_row, L.d_k, c0, grid, nr, scale, Y, accumulate);
+    return cudaGetLastError();
+}
+
+__global__ void mul_rpot_kernel(double2* __restrict__ grid, int nr, const double* __restrict__ v,
+                                const int* __restrict__ spin, int c0) {
+    const int c = blockIdx.y;
+    const double* vs = v + (long long)spin[c0 + c] * nr;
+    double2* g = grid + (long long)c * nr;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += gridDim.x * blockDim.x) {
+        const double s = vs[r];
+        const double2 z = g[r];
+        g[r] = cmk(z.x * s, z.y * s);
+    }
+}
+
+cudaError_t k_mul_rpot(double2* grid, int nc, int nr, const double* v, const BandList& L, int c0, cudaStream_t st) {
+    if (nc <= 0) return cudaSuccess;
+    dim3 g(cdiv(nr, 256 * 4), nc);
+    mul_rpot_kernel<<<g, 256, 0, st>>>(grid, nr, v, L.d_spin, c0);
+    return cudaGetLastError();
+}
+
+// grid[c] = v[spin] * src_rows[src_row_of_item[c]]   (complex potential times a cached real-space u)
+__global__ void mul_cpot_kernel(double2* __restrict__ grid, const double2* __restrict__ src,
+                                const int* __restrict__ src_row, int nr, const double2* __restrict__ v,
+                                const int* __restrict__ spin, int c0) {
+    const int c = blockIdx.y;
+    const double2* vs = v + (long long)spin[c0 + c] * nr;
+    const double2* u = src + (long long)src_row[c0 + c] * nr;
+    double2* g = grid + (long long)c * nr;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += gridDim.x * blockDim.x) g[r] = cmul(vs[r], u[r]);
+}
+
+cudaError_t k_mul_cpot(double2* grid, const double2* src_rows, const int* src_row_of_item, int nc, int nr,
+                       const double2* v, const BandList& L, int c0, cudaStream_t st) {
+    if (nc <= 0) return cudaSuccess;
+    dim3 g(cdiv(nr, 256 * 4), nc);
+    mul_cpot_kernel<<<g, 256, 0, st>>>(grid, src_rows, src_row_of_item, nr, v, L.d_spin, c0);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
+// segmented projector contractions
+//   proj:   P[c][p]  = sum_G conj(A_seg[row0 + p][G]) X[row[c]][G]          (p < nrow)
+//   expand: Y[row[c]][G] += alpha sum_p A_seg[row0 + p][G] pscale[p] P[c][p]
+// P is indexed by list item c with a row stride of 128.
+// ------------------------------------------------------------------------------------------------
+constexpr int kPStride = 128;
+constexpr int TP = 32, TC = 32, TG = 32;
+
+__global__ void __launch_bounds__(256) proj_kernel(const double2* __restrict__ Abase, long long sa_s, long long sa_k,
+                                                   int row0, int nrow, int ld, const double2* __restrict__ X,
+                                                   const int* __restrict__ row, const int* __restrict__ seg_start,
+                                                   const int* __restrict__ seg_k, const int* __restrict__ seg_s,
+                                                   const int* __restrict__ npw_of_k, const int* __restrict__ kmap,
+                                                   int ksplit, double2* __restrict__ part, int nb) {
+    __shared__ double2 As[TG][TP + 1];
+    __shared__ double2 Xs[TG][TC + 1];
+    const int seg = blockIdx.x, ks = blockIdx.y;
+    const int cbeg = seg_start[seg], cend = seg_start[seg + 1];
+    const int k = seg_k[seg];
+    const int npw = npw_of_k[k];
+    const int chunk = ((npw + ksplit - 1) / ksplit + TG - 1) / TG * TG;
+    const int g0 = ks * chunk;
+    const int g1 = min(npw, g0 + chunk);
+    const int mk = kmap ? kmap[k] : k;
+    const double2* A = Abase + seg_s[seg] * sa_s + mk * sa_k + (long long)row0 * ld;
+    const int tid = threadIdx.x;
+    const int tp = tid & 31, tc = tid >> 5;  // 8 warps
+    for (int pt = 0; pt < nrow; pt += TP) {
+        for (int ct = cbeg; ct < cend; ct += TC) {
+            double2 acc[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[i] = cmk(0.0, 0.0);
+            for (int gt = g0; gt < g1; gt += TG) {
+                // load A tile [TG][TP] and X tile [TG][TC]
+                for (int e = tid; e < TG * TP; e += 256) {
+                    const int gg = e & 31, pp = e >> 5;
+                    const int p = pt + pp, G = gt + gg;
+                    As[gg][pp] = (p < nrow && G < g1) ? A[(long long)p * ld + G] : cmk(0.0, 0.0);
+                }
+                for (int e = tid; e < TG * TC; e += 256) {
+                    const int gg = e & 31, cc = e >> 5;
+                    const int c = ct + cc, G = gt + gg;
+                    Xs[gg][cc] = (c < cend && G < g1) ? X[(long long)row[c] * ld + G] : cmk(0.0, 0.0);
+                }
+                __syncthreads();
+#pragma unroll 8
+                for (int gg = 0; gg < TG; ++gg) {
+                    const double2 a = As[gg][tp];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const double2 x = Xs[gg][tc + 8 * i];
+                        acc[i].x += a.x * x.x + a.y * x.y;
+                        acc[i].y += a.x * x.y - a.y * x.x;
+                    }
+                }
+                __syncthreads();
+            }
+            const int p = pt + tp;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int c = ct + tc + 8 * i;
+                if (p < nrow && c < cend) part[((long long)ks * nb + c) * kPStride + p] = acc[i];
+            }
+        }
+    }
+}
+
+__global__ void proj_reduce_kernel(const double2* __restrict__ part, int ksplit, int nb, int nrow,
+                                   double2* __restrict__ P) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)nb * nrow) return;
+    const int c = (int)(e / nrow), p = (int)(e % nrow);
+    double2 s = cmk(0.0, 0.0);
+    for (int ks = 0; ks < ksplit; ++ks) s = cadd(s, part[((long long)ks * nb + c) * kPStride + p]);
+    P[(long long)c * kPStride + p] = s;
+}
+
+cudaError_t k_proj(const BandList& L, const SphereSet& S, const ProjMat& A, const double2* X, int ld, double2* P,
+                   double2* scratch, size_t scratch_elems, cudaStream_t st) {
+    if (L.nb <= 0 || A.nrow <= 0) return cudaSuccess;
+    if (A.nrow > kPStride) return cudaErrorInvalidValue;
+    int ksplit = std::max(1, 2 * 152 / std::max(1, L.nseg));
+    ksplit = std::min(ksplit, std::max(1, S.ld / 128));
+    while (ksplit > 1 && (size_t)ksplit * L.nb * kPStride > scratch_elems) --ksplit;
+    if ((size_t)ksplit * L.nb * kPStride > scratch_elems) return cudaErrorMemoryAllocation;
+    dim3 g(L.nseg, ksplit);
+    proj_kernel<<<g, 256, 0, st>>>(A.base, A.stride_s, A.stride_k, A.row0, A.nrow, ld, X, L.d_row, L.d_seg_start,
+                                   L.d_seg_k, L.d_seg_s, S.d_npw, A.kmap, ksplit, scratch, L.nb);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    proj_reduce_kernel<<<cdiv((long long)L.nb * A.nrow, 256), 256, 0, st>>>(scratch, ksplit, L.nb, A.nrow, P);
+    return cudaGetLastError();
+}
+
+constexpr int kExpC = 8;
+
+__global__ void __launch_bounds__(128) expand_kernel(const double2* __restrict__ Abase, long long sa_s, long long sa_k,
+                                                     int row0, int nrow, int ld, const double2* __restrict__ P,
+                                                     const double* __restrict__ pscale, double alpha,
+                                                     double2* __restrict__ Y, const int* __restrict__ row,
+                                                     const int* __restrict__ seg_start, const int* __restrict__ seg_k,
+                                                     const int* __restrict__ seg_s, const int* __restrict__ npw_of_k,
+                                                     const int* __restrict__ kmap) {
+    __shared__ double2 Ps[kExpC][kPStride];
+    const int seg = blockIdx.y;
+    const int cbeg = seg_start[seg], cend = seg_start[seg + 1];
+    const int k = seg_k[seg];
+    const int npw = npw_of_k[k];
+    const int G = blockIdx.x * blockDim.x + threadIdx.x;
+    const int mk = kmap ? kmap[k] : k;
+    const double2* A = Abase + seg_s[seg] * sa_s + mk * sa_k + (long long)row0 * ld;
+    for (int ct = cbeg; ct < cend; ct += kExpC) {
+        for (int e = threadIdx.x; e < kExpC * nrow; e += blockDim.x) {
+            const int cc = e / nrow, p = e % nrow;
+            const int c = ct + cc;
+            double2 v = cmk(0.0, 0.0);
+            if (c < cend) {
+                v = P[(long long)c * kPStride + p];
+                const double s = alpha * (pscale ? pscale[p] : 1.0);
+                v = cscale(v, s);
+            }
+            Ps[cc][p] = v;
+        }
+        __syncthreads();
+        if (G < npw) {
+            double2 acc[kExpC];
+#pragma unroll
+            for (int i = 0; i < kExpC; ++i) acc[i] = cmk(0.0, 0.0);
+            for (int p = 0; p < nrow; ++p) {
+                const double2 a = A[(long long)p * ld + G];
+#pragma unroll
+                for (int i = 0; i < kExpC; ++i) {
+                    const double2 q = Ps[i][p];
+                    acc[i].x += a.x * q.x - a.y * q.y;
+                    acc[i].y += a.x * q.y + a.y * q.x;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < kExpC; ++i) {
+                const int c = ct + i;
+                if (c < cend) {
+                    const long long o = (long long)row[c] * ld + G;
+                    Y[o] = cadd(Y[o], acc[i]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t k_expand(const BandList& L, const SphereSet& S, const ProjMat& A, const double2* P, const double* pscale,
+                     double alpha, double2* Y, int ld, cudaStream_t st) {
+    if (L.nb <= 0 || A.nrow <= 0) return cudaSuccess;
+    if (A.nrow > kPStride) return cudaErrorInvalidValue;
+    dim3 g(cdiv(ld, 128), L.nseg);
+    expand_kernel<<<g, 128, 0, st>>>(A.base, A.stride_s, A.stride_k, A.row0, A.nrow, ld, P, pscale, alpha, Y, L.d_row,
+                                     L.d_seg_start, L.d_seg_k, L.d_seg_s, S.d_npw, A.kmap);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
+// per-band reductions and CG updates (one CTA per list item, fixed reduction order)
+// preconditioner M^-1 = 1 / (1 + |k+G|^2 / 2)
+// ------------------------------------------------------------------------------------------------
+__global__ void band_dot_kernel(const int* __restrict__ row, const int* __restrict__ kk, const int* __restrict__ npw,
+                               const double2* __restrict__ X, const double2* __restrict__ Y, int ld,
+                               double* __restrict__ out) {
+    __shared__ double sh[32];
+    const int c = blockIdx.x;
+    const int n = npw[kk[c]];
+    const long long o = (long long)row[c] * ld;
+    double s = 0.0;
+    for (int G = threadIdx.x; G < n; G += blockDim.x) {
+        const double2 a = X[o + G], b = Y[o + G];
+        s += a.x * b.x + a.y * b.y;
+    }
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) out[row[c]] = s;
+}
+
+cudaError_t k_band_dot(const BandList& L, const SphereSet& S, const double2* X, const double2* Y, int ld, double* out,
+                       cudaStream_t st) {
+    if (L.nb <= 0) return cudaSuccess;
+    band_dot_kernel<<<L.nb, 256, 0, st>>>(L.d_row, L.d_k, S.d_npw, X, Y, ld, out);
+    return cudaGetLastError();
+}
+
+// p = M r; rz = <r, M r>; rr = <r, r>
+__global__ void cg_init_kernel(const int* __restrict__ row, const int* __restrict__ kk, const int* __restrict__ npw,
+                               const double* __restrict__ g2, const double2* __restrict__ r, double2* __restrict__ p,
+                               int ld, double* __restrict__ rz, double* __restrict__ rr) {
+    __shared__ double sh[32];
+    const int c = blockIdx.x, k = kk[c];
+    const int n = npw[k];
+    const long long o = (long long)row[c] * ld;
+    double s1 = 0.0, s2 = 0.0;
+    for (int G = threadIdx.x; G < n; G += blockDim.x) {
+        const double m = 1.0 / (1.0 + 0.5 * g2[(long long)k * ld + G]);
+        const double2 x = r[o + G];
+        const double q = x.x * x.x + x.y * x.y;
+        p[o + G] = cscale(x, m);
+        s1 += m * q;
+        s2 += q;
+    }
+    s1 = block_sum(s1, sh);
+    s2 = block_sum(s2, sh);
+    if (threadIdx.x == 0) {
+        rz[row[c]] = s1;
+        rr[row[c]] = s2;
+    }
+}
+
+cudaError_t k_cg_init(const BandList& L, const SphereSet& S, const double2* r, double2* p, int ld, double* rz,
+                      double* rr, cudaStream_t st) {
+    if (L.nb <= 0) return cudaSuccess;
+    cg_init_kernel<<<L.nb, 256, 0, st>>>(L.d_row, L.d_k, S.d_npw, S.d_g2, r, p, ld, rz, rr);
+    return cudaGetLastError();
+}
+
+// a = rz / pAp; x += a p; r -= a Ap; rz_old = rz; rz = <r, M r>; rr = <r, r>
+__global__ void cg_update_kernel(const int* __restrict__ row, const int* __restrict__ kk, const int* __restrict__ npw,
+                                 const double* __restrict__ g2, const double* __restrict__ pap, double2* __restrict__ x,
+                                 double2* __restrict__ r, const double2* __restrict__ p, const double2* __restrict__ ap,
+                                 int ld, double* __restrict__ rz, double* __restrict__ rr, double* __restrict__ rz_old) {
+    __shared__ double sh[32];
+    const int c = blockIdx.x, k = kk[c];
+    const int b = row[c];
+    const int n = npw[k];
+    const long long o = (long long)b * ld;
+    const double a = rz[b] / pap[b];
+    double s1 = 0.0, s2 = 0.0;
+    for (int G = threadIdx.x; G < n; G += blockDim.x) {
+        const double2 pv = p[o + G], av = ap[o + G];
+        double2 xv = x[o + G], rv = r[o + G];
+        xv.x += a * pv.x;
+        xv.y += a * pv.y;
+        rv.x -= a * av.x;
+        rv.y -= a * av.y;
+        x[o + G] = xv;
+        r[o + G] = rv;
+        const double m = 1.0 / (1.0 + 0.5 * g2[(long long)k * ld + G]);
+        const double q = rv.x * rv.x + rv.y * rv.y;
+        s1 += m * q;
+        s2 += q;
+    }
+    s1 = block_sum(s1, sh);
+    s2 = block_sum(s2, sh);
+    if (threadIdx.x == 0) {
+        rz_old[b] = rz[b];
+        rz[b] = s1;
+        rr[b] = s2;
+    }
+}
+
+cudaError_t k_cg_update(const BandList& L, const SphereSet& S, const double* pap, double2* x, double2* r,
+                        const double2* p, const double2* ap, int ld, double* rz, double* rr, double* rz_old,
+                        cudaStream_t st) {
+    if (L.nb <= 0) return cudaSuccess;
+    cg_update_kernel<<<L.nb, 256, 0, st>>>(L.d_row, L.d_k, S.d_npw, S.d_g2, pap, x, r, p, ap, ld, rz, rr, rz_old);
+    return cudaGetLastError();
+}
+
+// p = M r + (rz / rz_old) p
+__global__ void cg_dir_kernel(const int* __restrict__ row, const int* __restrict__ kk, const int* __restrict__ npw,
+                              const double* __restrict__ g2, const double* __restrict__ rz,
+                              const double* __restrict__ rz_old, const double2* __restrict__ r, double2* __restrict__ p,
+                              int ld) {
+    const int c = blockIdx.x, k = kk[c];
+    const int b = row[c];
+    const int n = npw[k];
+    const long long o = (long long)b * ld;
+    const double beta = rz[b] / rz_old[b];
+    for (int G = threadIdx.x; G < n; G += blockDim.x) {
+        const double m = 1.0 / (1.0 + 0.5 * g2[(long long)k * ld + G]);
+        const double2 rv = r[o + G], pv = p[o + G];
+        p[o + G] = cmk(m * rv.x + beta * pv.x, m * rv.y + beta * pv.y);
+    }
+}
+
+cudaError_t k_cg_direction(const BandList& L, const SphereSet& S, const double* rz, const double* rz_old,
+                           const double2* r, double2* p, int ld, cudaStream_t st) {
+    if (L.nb <= 0) return cudaSuccess;
+    cg_dir_kernel<<<L.nb, 256, 0, st>>>(L.d_row, L.d_k, S.d_npw, S.d_g2, rz, rz_old, r, p, ld);
+    return cudaGetLastError();
+}
+
+// Y = a X + b Y on the rows of the list (full padded rows)
+__global__ void rows_axpby_kernel(const int* __restrict__ row, double a, const double2* __restrict__ X, double b,
+                                  double2* __restrict__ Y, int ld) {
+    const int c = blockIdx.y;
+    const int G = blockIdx.x * blockDim.x + threadIdx.x;
+    if (G >= ld) return;
+    const long long o = (long long)row[c] * ld + G;
+    const double2 x = X ? X[o] : cmk(0.0, 0.0);
+    const double2 y = Y[o];
+    Y[o] = cmk(a * x.x + b * y.x, a * x.y + b * y.y);
+}
+
+cudaError_t k_rows_axpby(const BandList& L, const SphereSet& S, double a, const double2* X, double b, double2* Y,
+                         int ld, cudaStream_t st) {
+    if (L.nb <= 0) return cudaSuccess;
+    dim3 g(cdiv(ld, 128), L.nb);
+    rows_axpby_kernel<<<g, 128, 0, st>>>(L.d_row, a, X, b, Y, ld);
+    (void)S;
+    return cudaGetLastError();
+}
+
+// u_{k+q}[s][k][v][G] = psi[s][k'][v][map[k][G]]  (k+q = k' + G0 re-indexing), zero padding
+__global__ void gather_kq_kernel(const int* __restrict__ map, const int* __restrict__ npw_kq,
+                                 const int* __restrict__ kprime, int nk, int nocc, int ld,
+                                 const double2* __restrict__ psi, int nbnd, double2* __restrict__ ukq) {
+    const int item = blockIdx.y;  // (s * nk + k) * nocc + v
+    const int v = item % nocc;
+    const int sk = item / nocc;
+    const int k = sk % nk, s = sk / nk;
+    const int G = blockIdx.x * blockDim.x + threadIdx.x;
+    if (G >= ld) return;
+    double2 z = cmk(0.0, 0.0);
+    if (G < npw_kq[k]) {
+        const long long src = ((long long)(s * nk + kprime[k]) * nbnd + v) * ld + map[(long long)k * ld + G];
+        z = psi[src];
+    }
+    ukq[(long long)item * ld + G] = z;
+}
+
+cudaError_t k_gather_kq(const int* map, const int* npw_kq, const int* kprime, int nk, int nspin, int nocc, int ld,
+                        const double2* psi, int nbnd, double2* ukq, cudaStream_t st) {
+    dim3 g(cdiv(ld, 128), nspin * nk * nocc);
+    gather_kq_kernel<<<g, 128, 0, st>>>(map, npw_kq, kprime, nk, nocc, ld, psi, nbnd, ukq);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
+// closed-form atomic form factors <k+G|f_lm>:
+//   (4 pi / sqrt(Omega)) (-i)^l Y_lm(K) N_R sqrt(pi/2) s^(2l+3) |K|^l exp(-|K|^2 s^2 / 2) exp(-i K.tau)
+// with the prefactor (all but the K dependence) computed on the host per row.
+// Real harmonics: l=1 (x, y, z); l=2 (xy, yz, 3z^2-r^2, xz, x^2-y^2) in that order.
+// ------------------------------------------------------------------------------------------------
+__device__ double real_harmonic(int l, int m, double x, double y, double z, double r) {
+    const double PI = 3.14159265358979323846;
+    if (l == 0) return 0.5 / sqrt(PI);
+    if (r <= 0.0) return 0.0;
+    const double ir = 1.0 / r;
+    x *= ir;
+    y *= ir;
+    z *= ir;
+    if (l == 1) {
+        const double c = sqrt(3.0 / (4.0 * PI));
+        return c * (m == 0 ? x : (m == 1 ? y : z));
+    }
+    const double c1 = sqrt(15.0 / (4.0 * PI));
+    switch (m) {
+        case 0: return c1 * x * y;
+        case 1: return c1 * y * z;
+        case 2: return sqrt(5.0 / (16.0 * PI)) * (3.0 * z * z - 1.0);
+        case 3: return c1 * x * z;
+        default: return sqrt(15.0 / (16.0 * PI)) * (x * x - y * y);
+    }
+}
+
+__global__ void formfactor_kernel(const double* __restrict__ kcart, const int* __restrict__ miller,
+                                  const int* __restrict__ npw, int ld, const double* __restrict__ bvec, int nrow,
+                                  const int* __restrict__ row_atom, const int* __restrict__ row_l,
+                                  const int* __restrict__ row_m, const double* __restrict__ row_width,
+                                  const double* __restrict__ row_pref, const double* __restrict__ tau,
+                                  double2* __restrict__ out) {
+    const int k = blockIdx.z;
+    const int rw = blockIdx.y;
+    const int G = blockIdx.x * blockDim.x + threadIdx.x;
+    if (G >= ld) return;
+    const long long o = ((long long)k * nrow + rw) * ld + G;
+    if (G >= npw[k]) {
+        out[o] = cmk(0.0, 0.0);
+        return;
+    }
+    const int* m = miller + ((long long)k * ld + G) * 3;
+    double K[3];
+    for (int i = 0; i < 3; ++i)
+        K[i] = kcart[3 * k + i] + m[0] * bvec[0 * 3 + i] + m[1] * bvec[1 * 3 + i] + m[2] * bvec[2 * 3 + i];
+    const double g = sqrt(K[0] * K[0] + K[1] * K[1] + K[2] * K[2]);
+    const int l = row_l[rw], a = row_atom[rw];
+    const double s = row_width[rw];
+    const double Y = real_harmonic(l, row_m[rw], K[0], K[1], K[2], g);
+    double gl = 1.0;
+    for (int i = 0; i < l; ++i) gl *= g;
+    const double mag = row_pref[rw] * Y * gl * exp(-0.5 * g * g * s * s);
+    const double ph = -(K[0] * tau[3 * a] + K[1] * tau[3 * a + 1] + K[2] * tau[3 * a + 2]);
+    double sp, cp;
+    sincos(ph, &sp, &cp);
+    double2 z = cmk(mag * cp, mag * sp);
+    // (-i)^l
+    if (l == 1) z = cmk(z.y, -z.x);
+    else if (l == 2) z = cmk(-z.x, -z.y);
+    out[o] = z;
+}
+
+cudaError_t k_formfactor(const double* kcart, int nk, const int* miller, const int* npw, int ld, const double* bvec,
+                         int nrow, const int* row_atom, const int* row_l, const int* row_m, const double* row_width,
+                         const double* row_pref, const double* tau, double2* out, cudaStream_t st) {
+    if (nrow <= 0 || nk <= 0) return cudaSuccess;
+    dim3 g(cdiv(ld, 128), nrow, nk);
+    formfactor_kernel<<<g, 128, 0, st>>>(kcart, miller, npw, ld, bvec, nrow, row_atom, row_l, row_m, row_width, row_pref,
+                                         tau, out);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
+// densities
+// ------------------------------------------------------------------------------------------------
+// drho[s][r] += weight * sum_c conj(ur[ur_row[c]][r]) xr[c][r]   (items of spin s), fixed order
+__global__ void drho_acc_kernel(const double2* __restrict__ ur, const int* __restrict__ ur_row,
+                                const double2* __restrict__ xr, int nc, int nr, const int* __restrict__ spin, int c0,
+                                double weight, int nspin, double2* __restrict__ drho) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += gridDim.x * blockDim.x) {
+        double2 acc0 = cmk(0.0, 0.0), acc1 = cmk(0.0, 0.0);
+        for (int c = 0; c < nc; ++c) {
+            const double2 u = ur[(long long)ur_row[c0 + c] * nr + r];
+            const double2 x = xr[(long long)c * nr + r];
+            const double2 t = cmulc(u, x);
+            if (spin[c0 + c] == 0) acc0 = cadd(acc0, t);
+            else acc1 = cadd(acc1, t);
+        }
+        drho[r] = cadd(drho[r], cscale(acc0, weight));
+        if (nspin == 2) drho[(long long)nr + r] = cadd(drho[(long long)nr + r], cscale(acc1, weight));
+    }
+}
+
+cudaError_t k_drho_acc(const double2* ur, const int* ur_row_of_item, const double2* xr, int nc, int nr,
+                       const BandList& L, int c0, double weight, int nspin, double2* drho, cudaStream_t st) {
+    if (nc <= 0) return cudaSuccess;
+    drho_acc_kernel<<<cdiv(nr, 256), 256, 0, st>>>(ur, ur_row_of_item, xr, nc, nr, L.d_spin, c0, weight, nspin, drho);
+    return cudaGetLastError();
+}
+
+// rho[s][r] += weight * sum_c |ur[c][r]|^2
+__global__ void density_acc_kernel(const double2* __restrict__ ur, int nc, int nr, const int* __restrict__ spin, int c0,
+                                   double weight, int nspin, double* __restrict__ rho) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += gridDim.x * blockDim.x) {
+        double a0 = 0.0, a1 = 0.0;
+        for (int c = 0; c < nc; ++c) {
+            const double2 u = ur[(long long)c * nr + r];
+            const double q = u.x * u.x + u.y * u.y;
+            if (spin[c0 + c] == 0) a0 += q;
+            else a1 += q;
+        }
+        rho[r] += weight * a0;
+        if (nspin == 2) rho[(long long)nr + r] += weight * a1;
+    }
+}
+
+cudaError_t k_density_acc(const double2* ur, int nc, int nr, const BandList& L, int c0, double weight, int nspin,
+                          double* rho, cudaStream_t st) {
+    if (nc <= 0) return cudaSuccess;
+    density_acc_kernel<<<cdiv(nr, 256), 256, 0, st>>>(ur, nc, nr, L.d_spin, c0, weight, nspin, rho);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
+// reciprocal-space potentials
+// For grid index j_i the representative Miller index m_i satisfies m_i + q_i in (-N_i/2, N_i/2); an
+// index without one (the Nyquist plane of an even grid at q_i = 0) and every |q+G|^2 > ecut4 are
+// dropped.
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ bool qg_vector(long long flat, const int* N, const double* q, const double* b, double* v) {
+    int j[3];
+    j[2] = (int)(flat % N[2]);
+    j[1] = (int)((flat / N[2]) % N[1]);
+    j[0] = (int)(flat / ((long long)N[1] * N[2]));
+    double f[3];
+    bool ok = true;
+    for (int i = 0; i < 3; ++i) {
+        double m = (j[i] + q[i] < 0.5 * N[i]) ? (double)j[i] : (double)(j[i] - N[i]);
+        const double x = m + q[i];
+        if (!(x > -0.5 * N[i] && x < 0.5 * N[i])) ok = false;
+        f[i] = x;
+    }
+    for (int i = 0; i < 3; ++i) v[i] = f[0] * b[0 * 3 + i] + f[1] * b[1 * 3 + i] + f[2] * b[2 * 3 + i];
+    return ok;
+}
+
+struct Int3 { int v[3]; };
+struct Dbl3 { double v[3]; };
+
+__global__ void hartree_q_kernel(double2* __restrict__ rg, Int3 N, const double* __restrict__ bvec, Dbl3 q,
+                                 double ecut4, double scale) {
+    const long long nr = (long long)N.v[0] * N.v[1] * N.v[2];
+    const double FOURPI = 12.566370614359172954;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nr; e += (long long)gridDim.x * blockDim.x) {
+        double v[3];
+        const bool ok = qg_vector(e, N.v, q.v, bvec, v);
+        const double g2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+        double f = 0.0;
+        if (ok && g2 <= ecut4 && g2 > 1e-12) f = scale * FOURPI / g2;
+        rg[e] = cscale(rg[e], f);
+    }
+}
+
+cudaError_t k_hartree_q(double2* rho_g, const int N[3], const double* bvec, const double qfrac[3], double ecut4,
+                        double scale, cudaStream_t st) {
+    Int3 n = {{N[0], N[1], N[2]}};
+    Dbl3 q = {{qfrac[0], qfrac[1], qfrac[2]}};
+    const long long nr = (long long)N[0] * N[1] * N[2];
+    hartree_q_kernel<<<cdiv(nr, 256), 256, 0, st>>>(rho_g, n, bvec, q, ecut4, scale);
+    return cudaGetLastError();
+}
+
+__global__ void vloc_g_kernel(double2* __restrict__ vg, Int3 N, const double* __restrict__ bvec, double ecut4, int nat,
+                              const double* __restrict__ tau, const double* __restrict__ amp,
+                              const double* __restrict__ width, double omega) {
+    const long long nr = (long long)N.v[0] * N.v[1] * N.v[2];
+    const double PI = 3.14159265358979323846;
+    const double zq[3] = {0.0, 0.0, 0.0};
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nr; e += (long long)gridDim.x * blockDim.x) {
+        double G[3];
+        const bool ok = qg_vector(e, N.v, zq, bvec, G);
+        const double g2 = G[0] * G[0] + G[1] * G[1] + G[2] * G[2];
+        double2 acc = cmk(0.0, 0.0);
+        if (ok && g2 <= ecut4) {
+            for (int a = 0; a < nat; ++a) {
+                const double w = width[a];
+                const double mag = amp[a] * pow(2.0 * PI * w * w, 1.5) / omega * exp(-0.5 * g2 * w * w);
+                const double ph = -(G[0] * tau[3 * a] + G[1] * tau[3 * a + 1] + G[2] * tau[3 * a + 2]);
+                double sp, cp;
+                sincos(ph, &sp, &cp);
+                acc = cadd(acc, cmk(mag * cp, mag * sp));
+            }
+        }
+        vg[e] = acc;
+    }
+}
+
+cudaError_t k_vloc_g(double2* vg, const int N[3], const double* bvec, double ecut4, int nat, const double* tau,
+                     const double* amp, const double* width, double omega, cudaStream_t st) {
+    Int3 n = {{N[0], N[1], N[2]}};
+    const long long nr = (long long)N[0] * N[1] * N[2];
+    vloc_g_kernel<<<cdiv(nr, 256), 256, 0, st>>>(vg, n, bvec, ecut4, nat, tau, amp, width, omega);
+    return cudaGetLastError();
+}
+
+__global__ void real_part_kernel(const double2* __restrict__ z, double* __restrict__ out, int n, double scale) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = z[i].x * scale;
+}
+
+cudaError_t k_real_part(const double2* z, double* out, int n, double scale, cudaStream_t st) {
+    real_part_kernel<<<cdiv(n, 256), 256, 0, st>>>(z, out, n, scale);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
+// LDA: Slater exchange + Perdew-Zunger 1981 correlation (parameters from Table XII of that paper),
+// spin interpolation f(z) = ((1+z)^(4/3) + (1-z)^(4/3) - 2) / (2^(4/3) - 2).
+// eps(rs, z) and its derivatives d/drs, d/dz, d2/drs2, d2/drsdz, d2/dz2; then
+// v_s = eps - rs/3 eps_r + (s - z) eps_z and f_ss' = dv_s/drho_s'.
+// ------------------------------------------------------------------------------------------------
+struct PZ { double g, b1, b2, A, B, C, D; };
+
+__device__ void pz_corr(double rs, const PZ& p, double& e, double& e1, double& e2) {
+    if (rs >= 1.0) {
+        const double sq = sqrt(rs);
+        const double den = 1.0 + p.b1 * sq + p.b2 * rs;
+        const double d1 = 0.5 * p.b1 / sq + p.b2;
+        const double d2 = -0.25 * p.b1 / (rs * sq);
+        e = p.g / den;
+        e1 = -p.g * d1 / (den * den);
+        e2 = p.g * (2.0 * d1 * d1 - den * d2) / (den * den * den);
+    } else {
+        const double lr = log(rs);
+        e = p.A * lr + p.B + p.C * rs * lr + p.D * rs;
+        e1 = p.A / rs + p.C * (lr + 1.0) + p.D;
+        e2 = -p.A / (rs * rs) + p.C / rs;
+    }
+}
+
+struct XcD { double e, er, ez, err, erz, ezz; };
+
+__device__ XcD lda_derivs(double rs, double z) {
+    const double PI = 3.14159265358979323846;
+    const PZ U = {-0.1423, 1.0529, 0.3334, 0.0311, -0.048, 0.0020, -0.0116};
+    const PZ P = {-0.0843, 1.3981, 0.2611, 0.01555, -0.0269, 0.0007, -0.0048};
+    const double X0 = -(3.0 / (4.0 * PI)) * cbrt(9.0 * PI / 4.0);
+    const double up = 1.0 + z, dn = 1.0 - z;
+    const double cu = cbrt(up), cd = cbrt(dn);
+    const double phi = 0.5 * (up * cu + dn * cd);                 // ((1+z)^(4/3) + (1-z)^(4/3)) / 2
+    const double dphi = (2.0 / 3.0) * (cu - cd);
+    const double ddphi = (2.0 / 9.0) * (1.0 / (cu * cu) + 1.0 / (cd * cd));
+    const double fden = 2.0 * cbrt(2.0) - 2.0;
+    const double f = (up * cu + dn * cd - 2.0) / fden;
+    const double df = (4.0 / 3.0) * (cu - cd) / fden;
+    const double ddf = (4.0 / 9.0) * (1.0 / (cu * cu) + 1.0 / (cd * cd)) / fden;
+    double eU, eU1, eU2, eP, eP1, eP2;
+    pz_corr(rs, U, eU, eU1, eU2);
+    pz_corr(rs, P, eP, eP1, eP2);
+    XcD o;
+    const double irs = 1.0 / rs;
+    o.e = X0 * irs * phi + eU + f * (eP - eU);
+    o.er = -X0 * irs * irs * phi + eU1 + f * (eP1 - eU1);
+    o.err = 2.0 * X0 * irs * irs * irs * phi + eU2 + f * (eP2 - eU2);
+    o.ez = X0 * irs * dphi + df * (eP - eU);
+    o.ezz = X0 * irs * ddphi + ddf * (eP - eU);
+    o.erz = -X0 * irs * irs * dphi + df * (eP1 - eU1);
+    return o;
+}
+
+__global__ void xc_kernel(const double* __restrict__ rho, int nspin, int nr, double* __restrict__ vxc,
+                          double* __restrict__ fxc) {
+    const double PI = 3.14159265358979323846;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += gridDim.x * blockDim.x) {
+        const double ru = nspin == 1 ? 0.5 * rho[r] : rho[r];
+        const double rd = nspin == 1 ? 0.5 * rho[r] : rho[nr + r];
+        const double n = ru + rd;
+        if (!(n >= 1e-10)) {
+            for (int s = 0; s < nspin; ++s) vxc[(long long)s * nr + r] = 0.0;
+            if (fxc) for (int s = 0; s < (nspin == 1 ? 1 : 3); ++s) fxc[(long long)s * nr + r] = 0.0;
+            continue;
+        }
+        const double rs = cbrt(3.0 / (4.0 * PI * n));
+        double z = (ru - rd) / n;
+        z = fmin(fmax(z, -1.0 + 1e-14), 1.0 - 1e-14);
+        const XcD d = lda_derivs(rs, z);
+        const double base = d.e - rs / 3.0 * d.er;
+        auto fss = [&](double s1, double s2) {
+            const double dvdrs = (2.0 / 3.0) * d.er - rs / 3.0 * d.err + (s1 - z) * d.erz;
+            const double dvdz = -rs / 3.0 * d.erz + (s1 - z) * d.ezz;
+            return dvdrs * (-rs / (3.0 * n)) + dvdz * (s2 - z) / n;
+        };
+        if (nspin == 1) {
+            vxc[r] = base;  // z = 0
+            if (fxc) fxc[r] = 0.5 * (fss(1.0, 1.0) + fss(1.0, -1.0));
+        } else {
+            vxc[r] = base + (1.0 - z) * d.ez;
+            vxc[(long long)nr + r] = base + (-1.0 - z) * d.ez;
+            if (fxc) {
+                fxc[r] = fss(1.0, 1.0);
+                fxc[(long long)nr + r] = fss(1.0, -1.0);
+                fxc[2LL * nr + r] = fss(-1.0, -1.0);
+            }
+        }
+    }
+}
+
+cudaError_t k_xc(const double* rho, int nspin, int nr, double* vxc, double* fxc, cudaStream_t st) {
+    xc_kernel<<<cdiv(nr, 256), 256, 0, st>>>(rho, nspin, nr, vxc, fxc);
+    return cudaGetLastError();
+}
+
+// dv[s] = vh + sum_t f_st drho[t]
+__global__ void hxc_combine_kernel(const double2* __restrict__ vh, const double2* __restrict__ drho,
+                                   const double* __restrict__ fxc, int nspin, int nr, double2* __restrict__ dv) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += gridDim.x * blockDim.x) {
+        const double2 h = vh[r];
+        if (nspin == 1) {
+            dv[r] = cadd(h, cscale(drho[r], fxc[r]));
+        } else {
+            const double2 a = drho[r], b = drho[(long long)nr + r];
+            const double fuu = fxc[r], fud = fxc[(long long)nr + r], fdd = fxc[2LL * nr + r];
+            dv[r] = cadd(h, cadd(cscale(a, fuu), cscale(b, fud)));
+            dv[(long long)nr + r] = cadd(h, cadd(cscale(a, fud), cscale(b, fdd)));
+        }
+    }
+}
+
+cudaError_t k_hxc_combine(const double2* vh, const double2* drho, const double* fxc, int nspin, int nr, double2* dv,
+                          cudaStream_t st) {
+    hxc_combine_kernel<<<cdiv(nr, 256), 256, 0, st>>>(vh, drho, fxc, nspin, nr, dv);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
+// response occupations: M[s][m1][m2] = (1/N_k) sum_k sum_v B[(s,k,v)][m1] conj(Aphi[(s,k,v)][m2])
+// B: projections <phi_m1,k+q|Delta u_v>, Aphi: <phi_m2,k|u_v>, both with row stride 128
+// ------------------------------------------------------------------------------------------------
+__global__ void occ_response_kernel(const double2* __restrict__ B, const double2* __restrict__ Aphi, int nk, int nocc,
+                                    int nhub, double2* __restrict__ M) {
+    __shared__ double sh[32];
+    const int m1 = blockIdx.x, m2 = blockIdx.y, s = blockIdx.z;
+    const int nit = nk * nocc;
+    double sr = 0.0, si = 0.0;
+    for (int i = threadIdx.x; i < nit; i += blockDim.x) {
+        const long long item = (long long)s * nit + i;
+        const double2 b = B[item * kPStride + m1];
+        const double2 a = Aphi[item * kPStride + m2];
+        sr += b.x * a.x + b.y * a.y;
+        si += b.y * a.x - b.x * a.y;
+    }
+    sr = block_sum(sr, sh);
+    si = block_sum(si, sh);
+    if (threadIdx.x == 0) M[((long long)s * nhub + m1) * nhub + m2] = cmk(sr / nk, si / nk);
+}
+
+cudaError_t k_occ_response(const double2* B, const double2* Aphi, int ngroups, int nocc, int nhub, int nk, int nspin,
+                           double2* M, cudaStream_t st) {
+    (void)ngroups;
+    dim3 g(nhub, nhub, nspin);
+    occ_response_kernel<<<g, 128, 0, st>>>(B, Aphi, nk, nocc, nhub, M);
+    return cudaGetLastError();
+}
+
+// dn[a][s][m1][m2] = M[s][o+m1][o+m2] + M[s][o+m2][o+m1]   (Eq. occ_matrix_response_lp_2, both terms)
+__global__ void dn_blocks_kernel(const double2* __restrict__ M, int nspin, int nhub, const int* __restrict__ off,
+                                 const int* __restrict__ mdim, int mmax, double2* __restrict__ dn) {
+    const int a = blockIdx.x;
+    const int s = blockIdx.y;
+    const int o = off[a], md = mdim[a];
+    for (int e = threadIdx.x; e < mmax * mmax; e += blockDim.x) {
+        const int m1 = e / mmax, m2 = e % mmax;
+        double2 v = cmk(0.0, 0.0);
+        if (m1 < md && m2 < md) {
+            v = cadd(M[((long long)s * nhub + o + m1) * nhub + o + m2], M[((long long)s * nhub + o + m2) * nhub + o + m1]);
+        }
+        dn[(((long long)a * nspin + s) * mmax + m1) * mmax + m2] = v;
+    }
+}
+
+// tr[a] = f sum_s sum_m dn[a][s][m][m]  (spin-summed trace; f = 2 for nspin = 1)
+__global__ void dn_traces_kernel(const double2* __restrict__ dn, int nh, int nspin, int mmax, double f,
+                                 double2* __restrict__ tr) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= nh) return;
+    double2 t = cmk(0.0, 0.0);
+    for (int s = 0; s < nspin; ++s)
+        for (int m = 0; m < mmax; ++m) t = cadd(t, dn[(((long long)a * nspin + s) * mmax + m) * mmax + m]);
+    tr[a] = cscale(t, f);
+}
+
+cudaError_t k_dn_traces(const double2* dn, int nh, int nspin, int mmax, double f, double2* tr, cudaStream_t st) {
+    dn_traces_kernel<<<cdiv(nh, 64), 64, 0, st>>>(dn, nh, nspin, mmax, f, tr);
+    return cudaGetLastError();
+}
+
+cudaError_t k_dn_blocks(const double2* M, int nspin, int nhub, int nhub_atoms, const int* off, const int* mdim, int mmax,
+                        double2* dn, cudaStream_t st) {
+    dim3 g(nhub_atoms, nspin);
+    dn_blocks_kernel<<<g, 64, 0, st>>>(M, nspin, nhub, off, mdim, mmax, dn);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
+// long-vector algebra for the mixing (deterministic two-stage reductions)
+// ------------------------------------------------------------------------------------------------
+constexpr int kRedBlocks = 256;
+
+__global__ void vec_dot_kernel(const double2* __restrict__ a, const double2* __restrict__ b, long long n,
+                               double* __restrict__ partial) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double2 x = a[i], y = b[i];
+        s += x.x * y.x + x.y * y.y;
+    }
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void sum_reduce_kernel(const double* __restrict__ partial, int nparts, double* __restrict__ out) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += partial[i];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) *out = s;
+}
+
+cudaError_t k_vec_dot(const double2* a, const double2* b, long long n, double* out, double* partial, cudaStream_t st) {
+    vec_dot_kernel<<<kRedBlocks, 256, 0, st>>>(a, b, n, partial);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    sum_reduce_kernel<<<1, 256, 0, st>>>(partial, kRedBlocks, out);
+    return cudaGetLastError();
+}
+
+cudaError_t k_sum_reduce(const double* partial, int nparts, double* out, cudaStream_t st) {
+    sum_reduce_kernel<<<1, 256, 0, st>>>(partial, nparts, out);
+    return cudaGetLastError();
+}
+
+__global__ void vec_axpy_kernel(double2* __restrict__ y, const double2* __restrict__ x, double a, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = cmk(y[i].x + a * x[i].x, y[i].y + a * x[i].y);
+}
+
+cudaError_t k_vec_axpy(double2* y, const double2* x, double a, long long n, cudaStream_t st) {
+    vec_axpy_kernel<<<std::min(cdiv(n, 256), 4096), 256, 0, st>>>(y, x, a, n);
+    return cudaGetLastError();
+}
+
+__global__ void vec_sub_kernel(double2* __restrict__ out, const double2* __restrict__ a, const double2* __restrict__ b,
+                               long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = csub(a[i], b[i]);
+}
+
+cudaError_t k_vec_sub(double2* out, const double2* a, const double2* b, long long n, cudaStream_t st) {
+    vec_sub_kernel<<<std::min(cdiv(n, 256), 4096), 256, 0, st>>>(out, a, b, n);
+    return cudaGetLastError();
+}
+
+__global__ void vec_scale_copy_kernel(double2* __restrict__ out, const double2* __restrict__ a, double s, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = cscale(a[i], s);
+}
+
+cudaError_t k_vec_scale_copy(double2* out, const double2* a, double s, long long n, cudaStream_t st) {
+    vec_scale_copy_kernel<<<std::min(cdiv(n, 256), 4096), 256, 0, st>>>(out, a, s, n);
+    return cudaGetLastError();
+}
+
+// Johnson's modified Broyden coefficients: dots = [m x m overlaps <dF_i|dF_j> | m projections
+// <dF_k|F>] (row stride ld); a = w0^2 I + overlaps; gamma = c^T a^-1 (Gauss-Jordan, m <= 8).
+__global__ void broyden_coef_kernel(const double* __restrict__ dots, int m, int ld, double w0, double* __restrict__ gamma) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double a[8][9];
+    for (int i = 0; i < m; ++i) {
+        for (int j = 0; j < m; ++j) a[i][j] = dots[i * ld + j] + (i == j ? w0 * w0 : 0.0);
+        a[i][m] = dots[i * ld + m];  // c_i ; a symmetric, so gamma = a^-1 c
+    }
+    for (int col = 0; col < m; ++col) {
+        int piv = col;
+        for (int i = col + 1; i < m; ++i)
+            if (fabs(a[i][col]) > fabs(a[piv][col])) piv = i;
+        if (piv != col)
+            for (int j = 0; j <= m; ++j) {
+                const double t = a[col][j];
+                a[col][j] = a[piv][j];
+                a[piv][j] = t;
+            }
+        const double d = a[col][col];
+        for (int j = col; j <= m; ++j) a[col][j] /= d;
+        for (int i = 0; i < m; ++i) {
+            if (i == col) continue;
+            const double f = a[i][col];
+            for (int j = col; j <= m; ++j) a[i][j] -= f * a[col][j];
+        }
+    }
+    for (int i = 0; i < m; ++i) gamma[i] = a[i][m];
+}
+
+cudaError_t k_broyden_coef(const double* dots, int m, int ld, double w0, double* gamma, cudaStream_t st) {
+    if (m <= 0) return cudaSuccess;
+    if (m > 8) return cudaErrorInvalidValue;
+    broyden_coef_kernel<<<1, 32, 0, st>>>(dots, m, ld, w0, gamma);
+    return cudaGetLastError();
+}
+
+// x += alpha f - sum_l gamma_l (dx_l + alpha df_l)
+__global__ void broyden_apply_kernel(double2* __restrict__ x, const double2* __restrict__ f,
+                                     const double2* const* __restrict__ dx, const double2* const* __restrict__ df,
+                                     const double* __restrict__ gamma, int m, double alpha, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double2 v = cadd(x[i], cscale(f[i], alpha));
+        for (int l = 0; l < m; ++l) {
+            const double2 t = cadd(dx[l][i], cscale(df[l][i], alpha));
+            v = csub(v, cscale(t, gamma[l]));
+        }
+        x[i] = v;
+    }
+}
+
+cudaError_t k_broyden_apply(double2* x, const double2* f, const double2* const* dx, const double2* const* df,
+                            const double* gamma, int m, double alpha, long long n, cudaStream_t st) {
+    broyden_apply_kernel<<<std::min(cdiv(n, 256), 4096), 256, 0, st>>>(x, f, dx, df, gamma, m, alpha, n);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
+// chi assembly (Eq. occ_matrix_response_lp_1) and FP64 inversion
+//   chi[(l,s)][(l',s')] = (1/N_q) sum_q exp(2 pi i q.(R_l - R_l')) col[q][s'][s]
+// cols: [nq][nh (perturbed s')][nh (responding s)] complex
+// ------------------------------------------------------------------------------------------------
+__global__ void chi_assemble_kernel(const double2* __restrict__ cols, int nq, int nh, const double* __restrict__ qfrac,
+                                    const double* __restrict__ Rl, int ncell, double* __restrict__ chi_re,
+                                    double* __restrict__ chi_im) {
+    const int n = ncell * nh;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n * n) return;
+    const int I = e / n, J = e % n;
+    const int l = I / nh, s = I % nh, lp = J / nh, sp = J % nh;
+    const double PI2 = 6.28318530717958647692;
+    double re = 0.0, im = 0.0;
+    for (int iq = 0; iq < nq; ++iq) {
+        const double d = qfrac[3 * iq] * (Rl[3 * l] - Rl[3 * lp]) + qfrac[3 * iq + 1] * (Rl[3 * l + 1] - Rl[3 * lp + 1]) +
+                         qfrac[3 * iq + 2] * (Rl[3 * l + 2] - Rl[3 * lp + 2]);
+        double sp_, cp;
+        sincos(PI2 * d, &sp_, &cp);
+        const double2 c = cols[((long long)iq * nh + sp) * nh + s];
+        re += cp * c.x - sp_ * c.y;
+        im += cp * c.y + sp_ * c.x;
+    }
+    chi_re[e] = re / nq;
+    chi_im[e] = im / nq;
+}
+
+cudaError_t k_chi_assemble(const double2* cols, int nq, int nh, const double* qfrac, const double* Rl, int ncell,
+                           double* chi_re, double* chi_im, cudaStream_t st) {
+    const int n = ncell * nh;
+    chi_assemble_kernel<<<cdiv((long long)n * n, 128), 128, 0, st>>>(cols, nq, nh, qfrac, Rl, ncell, chi_re, chi_im);
+    return cudaGetLastError();
+}
+
+// in-place Gauss-Jordan inverse with partial pivoting, one CTA (n <= 512); work: n doubles
+__global__ void invert_kernel(double* __restrict__ a, double* __restrict__ work, int n, int* __restrict__ singular) {
+    __shared__ int piv_s;
+    __shared__ double pv_s;
+    extern __shared__ int perm[];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) perm[i] = i;
+    if (threadIdx.x == 0) *singular = 0;
+    __syncthreads();
+    double amax = 0.0;
+    for (int col = 0; col < n; ++col) {
+        if (threadIdx.x == 0) {
+            int p = col;
+            double best = fabs(a[(long long)col * n + col]);
+            for (int i = col + 1; i < n; ++i) {
+                const double v = fabs(a[(long long)i * n + col]);
+                if (v > best) { best = v; p = i; }
+            }
+            piv_s = p;
+            if (col == 0) amax = best;
+            if (best <= 1e-300) *singular = 1;
+        }
+        __syncthreads();
+        const int p = piv_s;
+        if (p != col) {
+            for (int j = threadIdx.x; j < n; j += blockDim.x) {
+                const double t = a[(long long)col * n + j];
+                a[(long long)col * n + j] = a[(long long)p * n + j];
+                a[(long long)p * n + j] = t;
+            }
+            if (threadIdx.x == 0) {
+                const int t = perm[col];
+                perm[col] = perm[p];
+                perm[p] = t;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) pv_s = a[(long long)col * n + col];
+        __syncthreads();
+        const double pv = pv_s;
+        // scale the pivot row (the pivot element becomes 1/pv)
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            if (j == col) continue;
+            a[(long long)col * n + j] /= pv;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) a[(long long)col * n + col] = 1.0 / pv;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) work[i] = (i == col) ? 0.0 : a[(long long)i * n + col];
+        __syncthreads();
+        // eliminate
+        for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) {
+            const int i = (int)(e / n), j = (int)(e % n);
+            if (i == col) continue;
+            const double f = work[i];
+            if (j == col) a[e] = -f * a[(long long)col * n + col];
+            else a[e] -= f * a[(long long)col * n + j];
+        }
+        __syncthreads();
+    }
+    (void)amax;
+    // undo the row permutation: the sweep inverted P A, and A^-1 = (P A)^-1 P
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < n; ++i) {
+            for (int j = 0; j < n; ++j) work[j] = a[(long long)i * n + j];
+            for (int j = 0; j < n; ++j) a[(long long)i * n + perm[j]] = work[j];
+        }
+    }
+}
+
+cudaError_t k_invert(double* a, double* work, int n, int* singular, cudaStream_t st) {
+    invert_kernel<<<1, 256, sizeof(int) * n, st>>>(a, work, n, singular);
+    return cudaGetLastError();
+}
+
+__global__ void hub_matrix_kernel(const double* __restrict__ inv0, const double* __restrict__ inv, int n, double scale,
+                                  double* __restrict__ hub) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n * n) hub[e] = (inv0[e] - inv[e]) * scale;
+}
+
+cudaError_t k_hub_matrix(const double* inv0, const double* inv, int n, double scale, double* hub, cudaStream_t st) {
+    hub_matrix_kernel<<<cdiv((long long)n * n, 128), 128, 0, st>>>(inv0, inv, n, scale, hub);
+    return cudaGetLastError();
+}
+
+__global__ void add_real_kernel(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ out, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = a[i] + b[i];
+}
+
+cudaError_t k_add_real(const double* a, const double* b, double* out, int n, cudaStream_t st) {
+    add_real_kernel<<<cdiv(n, 256), 256, 0, st>>>(a, b, out, n);
+    return cudaGetLastError();
+}
+
+}  // namespace hp
