@@ -18,7 +18,7 @@
 
 using namespace hp;
 
-namespace {
+namespace hp {
 
 constexpr double kHaToEv = 27.211386245988;
 constexpr int kMmax = 5;
@@ -36,38 +36,12 @@ hp_status cuda_fail(hp_ctx* c, cudaError_t e, const char* what) {
     return e == cudaErrorMemoryAllocation ? HP_ENOMEM : HP_ECUDA;
 }
 
-#define CK(call)                                                   \
-    do {                                                           \
-        cudaError_t e_ = (call);                                   \
-        if (e_ != cudaSuccess) return cuda_fail(c, e_, #call);     \
-    } while (0)
-
-template <class T>
-cudaError_t dalloc(hp_ctx* c, T** p, size_t n) {
-    *p = nullptr;
-    if (n == 0) n = 1;
-    cudaError_t e = cudaMalloc((void**)p, sizeof(T) * n);
-    if (e == cudaSuccess) c->owned.push_back((void*)*p);
-    return e;
-}
 
 void dfree(hp_ctx* c, void* p) {
     if (!p) return;
     auto it = std::find(c->owned.begin(), c->owned.end(), p);
     if (it != c->owned.end()) c->owned.erase(it);
     cudaFree(p);
-}
-
-template <class T>
-cudaError_t h2d(T* d, const T* h, size_t n, cudaStream_t st) {
-    return cudaMemcpyAsync(d, h, sizeof(T) * n, cudaMemcpyHostToDevice, st);
-}
-
-template <class T>
-cudaError_t d2h(T* h, const T* d, size_t n, cudaStream_t st) {
-    cudaError_t e = cudaMemcpyAsync(h, d, sizeof(T) * n, cudaMemcpyDeviceToHost, st);
-    if (e != cudaSuccess) return e;
-    return cudaStreamSynchronize(st);
 }
 
 int good_fft_size(int n) {
@@ -283,8 +257,10 @@ hp_status apply_nonlocal(hp_ctx* c, const SphereSet& S, const BandList& L, const
     return HP_OK;
 }
 
-hp_status resp_alloc(hp_ctx* c);
+}  // namespace hp
 
+namespace {
+hp_status resp_alloc(hp_ctx* c);
 }  // namespace
 
 // ================================================================================================
@@ -577,7 +553,7 @@ static hp_status gs_alloc(hp_ctx* c, int nspin, int nbnd) {
     return HP_OK;
 }
 
-static void invalidate_response(hp_ctx* c) {
+void hp::invalidate_response(hp_ctx* c) {
     c->resp_ready = false;
     c->qc.iq = -1;
     c->cols.clear();

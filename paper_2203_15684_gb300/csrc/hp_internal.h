@@ -189,6 +189,22 @@ struct QCache {                    // per-q data: k+q spheres, projectors and oc
     int* d_miller = nullptr;
 };
 
+// engine.cu helpers shared with the ground-state driver
+hp_status fail(hp_ctx* c, hp_status s, const std::string& msg);
+hp_status cuda_fail(hp_ctx* c, cudaError_t e, const char* what);
+void dfree(hp_ctx* c, void* p);
+hp_status upload_list(hp_ctx* c, BandList& L);
+void list_clear(BandList& L);
+void list_add(BandList& L, int row, int k, int spin, double shift);
+hp_status ensure_grid(hp_ctx* c, int want);
+int band_batch(const hp_ctx* c, int nb);
+hp_status apply_local(hp_ctx* c, const SphereSet& S, const BandList& L, const double2* X, double2* Y,
+                      const double* veff);
+hp_status project(hp_ctx* c, const SphereSet& S, const BandList& L, const ProjMat& A, const double2* X, double2* P);
+hp_status apply_nonlocal(hp_ctx* c, const SphereSet& S, const BandList& L, const double2* X, double2* Y, double2* P,
+                         const int* kmap);
+void invalidate_response(hp_ctx* c);
+
 }  // namespace hp
 
 struct hp_ctx {
@@ -263,3 +279,34 @@ struct hp_ctx {
     hp::BandList L1, L2, L3;           // reusable band lists
     std::vector<void*> owned;          // device allocations freed in hp_destroy
 };
+
+namespace hp {
+
+template <class T>
+cudaError_t dalloc(hp_ctx* c, T** p, size_t n) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc((void**)p, sizeof(T) * n);
+    if (e == cudaSuccess) c->owned.push_back((void*)*p);
+    return e;
+}
+
+template <class T>
+cudaError_t h2d(T* d, const T* h, size_t n, cudaStream_t st) {
+    return cudaMemcpyAsync(d, h, sizeof(T) * n, cudaMemcpyHostToDevice, st);
+}
+
+template <class T>
+cudaError_t d2h(T* h, const T* d, size_t n, cudaStream_t st) {
+    cudaError_t e = cudaMemcpyAsync(h, d, sizeof(T) * n, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return e;
+    return cudaStreamSynchronize(st);
+}
+
+}  // namespace hp
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return hp::cuda_fail(c, e_, #call); \
+    } while (0)

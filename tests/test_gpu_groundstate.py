@@ -1,0 +1,56 @@
+"""The library's own ground state (GPU SCF) and the full config-0 path (ground state -> response
+-> chi -> U) against the oracle.  Each side converges its own SCF; the comparison bars allow for
+that (eigenvalues 1e-9 Ha, densities 1e-8 relative, chi and U 1e-8 relative)."""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import groundstate as G
+from oracle.model import Model
+
+pytestmark = pytest.mark.gpu
+
+P = pytest.importorskip("paper_2203_15684_gb300")
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _gs_compare(w, moments=None):
+    m = Model(w)
+    gs = G.scf(m, tol=1e-12)
+    ctx = P.Context.from_workload(w, gs_tol=1e-12)
+    info = ctx.ground_state(w["nelec"], w["nspin"], moments)
+    eps, rho, vhxc = ctx.get_ground_state()
+    assert np.abs(eps - gs.eps[:, :, : m.nocc]).max() < 1e-9
+    assert np.abs(rho - gs.rho).max() < 1e-8 * np.abs(gs.rho).max()
+    assert abs(info["gap"] - gs.gap()) < 1e-9
+    return ctx, m, gs, info
+
+
+def test_ground_state_tiny_low():
+    _gs_compare(W.tiny_lowcut(ecut=10.0, grid=(12, 12, 12)))
+
+
+def test_ground_state_spin_polarised():
+    w = W.medium_small(ecut=6.0, grid=(16, 16, 16), kmesh=(2, 1, 1), qmesh=(1, 1, 1))
+    _gs_compare(w, moments=w["moments"])
+
+
+def test_config0_end_to_end_against_golden():
+    """Two-atom cube at full size: GPU ground state, response, chi and U vs the stored oracle run."""
+    ref = json.load(open(os.path.join(HERE, "golden", "tiny_config0.json")))
+    w = W.tiny()
+    ctx = P.Context.from_workload(w, gs_tol=1e-12, cg_tol=1e-12, scf_tol=1e-11, conv_thr_chi=1e-11)
+    info = ctx.ground_state(w["nelec"], w["nspin"])
+    assert abs(info["gap"] - ref["gap"]) < 1e-9
+    eps, _, _ = ctx.get_ground_state()
+    assert np.abs(eps[0, 0] - np.array(ref["eps_gamma"][:5])).max() < 1e-9
+    atoms, _ = ctx.hubbard_atoms()
+    ctx.response(0, int(atoms[0]))
+    chi0, chi, hub = ctx.hubbard()
+    assert abs(chi0[0, 0] - ref["chi0"][0][0]) < 1e-8 * abs(ref["chi0"][0][0])
+    assert abs(chi[0, 0] - ref["chi"][0][0]) < 1e-8 * abs(ref["chi"][0][0])
+    assert abs(hub[0, 0] - ref["U"]) < 1e-8 * abs(ref["U"])
