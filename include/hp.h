@@ -182,6 +182,12 @@ void hp_destroy(hp_ctx* ctx);
  * in/out: nlines x n complex; sign -1 forward exp(-2 pi i jk/n), +1 backward (unnormalised). */
 hp_status hp_selftest_fft_host(int n, int nlines, int sign, const double* in, double* out);
 
+/* Device self-test of the batched Hermitian eigensolver used by the ground state (one CTA per
+ * matrix, cyclic Jacobi).  A: nbatch complex n x n Hermitian matrices, row-major, interleaved;
+ * w: nbatch x n eigenvalues ascending; V: nbatch n x n, eigenvectors in the columns.  n <= 512.
+ * Allocates its own device buffers.  Errors: HP_EINVAL, HP_ECUDA. */
+hp_status hp_selftest_eigh(int n, int nbatch, const double* A, double* w, double* V);
+
 #ifdef __cplusplus
 }
 #endif

@@ -62,7 +62,7 @@ _lib = None
 
 SYMBOLS = ["hp_default_options", "hp_setup", "hp_query_sizes", "hp_sphere", "hp_hubbard_atoms", "hp_ground_state",
            "hp_set_ground_state", "hp_get_ground_state", "hp_apply_h", "hp_response", "hp_hubbard", "hp_last_error",
-           "hp_destroy", "hp_selftest_fft_host"]
+           "hp_destroy", "hp_selftest_fft_host", "hp_selftest_eigh"]
 
 
 def lib():
@@ -92,6 +92,7 @@ def lib():
     L.hp_destroy.argtypes = [V]
     L.hp_destroy.restype = None
     L.hp_selftest_fft_host.argtypes = [I, I, I, P(D), P(D)]
+    L.hp_selftest_eigh.argtypes = [I, I, P(D), P(D), P(D)]
     for n in SYMBOLS:
         f = getattr(L, n)
         if n not in ("hp_default_options", "hp_last_error", "hp_destroy"):
@@ -129,6 +130,18 @@ def selftest_fft_host(x, sign):
     if st != HP_OK:
         raise HPError(st, "hp_selftest_fft_host")
     return out
+
+
+def selftest_eigh(A):
+    """Batched Hermitian eigensolver of the ground state on the GPU: A (nbatch, n, n) complex."""
+    A = np.ascontiguousarray(A, dtype=np.complex128)
+    nb, n, _ = A.shape
+    w = np.zeros((nb, n))
+    V = np.zeros_like(A)
+    st = lib().hp_selftest_eigh(n, nb, _dptr(A.view(np.float64)), _dptr(w), _dptr(V.view(np.float64)))
+    if st != HP_OK:
+        raise HPError(st, "hp_selftest_eigh")
+    return w, V
 
 
 class Context:

@@ -10,6 +10,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "hp_internal.h"
@@ -24,6 +26,7 @@ constexpr int kPS = 128;  // row stride of projection buffers
 // eigenvectors as the columns of V.  One CTA per matrix; A and V in global memory.
 // A plane rotation on (p, q) with a_pq = |a_pq| e:  U = [[c, s], [-s conj(e), c conj(e)]],
 // t = tan(theta) = sign(tau) / (|tau| + sqrt(1 + tau^2)), tau = (a_qq - a_pp) / (2 |a_pq|).
+// Sweeps stop once a whole sweep skips every pair (|a_pq| <= 1e-16 (|a_pp| + |a_qq|)).
 // ------------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) jacobi_kernel(double2* __restrict__ Ab, double2* __restrict__ Vb,
                                                      double* __restrict__ wb, double2* __restrict__ tmpb, int n,
@@ -37,8 +40,7 @@ __global__ void __launch_bounds__(256) jacobi_kernel(double2* __restrict__ Ab, d
     double* ei = er + np;        // [np] Im e
     int* pp = (int*)(ei + np);   // [np]
     int* qq = pp + np;           // [np]
-    __shared__ double red[32];
-    __shared__ int stop_flag;
+    __shared__ int rot_count;
     double2* A = Ab + (long long)blockIdx.x * n * n;
     double2* V = Vb + (long long)blockIdx.x * n * n;
     double* w = wb + (long long)blockIdx.x * n;
@@ -46,38 +48,11 @@ __global__ void __launch_bounds__(256) jacobi_kernel(double2* __restrict__ Ab, d
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) V[e] = cmk((e / n) == (e % n) ? 1.0 : 0.0, 0.0);
     __syncthreads();
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-        // convergence: off-diagonal vs diagonal magnitude
-        double off = 0.0, dia = 0.0;
-        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-            const double2 a = A[e];
-            const double q = a.x * a.x + a.y * a.y;
-            if ((e / n) == (e % n)) dia += q;
-            else off += q;
-        }
-        // block sums
-        for (int o = 16; o > 0; o >>= 1) {
-            off += __shfl_down_sync(0xffffffffu, off, o);
-            dia += __shfl_down_sync(0xffffffffu, dia, o);
-        }
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = off;
+        // a sweep that finds every |a_pq| below 1e-16 (|a_pp| + |a_qq|) ends the iteration; pairs
+        // below that threshold are skipped, so the rotation phase a_pq / |a_pq| is never formed
+        // from underflowing (denormal) entries, which would make the rotation non-unitary
+        if (threadIdx.x == 0) rot_count = 0;
         __syncthreads();
-        if (threadIdx.x == 0) {
-            double so = 0.0;
-            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) so += red[i];
-            red[0] = so;
-        }
-        __syncthreads();
-        const double offs = red[0];
-        __syncthreads();
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dia;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double sd = 0.0;
-            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) sd += red[i];
-            stop_flag = (offs <= 1e-30 * sd) ? 1 : 0;
-        }
-        __syncthreads();
-        if (stop_flag) break;
         for (int r = 0; r < m - 1; ++r) {
             // round-robin pairs: position 0 fixed, others rotate
             for (int i = threadIdx.x; i < np; i += blockDim.x) {
@@ -89,9 +64,10 @@ __global__ void __launch_bounds__(256) jacobi_kernel(double2* __restrict__ Ab, d
                 double c = 1.0, s = 0.0, ere = 1.0, eim = 0.0;
                 if (q < n) {
                     const double2 apq = A[(long long)p * n + q];
-                    const double mag = sqrt(apq.x * apq.x + apq.y * apq.y);
-                    if (mag > 1e-300) {
-                        const double app = A[(long long)p * n + p].x, aqq = A[(long long)q * n + q].x;
+                    const double mag = hypot(apq.x, apq.y);
+                    const double app = A[(long long)p * n + p].x, aqq = A[(long long)q * n + q].x;
+                    if (mag > 1e-16 * (fabs(app) + fabs(aqq)) + 1e-300) {
+                        atomicAdd(&rot_count, 1);
                         const double tau = (aqq - app) / (2.0 * mag);
                         const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
                         c = 1.0 / sqrt(1.0 + t * t);
@@ -141,6 +117,8 @@ __global__ void __launch_bounds__(256) jacobi_kernel(double2* __restrict__ Ab, d
             }
             __syncthreads();
         }
+        if (rot_count == 0) break;
+        __syncthreads();
     }
     // eigenvalues, ascending order, columns of V permuted accordingly (copy through tmp)
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) tmp[e] = V[e];
@@ -322,6 +300,21 @@ hp_status rayleigh_ritz(hp_ctx* c, BandList& L, BandList& L0, GsWork& W, double2
     const size_t jsh = (size_t)(n / 2 + 1) * (4 * sizeof(double) + 2 * sizeof(int));
     jacobi_kernel<<<nseg, 256, jsh, c->st>>>(W.Mb, W.Vb, W.w, W.Tmp, n, 40);
     CK(cudaGetLastError());
+    if (getenv("HP_VERBOSE")) {
+        std::vector<double> ws((size_t)nseg * n);
+        CK(d2h(ws.data(), W.w, ws.size(), c->st));
+        double worst = 1.0;
+        int wg = 0;
+        for (int g = 0; g < nseg; ++g) {
+            double lo = INFINITY, hi = 0;
+            for (int j = 0; j < n; ++j) {
+                lo = std::min(lo, ws[(size_t)g * n + j]);
+                hi = std::max(hi, ws[(size_t)g * n + j]);
+            }
+            if (lo / hi < worst) { worst = lo / hi; wg = g; }
+        }
+        fprintf(stderr, "  overlap conditioning: worst min/max eigenvalue %.3e (segment %d)\n", worst, wg);
+    }
     CK(cudaMemsetAsync(W.bad, 0, sizeof(int), c->st));
     seg_transform_kernel<<<nseg, 256, 0, c->st>>>(W.Vb, W.w, 1, L.d_seg_start, n, W.Pb, W.bad);
     CK(cudaGetLastError());
@@ -398,7 +391,7 @@ extern "C" hp_status hp_ground_state(hp_ctx* c, double nelec, int nspin, const i
     const int nocc = (int)std::lround(nelec / 2.0);
     if (nocc < 1 || std::fabs(nelec - 2.0 * nocc) > 1e-9)
         return fail(c, HP_EINVAL, "hp_ground_state: nelec must be an even positive number");
-    const int nextra = std::max(4, nocc / 5);
+    const int nextra = std::max(6, nocc / 4);
     const int nbnd = std::min(kPS, nocc + nextra);
     if (nbnd <= nocc) return fail(c, HP_EINVAL, "hp_ground_state: too many bands (at most 127 occupied)");
     for (int k = 0; k < c->nk; ++k)
@@ -538,6 +531,7 @@ extern "C" hp_status hp_ground_state(hp_ctx* c, double nelec, int nspin, const i
     const int nseg = nspin * nk;
     std::vector<double> aseg(nseg, 0.0);
     const int deg = 10;
+    const bool verbose = getenv("HP_VERBOSE") != nullptr;
     for (it = 1; it <= c->opt.gs_maxiter; ++it) {
         veff_kernel<<<cdiv_(nr, 256), 256, 0, c->st>>>(c->d_vloc, vin, nspin, nr, c->d_veff, c->d_vhxc);
         CK(cudaGetLastError());
@@ -547,7 +541,7 @@ extern "C" hp_status hp_ground_state(hp_ctx* c, double nelec, int nspin, const i
         CK(d2h(&vmax, c->d_small + 100, 1, c->st));
         const double b = 0.5 * c->ecut + vmax + 2.0 * dplus + 1.0;
         // subspace iteration: a few passes on the first SCF steps, one afterwards
-        const int passes = it == 1 ? 4 : (it <= 3 ? 2 : 1);
+        const int passes = it == 1 ? 4 : (it <= 5 ? 2 : 1);
         for (int pass = 0; pass < passes; ++pass) {
             if (!ritz.empty()) {
                 for (int g = 0; g < nseg; ++g) aseg[g] = ritz[(size_t)g * nbnd + nbnd - 1];
@@ -580,6 +574,9 @@ extern "C" hp_status hp_ground_state(hp_ctx* c, double nelec, int nspin, const i
         CK(d2h(&ff, c->d_small, 1, c->st));
         if (!std::isfinite(ff)) return fail(c, HP_ENUMERIC, "hp_ground_state: non-finite residual");
         res = std::sqrt(ff / (double)ndv);
+        if (verbose)
+            fprintf(stderr, "hp_ground_state: it %d res %.3e vmax %.3f b %.3f top %.4f occ %.6f\n", it, res, vmax, b,
+                    aseg.empty() ? 0.0 : *std::max_element(ritz.begin(), ritz.end()), ritz[nocc - 1]);
         if (res < c->opt.gs_tol) {
             converged = true;
             break;
@@ -648,9 +645,20 @@ extern "C" hp_status hp_ground_state(hp_ctx* c, double nelec, int nspin, const i
         std::vector<double> nr2(rows);
         CK(d2h(nr2.data(), W.nrm, rows, c->st));
         rmax = 0.0;
+        int ws = 0, wk = 0, wv = 0;
         for (int s = 0; s < nspin; ++s)
             for (int k = 0; k < nk; ++k)
-                for (int v = 0; v < nocc + 1; ++v) rmax = std::max(rmax, std::sqrt(nr2[(size_t)(s * nk + k) * nbnd + v]));
+                for (int v = 0; v < nocc; ++v) {
+                    const double r = std::sqrt(nr2[(size_t)(s * nk + k) * nbnd + v]);
+                    if (r > rmax) { rmax = r; ws = s; wk = k; wv = v; }
+                }
+        if (verbose) {
+            fprintf(stderr, "  worst s %d k %d v %d ritz:", ws, wk, wv);
+            for (int v = 0; v < nbnd; ++v) fprintf(stderr, " %.4f(%.0e)", ritz[(size_t)(ws * nk + wk) * nbnd + v],
+                                                   std::sqrt(nr2[(size_t)(ws * nk + wk) * nbnd + v]));
+            fprintf(stderr, "\n");
+        }
+        if (verbose) fprintf(stderr, "hp_ground_state: polish %d max occupied residual %.3e\n", pass, rmax);
         if (rmax < 1e-11) break;
     }
     // the density of the final states (consistent with the eigenpairs kept)
@@ -704,4 +712,29 @@ extern "C" hp_status hp_ground_state(hp_ctx* c, double nelec, int nspin, const i
     if (!converged || rmax > 1e-9) return fail(c, HP_ENOTCONV, "hp_ground_state: SCF or eigenvector residual cap reached");
     if (!(gap > 1e-4)) return fail(c, HP_ENOGAP, "hp_ground_state: no gap at the fixed band count");
     return HP_OK;
+}
+
+extern "C" hp_status hp_selftest_eigh(int n, int nbatch, const double* A, double* w, double* V) {
+    if (n < 1 || n > 512 || nbatch < 1 || !A || !w || !V) return HP_EINVAL;
+    const size_t nn = (size_t)n * n * nbatch;
+    double2 *dA = nullptr, *dV = nullptr, *dT = nullptr;
+    double* dw = nullptr;
+    hp_status st = HP_OK;
+    if (cudaMalloc(&dA, sizeof(double2) * nn) != cudaSuccess || cudaMalloc(&dV, sizeof(double2) * nn) != cudaSuccess ||
+        cudaMalloc(&dT, sizeof(double2) * nn) != cudaSuccess || cudaMalloc(&dw, sizeof(double) * n * nbatch) != cudaSuccess)
+        st = HP_ECUDA;
+    if (st == HP_OK && cudaMemcpy(dA, A, sizeof(double2) * nn, cudaMemcpyHostToDevice) != cudaSuccess) st = HP_ECUDA;
+    if (st == HP_OK) {
+        const size_t jsh = (size_t)(n / 2 + 1) * (4 * sizeof(double) + 2 * sizeof(int));
+        hp::jacobi_kernel<<<nbatch, 256, jsh>>>(dA, dV, dw, dT, n, 40);
+        if (cudaDeviceSynchronize() != cudaSuccess) st = HP_ECUDA;
+    }
+    if (st == HP_OK && (cudaMemcpy(V, dV, sizeof(double2) * nn, cudaMemcpyDeviceToHost) != cudaSuccess ||
+                        cudaMemcpy(w, dw, sizeof(double) * n * nbatch, cudaMemcpyDeviceToHost) != cudaSuccess))
+        st = HP_ECUDA;
+    cudaFree(dA);
+    cudaFree(dV);
+    cudaFree(dT);
+    cudaFree(dw);
+    return st;
 }

@@ -1,0 +1,51 @@
+"""Device kernels checked one by one against numpy: the batched Hermitian eigensolver of the
+ground state (including matrices whose off-diagonal entries underflow during the sweeps)."""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+P = pytest.importorskip("paper_2203_15684_gb300")
+
+
+def _check(A, tol=1e-12):
+    w, V = P.selftest_eigh(A)
+    n = A.shape[-1]
+    for b in range(len(A)):
+        ref = np.linalg.eigvalsh(A[b])
+        scale = max(1.0, np.abs(ref).max())
+        assert np.abs(w[b] - ref).max() < tol * scale
+        assert np.abs(V[b].conj().T @ V[b] - np.eye(n)).max() < tol
+        assert np.abs(A[b] @ V[b] - V[b] * w[b][None, :]).max() < tol * scale
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 24, 30, 31, 64, 128])
+def test_eigh_random_and_degenerate(n):
+    rng = np.random.default_rng(n)
+    As = []
+    for b in range(5):
+        Q = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))[0]
+        ev = rng.standard_normal(n) * 3
+        if b % 2:
+            ev[: n // 3] = ev[0]
+        As.append(Q @ np.diag(ev) @ Q.conj().T)
+    _check(np.array(As))
+
+
+def test_eigh_block_structure_with_underflowing_couplings():
+    """Degenerate blocks embedded in a permuted basis with 1e-170 couplings between blocks: the
+    sweeps must skip pairs whose coupling is negligible instead of forming their phase."""
+    rng = np.random.default_rng(7)
+    n, As = 30, []
+    for b in range(4):
+        A = np.zeros((n, n), dtype=complex)
+        for s in range(0, n, 3):
+            Qb = np.linalg.qr(rng.standard_normal((3, 3)) + 1j * rng.standard_normal((3, 3)))[0]
+            ev = -3 + 0.1 * (s // 3) + np.array([0.0, 0.0, 1e-9])
+            A[s:s + 3, s:s + 3] = Qb @ np.diag(ev) @ Qb.conj().T
+        C = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) * 1e-170
+        A = A + C + C.conj().T
+        perm = rng.permutation(n)
+        As.append(A[np.ix_(perm, perm)])
+    _check(np.array(As))
