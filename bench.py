@@ -1,0 +1,326 @@
+#!/usr/bin/env python3
+"""Benchmark of the DFPT Hubbard-parameter hot path on GB300.
+
+Workload: the medium rocksalt-like cell (8.4 bohr cube, 4 H + 4 L, 40 electrons, collinear
+nspin = 2 with an antiferromagnetic start, 35 Ry, FFT 36^3, k 4x4x4, q 2x2x2).  The ground state
+is computed on the GPU before timing.  One step = one (q, J) self-consistent Sternheimer response
+(the per-q set-up a1 and a3-a10): every (spin, k, band) system of that pair, to the FP64
+tolerances the parity tests use.  The 64 (q, J) pairs of the full chi matrix are independent and
+alike, so the full-matrix wall time is reported as steps-per-matrix x time per step.
+
+Metric: H.psi/s (single-band applications of the Sternheimer operator, summed over ranks).
+N > 1 (torchrun): the (q, J) pairs are sharded round-robin over ranks (weak scaling, no collective
+on the data path); timing is the max over ranks between barriers.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "full χ-matrix wall time & H·ψ/s, mixed vs FP64 on 1 GB300 at |ΔU|≤1 meV"
+UNIT = "Hpsi/s"
+FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 rate (no measured FP64 peak is available; see DESIGN)
+WORKLOAD_DESC = ("medium: rocksalt cube a=8.4 bohr, 4 H + 4 L, 40 electrons, nspin=2 (AFM start), "
+                 "ecutwfc 35 Ry (npw<=2103), FFT 36^3, k 4x4x4, q 2x2x2")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--band-batch", type=int, default=0, help="grids per FFT batch (0 = automatic)")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------------
+QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + QUERY, "--format=csv",
+                                          "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path).read().splitlines()[1:]:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1].split()[0]))
+                smax.append(float(f[2].split()[0]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------------
+# oracle timing (CPU baseline and the reference arm)
+# ------------------------------------------------------------------------------------------------
+def _oracle_sample(seconds):
+    """The oracle's Sternheimer operator (H + alpha P_v - eps) applied to blocks of 20 bands on the
+    workload's spheres and grid, with the oracle's own starting-density potential, for about
+    ``seconds``; returns (H.psi count, elapsed)."""
+    import numpy as np
+
+    import workloads as W
+    from oracle import groundstate as G
+    from oracle.hamiltonian import apply_h
+    from oracle.model import Model
+
+    w = W.medium()
+    m = Model(w)
+    vr = m.vloc_r() + G.hxc_potential(m, G.initial_density(m))[0]
+    rng = np.random.default_rng(2203)
+    n, t0, ik = 0, time.perf_counter(), 0
+    while True:
+        kd = m.kdata(m.kpts[ik % len(m.kpts)])
+        U = np.linalg.qr(rng.standard_normal((kd.npw, m.nocc)) + 1j * rng.standard_normal((kd.npw, m.nocc)))[0]
+        X = rng.standard_normal((kd.npw, m.nocc)) + 1j * rng.standard_normal((kd.npw, m.nocc))
+        Y = apply_h(m, kd, vr, X) + 2.0 * (U @ (U.conj().T @ X)) - X * 0.5
+        n += X.shape[1]
+        ik += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            return n, el, float(np.abs(Y).max())
+
+
+def run_oracle_subprocess(seconds):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; n, el, _ = bench._oracle_sample(%f); "
+            "print(json.dumps(dict(n=n, el=el)))" % (ROOT, seconds))
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return d["n"], d["el"]
+
+
+def cpu_baseline(seconds):
+    n, el = run_oracle_subprocess(seconds)
+    return {"value": n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "oracle Sternheimer operator (H + alpha P_v - eps) on %d single-band vectors of the medium "
+                      "workload (20-band blocks cycling over its 64 k spheres, FFT 36^3), %.1f s, 1 thread" % (n, el)}
+
+
+def reference_arm(args, rank):
+    if rank != 0:
+        return
+    vals = []
+    n_tot, el_tot = 0, 0.0
+    for _ in range(args.warmup):
+        run_oracle_subprocess(2.0)
+    for _ in range(args.steps):
+        n, el = run_oracle_subprocess(5.0)
+        vals.append(n / el)
+        n_tot += n
+        el_tot += el
+    value = n_tot / el_tot
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * el_tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC, "step": "about 5 s of the oracle's Sternheimer operator on the "
+                                                          "workload's spheres (1 thread)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "%d H.psi in %.1f s over %d steps" % (n_tot, el_tot, args.steps)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------------
+def ncu_traffic():
+    """Per-launch DRAM bytes of the FFT pass kernel from the committed ncu summary, if the kernel
+    source is unchanged since the capture."""
+    path = os.path.join(ROOT, "profiles", "fft_axis_kernel_medium.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    src = open(os.path.join(ROOT, "paper_2203_15684_gb300", "csrc", "fft.cu"), "rb").read()
+    if d.get("fft_cu_sha256") != hashlib.sha256(src).hexdigest():
+        return None
+    return d.get("dram_bytes_per_launch_full_batch")
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank)
+        return
+    import numpy as np
+    import torch
+
+    import paper_2203_15684_gb300 as P
+    import workloads as W
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    stream = torch.cuda.current_stream()
+    w = W.medium()
+    ctx = P.Context.from_workload(w, cuda_stream=stream.cuda_stream, band_batch=args.band_batch)
+    t0 = time.perf_counter()
+    gs = ctx.ground_state(w["nelec"], w["nspin"], w["moments"])
+    gs_seconds = time.perf_counter() - t0
+    atoms, _ = ctx.hubbard_atoms()
+    nq = ctx.query_sizes()["nq"]
+    pairs = [(iq, int(J)) for J in atoms for iq in range(nq)]
+    mine = pairs[rank::world]
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    k = 0
+    for _ in range(args.warmup):
+        iq, J = mine[k % len(mine)]
+        ctx.response(iq, J)
+        k += 1
+    barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    P.profile_begin()
+    l0 = P.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    hpsi = 0
+    iters = []
+    for _ in range(args.steps):
+        iq, J = mine[k % len(mine)]
+        torch.cuda.nvtx.range_push("timed_step")
+        _, _, info = ctx.response(iq, J)
+        torch.cuda.nvtx.range_pop()
+        hpsi += info["hpsi"]
+        iters.append(info["iterations"])
+        k += 1
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = P.launch_count() - l0
+    prof = P.profile_end()
+    clk = clocks.stop()
+    elapsed = e0.elapsed_time(e1) / 1000.0
+    t = torch.tensor([elapsed, float(hpsi)], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        tmax = t.clone()
+        dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
+        elapsed, hpsi_all = float(tmax[0]), float(t[1])
+    else:
+        hpsi_all = float(hpsi)
+    value = hpsi_all / elapsed
+    ms_per_step = 1000.0 * elapsed / args.steps
+
+    # end to end through the C ABI: ground state from pinned host memory, response, results to host
+    eps, rho, vhxc = ctx.get_ground_state()
+    psi = ctx.get_wavefunctions()
+    host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in (vhxc, rho, eps)]
+    psi_h = torch.from_numpy(psi.view(np.float64)).pin_memory().numpy().view(np.complex128)
+    h2d = sum(a.nbytes for a in host) + psi_h.nbytes
+    s = ctx.query_sizes()
+    d2h = 2 * s["nhub_atoms"] * s["nspin"] * s["mmax"] ** 2 * 16
+    barrier()
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    hpsi_e = 0
+    for _ in range(args.e2e_steps):
+        iq, J = mine[k % len(mine)]
+        ctx.set_ground_state_packed(w["nspin"], w["nelec"], host[0], host[1], host[2], psi_h)
+        _, _, info = ctx.response(iq, J)
+        hpsi_e += info["hpsi"]
+        k += 1
+    torch.cuda.synchronize()
+    e2e_el = time.perf_counter() - te
+    barrier()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    hpsi_e = max(hpsi_e, 1)
+    e2e_el = max(e2e_el, 1e-9)
+    achieved = (prof["flops"] / prof["launches"]) / (prof["ms"] / prof["launches"] / 1000.0) / 1e12
+    traffic = ncu_traffic()
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "kernel": "fft_axis_kernel (FP64 Stockham pass)", "peak_source": "GB300 FP64 rate (nominal)",
+                "launches": prof["launches"], "avg_launch_ms": prof["ms"] / prof["launches"],
+                "achieved_hbm_gbs": (prof["bytes"] / prof["ms"] * 1e-6) if prof["ms"] > 0 else None,
+                "share_of_step": prof["ms"] / 1000.0 / elapsed}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC,
+                       "step": "one (q, J) self-consistent Sternheimer response, %d band systems, FP64"
+                               % (s["nspin"] * s["nk"] * s["nocc"]),
+                       "pairs_per_chi_matrix": len(pairs),
+                       "chi_matrix_s": ms_per_step * len(pairs) / 1000.0 / world,
+                       "outer_iterations_per_step": iters,
+                       "ground_state_s": gs_seconds, "gap_ha": gs["gap"],
+                       "l2": "inputs larger than L2 (response working set about 2.6 GB)",
+                       "parallelism": "(q, J) pairs round-robin over %d rank(s)" % world},
+            "clocks": clk,
+            "e2e": {"value": hpsi_e / e2e_el, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "roofline": roofline}
+    if args.cpu_seconds > 0:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -154,6 +154,11 @@ hp_status hp_set_ground_state(hp_ctx* ctx, int nspin, double nelec, const double
  * nspin x nr.  Errors: HP_ESTATE before a ground state. */
 hp_status hp_get_ground_state(const hp_ctx* ctx, double* eps, double* rho, double* vhxc);
 
+/* Reads back the occupied ground-state wavefunctions in the layout hp_set_ground_state takes: for
+ * each spin, each k, nocc vectors of npw_k complex coefficients (hp_sphere order), packed.
+ * Errors: HP_ESTATE before a ground state. */
+hp_status hp_get_wavefunctions(const hp_ctx* ctx, double* psi);
+
 /* Kohn-Sham operator at mesh point ik and spin s applied to nb host vectors (npw_k complex each,
  * hp_sphere order): out = H psi with H = T + V_loc + V_Hxc,s + V_NL (needs a ground state). */
 hp_status hp_apply_h(hp_ctx* ctx, int ik, int spin, int nb, const double* psi, double* out);
@@ -177,6 +182,17 @@ const char* hp_last_error(const hp_ctx* ctx);
 
 /* Frees the context and all device memory it owns.  NULL is ignored. */
 void hp_destroy(hp_ctx* ctx);
+
+/* Live timing of the FFT passes (the dominant kernel of H.psi): between hp_profile_begin and
+ * hp_profile_end every FFT pass launch is bracketed by CUDA events recorded on its launch stream;
+ * hp_profile_end waits for them and returns the summed kernel time (ms), the number of pass
+ * launches, and their algorithmic flops (5 n log2 n per transformed line of n points) and bytes
+ * (every grid point read and written once per pass).  Process-wide, not per context. */
+void hp_profile_begin(void);
+hp_status hp_profile_end(double* fft_ms, long long* fft_launches, double* fft_flops, double* fft_bytes);
+
+/* Number of CUDA kernels this library has launched in this process (monotonic counter). */
+long long hp_launch_count(void);
 
 /* Host-only self-test of the FFT engine's stage logic (runs the same Stockham code on the CPU).
  * in/out: nlines x n complex; sign -1 forward exp(-2 pi i jk/n), +1 backward (unnormalised). */

@@ -62,7 +62,8 @@ _lib = None
 
 SYMBOLS = ["hp_default_options", "hp_setup", "hp_query_sizes", "hp_sphere", "hp_hubbard_atoms", "hp_ground_state",
            "hp_set_ground_state", "hp_get_ground_state", "hp_apply_h", "hp_response", "hp_hubbard", "hp_last_error",
-           "hp_destroy", "hp_selftest_fft_host", "hp_selftest_eigh"]
+           "hp_destroy", "hp_selftest_fft_host", "hp_selftest_eigh", "hp_get_wavefunctions", "hp_profile_begin",
+           "hp_profile_end", "hp_launch_count"]
 
 
 def lib():
@@ -93,9 +94,16 @@ def lib():
     L.hp_destroy.restype = None
     L.hp_selftest_fft_host.argtypes = [I, I, I, P(D), P(D)]
     L.hp_selftest_eigh.argtypes = [I, I, P(D), P(D), P(D)]
+    L.hp_get_wavefunctions.argtypes = [V, P(D)]
+    L.hp_profile_begin.argtypes = []
+    L.hp_profile_begin.restype = None
+    L.hp_profile_end.argtypes = [P(D), P(C.c_longlong), P(D), P(D)]
+    L.hp_launch_count.argtypes = []
     for n in SYMBOLS:
         f = getattr(L, n)
-        if n not in ("hp_default_options", "hp_last_error", "hp_destroy"):
+        if n == "hp_launch_count":
+            f.restype = C.c_longlong
+        elif n not in ("hp_default_options", "hp_last_error", "hp_destroy", "hp_profile_begin"):
             f.restype = I
     _lib = L
     return L
@@ -142,6 +150,24 @@ def selftest_eigh(A):
     if st != HP_OK:
         raise HPError(st, "hp_selftest_eigh")
     return w, V
+
+
+def profile_begin():
+    lib().hp_profile_begin()
+
+
+def profile_end():
+    """-> dict(ms, launches, flops, bytes) of the FFT passes since profile_begin()."""
+    ms, fl, by = C.c_double(), C.c_double(), C.c_double()
+    n = C.c_longlong()
+    st = lib().hp_profile_end(C.byref(ms), C.byref(n), C.byref(fl), C.byref(by))
+    if st != HP_OK:
+        raise HPError(st, "hp_profile_end")
+    return dict(ms=ms.value, launches=n.value, flops=fl.value, bytes=by.value)
+
+
+def launch_count():
+    return int(lib().hp_launch_count())
 
 
 class Context:
@@ -238,6 +264,22 @@ class Context:
         vhxc = np.zeros((s["nspin"], s["nr"]))
         self._check(lib().hp_get_ground_state(self._ptr, _dptr(eps), _dptr(rho), _dptr(vhxc)), "hp_get_ground_state")
         return eps, rho, vhxc
+
+    def get_wavefunctions(self):
+        """Packed occupied wavefunctions (complex), the layout set_ground_state reads."""
+        s = self.query_sizes()
+        n = sum(len(self.sphere(k)) for k in range(s["nk"])) * s["nocc"] * s["nspin"]
+        out = np.zeros(n, dtype=np.complex128)
+        self._check(lib().hp_get_wavefunctions(self._ptr, _dptr(out.view(np.float64))), "hp_get_wavefunctions")
+        return out
+
+    def set_ground_state_packed(self, nspin, nelec, vhxc, rho, eps, psi_packed):
+        vh = np.ascontiguousarray(vhxc, dtype=np.float64).reshape(-1)
+        rh = np.ascontiguousarray(rho, dtype=np.float64).reshape(-1)
+        ep = np.ascontiguousarray(eps, dtype=np.float64).reshape(-1)
+        ps = np.ascontiguousarray(psi_packed, dtype=np.complex128)
+        self._check(lib().hp_set_ground_state(self._ptr, int(nspin), float(nelec), _dptr(vh), _dptr(rh), _dptr(ep),
+                                              _dptr(ps.view(np.float64))), "hp_set_ground_state")
 
     def apply_h(self, ik, spin, psi):
         """psi: (nb, npw_k) complex in sphere order -> H psi, same shape."""

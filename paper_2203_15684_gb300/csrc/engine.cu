@@ -20,6 +20,8 @@ using namespace hp;
 
 namespace hp {
 
+std::atomic<long long> g_launches{0};
+
 constexpr double kHaToEv = 27.211386245988;
 constexpr int kMmax = 5;
 constexpr int kPStride = 128;
@@ -609,6 +611,26 @@ extern "C" hp_status hp_get_ground_state(const hp_ctx* cc, double* eps, double* 
     }
     if (rho) CK(d2h(rho, c->d_rho, (size_t)c->nspin * c->nr, c->st));
     if (vhxc) CK(d2h(vhxc, c->d_vhxc, (size_t)c->nspin * c->nr, c->st));
+    return HP_OK;
+}
+
+extern "C" hp_status hp_get_wavefunctions(const hp_ctx* cc, double* psi) {
+    hp_ctx* c = const_cast<hp_ctx*>(cc);
+    if (!c || !psi) return HP_EINVAL;
+    if (!c->have_gs) return fail(c, HP_ESTATE, "no ground state");
+    std::vector<double2> row(c->ld);
+    size_t off = 0;
+    for (int sp = 0; sp < c->nspin; ++sp)
+        for (int k = 0; k < c->nk; ++k)
+            for (int v = 0; v < c->nocc; ++v) {
+                CK(cudaMemcpy(row.data(), c->d_psi + ((size_t)(sp * c->nk + k) * c->nbnd + v) * c->ld,
+                              sizeof(double2) * c->ld, cudaMemcpyDeviceToHost));
+                for (int i = 0; i < c->ks[k].npw; ++i) {
+                    psi[2 * (off + i)] = row[i].x;
+                    psi[2 * (off + i) + 1] = row[i].y;
+                }
+                off += c->ks[k].npw;
+            }
     return HP_OK;
 }
 

@@ -290,15 +290,18 @@ hp_status rayleigh_ritz(hp_ctx* c, BandList& L, BandList& L0, GsWork& W, double2
     {
         dim3 g(cdiv_(ld, 128), L.nb);
         rows_normalize_kernel<<<g, 128, 0, c->st>>>(L.d_row, W.nrm, Y, ld);
+        HP_LAUNCHED();
         CK(cudaGetLastError());
     }
     fam.base = Y;
     hp_status s = project(c, c->kset, L, fam, Y, W.Pb);
     if (s != HP_OK) return s;
     pack_seg_kernel<<<nseg, 256, 0, c->st>>>(W.Pb, L.d_seg_start, n, W.Mb);
+    HP_LAUNCHED();
     CK(cudaGetLastError());
     const size_t jsh = (size_t)(n / 2 + 1) * (4 * sizeof(double) + 2 * sizeof(int));
     jacobi_kernel<<<nseg, 256, jsh, c->st>>>(W.Mb, W.Vb, W.w, W.Tmp, n, 40);
+    HP_LAUNCHED();
     CK(cudaGetLastError());
     if (getenv("HP_VERBOSE")) {
         std::vector<double> ws((size_t)nseg * n);
@@ -317,6 +320,7 @@ hp_status rayleigh_ritz(hp_ctx* c, BandList& L, BandList& L0, GsWork& W, double2
     }
     CK(cudaMemsetAsync(W.bad, 0, sizeof(int), c->st));
     seg_transform_kernel<<<nseg, 256, 0, c->st>>>(W.Vb, W.w, 1, L.d_seg_start, n, W.Pb, W.bad);
+    HP_LAUNCHED();
     CK(cudaGetLastError());
     CK(cudaMemsetAsync(X, 0, sizeof(double2) * nvec, c->st));
     CK(k_expand(L, c->kset, fam, W.Pb, nullptr, 1.0, X, ld, c->st));
@@ -327,10 +331,13 @@ hp_status rayleigh_ritz(hp_ctx* c, BandList& L, BandList& L0, GsWork& W, double2
     s = project(c, c->kset, L, fam, W.T, W.Pb);
     if (s != HP_OK) return s;
     pack_seg_kernel<<<nseg, 256, 0, c->st>>>(W.Pb, L.d_seg_start, n, W.Mb);
+    HP_LAUNCHED();
     CK(cudaGetLastError());
     jacobi_kernel<<<nseg, 256, jsh, c->st>>>(W.Mb, W.Vb, W.w, W.Tmp, n, 40);
+    HP_LAUNCHED();
     CK(cudaGetLastError());
     seg_transform_kernel<<<nseg, 256, 0, c->st>>>(W.Vb, W.w, 0, L.d_seg_start, n, W.Pb, nullptr);
+    HP_LAUNCHED();
     CK(cudaGetLastError());
     CK(cudaMemsetAsync(Y, 0, sizeof(double2) * nvec, c->st));
     CK(k_expand(L, c->kset, fam, W.Pb, nullptr, 1.0, Y, ld, c->st));
@@ -373,6 +380,7 @@ hp_status cheb_filter(hp_ctx* c, BandList& L, GsWork& W, double2* X, int m, cons
         if (s != HP_OK) return s;
         // y_{k} = 2/e (H - c) y_{k-1} - y_{k-2}, written over y_{k-2}
         vec_axmy_kernel<<<std::min(cdiv_(nvec, 256), 4096), 256, 0, c->st>>>(ym1, W.T, 2.0 / e, nvec);
+        HP_LAUNCHED();
         CK(cudaGetLastError());
         double2* t = ym1;
         ym1 = y;
@@ -494,6 +502,7 @@ extern "C" hp_status hp_ground_state(hp_ctx* c, double nelec, int nspin, const i
         CK(h2d(d_mom, mom.data(), nat, c->st));
         init_density_kernel<<<cdiv_(nr, 256), 256, 0, c->st>>>(c->d_rho, c->N[0], c->N[1], c->N[2], d_cell, nat, d_frac,
                                                                 d_mom, nelec / c->omega, nspin);
+        HP_LAUNCHED();
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(c->st));
         dfree(c, d_cell);
@@ -504,10 +513,12 @@ extern "C" hp_status hp_ground_state(hp_ctx* c, double nelec, int nspin, const i
     auto hxc = [&](double2* out) -> hp_status {
         // V_H[rho_tot]
         to_complex_kernel<<<cdiv_(nr, 256), 256, 0, c->st>>>(c->d_rho, dvh, nr);
+        HP_LAUNCHED();
         CK(cudaGetLastError());
         if (nspin == 2) {
             double2* tmp = out;  // use out as scratch for the second spin
             to_complex_kernel<<<cdiv_(nr, 256), 256, 0, c->st>>>(c->d_rho + nr, tmp, nr);
+            HP_LAUNCHED();
             CK(cudaGetLastError());
             CK(k_vec_axpy(dvh, tmp, 1.0, nr, c->st));
         }
@@ -516,6 +527,7 @@ extern "C" hp_status hp_ground_state(hp_ctx* c, double nelec, int nspin, const i
         CK(fft3d(c->fft, dvh, 1, +1, c->st));
         CK(k_xc(c->d_rho, nspin, nr, vxc, nullptr, c->st));
         hxc_assemble_kernel<<<cdiv_(nr, 256), 256, 0, c->st>>>(dvh, vxc, nspin, nr, out);
+        HP_LAUNCHED();
         return cudaGetLastError() == cudaSuccess ? HP_OK : fail(c, HP_ECUDA, "hxc");
     };
     if ((st = hxc(vin)) != HP_OK) return st;
@@ -534,8 +546,10 @@ extern "C" hp_status hp_ground_state(hp_ctx* c, double nelec, int nspin, const i
     const bool verbose = getenv("HP_VERBOSE") != nullptr;
     for (it = 1; it <= c->opt.gs_maxiter; ++it) {
         veff_kernel<<<cdiv_(nr, 256), 256, 0, c->st>>>(c->d_vloc, vin, nspin, nr, c->d_veff, c->d_vhxc);
+        HP_LAUNCHED();
         CK(cudaGetLastError());
         vec_max_kernel<<<1, 256, 0, c->st>>>(c->d_veff, ndv, c->d_small + 100);
+        HP_LAUNCHED();
         CK(cudaGetLastError());
         double vmax = 0.0;
         CK(d2h(&vmax, c->d_small + 100, 1, c->st));
@@ -623,10 +637,12 @@ extern "C" hp_status hp_ground_state(hp_ctx* c, double nelec, int nspin, const i
     }
     // polish: extra filter passes at the final potential until the occupied residuals are small
     veff_kernel<<<cdiv_(nr, 256), 256, 0, c->st>>>(c->d_vloc, vin, nspin, nr, c->d_veff, c->d_vhxc);
+    HP_LAUNCHED();
     CK(cudaGetLastError());
     double rmax = INFINITY;
     for (int pass = 0; pass < 30; ++pass) {
         vec_max_kernel<<<1, 256, 0, c->st>>>(c->d_veff, ndv, c->d_small + 100);
+        HP_LAUNCHED();
         double vmax = 0.0;
         CK(d2h(&vmax, c->d_small + 100, 1, c->st));
         const double b = 0.5 * c->ecut + vmax + 2.0 * dplus + 1.0;
@@ -727,6 +743,7 @@ extern "C" hp_status hp_selftest_eigh(int n, int nbatch, const double* A, double
     if (st == HP_OK) {
         const size_t jsh = (size_t)(n / 2 + 1) * (4 * sizeof(double) + 2 * sizeof(int));
         hp::jacobi_kernel<<<nbatch, 256, jsh>>>(dA, dV, dw, dT, n, 40);
+        HP_LAUNCHED();
         if (cudaDeviceSynchronize() != cudaSuccess) st = HP_ECUDA;
     }
     if (st == HP_OK && (cudaMemcpy(V, dV, sizeof(double2) * nn, cudaMemcpyDeviceToHost) != cudaSuccess ||

@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <map>
 #include <string>
@@ -31,6 +32,10 @@ HD double2 cscale(double2 a, double s) { return cmk(a.x * s, a.y * s); }
 HD double2 cconj(double2 a) { return cmk(a.x, -a.y); }
 // a * (s i) for s = +-1
 HD double2 cmul_si(double2 a, int s) { return s > 0 ? cmk(-a.y, a.x) : cmk(a.y, -a.x); }
+
+// every kernel launch of the library increments this counter (read by hp_launch_count)
+extern std::atomic<long long> g_launches;
+#define HP_LAUNCHED() (hp::g_launches.fetch_add(1, std::memory_order_relaxed))
 
 // ------------------------------------------------------------------------------------------------
 // FFT (batched 3D complex, mixed radix 2/3/4/5 Stockham in shared memory, one pass per axis)

@@ -47,6 +47,7 @@ cudaError_t k_scatter(const SphereSet& S, const BandList& L, int c0, int nc, con
     if (e != cudaSuccess) return e;
     dim3 g(cdiv(S.ld, 128), nc);
     scatter_kernel<<<g, 128, 0, st>>>(S.d_npw, S.d_idx, S.ld, L.d_row, L.d_k, c0, X, grid, nr);
+    HP_LAUNCHED();
     (void)ldx;
     return cudaGetLastError();
 }
@@ -78,6 +79,7 @@ cudaError_t k_gather_h(const SphereSet& S, const BandList& L, int c0, int nc, co
     if (nc <= 0) return cudaSuccess;
     dim3 g(cdiv(ld, 128), nc);
     gather_h_kernel<<<g, 128, 0, st>>>(S.d_npw, S.d_idx, S.d_g2, ld, L.d_row, L.d_k, L.d_shift, c0, grid, nr, X, Y);
+    HP_LAUNCHED();
     return cudaGetLastError();
 }
 
@@ -100,6 +102,7 @@ cudaError_t k_gather_scaled(const SphereSet& S, const BandList& L, int c0, int n
     if (nc <= 0) return cudaSuccess;
     dim3 g(cdiv(ld, 128), nc);
     gather_scaled_kernel<<<g, 128, 0, st>>>(S.d_npw, S.d_idx, ld, L.d_row, L.d_k, c0, grid, nr, scale, Y, accumulate);
+    HP_LAUNCHED();
     return cudaGetLastError();
 }
 
@@ -119,6 +122,7 @@ cudaError_t k_mul_rpot(double2* grid, int nc, int nr, const double* v, const Ban
     if (nc <= 0) return cudaSuccess;
     dim3 g(cdiv(nr, 256 * 4), nc);
     mul_rpot_kernel<<<g, 256, 0, st>>>(grid, nr, v, L.d_spin, c0);
+    HP_LAUNCHED();
     return cudaGetLastError();
 }
 
@@ -138,6 +142,7 @@ cudaError_t k_mul_cpot(double2* grid, const double2* src_rows, const int* src_ro
     if (nc <= 0) return cudaSuccess;
     dim3 g(cdiv(nr, 256 * 4), nc);
     mul_cpot_kernel<<<g, 256, 0, st>>>(grid, src_rows, src_row_of_item, nr, v, L.d_spin, c0);
+    HP_LAUNCHED();
     return cudaGetLastError();
 }
 
@@ -230,9 +235,11 @@ cudaError_t k_proj(const BandList& L, const SphereSet& S, const ProjMat& A, cons
     dim3 g(L.nseg, ksplit);
     proj_kernel<<<g, 256, 0, st>>>(A.base, A.stride_s, A.stride_k, A.row0, A.nrow, ld, X, L.d_row, L.d_seg_start,
                                    L.d_seg_k, L.d_seg_s, S.d_npw, A.kmap, ksplit, scratch, L.nb);
+    HP_LAUNCHED();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     proj_reduce_kernel<<<cdiv((long long)L.nb * A.nrow, 256), 256, 0, st>>>(scratch, ksplit, L.nb, A.nrow, P);
+    HP_LAUNCHED();
     return cudaGetLastError();
 }
 
@@ -299,6 +306,7 @@ cudaError_t k_expand(const BandList& L, const SphereSet& S, const ProjMat& A, co
     dim3 g(cdiv(ld, 128), L.nseg);
     expand_kernel<<<g, 128, 0, st>>>(A.base, A.stride_s, A.stride_k, A.row0, A.nrow, ld, P, pscale, alpha, Y, L.d_row,
                                      L.d_seg_start, L.d_seg_k, L.d_seg_s, S.d_npw, A.kmap);
+    HP_LAUNCHED();
     return cudaGetLastError();
 }
 
@@ -326,6 +334,7 @@ cudaError_t k_band_dot(const BandList& L, const SphereSet& S, const double2* X, 
                        cudaStream_t st) {
     if (L.nb <= 0) return cudaSuccess;
     band_dot_kernel<<<L.nb, 256, 0, st>>>(L.d_row, L.d_k, S.d_npw, X, Y, ld, out);
+    HP_LAUNCHED();
     return cudaGetLastError();
 }
 
@@ -358,6 +367,7 @@ cudaError_t k_cg_init(const BandList& L, const SphereSet& S, const double2* r, d
                       double* rr, cudaStream_t st) {
     if (L.nb <= 0) return cudaSuccess;
     cg_init_kernel<<<L.nb, 256, 0, st>>>(L.d_row, L.d_k, S.d_npw, S.d_g2, r, p, ld, rz, rr);
+    HP_LAUNCHED();
     return cudaGetLastError();
 }
 
@@ -401,6 +411,7 @@ cudaError_t k_cg_update(const BandList& L, const SphereSet& S, const double* pap
                         cudaStream_t st) {
     if (L.nb <= 0) return cudaSuccess;
     cg_update_kernel<<<L.nb, 256, 0, st>>>(L.d_row, L.d_k, S.d_npw, S.d_g2, pap, x, r, p, ap, ld, rz, rr, rz_old);
+    HP_LAUNCHED();
     return cudaGetLastError();
 }
 
@@ -425,6 +436,7 @@ cudaError_t k_cg_direction(const BandList& L, const SphereSet& S, const double* 
                            const double2* r, double2* p, int ld, cudaStream_t st) {
     if (L.nb <= 0) return cudaSuccess;
     cg_dir_kernel<<<L.nb, 256, 0, st>>>(L.d_row, L.d_k, S.d_npw, S.d_g2, rz, rz_old, r, p, ld);
+    HP_LAUNCHED();
     return cudaGetLastError();
 }
 
@@ -445,6 +457,7 @@ cudaError_t k_rows_axpby(const BandList& L, const SphereSet& S, double a, const 
     if (L.nb <= 0) return cudaSuccess;
     dim3 g(cdiv(ld, 128), L.nb);
     rows_axpby_kernel<<<g, 128, 0, st>>>(L.d_row, a, X, b, Y, ld);
+    HP_LAUNCHED();
     (void)S;
     return cudaGetLastError();
 }
@@ -471,6 +484,7 @@ cudaError_t k_gather_kq(const int* map, const int* npw_kq, const int* kprime, in
                         const double2* psi, int nbnd, double2* ukq, cudaStream_t st) {
     dim3 g(cdiv(ld, 128), nspin * nk * nocc);
     gather_kq_kernel<<<g, 128, 0, st>>>(map, npw_kq, kprime, nk, nocc, ld, psi, nbnd, ukq);
+    HP_LAUNCHED();
     return cudaGetLastError();
 }
 
@@ -545,6 +559,7 @@ cudaError_t k_formfactor(const double* kcart, int nk, const int* miller, const i
     dim3 g(cdiv(ld, 128), nrow, nk);
     formfactor_kernel<<<g, 128, 0, st>>>(kcart, miller, npw, ld, bvec, nrow, row_atom, row_l, row_m, row_width, row_pref,
                                          tau, out);
+    HP_LAUNCHED();
     return cudaGetLastError();
 }
 
@@ -573,6 +588,7 @@ cudaError_t k_drho_acc(const double2* ur, const int* ur_row_of_item, const doubl
                        const BandList& L, int c0, double weight, int nspin, double2* drho, cudaStream_t st) {
     if (nc <= 0) return cudaSuccess;
     drho_acc_kernel<<<cdiv(nr, 256), 256, 0, st>>>(ur, ur_row_of_item, xr, nc, nr, L.d_spin, c0, weight, nspin, drho);
+    HP_LAUNCHED();
     return cudaGetLastError();
 }
 
@@ -596,6 +612,7 @@ cudaError_t k_density_acc(const double2* ur, int nc, int nr, const BandList& L, 
                           double* rho, cudaStream_t st) {
     if (nc <= 0) return cudaSuccess;
     density_acc_kernel<<<cdiv(nr, 256), 256, 0, st>>>(ur, nc, nr, L.d_spin, c0, weight, nspin, rho);
+    HP_LAUNCHED();
     return cudaGetLastError();
 }
 
@@ -645,6 +662,7 @@ cudaError_t k_hartree_q(double2* rho_g, const int N[3], const double* bvec, cons
     Dbl3 q = {{qfrac[0], qfrac[1], qfrac[2]}};
     const long long nr = (long long)N[0] * N[1] * N[2];
     hartree_q_kernel<<<cdiv(nr, 256), 256, 0, st>>>(rho_g, n, bvec, q, ecut4, scale);
+    HP_LAUNCHED();
     return cudaGetLastError();
 }
 
@@ -678,6 +696,7 @@ cudaError_t k_vloc_g(double2* vg, const int N[3], const double* bvec, double ecu
     Int3 n = {{N[0], N[1], N[2]}};
     const long long nr = (long long)N[0] * N[1] * N[2];
     vloc_g_kernel<<<cdiv(nr, 256), 256, 0, st>>>(vg, n, bvec, ecut4, nat, tau, amp, width, omega);
+    HP_LAUNCHED();
     return cudaGetLastError();
 }
 
@@ -688,6 +707,7 @@ __global__ void real_part_kernel(const double2* __restrict__ z, double* __restri
 
 cudaError_t k_real_part(const double2* z, double* out, int n, double scale, cudaStream_t st) {
     real_part_kernel<<<cdiv(n, 256), 256, 0, st>>>(z, out, n, scale);
+    HP_LAUNCHED();
     return cudaGetLastError();
 }
 
@@ -785,6 +805,7 @@ __global__ void xc_kernel(const double* __restrict__ rho, int nspin, int nr, dou
 
 cudaError_t k_xc(const double* rho, int nspin, int nr, double* vxc, double* fxc, cudaStream_t st) {
     xc_kernel<<<cdiv(nr, 256), 256, 0, st>>>(rho, nspin, nr, vxc, fxc);
+    HP_LAUNCHED();
     return cudaGetLastError();
 }
 
@@ -807,6 +828,7 @@ __global__ void hxc_combine_kernel(const double2* __restrict__ vh, const double2
 cudaError_t k_hxc_combine(const double2* vh, const double2* drho, const double* fxc, int nspin, int nr, double2* dv,
                           cudaStream_t st) {
     hxc_combine_kernel<<<cdiv(nr, 256), 256, 0, st>>>(vh, drho, fxc, nspin, nr, dv);
+    HP_LAUNCHED();
     return cudaGetLastError();
 }
 
@@ -837,6 +859,7 @@ cudaError_t k_occ_response(const double2* B, const double2* Aphi, int ngroups, i
     (void)ngroups;
     dim3 g(nhub, nhub, nspin);
     occ_response_kernel<<<g, 128, 0, st>>>(B, Aphi, nk, nocc, nhub, M);
+    HP_LAUNCHED();
     return cudaGetLastError();
 }
 
@@ -869,6 +892,7 @@ __global__ void dn_traces_kernel(const double2* __restrict__ dn, int nh, int nsp
 
 cudaError_t k_dn_traces(const double2* dn, int nh, int nspin, int mmax, double f, double2* tr, cudaStream_t st) {
     dn_traces_kernel<<<cdiv(nh, 64), 64, 0, st>>>(dn, nh, nspin, mmax, f, tr);
+    HP_LAUNCHED();
     return cudaGetLastError();
 }
 
@@ -876,6 +900,7 @@ cudaError_t k_dn_blocks(const double2* M, int nspin, int nhub, int nhub_atoms, c
                         double2* dn, cudaStream_t st) {
     dim3 g(nhub_atoms, nspin);
     dn_blocks_kernel<<<g, 64, 0, st>>>(M, nspin, nhub, off, mdim, mmax, dn);
+    HP_LAUNCHED();
     return cudaGetLastError();
 }
 
@@ -906,14 +931,17 @@ __global__ void sum_reduce_kernel(const double* __restrict__ partial, int nparts
 
 cudaError_t k_vec_dot(const double2* a, const double2* b, long long n, double* out, double* partial, cudaStream_t st) {
     vec_dot_kernel<<<kRedBlocks, 256, 0, st>>>(a, b, n, partial);
+    HP_LAUNCHED();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     sum_reduce_kernel<<<1, 256, 0, st>>>(partial, kRedBlocks, out);
+    HP_LAUNCHED();
     return cudaGetLastError();
 }
 
 cudaError_t k_sum_reduce(const double* partial, int nparts, double* out, cudaStream_t st) {
     sum_reduce_kernel<<<1, 256, 0, st>>>(partial, nparts, out);
+    HP_LAUNCHED();
     return cudaGetLastError();
 }
 
@@ -924,6 +952,7 @@ __global__ void vec_axpy_kernel(double2* __restrict__ y, const double2* __restri
 
 cudaError_t k_vec_axpy(double2* y, const double2* x, double a, long long n, cudaStream_t st) {
     vec_axpy_kernel<<<std::min(cdiv(n, 256), 4096), 256, 0, st>>>(y, x, a, n);
+    HP_LAUNCHED();
     return cudaGetLastError();
 }
 
@@ -935,6 +964,7 @@ __global__ void vec_sub_kernel(double2* __restrict__ out, const double2* __restr
 
 cudaError_t k_vec_sub(double2* out, const double2* a, const double2* b, long long n, cudaStream_t st) {
     vec_sub_kernel<<<std::min(cdiv(n, 256), 4096), 256, 0, st>>>(out, a, b, n);
+    HP_LAUNCHED();
     return cudaGetLastError();
 }
 
@@ -945,6 +975,7 @@ __global__ void vec_scale_copy_kernel(double2* __restrict__ out, const double2* 
 
 cudaError_t k_vec_scale_copy(double2* out, const double2* a, double s, long long n, cudaStream_t st) {
     vec_scale_copy_kernel<<<std::min(cdiv(n, 256), 4096), 256, 0, st>>>(out, a, s, n);
+    HP_LAUNCHED();
     return cudaGetLastError();
 }
 
@@ -982,6 +1013,7 @@ cudaError_t k_broyden_coef(const double* dots, int m, int ld, double w0, double*
     if (m <= 0) return cudaSuccess;
     if (m > 8) return cudaErrorInvalidValue;
     broyden_coef_kernel<<<1, 32, 0, st>>>(dots, m, ld, w0, gamma);
+    HP_LAUNCHED();
     return cudaGetLastError();
 }
 
@@ -1002,6 +1034,7 @@ __global__ void broyden_apply_kernel(double2* __restrict__ x, const double2* __r
 cudaError_t k_broyden_apply(double2* x, const double2* f, const double2* const* dx, const double2* const* df,
                             const double* gamma, int m, double alpha, long long n, cudaStream_t st) {
     broyden_apply_kernel<<<std::min(cdiv(n, 256), 4096), 256, 0, st>>>(x, f, dx, df, gamma, m, alpha, n);
+    HP_LAUNCHED();
     return cudaGetLastError();
 }
 
@@ -1037,6 +1070,7 @@ cudaError_t k_chi_assemble(const double2* cols, int nq, int nh, const double* qf
                            double* chi_re, double* chi_im, cudaStream_t st) {
     const int n = ncell * nh;
     chi_assemble_kernel<<<cdiv((long long)n * n, 128), 128, 0, st>>>(cols, nq, nh, qfrac, Rl, ncell, chi_re, chi_im);
+    HP_LAUNCHED();
     return cudaGetLastError();
 }
 
@@ -1110,6 +1144,7 @@ __global__ void invert_kernel(double* __restrict__ a, double* __restrict__ work,
 
 cudaError_t k_invert(double* a, double* work, int n, int* singular, cudaStream_t st) {
     invert_kernel<<<1, 256, sizeof(int) * n, st>>>(a, work, n, singular);
+    HP_LAUNCHED();
     return cudaGetLastError();
 }
 
@@ -1121,6 +1156,7 @@ __global__ void hub_matrix_kernel(const double* __restrict__ inv0, const double*
 
 cudaError_t k_hub_matrix(const double* inv0, const double* inv, int n, double scale, double* hub, cudaStream_t st) {
     hub_matrix_kernel<<<cdiv((long long)n * n, 128), 128, 0, st>>>(inv0, inv, n, scale, hub);
+    HP_LAUNCHED();
     return cudaGetLastError();
 }
 
@@ -1131,6 +1167,7 @@ __global__ void add_real_kernel(const double* __restrict__ a, const double* __re
 
 cudaError_t k_add_real(const double* a, const double* b, double* out, int n, cudaStream_t st) {
     add_real_kernel<<<cdiv(n, 256), 256, 0, st>>>(a, b, out, n);
+    HP_LAUNCHED();
     return cudaGetLastError();
 }
 
