@@ -154,6 +154,24 @@ hp_status hp_set_ground_state(hp_ctx* ctx, int nspin, double nelec, const double
  * nspin x nr.  Errors: HP_ESTATE before a ground state. */
 hp_status hp_get_ground_state(const hp_ctx* ctx, double* eps, double* rho, double* vhxc);
 
+/* H psi without allocating: the same operator and kernels as hp_apply_h, for callers that cannot
+ * call cudaMalloc while they compute -- applications whose own pool allocator holds all free
+ * device memory, and loops that must not call cudaMalloc/cudaFree because those calls can
+ * synchronise the device.  The paper has no counterpart; it is a calling convention of this library.
+ * psi_dev, out_dev: caller-owned device arrays of nb rows of npw_max complex numbers (interleaved
+ * FP64; npw_max from hp_query_sizes; row b holds band b in hp_sphere(ik) order, entries beyond
+ * npw_k zero on input and written as zero on output).  stream: a cudaStream_t, or NULL for the
+ * context's stream; the call waits for its work on that stream before returning.
+ * Scratch: one fixed 64 MiB file-scope device array, which every GPU that loads the library holds
+ * until the process exits.  The first call on a device looks up that array's device address with
+ * that device current (cudaGetSymbolAddress) and caches it.  Every call reuses the same array and
+ * leaves its contents behind; the call clears what it needs cleared.  Calls whose work overlaps on
+ * the GPU (other streams, other host threads) race on the array and must be serialised by the
+ * caller.  Errors: HP_EINVAL (bad arguments, or nb too large for the fixed scratch on this grid:
+ * call it on fewer bands), HP_ESTATE (no ground state), HP_ECUDA. */
+hp_status hp_apply_h_noalloc(hp_ctx* ctx, int ik, int spin, int nb, const double* psi_dev, double* out_dev,
+                             void* stream);
+
 /* Reads back the occupied ground-state wavefunctions in the layout hp_set_ground_state takes: for
  * each spin, each k, nocc vectors of npw_k complex coefficients (hp_sphere order), packed.
  * Errors: HP_ESTATE before a ground state. */

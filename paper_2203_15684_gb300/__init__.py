@@ -63,7 +63,7 @@ _lib = None
 SYMBOLS = ["hp_default_options", "hp_setup", "hp_query_sizes", "hp_sphere", "hp_hubbard_atoms", "hp_ground_state",
            "hp_set_ground_state", "hp_get_ground_state", "hp_apply_h", "hp_response", "hp_hubbard", "hp_last_error",
            "hp_destroy", "hp_selftest_fft_host", "hp_selftest_eigh", "hp_get_wavefunctions", "hp_profile_begin",
-           "hp_profile_end", "hp_launch_count"]
+           "hp_profile_end", "hp_launch_count", "hp_apply_h_noalloc"]
 
 
 def lib():
@@ -99,6 +99,7 @@ def lib():
     L.hp_profile_begin.restype = None
     L.hp_profile_end.argtypes = [P(D), P(C.c_longlong), P(D), P(D)]
     L.hp_launch_count.argtypes = []
+    L.hp_apply_h_noalloc.argtypes = [V, I, I, I, V, V, V]
     for n in SYMBOLS:
         f = getattr(L, n)
         if n == "hp_launch_count":
@@ -288,6 +289,12 @@ class Context:
         self._check(lib().hp_apply_h(self._ptr, ik, spin, x.shape[0], _dptr(x.view(np.float64)),
                                      _dptr(out.view(np.float64))), "hp_apply_h")
         return out
+
+    def apply_h_noalloc(self, ik, spin, nb, psi_dev_ptr, out_dev_ptr, stream=None):
+        """H psi on caller-owned device rows (nb x npw_max complex); allocates nothing."""
+        st = lib().hp_apply_h_noalloc(self._ptr, int(ik), int(spin), int(nb), C.c_void_p(psi_dev_ptr),
+                                      C.c_void_p(out_dev_ptr), C.c_void_p(stream) if stream else None)
+        self._check(st, "hp_apply_h_noalloc")
 
     def response(self, iq, atom):
         """Returns (dn0, dn, info); dn arrays complex [nhub_atoms][nspin][mmax][mmax]."""
