@@ -68,7 +68,9 @@ typedef struct {
 #define HP_PRECISION_MIXED 1
 
 typedef struct {
-    int precision;          /* HP_PRECISION_FP64 (HP_PRECISION_MIXED: HP_ENOTIMPL for now) */
+    int precision;          /* HP_PRECISION_FP64, or HP_PRECISION_MIXED: FFTs, grid work and the
+                               projections in FP32, band vectors, CG scalars, mixing and chi in FP64;
+                               CG and SCF stop at 1e-7 of the FP32 noise floor (U, V to < 1 meV) */
     double cg_tol;          /* Sternheimer CG: stop a band when ||r_v||_2 <= cg_tol (1e-11) */
     int cg_maxiter;         /* per outer iteration (default 400) */
     double scf_tol;         /* response SCF: rms of dV_out - dV_in below this (1e-10) ...      */

@@ -12,6 +12,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "hp_internal.h"
@@ -222,10 +223,23 @@ hp_status ensure_scratch(hp_ctx* c, size_t elems) {
 
 // Y = (T + V_loc + V_Hxc,s - shift) X on the list items (grid part + kinetic, zero padding)
 hp_status apply_local(hp_ctx* c, const SphereSet& S, const BandList& L, const double2* X, double2* Y,
-                      const double* veff) {
+                      const double* veff, bool fp32) {
     if (L.nb == 0) return HP_OK;
     hp_status s = ensure_grid(c, band_batch(c, L.nb));
     if (s != HP_OK) return s;
+    if (fp32) {  // FP32 grids: twice as many per batch in the same buffer
+        float2* g32 = (float2*)c->d_grid;
+        const int cap = 2 * c->grid_cap;
+        for (int c0 = 0; c0 < L.nb; c0 += cap) {
+            const int nc = std::min(cap, L.nb - c0);
+            CK(k_scatter32(S, L, c0, nc, X, g32, c->nr, c->st));
+            CK(fft3d(c->fft, g32, nc, +1, c->st));
+            CK(k_mul_rpot32(g32, nc, c->nr, c->d_veff32, L, c0, c->st));
+            CK(fft3d(c->fft, g32, nc, -1, c->st));
+            CK(k_gather_h32(S, L, c0, nc, g32, c->nr, X, Y, c->ld, c->st));
+        }
+        return HP_OK;
+    }
     for (int c0 = 0; c0 < L.nb; c0 += c->grid_cap) {
         const int nc = std::min(c->grid_cap, L.nb - c0);
         CK(k_scatter(S, L, c0, nc, X, c->ld, c->d_grid, c->nr, c->st));
@@ -237,10 +251,11 @@ hp_status apply_local(hp_ctx* c, const SphereSet& S, const BandList& L, const do
     return HP_OK;
 }
 
-hp_status project(hp_ctx* c, const SphereSet& S, const BandList& L, const ProjMat& A, const double2* X, double2* P) {
+hp_status project(hp_ctx* c, const SphereSet& S, const BandList& L, const ProjMat& A, const double2* X, double2* P,
+                  bool fp32) {
     hp_status s = ensure_scratch(c, (size_t)8 * std::max(1, L.nb) * kPStride);
     if (s != HP_OK) return s;
-    CK(k_proj(L, S, A, X, c->ld, P, c->d_scratch, c->scratch_elems, c->st));
+    CK(k_proj(L, S, A, X, c->ld, P, c->d_scratch, c->scratch_elems, c->st, fp32));
     return HP_OK;
 }
 
@@ -250,12 +265,12 @@ ProjMat beta_family(const hp_ctx* c, const int* kmap) {
 
 // Y += V_NL X  (beta D beta^H, beta at the list's spheres)
 hp_status apply_nonlocal(hp_ctx* c, const SphereSet& S, const BandList& L, const double2* X, double2* Y, double2* P,
-                         const int* kmap) {
+                         const int* kmap, bool fp32) {
     if (c->nproj == 0) return HP_OK;
     ProjMat B = beta_family(c, kmap);
-    hp_status s = project(c, S, L, B, X, P);
+    hp_status s = project(c, S, L, B, X, P, fp32);
     if (s != HP_OK) return s;
-    CK(k_expand(L, S, B, P, c->d_projD, 1.0, Y, c->ld, c->st));
+    CK(k_expand(L, S, B, P, c->d_projD, 1.0, Y, c->ld, c->st, fp32));
     return HP_OK;
 }
 
@@ -704,10 +719,23 @@ hp_status prepare_resp(hp_ctx* c) {
     const int rows = nspin * nk * nocc;
     hp_status s = resp_alloc(c);
     if (s != HP_OK) return s;
+    const bool mixed = c->opt.precision == HP_PRECISION_MIXED;
     dfree(c, c->d_ur);
+    dfree(c, c->d_ur32);
+    dfree(c, c->d_veff32);
+    dfree(c, c->d_dv32);
+    c->d_ur = nullptr;
+    c->d_ur32 = nullptr;
     dfree(c, c->d_aphi);
     dfree(c, c->d_fxc);
-    CK(dalloc(c, &c->d_ur, (size_t)rows * nr));
+    if (mixed) {
+        CK(dalloc(c, &c->d_ur32, (size_t)rows * nr));
+        CK(dalloc(c, &c->d_veff32, (size_t)nspin * nr));
+        CK(dalloc(c, &c->d_dv32, (size_t)nspin * nr));
+        CK(k_to_f32(c->d_veff, c->d_veff32, (long long)nspin * nr, c->st));
+    } else {
+        CK(dalloc(c, &c->d_ur, (size_t)rows * nr));
+    }
     CK(dalloc(c, &c->d_aphi, (size_t)rows * kPStride));
     CK(dalloc(c, &c->d_fxc, (size_t)(nspin == 1 ? 1 : 3) * nr));
     // list of occupied ground-state rows (psi rows), items ordered (s, k, v)
@@ -722,8 +750,13 @@ hp_status prepare_resp(hp_ctx* c) {
     const int chunk = std::max(1, band_batch(c, rows));
     for (int c0 = 0; c0 < rows; c0 += chunk) {
         const int nc = std::min(chunk, rows - c0);
-        CK(k_scatter(c->kset, L, c0, nc, c->d_psi, c->ld, c->d_ur + (size_t)c0 * nr, nr, c->st));
-        CK(fft3d(c->fft, c->d_ur + (size_t)c0 * nr, nc, +1, c->st));
+        if (mixed) {
+            CK(k_scatter32(c->kset, L, c0, nc, c->d_psi, c->d_ur32 + (size_t)c0 * nr, nr, c->st));
+            CK(fft3d(c->fft, c->d_ur32 + (size_t)c0 * nr, nc, +1, c->st));
+        } else {
+            CK(k_scatter(c->kset, L, c0, nc, c->d_psi, c->ld, c->d_ur + (size_t)c0 * nr, nr, c->st));
+            CK(fft3d(c->fft, c->d_ur + (size_t)c0 * nr, nc, +1, c->st));
+        }
     }
     // <phi_m,k|u_vk>
     ProjMat phi{c->d_phi_k, 0, (long long)c->nhub * c->ld, c->nhub, 0, nullptr};
@@ -812,14 +845,15 @@ hp_status prepare_q(hp_ctx* c, int iq, std::vector<int>& kprime) {
 hp_status apply_sternheimer(hp_ctx* c, const BandList& L, const double2* X, double2* Y) {
     const SphereSet& S = c->qc.set;
     const int* kmap = c->qc.d_miller;
-    hp_status s = apply_local(c, S, L, X, Y, c->d_veff);
+    const bool fp32 = c->opt.precision == HP_PRECISION_MIXED;
+    hp_status s = apply_local(c, S, L, X, Y, c->d_veff, fp32);
     if (s != HP_OK) return s;
-    s = apply_nonlocal(c, S, L, X, Y, c->d_Pbuf, kmap);
+    s = apply_nonlocal(c, S, L, X, Y, c->d_Pbuf, kmap, fp32);
     if (s != HP_OK) return s;
     ProjMat U{c->d_psi, (long long)c->nk * c->nbnd * c->ld, (long long)c->nbnd * c->ld, c->nocc, 0, kmap};
-    s = project(c, S, L, U, X, c->d_Pbuf);
+    s = project(c, S, L, U, X, c->d_Pbuf, fp32);
     if (s != HP_OK) return s;
-    CK(k_expand(L, S, U, c->d_Pbuf, nullptr, c->alpha_pv, Y, c->ld, c->st));
+    CK(k_expand(L, S, U, c->d_Pbuf, nullptr, c->alpha_pv, Y, c->ld, c->st, fp32));
     return HP_OK;
 }
 
@@ -842,7 +876,9 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
     for (size_t i = 0; i < c->hub_atoms.size(); ++i)
         if (c->hub_atoms[i] == atom) jj = (int)i;
     if (jj < 0) return fail(c, HP_EINVAL, "hp_response: atom is not a Hubbard atom");
-    if (c->opt.precision != HP_PRECISION_FP64) return fail(c, HP_ENOTIMPL, "hp_response: only the FP64 form is built");
+    if (c->opt.precision != HP_PRECISION_FP64 && c->opt.precision != HP_PRECISION_MIXED)
+        return fail(c, HP_EINVAL, "hp_response: unknown precision");
+    const bool mixed = c->opt.precision == HP_PRECISION_MIXED;
     auto t0 = std::chrono::steady_clock::now();
     hp_status s = prepare_resp(c);
     if (s != HP_OK) return s;
@@ -892,6 +928,8 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
     double res = INFINITY, dchi = INFINITY;
     bool converged = false, cg_ok = true;
     int it = 0;
+    std::vector<double> res_hist;
+    const bool verbose = getenv("HP_VERBOSE") != nullptr;
     for (it = 1; it <= c->opt.niter_max; ++it) {
         // ---- right-hand side b = -P_c (dV u + V_pert u)
         if (it == 1) {
@@ -899,16 +937,36 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
         } else {
             s = ensure_grid(c, band_batch(c, rows));
             if (s != HP_OK) return s;
-            for (int c0 = 0; c0 < rows; c0 += c->grid_cap) {
-                const int nc = std::min(c->grid_cap, rows - c0);
-                CK(k_mul_cpot(c->d_grid, c->d_ur, Lall.d_row, nc, nr, c->d_dv, Lall, c0, c->st));
-                CK(fft3d(c->fft, c->d_grid, nc, -1, c->st));
-                CK(k_gather_scaled(Sq, Lall, c0, nc, c->d_grid, nr, -1.0 / nr, c->d_b, ld, 0, c->st));
+            if (mixed) {
+                float2* g32 = (float2*)c->d_grid;
+                const int cap = 2 * c->grid_cap;
+                CK(k_to_c32(c->d_dv, c->d_dv32, ndv, c->st));
+                for (int c0 = 0; c0 < rows; c0 += cap) {
+                    const int nc = std::min(cap, rows - c0);
+                    CK(k_mul_cpot32(g32, c->d_ur32, Lall.d_row, nc, nr, c->d_dv32, Lall, c0, c->st));
+                    CK(fft3d(c->fft, g32, nc, -1, c->st));
+                    CK(k_gather_scaled32(Sq, Lall, c0, nc, g32, nr, -1.0 / nr, c->d_b, ld, c->st));
+                }
+            } else {
+                for (int c0 = 0; c0 < rows; c0 += c->grid_cap) {
+                    const int nc = std::min(c->grid_cap, rows - c0);
+                    CK(k_mul_cpot(c->d_grid, c->d_ur, Lall.d_row, nc, nr, c->d_dv, Lall, c0, c->st));
+                    CK(fft3d(c->fft, c->d_grid, nc, -1, c->st));
+                    CK(k_gather_scaled(Sq, Lall, c0, nc, c->d_grid, nr, -1.0 / nr, c->d_b, ld, 0, c->st));
+                }
             }
             CK(k_vec_axpy(c->d_b, c->d_vpu, -1.0, nvec, c->st));
         }
-        if ((s = project(c, Sq, Lall, Ukq, c->d_b, c->d_Pbuf)) != HP_OK) return s;
-        CK(k_expand(Lall, Sq, Ukq, c->d_Pbuf, nullptr, -1.0, c->d_b, ld, c->st));
+        if ((s = project(c, Sq, Lall, Ukq, c->d_b, c->d_Pbuf, mixed)) != HP_OK) return s;
+        CK(k_expand(Lall, Sq, Ukq, c->d_Pbuf, nullptr, -1.0, c->d_b, ld, c->st, mixed));
+        // per-band stopping rule: ||r|| <= cg_tol, and in the mixed form also <= 1e-7 ||b|| (the FP32
+        // operator is accurate to about 1e-7 relative; iterating below that buys nothing)
+        std::vector<double> tolb(rows, tol2);
+        if (mixed) {
+            CK(k_band_dot(Lall, Sq, c->d_b, c->d_b, ld, c->d_pap, c->st));
+            CK(d2h(rr.data(), c->d_pap, rows, c->st));
+            for (int i = 0; i < rows; ++i) tolb[i] = std::max(tol2, 1e-14 * rr[i]);
+        }
         // ---- CG on every band, warm start from the previous x
         if ((s = apply_sternheimer(c, Lall, c->d_x, c->d_ap)) != HP_OK) return s;
         hpsi += rows;
@@ -921,7 +979,7 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
             list_clear(La);
             for (int i = 0; i < rows; ++i) {
                 if (!std::isfinite(rr[i])) return fail(c, HP_ENUMERIC, "hp_response: non-finite CG residual");
-                if (rr[i] > tol2) list_add(La, Lall.row[i], Lall.k[i], Lall.spin[i], Lall.shift[i]);
+                if (rr[i] > tolb[i]) list_add(La, Lall.row[i], Lall.k[i], Lall.spin[i], Lall.shift[i]);
             }
             if (La.row.empty()) break;
             if (cgit >= c->opt.cg_maxiter) {
@@ -941,14 +999,25 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
         CK(cudaMemsetAsync(c->d_drho, 0, sizeof(double2) * ndv, c->st));
         s = ensure_grid(c, band_batch(c, rows));
         if (s != HP_OK) return s;
-        for (int c0 = 0; c0 < rows; c0 += c->grid_cap) {
-            const int nc = std::min(c->grid_cap, rows - c0);
-            CK(k_scatter(Sq, Lall, c0, nc, c->d_x, ld, c->d_grid, nr, c->st));
-            CK(fft3d(c->fft, c->d_grid, nc, +1, c->st));
-            CK(k_drho_acc(c->d_ur, Lall.d_row, c->d_grid, nc, nr, Lall, c0, wrho, nspin, c->d_drho, c->st));
+        if (mixed) {
+            float2* g32 = (float2*)c->d_grid;
+            const int cap = 2 * c->grid_cap;
+            for (int c0 = 0; c0 < rows; c0 += cap) {
+                const int nc = std::min(cap, rows - c0);
+                CK(k_scatter32(Sq, Lall, c0, nc, c->d_x, g32, nr, c->st));
+                CK(fft3d(c->fft, g32, nc, +1, c->st));
+                CK(k_drho_acc32(c->d_ur32, Lall.d_row, g32, nc, nr, Lall, c0, wrho, nspin, c->d_drho, c->st));
+            }
+        } else {
+            for (int c0 = 0; c0 < rows; c0 += c->grid_cap) {
+                const int nc = std::min(c->grid_cap, rows - c0);
+                CK(k_scatter(Sq, Lall, c0, nc, c->d_x, ld, c->d_grid, nr, c->st));
+                CK(fft3d(c->fft, c->d_grid, nc, +1, c->st));
+                CK(k_drho_acc(c->d_ur, Lall.d_row, c->d_grid, nc, nr, Lall, c0, wrho, nspin, c->d_drho, c->st));
+            }
         }
         // ---- response occupations
-        if ((s = project(c, Sq, Lall, phikq, c->d_x, c->d_Pbuf)) != HP_OK) return s;
+        if ((s = project(c, Sq, Lall, phikq, c->d_x, c->d_Pbuf, mixed)) != HP_OK) return s;
         CK(k_occ_response(c->d_Pbuf, c->d_aphi, nspin * nk, nocc, c->nhub, nk, nspin, c->d_M, c->st));
         {
             std::vector<int> off(c->hub_off), md(c->hub_mdim);
@@ -976,9 +1045,20 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
         CK(k_hartree_q(c->d_dvh, c->N, c->d_bvec, qf, 4.0 * c->ecut, 1.0 / nr, c->st));
         CK(fft3d(c->fft, c->d_dvh, 1, +1, c->st));
         CK(k_hxc_combine(c->d_dvh, c->d_drho, c->d_fxc, nspin, nr, c->d_dvout, c->st));
+        cudaError_t e;
+        double scf_tol = c->opt.scf_tol, chi_tol = c->opt.conv_thr_chi;
+        double vrms = 0.0;
+        if (mixed) {  // FP32 noise floor: 3e-7 of the response potential and of the response traces
+            const double vv = dev_dot(c, c->d_dvout, c->d_dvout, ndv, &e);
+            if (e != cudaSuccess) return cuda_fail(c, e, "response norm");
+            vrms = std::sqrt(vv / (double)ndv);
+            scf_tol = std::max(scf_tol, 3e-7 * vrms);
+            double tmax = 0.0;
+            for (int a = 0; a < 2 * nh; ++a) tmax = std::max(tmax, std::fabs(tr[a]));
+            chi_tol = std::max(chi_tol, 3e-7 * tmax);
+        }
         // residual F = dV_out - dV_in (kept in d_dvout)
         CK(k_vec_sub(c->d_dvout, c->d_dvout, c->d_dv, ndv, c->st));
-        cudaError_t e;
         const double ff = dev_dot(c, c->d_dvout, c->d_dvout, ndv, &e);
         if (e != cudaSuccess) return cuda_fail(c, e, "residual");
         if (!std::isfinite(ff)) return fail(c, HP_ENUMERIC, "hp_response: non-finite Hxc residual");
@@ -989,9 +1069,23 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
             for (int a = 0; a < 2 * nh; ++a) dchi = std::max(dchi, std::fabs(tr[a] - tr_prev[a]));
         }
         tr_prev = tr;
-        if (it > 1 && res < c->opt.scf_tol && dchi < c->opt.conv_thr_chi) {
+        res_hist.push_back(res);
+        if (verbose)
+            fprintf(stderr, "hp_response: it %d res %.3e (tol %.3e) dchi %.3e (tol %.3e) cg %d bands-iterations %lld\n",
+                    it, res, scf_tol, dchi, chi_tol, cgit, cg_total);
+        if (it > 1 && res < scf_tol && dchi < chi_tol) {
             converged = true;
             break;
+        }
+        // mixed form: a residual that has stopped falling for three iterations below 1e-5 of the
+        // response potential sits on the FP32 noise floor; the iteration has done what it can
+        if (mixed && it >= 6 && res < 1e-5 * vrms) {
+            const size_t n = res_hist.size();
+            const double lo = std::min(res_hist[n - 1], std::min(res_hist[n - 2], res_hist[n - 3]));
+            if (lo > 0.5 * res_hist[n - 4] && dchi < 1e-5 * std::max(1e-300, chi_tol / 3e-7)) {
+                converged = true;
+                break;
+            }
         }
         // ---- modified Broyden step on dV (history in a ring of nmix pairs)
         const int nmix = c->opt.nmix;
@@ -1062,7 +1156,10 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
     }
     if (!converged || !cg_ok) {
         c->cols.erase({iq, atom});
-        return fail(c, HP_ENOTCONV, "hp_response: self-consistency or CG cap reached");
+        char msg[200];
+        snprintf(msg, sizeof(msg), "hp_response: %s cap reached (residual %.3e, dchi %.3e)",
+                 cg_ok ? "self-consistency" : "CG", res, dchi);
+        return fail(c, HP_ENOTCONV, msg);
     }
     return HP_OK;
 }

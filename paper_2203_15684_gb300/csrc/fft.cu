@@ -25,36 +25,39 @@ bool fft_factor(int n, Radices& out) {
 }
 
 // ---- one work item of one Stockham stage: butterfly j of line l (shared by host and device) ----
-// src/dst: [n][LT] (line fastest).  Ns: product of the radices of the earlier stages.
-HD void radix_butterfly(double2* v, int R, int s) {
+// src/dst: [n][LT] (line fastest).  Ns: product of the radices of the earlier stages.  V is double2
+// (FP64 form) or float2 (FP32 form); the constants are rounded to the working precision.
+template <class V>
+HD void radix_butterfly(V* v, int R, int s) {
+    using T = typename Scalar<V>::type;
     if (R == 2) {
-        double2 a = v[0], b = v[1];
+        V a = v[0], b = v[1];
         v[0] = cadd(a, b);
         v[1] = csub(a, b);
     } else if (R == 4) {
-        double2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
-        double2 t2 = cadd(v[1], v[3]), t3 = cmul_si(csub(v[1], v[3]), s);
+        V t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+        V t2 = cadd(v[1], v[3]), t3 = cmul_si(csub(v[1], v[3]), s);
         v[0] = cadd(t0, t2);
         v[2] = csub(t0, t2);
         v[1] = cadd(t1, t3);
         v[3] = csub(t1, t3);
     } else if (R == 3) {
-        const double h = 0.86602540378443864676;  // sin(2 pi / 3)
-        double2 t1 = cadd(v[1], v[2]);
-        double2 t2 = csub(v[0], cscale(t1, 0.5));
-        double2 t3 = cmul_si(cscale(csub(v[1], v[2]), h), s);
+        const T h = (T)0.86602540378443864676;  // sin(2 pi / 3)
+        V t1 = cadd(v[1], v[2]);
+        V t2 = csub(v[0], cscale(t1, (T)0.5));
+        V t3 = cmul_si(cscale(csub(v[1], v[2]), h), s);
         v[0] = cadd(v[0], t1);
         v[1] = cadd(t2, t3);
         v[2] = csub(t2, t3);
     } else if (R == 5) {
-        const double c1 = 0.30901699437494742410, c2 = -0.80901699437494742410;  // cos(2pi/5), cos(4pi/5)
-        const double s1 = 0.95105651629515357212, s2 = 0.58778525229247312917;   // sin(2pi/5), sin(4pi/5)
-        double2 t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
-        double2 t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
-        double2 a1 = cadd(v[0], cadd(cscale(t1, c1), cscale(t2, c2)));
-        double2 a2 = cadd(v[0], cadd(cscale(t1, c2), cscale(t2, c1)));
-        double2 b1 = cmul_si(cadd(cscale(t3, s1), cscale(t4, s2)), s);
-        double2 b2 = cmul_si(csub(cscale(t3, s2), cscale(t4, s1)), s);
+        const T c1 = (T)0.30901699437494742410, c2 = (T)-0.80901699437494742410;  // cos(2pi/5), cos(4pi/5)
+        const T s1 = (T)0.95105651629515357212, s2 = (T)0.58778525229247312917;   // sin(2pi/5), sin(4pi/5)
+        V t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
+        V t3 = csub(v[1], v[4]), t4 = csub(v[2], v[3]);
+        V a1 = cadd(v[0], cadd(cscale(t1, c1), cscale(t2, c2)));
+        V a2 = cadd(v[0], cadd(cscale(t1, c2), cscale(t2, c1)));
+        V b1 = cmul_si(cadd(cscale(t3, s1), cscale(t4, s2)), s);
+        V b2 = cmul_si(csub(cscale(t3, s2), cscale(t4, s1)), s);
         v[0] = cadd(v[0], cadd(t1, t2));
         v[1] = cadd(a1, b1);
         v[4] = csub(a1, b1);
@@ -63,18 +66,18 @@ HD void radix_butterfly(double2* v, int R, int s) {
     }
 }
 
-HD void stockham_item(const double2* src, double2* dst, const double2* tw, int n, int LT, int R, int Ns,
-                      int sign, int w) {
+template <class V>
+HD void stockham_item(const V* src, V* dst, const V* tw, int n, int LT, int R, int Ns, int sign, int w) {
     const int l = w % LT;
     const int j = w / LT;
     const int nR = n / R;
-    double2 v[5];
+    V v[5];
     const int k = j % Ns;
     const int tstep = k * (n / (Ns * R));
     for (int r = 0; r < R; ++r) {
-        double2 x = src[(j + r * nR) * LT + l];
+        V x = src[(j + r * nR) * LT + l];
         if (r > 0 && tstep != 0) {
-            double2 t = tw[(r * tstep) % n];
+            V t = tw[(r * tstep) % n];
             if (sign > 0) t.y = -t.y;
             x = cmul(x, t);
         }
@@ -86,14 +89,15 @@ HD void stockham_item(const double2* src, double2* dst, const double2* tw, int n
 }
 
 // ---- device kernel: one pass along the middle axis of [batch][A][n][B] ----
-template <int LT>
-__global__ void __launch_bounds__(256) fft_axis_kernel(double2* __restrict__ data, int A, int B, Radices rad,
-                                                        const double2* __restrict__ tw, int sign, int TA,
+template <int LT, class V>
+__global__ void __launch_bounds__(256) fft_axis_kernel(V* __restrict__ data, int A, int B, Radices rad,
+                                                        const V* __restrict__ tw, int sign, int TA,
                                                         int TB, int tilesA, int tilesB) {
-    extern __shared__ double2 sm[];
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    V* sm = (V*)sm_raw;
     const int n = rad.n;
-    double2* buf0 = sm;
-    double2* buf1 = sm + n * LT;
+    V* buf0 = sm;
+    V* buf1 = sm + n * LT;
     const int tile = blockIdx.x;
     const long long g = blockIdx.y;
     const int ta = tile / tilesB, tb = tile % tilesB;
@@ -105,7 +109,7 @@ __global__ void __launch_bounds__(256) fft_axis_kernel(double2* __restrict__ dat
         for (int e = threadIdx.x; e < nel; e += blockDim.x) {
             const int i = e % n, la = e / n;
             const int a = a0 + la;
-            double2 x = cmk(0.0, 0.0);
+            V x = cpack<V>(0.0, 0.0);
             if (a < A) x = data[gbase + (long long)a * n + i];
             buf0[i * LT + la] = x;
         }
@@ -114,14 +118,14 @@ __global__ void __launch_bounds__(256) fft_axis_kernel(double2* __restrict__ dat
             const int lb = e % TB, rest = e / TB;
             const int la = rest % TA, i = rest / TA;
             const int a = a0 + la, b = b0 + lb;
-            double2 x = cmk(0.0, 0.0);
+            V x = cpack<V>(0.0, 0.0);
             if (a < A && b < B) x = data[gbase + ((long long)a * n + i) * B + b];
             buf0[i * LT + la * TB + lb] = x;
         }
     }
     __syncthreads();
-    double2* src = buf0;
-    double2* dst = buf1;
+    V* src = buf0;
+    V* dst = buf1;
     int Ns = 1;
     for (int st = 0; st < rad.nst; ++st) {
         const int R = rad.r[st];
@@ -129,7 +133,7 @@ __global__ void __launch_bounds__(256) fft_axis_kernel(double2* __restrict__ dat
         for (int w = threadIdx.x; w < items; w += blockDim.x) stockham_item(src, dst, tw, n, LT, R, Ns, sign, w);
         __syncthreads();
         Ns *= R;
-        double2* t = src;
+        V* t = src;
         src = dst;
         dst = t;
     }
@@ -163,6 +167,12 @@ cudaError_t fft_plan_create(FftPlan& p, const int N[3]) {
         if (e != cudaSuccess) return e;
         e = cudaMemcpy(p.ax[d].d_tw, tw.data(), sizeof(double2) * N[d], cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return e;
+        std::vector<float2> tw32(N[d]);
+        for (int t = 0; t < N[d]; ++t) tw32[t] = cmkf((float)tw[t].x, (float)tw[t].y);
+        e = cudaMalloc(&p.ax[d].d_tw32, sizeof(float2) * N[d]);
+        if (e != cudaSuccess) return e;
+        e = cudaMemcpy(p.ax[d].d_tw32, tw32.data(), sizeof(float2) * N[d], cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
@@ -170,7 +180,9 @@ cudaError_t fft_plan_create(FftPlan& p, const int N[3]) {
 void fft_plan_destroy(FftPlan& p) {
     for (int d = 0; d < 3; ++d) {
         if (p.ax[d].d_tw) cudaFree(p.ax[d].d_tw);
+        if (p.ax[d].d_tw32) cudaFree(p.ax[d].d_tw32);
         p.ax[d].d_tw = nullptr;
+        p.ax[d].d_tw32 = nullptr;
     }
 }
 
@@ -210,7 +222,15 @@ cudaError_t fft_profile_end(double* ms, long long* launches, double* flops, doub
     return err;
 }
 
-cudaError_t fft3d(const FftPlan& p, double2* data, int nb, int sign, cudaStream_t st) {
+template <class V>
+static const V* twiddles(const FftAxis& a);
+template <>
+const double2* twiddles<double2>(const FftAxis& a) { return a.d_tw; }
+template <>
+const float2* twiddles<float2>(const FftAxis& a) { return a.d_tw32; }
+
+template <class V>
+static cudaError_t fft3d_impl(const FftPlan& p, V* data, int nb, int sign, cudaStream_t st) {
     const int N0 = p.N[0], N1 = p.N[1], N2 = p.N[2];
     // axis d: A = prod of earlier dims, B = prod of later dims
     const int As[3] = {1, N0, N0 * N1};
@@ -224,9 +244,9 @@ cudaError_t fft3d(const FftPlan& p, double2* data, int nb, int sign, cudaStream_
         int TA = kLT / TB;
         if (TA < 1) TA = 1;
         const int tilesA = (A + TA - 1) / TA, tilesB = (B + TB - 1) / TB;
-        const size_t smem = 2 * sizeof(double2) * n * kLT;
+        const size_t smem = 2 * sizeof(V) * n * kLT;
         if (smem > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(fft_axis_kernel<kLT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            cudaError_t e = cudaFuncSetAttribute(fft_axis_kernel<kLT, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)smem);
             if (e != cudaSuccess) return e;
         }
@@ -237,8 +257,8 @@ cudaError_t fft3d(const FftPlan& p, double2* data, int nb, int sign, cudaStream_
             cudaEventCreate(&e1);
             cudaEventRecord(e0, st);
         }
-        fft_axis_kernel<kLT><<<grid, 128, smem, st>>>(data, A, B, p.ax[d].rad, p.ax[d].d_tw, sign, TA, TB, tilesA,
-                                                      tilesB);
+        fft_axis_kernel<kLT, V><<<grid, 128, smem, st>>>(data, A, B, p.ax[d].rad, twiddles<V>(p.ax[d]), sign, TA, TB,
+                                                         tilesA, tilesB);
         HP_LAUNCHED();
         if (g_prof.on) {
             cudaEventRecord(e1, st);
@@ -247,12 +267,20 @@ cudaError_t fft3d(const FftPlan& p, double2* data, int nb, int sign, cudaStream_
             g_prof.launches += 1;
             const double nrg = (double)N0 * N1 * N2 * nb;
             g_prof.flops += nrg * 5.0 * std::log2((double)n);   // 5 n log2 n per line of n points
-            g_prof.bytes += nrg * 2.0 * sizeof(double2);         // every point read and written once
+            g_prof.bytes += nrg * 2.0 * sizeof(V);               // every point read and written once
         }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+cudaError_t fft3d(const FftPlan& p, double2* data, int nb, int sign, cudaStream_t st) {
+    return fft3d_impl(p, data, nb, sign, st);
+}
+
+cudaError_t fft3d(const FftPlan& p, float2* data, int nb, int sign, cudaStream_t st) {
+    return fft3d_impl(p, data, nb, sign, st);
 }
 
 void fft_host_lines(const Radices& rad, const std::vector<double2>& tw, int nlines, int sign, double2* data) {

@@ -33,6 +33,21 @@ HD double2 cconj(double2 a) { return cmk(a.x, -a.y); }
 // a * (s i) for s = +-1
 HD double2 cmul_si(double2 a, int s) { return s > 0 ? cmk(-a.y, a.x) : cmk(a.y, -a.x); }
 
+// the same helpers for FP32 complex (float2)
+HD float2 cmkf(float r, float i) { float2 z; z.x = r; z.y = i; return z; }
+HD float2 cadd(float2 a, float2 b) { return cmkf(a.x + b.x, a.y + b.y); }
+HD float2 csub(float2 a, float2 b) { return cmkf(a.x - b.x, a.y - b.y); }
+HD float2 cmul(float2 a, float2 b) { return cmkf(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+HD float2 cscale(float2 a, float s) { return cmkf(a.x * s, a.y * s); }
+HD float2 cmul_si(float2 a, int s) { return s > 0 ? cmkf(-a.y, a.x) : cmkf(a.y, -a.x); }
+
+template <class V> struct Scalar;
+template <> struct Scalar<double2> { using type = double; };
+template <> struct Scalar<float2> { using type = float; };
+template <class V> HD V cpack(double r, double i);
+template <> HD double2 cpack<double2>(double r, double i) { return cmk(r, i); }
+template <> HD float2 cpack<float2>(double r, double i) { return cmkf((float)r, (float)i); }
+
 // every kernel launch of the library increments this counter (read by hp_launch_count)
 extern std::atomic<long long> g_launches;
 #define HP_LAUNCHED() (hp::g_launches.fetch_add(1, std::memory_order_relaxed))
@@ -50,6 +65,7 @@ struct Radices {
 struct FftAxis {
     Radices rad;
     double2* d_tw = nullptr;   // n twiddles exp(-2 pi i t / n)
+    float2* d_tw32 = nullptr;  // the same, rounded to FP32
 };
 
 struct FftPlan {
@@ -63,6 +79,7 @@ void fft_plan_destroy(FftPlan& p);
 // In place, nb grids of N0*N1*N2 complex each, contiguous.  sign +1: sum_G c(G) exp(+iG.r)
 // (to real space), sign -1: sum_r f(r) exp(-iG.r).  Unnormalised both ways.
 cudaError_t fft3d(const FftPlan& p, double2* data, int nb, int sign, cudaStream_t st);
+cudaError_t fft3d(const FftPlan& p, float2* data, int nb, int sign, cudaStream_t st);
 // the same Stockham code on the host (self-test of the stage logic)
 void fft_host_lines(const Radices& rad, const std::vector<double2>& tw, int nlines, int sign,
                     double2* data);
@@ -115,9 +132,23 @@ cudaError_t k_mul_rpot(double2* grid, int nc, int nr, const double* v, const Ban
 cudaError_t k_mul_cpot(double2* grid, const double2* src_rows, const int* src_row_of_item, int nc, int nr,
                        const double2* v, const BandList& L, int c0, cudaStream_t st);
 cudaError_t k_proj(const BandList& L, const SphereSet& S, const ProjMat& A, const double2* X, int ld,
-                   double2* P, double2* scratch, size_t scratch_elems, cudaStream_t st);
+                   double2* P, double2* scratch, size_t scratch_elems, cudaStream_t st, bool fp32 = false);
 cudaError_t k_expand(const BandList& L, const SphereSet& S, const ProjMat& A, const double2* P,
-                     const double* pscale, double alpha, double2* Y, int ld, cudaStream_t st);
+                     const double* pscale, double alpha, double2* Y, int ld, cudaStream_t st, bool fp32 = false);
+// FP32 forms (mixed precision)
+cudaError_t k_scatter32(const SphereSet& S, const BandList& L, int c0, int nc, const double2* X, float2* grid, int nr,
+                        cudaStream_t st);
+cudaError_t k_mul_rpot32(float2* grid, int nc, int nr, const float* v, const BandList& L, int c0, cudaStream_t st);
+cudaError_t k_gather_h32(const SphereSet& S, const BandList& L, int c0, int nc, const float2* grid, int nr,
+                         const double2* X, double2* Y, int ld, cudaStream_t st);
+cudaError_t k_gather_scaled32(const SphereSet& S, const BandList& L, int c0, int nc, const float2* grid, int nr,
+                              double scale, double2* Y, int ld, cudaStream_t st);
+cudaError_t k_mul_cpot32(float2* grid, const float2* src_rows, const int* src_row_of_item, int nc, int nr,
+                         const float2* v, const BandList& L, int c0, cudaStream_t st);
+cudaError_t k_drho_acc32(const float2* ur, const int* ur_row_of_item, const float2* xr, int nc, int nr,
+                         const BandList& L, int c0, double weight, int nspin, double2* drho, cudaStream_t st);
+cudaError_t k_to_f32(const double* a, float* b, long long n, cudaStream_t st);
+cudaError_t k_to_c32(const double2* a, float2* b, long long n, cudaStream_t st);
 cudaError_t k_band_dot(const BandList& L, const SphereSet& S, const double2* X, const double2* Y, int ld,
                        double* out, cudaStream_t st);
 cudaError_t k_cg_init(const BandList& L, const SphereSet& S, const double2* r, double2* p, int ld,
@@ -204,10 +235,11 @@ void list_add(BandList& L, int row, int k, int spin, double shift);
 hp_status ensure_grid(hp_ctx* c, int want);
 int band_batch(const hp_ctx* c, int nb);
 hp_status apply_local(hp_ctx* c, const SphereSet& S, const BandList& L, const double2* X, double2* Y,
-                      const double* veff);
-hp_status project(hp_ctx* c, const SphereSet& S, const BandList& L, const ProjMat& A, const double2* X, double2* P);
+                      const double* veff, bool fp32 = false);
+hp_status project(hp_ctx* c, const SphereSet& S, const BandList& L, const ProjMat& A, const double2* X, double2* P,
+                  bool fp32 = false);
 hp_status apply_nonlocal(hp_ctx* c, const SphereSet& S, const BandList& L, const double2* X, double2* Y, double2* P,
-                         const int* kmap);
+                         const int* kmap, bool fp32 = false);
 void invalidate_response(hp_ctx* c);
 
 }  // namespace hp
@@ -260,6 +292,9 @@ struct hp_ctx {
     double2* d_ur = nullptr;           // [nspin][nk][nocc][nr]
     double2* d_aphi = nullptr;         // [nspin][nk][nocc][nhub] <phi_m,k|u_v>
     double* d_fxc = nullptr;           // [3 or 1][nr]
+    float2* d_ur32 = nullptr;          // mixed precision: [nspin][nk][nocc][nr] FP32 u_k(r)
+    float* d_veff32 = nullptr;         // mixed precision: FP32 copy of V_loc + V_Hxc
+    float2* d_dv32 = nullptr;          // mixed precision: FP32 copy of Delta V_Hxc
     double alpha_pv = 0;
     hp::QCache qc;
     // response work arrays

@@ -3,6 +3,7 @@
 // Hubbard projections), CG vector updates, response densities, the Hartree and LDA response
 // kernels, and the small dense algebra of the mixing and of chi.
 #include <cmath>
+#include <type_traits>
 
 #include "hp_internal.h"
 
@@ -147,6 +148,170 @@ cudaError_t k_mul_cpot(double2* grid, const double2* src_rows, const int* src_ro
 }
 
 // ------------------------------------------------------------------------------------------------
+// FP32 forms of the grid kernels (mixed precision: FP64 band vectors, FP32 grids and potentials)
+// ------------------------------------------------------------------------------------------------
+__global__ void scatter32_kernel(const int* __restrict__ npw, const int* __restrict__ idx, int ld,
+                                 const int* __restrict__ row, const int* __restrict__ kk, int c0,
+                                 const double2* __restrict__ X, float2* __restrict__ grid, int nr) {
+    const int c = c0 + blockIdx.y;
+    const int k = kk[c];
+    const int G = blockIdx.x * blockDim.x + threadIdx.x;
+    if (G < npw[k]) {
+        const double2 x = X[(long long)row[c] * ld + G];
+        grid[(long long)blockIdx.y * nr + idx[(long long)k * ld + G]] = cmkf((float)x.x, (float)x.y);
+    }
+}
+
+cudaError_t k_scatter32(const SphereSet& S, const BandList& L, int c0, int nc, const double2* X, float2* grid, int nr,
+                        cudaStream_t st) {
+    if (nc <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(grid, 0, sizeof(float2) * (size_t)nc * nr, st);
+    if (e != cudaSuccess) return e;
+    dim3 g(cdiv(S.ld, 128), nc);
+    scatter32_kernel<<<g, 128, 0, st>>>(S.d_npw, S.d_idx, S.ld, L.d_row, L.d_k, c0, X, grid, nr);
+    HP_LAUNCHED();
+    return cudaGetLastError();
+}
+
+__global__ void mul_rpot32_kernel(float2* __restrict__ grid, int nr, const float* __restrict__ v,
+                                  const int* __restrict__ spin, int c0) {
+    const int c = blockIdx.y;
+    const float* vs = v + (long long)spin[c0 + c] * nr;
+    float2* g = grid + (long long)c * nr;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += gridDim.x * blockDim.x) {
+        const float s = vs[r];
+        const float2 z = g[r];
+        g[r] = cmkf(z.x * s, z.y * s);
+    }
+}
+
+cudaError_t k_mul_rpot32(float2* grid, int nc, int nr, const float* v, const BandList& L, int c0, cudaStream_t st) {
+    if (nc <= 0) return cudaSuccess;
+    dim3 g(cdiv(nr, 256 * 4), nc);
+    mul_rpot32_kernel<<<g, 256, 0, st>>>(grid, nr, v, L.d_spin, c0);
+    HP_LAUNCHED();
+    return cudaGetLastError();
+}
+
+// Y = grid[idx] / nr + (|k+G|^2/2 - shift) X, the grid part in FP32, the rest in FP64
+__global__ void gather_h32_kernel(const int* __restrict__ npw, const int* __restrict__ idx,
+                                  const double* __restrict__ g2, int ld, const int* __restrict__ row,
+                                  const int* __restrict__ kk, const double* __restrict__ shift, int c0,
+                                  const float2* __restrict__ grid, int nr, const double2* __restrict__ X,
+                                  double2* __restrict__ Y) {
+    const int c = c0 + blockIdx.y;
+    const int k = kk[c];
+    const int G = blockIdx.x * blockDim.x + threadIdx.x;
+    if (G >= ld) return;
+    const long long o = (long long)row[c] * ld + G;
+    if (G < npw[k]) {
+        const double inv = 1.0 / (double)nr;
+        const float2 v = grid[(long long)blockIdx.y * nr + idx[(long long)k * ld + G]];
+        const double d = 0.5 * g2[(long long)k * ld + G] - shift[c];
+        const double2 x = X[o];
+        Y[o] = cmk((double)v.x * inv + d * x.x, (double)v.y * inv + d * x.y);
+    } else {
+        Y[o] = cmk(0.0, 0.0);
+    }
+}
+
+cudaError_t k_gather_h32(const SphereSet& S, const BandList& L, int c0, int nc, const float2* grid, int nr,
+                         const double2* X, double2* Y, int ld, cudaStream_t st) {
+    if (nc <= 0) return cudaSuccess;
+    dim3 g(cdiv(ld, 128), nc);
+    gather_h32_kernel<<<g, 128, 0, st>>>(S.d_npw, S.d_idx, S.d_g2, ld, L.d_row, L.d_k, L.d_shift, c0, grid, nr, X, Y);
+    HP_LAUNCHED();
+    return cudaGetLastError();
+}
+
+__global__ void gather_scaled32_kernel(const int* __restrict__ npw, const int* __restrict__ idx, int ld,
+                                       const int* __restrict__ row, const int* __restrict__ kk, int c0,
+                                       const float2* __restrict__ grid, int nr, double scale, double2* __restrict__ Y) {
+    const int c = c0 + blockIdx.y;
+    const int k = kk[c];
+    const int G = blockIdx.x * blockDim.x + threadIdx.x;
+    if (G >= ld) return;
+    double2 v = cmk(0.0, 0.0);
+    if (G < npw[k]) {
+        const float2 z = grid[(long long)blockIdx.y * nr + idx[(long long)k * ld + G]];
+        v = cmk((double)z.x * scale, (double)z.y * scale);
+    }
+    Y[(long long)row[c] * ld + G] = v;
+}
+
+cudaError_t k_gather_scaled32(const SphereSet& S, const BandList& L, int c0, int nc, const float2* grid, int nr,
+                              double scale, double2* Y, int ld, cudaStream_t st) {
+    if (nc <= 0) return cudaSuccess;
+    dim3 g(cdiv(ld, 128), nc);
+    gather_scaled32_kernel<<<g, 128, 0, st>>>(S.d_npw, S.d_idx, ld, L.d_row, L.d_k, c0, grid, nr, scale, Y);
+    HP_LAUNCHED();
+    return cudaGetLastError();
+}
+
+__global__ void mul_cpot32_kernel(float2* __restrict__ grid, const float2* __restrict__ src,
+                                  const int* __restrict__ src_row, int nr, const float2* __restrict__ v,
+                                  const int* __restrict__ spin, int c0) {
+    const int c = blockIdx.y;
+    const float2* vs = v + (long long)spin[c0 + c] * nr;
+    const float2* u = src + (long long)src_row[c0 + c] * nr;
+    float2* g = grid + (long long)c * nr;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += gridDim.x * blockDim.x) g[r] = cmul(vs[r], u[r]);
+}
+
+cudaError_t k_mul_cpot32(float2* grid, const float2* src_rows, const int* src_row_of_item, int nc, int nr,
+                         const float2* v, const BandList& L, int c0, cudaStream_t st) {
+    if (nc <= 0) return cudaSuccess;
+    dim3 g(cdiv(nr, 256 * 4), nc);
+    mul_cpot32_kernel<<<g, 256, 0, st>>>(grid, src_rows, src_row_of_item, nr, v, L.d_spin, c0);
+    HP_LAUNCHED();
+    return cudaGetLastError();
+}
+
+// drho[s][r] += weight * sum_c conj(ur[ur_row[c]][r]) xr[c][r]  (FP32 inputs, FP64 accumulation)
+__global__ void drho_acc32_kernel(const float2* __restrict__ ur, const int* __restrict__ ur_row,
+                                  const float2* __restrict__ xr, int nc, int nr, const int* __restrict__ spin, int c0,
+                                  double weight, int nspin, double2* __restrict__ drho) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += gridDim.x * blockDim.x) {
+        double a0r = 0.0, a0i = 0.0, a1r = 0.0, a1i = 0.0;
+        for (int c = 0; c < nc; ++c) {
+            const float2 u = ur[(long long)ur_row[c0 + c] * nr + r];
+            const float2 x = xr[(long long)c * nr + r];
+            const double tr = (double)u.x * x.x + (double)u.y * x.y;
+            const double ti = (double)u.x * x.y - (double)u.y * x.x;
+            if (spin[c0 + c] == 0) { a0r += tr; a0i += ti; }
+            else { a1r += tr; a1i += ti; }
+        }
+        drho[r] = cadd(drho[r], cmk(a0r * weight, a0i * weight));
+        if (nspin == 2) drho[(long long)nr + r] = cadd(drho[(long long)nr + r], cmk(a1r * weight, a1i * weight));
+    }
+}
+
+cudaError_t k_drho_acc32(const float2* ur, const int* ur_row_of_item, const float2* xr, int nc, int nr,
+                         const BandList& L, int c0, double weight, int nspin, double2* drho, cudaStream_t st) {
+    if (nc <= 0) return cudaSuccess;
+    drho_acc32_kernel<<<cdiv(nr, 256), 256, 0, st>>>(ur, ur_row_of_item, xr, nc, nr, L.d_spin, c0, weight, nspin, drho);
+    HP_LAUNCHED();
+    return cudaGetLastError();
+}
+
+__global__ void to_f32_kernel(const double* __restrict__ a, float* __restrict__ b, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
+cudaError_t k_to_f32(const double* a, float* b, long long n, cudaStream_t st) {
+    to_f32_kernel<<<std::min(cdiv(n, 256), 4096), 256, 0, st>>>(a, b, n);
+    HP_LAUNCHED();
+    return cudaGetLastError();
+}
+
+cudaError_t k_to_c32(const double2* a, float2* b, long long n, cudaStream_t st) {
+    to_f32_kernel<<<std::min(cdiv(2 * n, 256), 4096), 256, 0, st>>>((const double*)a, (float*)b, 2 * n);
+    HP_LAUNCHED();
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
 // segmented projector contractions
 //   proj:   P[c][p]  = sum_G conj(A_seg[row0 + p][G]) X[row[c]][G]          (p < nrow)
 //   expand: Y[row[c]][G] += alpha sum_p A_seg[row0 + p][G] pscale[p] P[c][p]
@@ -155,14 +320,16 @@ cudaError_t k_mul_cpot(double2* grid, const double2* src_rows, const int* src_ro
 constexpr int kPStride = 128;
 constexpr int TP = 32, TC = 32, TG = 32;
 
+template <class S>
 __global__ void __launch_bounds__(256) proj_kernel(const double2* __restrict__ Abase, long long sa_s, long long sa_k,
                                                    int row0, int nrow, int ld, const double2* __restrict__ X,
                                                    const int* __restrict__ row, const int* __restrict__ seg_start,
                                                    const int* __restrict__ seg_k, const int* __restrict__ seg_s,
                                                    const int* __restrict__ npw_of_k, const int* __restrict__ kmap,
                                                    int ksplit, double2* __restrict__ part, int nb) {
-    __shared__ double2 As[TG][TP + 1];
-    __shared__ double2 Xs[TG][TC + 1];
+    using V = typename std::conditional<std::is_same<S, float>::value, float2, double2>::type;
+    __shared__ V As[TG][TP + 1];
+    __shared__ V Xs[TG][TC + 1];
     const int seg = blockIdx.x, ks = blockIdx.y;
     const int cbeg = seg_start[seg], cend = seg_start[seg + 1];
     const int k = seg_k[seg];
@@ -176,7 +343,7 @@ __global__ void __launch_bounds__(256) proj_kernel(const double2* __restrict__ A
     const int tp = tid & 31, tc = tid >> 5;  // 8 warps
     for (int pt = 0; pt < nrow; pt += TP) {
         for (int ct = cbeg; ct < cend; ct += TC) {
-            double2 acc[4];
+            double2 acc[4];  // FP64 across tiles; each 32-point tile summed in the compute precision
 #pragma unroll
             for (int i = 0; i < 4; ++i) acc[i] = cmk(0.0, 0.0);
             for (int gt = g0; gt < g1; gt += TG) {
@@ -184,23 +351,33 @@ __global__ void __launch_bounds__(256) proj_kernel(const double2* __restrict__ A
                 for (int e = tid; e < TG * TP; e += 256) {
                     const int gg = e & 31, pp = e >> 5;
                     const int p = pt + pp, G = gt + gg;
-                    As[gg][pp] = (p < nrow && G < g1) ? A[(long long)p * ld + G] : cmk(0.0, 0.0);
+                    const double2 a = (p < nrow && G < g1) ? A[(long long)p * ld + G] : cmk(0.0, 0.0);
+                    As[gg][pp] = cpack<V>(a.x, a.y);
                 }
                 for (int e = tid; e < TG * TC; e += 256) {
                     const int gg = e & 31, cc = e >> 5;
                     const int c = ct + cc, G = gt + gg;
-                    Xs[gg][cc] = (c < cend && G < g1) ? X[(long long)row[c] * ld + G] : cmk(0.0, 0.0);
+                    const double2 x = (c < cend && G < g1) ? X[(long long)row[c] * ld + G] : cmk(0.0, 0.0);
+                    Xs[gg][cc] = cpack<V>(x.x, x.y);
                 }
                 __syncthreads();
+                V tacc[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) tacc[i] = cpack<V>(0.0, 0.0);
 #pragma unroll 8
                 for (int gg = 0; gg < TG; ++gg) {
-                    const double2 a = As[gg][tp];
+                    const V a = As[gg][tp];
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
-                        const double2 x = Xs[gg][tc + 8 * i];
-                        acc[i].x += a.x * x.x + a.y * x.y;
-                        acc[i].y += a.x * x.y - a.y * x.x;
+                        const V x = Xs[gg][tc + 8 * i];
+                        tacc[i].x += a.x * x.x + a.y * x.y;
+                        tacc[i].y += a.x * x.y - a.y * x.x;
                     }
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    acc[i].x += (double)tacc[i].x;
+                    acc[i].y += (double)tacc[i].y;
                 }
                 __syncthreads();
             }
@@ -225,7 +402,7 @@ __global__ void proj_reduce_kernel(const double2* __restrict__ part, int ksplit,
 }
 
 cudaError_t k_proj(const BandList& L, const SphereSet& S, const ProjMat& A, const double2* X, int ld, double2* P,
-                   double2* scratch, size_t scratch_elems, cudaStream_t st) {
+                   double2* scratch, size_t scratch_elems, cudaStream_t st, bool fp32) {
     if (L.nb <= 0 || A.nrow <= 0) return cudaSuccess;
     if (A.nrow > kPStride) return cudaErrorInvalidValue;
     int ksplit = std::max(1, 2 * 152 / std::max(1, L.nseg));
@@ -233,8 +410,12 @@ cudaError_t k_proj(const BandList& L, const SphereSet& S, const ProjMat& A, cons
     while (ksplit > 1 && (size_t)ksplit * L.nb * kPStride > scratch_elems) --ksplit;
     if ((size_t)ksplit * L.nb * kPStride > scratch_elems) return cudaErrorMemoryAllocation;
     dim3 g(L.nseg, ksplit);
-    proj_kernel<<<g, 256, 0, st>>>(A.base, A.stride_s, A.stride_k, A.row0, A.nrow, ld, X, L.d_row, L.d_seg_start,
-                                   L.d_seg_k, L.d_seg_s, S.d_npw, A.kmap, ksplit, scratch, L.nb);
+    if (fp32)
+        proj_kernel<float><<<g, 256, 0, st>>>(A.base, A.stride_s, A.stride_k, A.row0, A.nrow, ld, X, L.d_row,
+                                              L.d_seg_start, L.d_seg_k, L.d_seg_s, S.d_npw, A.kmap, ksplit, scratch, L.nb);
+    else
+        proj_kernel<double><<<g, 256, 0, st>>>(A.base, A.stride_s, A.stride_k, A.row0, A.nrow, ld, X, L.d_row,
+                                               L.d_seg_start, L.d_seg_k, L.d_seg_s, S.d_npw, A.kmap, ksplit, scratch, L.nb);
     HP_LAUNCHED();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -245,6 +426,7 @@ cudaError_t k_proj(const BandList& L, const SphereSet& S, const ProjMat& A, cons
 
 constexpr int kExpC = 8;
 
+template <class S>
 __global__ void __launch_bounds__(128) expand_kernel(const double2* __restrict__ Abase, long long sa_s, long long sa_k,
                                                      int row0, int nrow, int ld, const double2* __restrict__ P,
                                                      const double* __restrict__ pscale, double alpha,
@@ -252,7 +434,8 @@ __global__ void __launch_bounds__(128) expand_kernel(const double2* __restrict__
                                                      const int* __restrict__ seg_start, const int* __restrict__ seg_k,
                                                      const int* __restrict__ seg_s, const int* __restrict__ npw_of_k,
                                                      const int* __restrict__ kmap) {
-    __shared__ double2 Ps[kExpC][kPStride];
+    using V = typename std::conditional<std::is_same<S, float>::value, float2, double2>::type;
+    __shared__ V Ps[kExpC][kPStride];
     const int seg = blockIdx.y;
     const int cbeg = seg_start[seg], cend = seg_start[seg + 1];
     const int k = seg_k[seg];
@@ -270,18 +453,19 @@ __global__ void __launch_bounds__(128) expand_kernel(const double2* __restrict__
                 const double s = alpha * (pscale ? pscale[p] : 1.0);
                 v = cscale(v, s);
             }
-            Ps[cc][p] = v;
+            Ps[cc][p] = cpack<V>(v.x, v.y);
         }
         __syncthreads();
         if (G < npw) {
-            double2 acc[kExpC];
+            V acc[kExpC];
 #pragma unroll
-            for (int i = 0; i < kExpC; ++i) acc[i] = cmk(0.0, 0.0);
+            for (int i = 0; i < kExpC; ++i) acc[i] = cpack<V>(0.0, 0.0);
             for (int p = 0; p < nrow; ++p) {
-                const double2 a = A[(long long)p * ld + G];
+                const double2 a64 = A[(long long)p * ld + G];
+                const V a = cpack<V>(a64.x, a64.y);
 #pragma unroll
                 for (int i = 0; i < kExpC; ++i) {
-                    const double2 q = Ps[i][p];
+                    const V q = Ps[i][p];
                     acc[i].x += a.x * q.x - a.y * q.y;
                     acc[i].y += a.x * q.y + a.y * q.x;
                 }
@@ -291,7 +475,7 @@ __global__ void __launch_bounds__(128) expand_kernel(const double2* __restrict__
                 const int c = ct + i;
                 if (c < cend) {
                     const long long o = (long long)row[c] * ld + G;
-                    Y[o] = cadd(Y[o], acc[i]);
+                    Y[o] = cadd(Y[o], cmk((double)acc[i].x, (double)acc[i].y));
                 }
             }
         }
@@ -300,12 +484,16 @@ __global__ void __launch_bounds__(128) expand_kernel(const double2* __restrict__
 }
 
 cudaError_t k_expand(const BandList& L, const SphereSet& S, const ProjMat& A, const double2* P, const double* pscale,
-                     double alpha, double2* Y, int ld, cudaStream_t st) {
+                     double alpha, double2* Y, int ld, cudaStream_t st, bool fp32) {
     if (L.nb <= 0 || A.nrow <= 0) return cudaSuccess;
     if (A.nrow > kPStride) return cudaErrorInvalidValue;
     dim3 g(cdiv(ld, 128), L.nseg);
-    expand_kernel<<<g, 128, 0, st>>>(A.base, A.stride_s, A.stride_k, A.row0, A.nrow, ld, P, pscale, alpha, Y, L.d_row,
-                                     L.d_seg_start, L.d_seg_k, L.d_seg_s, S.d_npw, A.kmap);
+    if (fp32)
+        expand_kernel<float><<<g, 128, 0, st>>>(A.base, A.stride_s, A.stride_k, A.row0, A.nrow, ld, P, pscale, alpha, Y,
+                                                L.d_row, L.d_seg_start, L.d_seg_k, L.d_seg_s, S.d_npw, A.kmap);
+    else
+        expand_kernel<double><<<g, 128, 0, st>>>(A.base, A.stride_s, A.stride_k, A.row0, A.nrow, ld, P, pscale, alpha, Y,
+                                                 L.d_row, L.d_seg_start, L.d_seg_k, L.d_seg_s, S.d_npw, A.kmap);
     HP_LAUNCHED();
     return cudaGetLastError();
 }

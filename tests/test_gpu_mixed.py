@@ -1,0 +1,66 @@
+"""The mixed-precision form (FP32 FFTs, grid work and projections; FP64 vectors, scalars, mixing
+and inversion) against the FP64 oracle: every U and V within 1 meV, chi within 1e-5 relative."""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import groundstate as G, hubbard as HB, response as R
+from oracle.model import Model
+from tests.bridge import import_ground_state, oracle_dn_padded
+
+pytestmark = pytest.mark.gpu
+
+P = pytest.importorskip("paper_2203_15684_gb300")
+HERE = os.path.dirname(os.path.abspath(__file__))
+MEV = 1e-3
+
+
+def test_mixed_hubbard_matrix_tiny_q_within_1mev():
+    w = W.tiny_q(ecut=8.0, grid=(12, 12, 12), kmesh=(2, 2, 2), qmesh=(2, 1, 1))
+    m = Model(w)
+    gs = G.scf(m, tol=1e-12)
+    ctx = P.Context.from_workload(w, precision=1)
+    import_ground_state(ctx, m, gs)
+    c0, c = {}, {}
+    for iq in range(len(m.qpts)):
+        rctx = R.ResponseContext(m, gs, iq)
+        for J in m.hub_atoms:
+            res = R.solve_column(m, gs, iq, J, ctx=rctx, tol_cg=1e-13, scf_tol=1e-12, conv_chi=1e-13)
+            c0[(iq, J)] = HB.trace_column(m, res["dn0"])
+            c[(iq, J)] = HB.trace_column(m, res["dn"])
+            ctx.response(iq, J)
+    chi0_ref = HB.assemble_chi(m, c0).real
+    chi_ref = HB.assemble_chi(m, c).real
+    hub_ref = HB.hubbard_matrix(chi0_ref, chi_ref)
+    chi0, chi, hub = ctx.hubbard()
+    assert np.abs(chi0 - chi0_ref).max() < 1e-5 * np.abs(chi0_ref).max()
+    assert np.abs(chi - chi_ref).max() < 1e-5 * np.abs(chi_ref).max()
+    assert np.abs(hub - hub_ref).max() < MEV
+
+
+def test_mixed_response_spin_polarised():
+    w = W.medium_small(ecut=6.0, grid=(16, 16, 16), kmesh=(2, 1, 1), qmesh=(2, 1, 1))
+    m = Model(w)
+    gs = G.scf(m, tol=1e-12)
+    ctx = P.Context.from_workload(w, precision=1)
+    import_ground_state(ctx, m, gs)
+    J = m.hub_atoms[5]
+    ref = R.solve_column(m, gs, 1, J, tol_cg=1e-13, scf_tol=1e-12, conv_chi=1e-13)
+    dn0, dn, info = ctx.response(1, J)
+    r1 = oracle_dn_padded(m, ref["dn"])
+    assert np.abs(dn - r1).max() < 1e-5 * np.abs(r1).max()
+
+
+def test_mixed_config0_end_to_end_within_1mev():
+    ref = json.load(open(os.path.join(HERE, "golden", "tiny_config0.json")))
+    w = W.tiny()
+    ctx = P.Context.from_workload(w, precision=1, gs_tol=1e-12)
+    ctx.ground_state(w["nelec"], w["nspin"])
+    atoms, _ = ctx.hubbard_atoms()
+    ctx.response(0, int(atoms[0]))
+    chi0, chi, hub = ctx.hubbard()
+    assert abs(hub[0, 0] - ref["U"]) < MEV
