@@ -6,7 +6,9 @@ nspin = 2 with an antiferromagnetic start, 35 Ry, FFT 36^3, k 4x4x4, q 2x2x2).  
 is computed on the GPU before timing.  One step = one (q, J) self-consistent Sternheimer response
 (the per-q set-up a1 and a3-a10): every (spin, k, band) system of that pair, to the FP64
 tolerances the parity tests use.  The 64 (q, J) pairs of the full chi matrix are independent and
-alike, so the full-matrix wall time is reported as steps-per-matrix x time per step.
+alike, so the full-matrix wall time is reported as steps-per-matrix x time per step.  The headline
+is the mixed-precision form (FP32 FFTs, grid work and projections; FP64 vectors, CG scalars,
+mixing and inversion); the FP64 form is timed on the same ground state and pairs for comparison.
 
 Metric: H.psi/s (single-band applications of the Sternheimer operator, summed over ranks).
 N > 1 (torchrun): the (q, J) pairs are sharded round-robin over ranks (weak scaling, no collective
@@ -40,8 +42,10 @@ WORKLOAD_DESC = ("medium: rocksalt cube a=8.4 bohr, 4 H + 4 L, 40 electrons, nsp
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--fp64-steps", type=int, default=2)
+    p.add_argument("--fp64-warmup", type=int, default=1)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -178,7 +182,7 @@ def reference_arm(args, rank):
 def ncu_traffic():
     """Per-launch DRAM bytes of the FFT pass kernel from the committed ncu summary, if the kernel
     source is unchanged since the capture."""
-    path = os.path.join(ROOT, "profiles", "fft_axis_kernel_medium.json")
+    path = os.path.join(ROOT, "profiles", "fft_axis_kernel_fp32_medium.json")
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
@@ -186,6 +190,14 @@ def ncu_traffic():
     if d.get("fft_cu_sha256") != hashlib.sha256(src).hexdigest():
         return None
     return d.get("dram_bytes_per_launch_full_batch")
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)"
+    return 6800.0, "fallback (no MEASURED_PEAKS.json)"
 
 
 def main():
@@ -214,68 +226,81 @@ def main():
     gs = ctx.ground_state(w["nelec"], w["nspin"], w["moments"])
     gs_seconds = time.perf_counter() - t0
     atoms, _ = ctx.hubbard_atoms()
-    nq = ctx.query_sizes()["nq"]
-    pairs = [(iq, int(J)) for J in atoms for iq in range(nq)]
+    s = ctx.query_sizes()
+    pairs = [(iq, int(J)) for J in atoms for iq in range(s["nq"])]
     mine = pairs[rank::world]
 
     def barrier():
         if dist is not None:
             dist.barrier()
 
-    k = 0
-    for _ in range(args.warmup):
-        iq, J = mine[k % len(mine)]
-        ctx.response(iq, J)
-        k += 1
-    barrier()
-    torch.cuda.synchronize()
-    clocks = ClockSampler(torch.cuda.current_device())
-    clocks.start()
-    P.profile_begin()
-    l0 = P.launch_count()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    hpsi = 0
-    iters = []
-    for _ in range(args.steps):
-        iq, J = mine[k % len(mine)]
-        torch.cuda.nvtx.range_push("timed_step")
-        _, _, info = ctx.response(iq, J)
-        torch.cuda.nvtx.range_pop()
-        hpsi += info["hpsi"]
-        iters.append(info["iterations"])
-        k += 1
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    launches = P.launch_count() - l0
-    prof = P.profile_end()
-    clk = clocks.stop()
-    elapsed = e0.elapsed_time(e1) / 1000.0
-    t = torch.tensor([elapsed, float(hpsi)], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        tmax = t.clone()
-        dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
-        elapsed, hpsi_all = float(tmax[0]), float(t[1])
-    else:
-        hpsi_all = float(hpsi)
-    value = hpsi_all / elapsed
-    ms_per_step = 1000.0 * elapsed / args.steps
+    def leg(precision, first, warmup, steps, profile=False, clocks=None):
+        """warm-up and timed (q, J) responses of one precision form; returns timings and traces."""
+        ctx.set_precision(precision)
+        traces = {}
+        k = first
+        for _ in range(warmup):
+            iq, J = mine[k % len(mine)]
+            _, dn, _ = ctx.response(iq, J)
+            traces[(iq, J)] = np.array([np.trace(dn[a].sum(0)) for a in range(len(atoms))])
+            k += 1
+        barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        if profile:
+            P.profile_begin()
+        l0 = P.launch_count()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hpsi, iters = 0, []
+        for _ in range(steps):
+            iq, J = mine[k % len(mine)]
+            torch.cuda.nvtx.range_push("timed_step")
+            _, dn, info = ctx.response(iq, J)
+            torch.cuda.nvtx.range_pop()
+            traces[(iq, J)] = np.array([np.trace(dn[a].sum(0)) for a in range(len(atoms))])
+            hpsi += info["hpsi"]
+            iters.append(info["iterations"])
+            k += 1
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        out = dict(launches=P.launch_count() - l0, prof=P.profile_end() if profile else None,
+                   clocks=clocks.stop() if clocks else None, elapsed=e0.elapsed_time(e1) / 1000.0,
+                   hpsi=hpsi, iters=iters, traces=traces, k=k)
+        t = torch.tensor([out["elapsed"], float(hpsi)], dtype=torch.float64, device="cuda")
+        if dist is not None:
+            tmax = t.clone()
+            dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
+            dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
+            out["elapsed"], out["hpsi_all"] = float(tmax[0]), float(t[1])
+        else:
+            out["hpsi_all"] = float(hpsi)
+        out["value"] = out["hpsi_all"] / out["elapsed"] if steps else None
+        out["ms_per_step"] = 1000.0 * out["elapsed"] / steps if steps else None
+        return out
 
-    # end to end through the C ABI: ground state from pinned host memory, response, results to host
+    # FP64 form (comparison) then the mixed form (headline), on the same ground state and pairs
+    f64 = leg(0, 0, args.fp64_warmup, args.fp64_steps)
+    mix = leg(1, 0, args.warmup, args.steps, profile=True, clocks=ClockSampler(torch.cuda.current_device()))
+    common = [p for p in f64["traces"] if p in mix["traces"]]
+    chi_rel = max(float(np.abs(mix["traces"][p] - f64["traces"][p]).max() / np.abs(f64["traces"][p]).max())
+                  for p in common) if common else None
+
+    # end to end through the C ABI (mixed form): ground state from pinned host memory, response,
+    # Delta n back to the host, every step
     eps, rho, vhxc = ctx.get_ground_state()
     psi = ctx.get_wavefunctions()
     host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in (vhxc, rho, eps)]
     psi_h = torch.from_numpy(psi.view(np.float64)).pin_memory().numpy().view(np.complex128)
     h2d = sum(a.nbytes for a in host) + psi_h.nbytes
-    s = ctx.query_sizes()
     d2h = 2 * s["nhub_atoms"] * s["nspin"] * s["mmax"] ** 2 * 16
     barrier()
     torch.cuda.synchronize()
     te = time.perf_counter()
-    hpsi_e = 0
+    hpsi_e, k = 0, mix["k"]
     for _ in range(args.e2e_steps):
         iq, J = mine[k % len(mine)]
         ctx.set_ground_state_packed(w["nspin"], w["nelec"], host[0], host[1], host[2], psi_h)
@@ -283,38 +308,46 @@ def main():
         hpsi_e += info["hpsi"]
         k += 1
     torch.cuda.synchronize()
-    e2e_el = time.perf_counter() - te
+    e2e_el = max(time.perf_counter() - te, 1e-9)
     barrier()
-
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
-    hpsi_e = max(hpsi_e, 1)
-    e2e_el = max(e2e_el, 1e-9)
-    achieved = (prof["flops"] / prof["launches"]) / (prof["ms"] / prof["launches"] / 1000.0) / 1e12
-    traffic = ncu_traffic()
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                "kernel": "fft_axis_kernel (FP64 Stockham pass)", "peak_source": "GB300 FP64 rate (nominal)",
-                "launches": prof["launches"], "avg_launch_ms": prof["ms"] / prof["launches"],
-                "achieved_hbm_gbs": (prof["bytes"] / prof["ms"] * 1e-6) if prof["ms"] > 0 else None,
-                "share_of_step": prof["ms"] / 1000.0 / elapsed}
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+
+    prof = mix["prof"]
+    peak, peak_src = measured_peaks()
+    avg_s = prof["ms"] / prof["launches"] / 1000.0
+    achieved = prof["bytes"] / prof["launches"] / avg_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": ncu_traffic(), "kernel": "fft_axis_kernel (FP32 Stockham pass)", "peak_source": peak_src,
+                "launches": prof["launches"], "avg_launch_ms": avg_s * 1000.0,
+                "algorithmic_bytes_per_launch": prof["bytes"] / prof["launches"],
+                "achieved_tflops": prof["flops"] / prof["ms"] * 1e-9, "share_of_step": prof["ms"] / 1000.0 / mix["elapsed"]}
+    line = {"metric": METRIC, "value": mix["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": mix["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64 (mixed: FP32 grids and projections, FP64 vectors and scalars)",
+            "data": "synthetic",
             "config": {"workload": WORKLOAD_DESC,
-                       "step": "one (q, J) self-consistent Sternheimer response, %d band systems, FP64"
+                       "step": "one (q, J) self-consistent Sternheimer response, %d band systems"
                                % (s["nspin"] * s["nk"] * s["nocc"]),
                        "pairs_per_chi_matrix": len(pairs),
-                       "chi_matrix_s": ms_per_step * len(pairs) / 1000.0 / world,
-                       "outer_iterations_per_step": iters,
+                       "chi_matrix_s": mix["ms_per_step"] * len(pairs) / 1000.0 / world,
+                       "outer_iterations_per_step": mix["iters"],
+                       "fp64": {"hpsi_per_s": f64["value"], "ms_per_step": f64["ms_per_step"],
+                                "chi_matrix_s": (f64["ms_per_step"] * len(pairs) / 1000.0 / world
+                                                 if f64["ms_per_step"] else None),
+                                "steps": args.fp64_steps, "warmup": args.fp64_warmup,
+                                "outer_iterations_per_step": f64["iters"], "gpu_launches": f64["launches"]},
+                       "chi_matrix_speedup_mixed_vs_fp64": (f64["ms_per_step"] / mix["ms_per_step"]
+                                                            if f64["ms_per_step"] else None),
+                       "chi_max_rel_diff_mixed_vs_fp64": chi_rel,
                        "ground_state_s": gs_seconds, "gap_ha": gs["gap"],
-                       "l2": "inputs larger than L2 (response working set about 2.6 GB)",
+                       "l2": "inputs larger than L2 (response working set about 1.7 GB mixed, 2.6 GB FP64)",
                        "parallelism": "(q, J) pairs round-robin over %d rank(s)" % world},
-            "clocks": clk,
+            "clocks": mix["clocks"],
             "e2e": {"value": hpsi_e / e2e_el, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches, "roofline": roofline}
+            "gpu_launches": mix["launches"], "roofline": roofline}
     if args.cpu_seconds > 0:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     print(json.dumps(line), flush=True)

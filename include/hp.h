@@ -128,6 +128,10 @@ hp_status hp_setup(const double cell[9], int nspecies, const hp_species* sp, int
 
 hp_status hp_query_sizes(const hp_ctx* ctx, hp_sizes* out);
 
+/* Switches the precision form of later hp_response calls (HP_PRECISION_FP64 or _MIXED) without
+ * touching the ground state; response columns computed so far are discarded.  Errors: HP_EINVAL. */
+hp_status hp_set_precision(hp_ctx* ctx, int precision);
+
 /* Wavefunction sphere at k point ik of the mesh: *npw receives its size; if miller != NULL it
  * receives npw x 3 Miller indices (int) in the library's coefficient order. */
 hp_status hp_sphere(const hp_ctx* ctx, int ik, int* npw, int* miller);

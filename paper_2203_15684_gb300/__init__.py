@@ -63,7 +63,7 @@ _lib = None
 SYMBOLS = ["hp_default_options", "hp_setup", "hp_query_sizes", "hp_sphere", "hp_hubbard_atoms", "hp_ground_state",
            "hp_set_ground_state", "hp_get_ground_state", "hp_apply_h", "hp_response", "hp_hubbard", "hp_last_error",
            "hp_destroy", "hp_selftest_fft_host", "hp_selftest_eigh", "hp_get_wavefunctions", "hp_profile_begin",
-           "hp_profile_end", "hp_launch_count", "hp_apply_h_noalloc"]
+           "hp_profile_end", "hp_launch_count", "hp_apply_h_noalloc", "hp_set_precision"]
 
 
 def lib():
@@ -100,6 +100,7 @@ def lib():
     L.hp_profile_end.argtypes = [P(D), P(C.c_longlong), P(D), P(D)]
     L.hp_launch_count.argtypes = []
     L.hp_apply_h_noalloc.argtypes = [V, I, I, I, V, V, V]
+    L.hp_set_precision.argtypes = [V, I]
     for n in SYMBOLS:
         f = getattr(L, n)
         if n == "hp_launch_count":
@@ -216,6 +217,10 @@ class Context:
             self.destroy()
         except Exception:
             pass
+
+    def set_precision(self, precision):
+        """0 = FP64, 1 = mixed (FP32 grids and projections, FP64 vectors and scalars)."""
+        self._check(lib().hp_set_precision(self._ptr, int(precision)), "hp_set_precision")
 
     def query_sizes(self):
         s = Sizes()

@@ -519,6 +519,18 @@ extern "C" hp_status hp_setup(const double cell[9], int nspecies, const hp_speci
     return HP_OK;
 }
 
+extern "C" hp_status hp_set_precision(hp_ctx* c, int precision) {
+    if (!c) return HP_EINVAL;
+    if (precision != HP_PRECISION_FP64 && precision != HP_PRECISION_MIXED)
+        return fail(c, HP_EINVAL, "hp_set_precision: unknown precision");
+    if (precision != c->opt.precision) {
+        c->opt.precision = precision;
+        c->resp_ready = false;  // caches are precision-specific; the ground state is kept
+        c->cols.clear();
+    }
+    return HP_OK;
+}
+
 extern "C" hp_status hp_query_sizes(const hp_ctx* c, hp_sizes* o) {
     if (!c || !o) return HP_EINVAL;
     o->nk = c->nk;
