@@ -154,6 +154,175 @@ __global__ void __launch_bounds__(256) fft_axis_kernel(V* __restrict__ data, int
     }
 }
 
+
+// ---- compile-time form of the pass: sizes, radices, strides and the sign are template constants,
+// so every index division and modulo folds into multiplies and shifts and the stage loops unroll.
+// Shared-memory rows are padded by one element (LDS = LT + 1) against bank conflicts when a warp
+// loads consecutive points of one line.
+template <int... R>
+struct RadixList {};
+
+template <int N> struct Factor;
+template <> struct Factor<8> { using type = RadixList<4, 2>; };
+template <> struct Factor<9> { using type = RadixList<3, 3>; };
+template <> struct Factor<10> { using type = RadixList<2, 5>; };
+template <> struct Factor<12> { using type = RadixList<4, 3>; };
+template <> struct Factor<15> { using type = RadixList<3, 5>; };
+template <> struct Factor<16> { using type = RadixList<4, 4>; };
+template <> struct Factor<18> { using type = RadixList<2, 3, 3>; };
+template <> struct Factor<20> { using type = RadixList<4, 5>; };
+template <> struct Factor<24> { using type = RadixList<4, 2, 3>; };
+template <> struct Factor<25> { using type = RadixList<5, 5>; };
+template <> struct Factor<27> { using type = RadixList<3, 3, 3>; };
+template <> struct Factor<30> { using type = RadixList<2, 3, 5>; };
+template <> struct Factor<32> { using type = RadixList<4, 4, 2>; };
+template <> struct Factor<36> { using type = RadixList<4, 3, 3>; };
+template <> struct Factor<40> { using type = RadixList<4, 2, 5>; };
+template <> struct Factor<45> { using type = RadixList<3, 3, 5>; };
+template <> struct Factor<48> { using type = RadixList<4, 4, 3>; };
+template <> struct Factor<50> { using type = RadixList<2, 5, 5>; };
+template <> struct Factor<54> { using type = RadixList<2, 3, 3, 3>; };
+template <> struct Factor<60> { using type = RadixList<4, 3, 5>; };
+template <> struct Factor<64> { using type = RadixList<4, 4, 4>; };
+template <> struct Factor<72> { using type = RadixList<4, 2, 3, 3>; };
+template <> struct Factor<75> { using type = RadixList<3, 5, 5>; };
+template <> struct Factor<80> { using type = RadixList<4, 4, 5>; };
+template <> struct Factor<90> { using type = RadixList<2, 3, 3, 5>; };
+template <> struct Factor<96> { using type = RadixList<4, 4, 2, 3>; };
+
+constexpr int kFixedThreads = 128;
+constexpr int kFixedLT = 16;
+constexpr int kFixedLDS = kFixedLT + 1;
+
+template <class V, int N, int SIGN, int NS, int R, int... Rest>
+__device__ __forceinline__ V* fixed_stages(V* src, V* dst, const V* __restrict__ tw) {
+    constexpr int NR = N / R;
+    constexpr int ITEMS = kFixedLT * NR;
+    constexpr int TSTEP = N / (NS * R);
+#pragma unroll
+    for (int w0 = 0; w0 < ITEMS; w0 += kFixedThreads) {
+        const int w = w0 + (int)threadIdx.x;
+        if ((ITEMS % kFixedThreads) == 0 || w < ITEMS) {
+            const int l = w % kFixedLT;
+            const int j = w / kFixedLT;
+            const int k = j % NS;
+            V v[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                V x = src[(j + r * NR) * kFixedLDS + l];
+                if (NS > 1 && r > 0) {
+                    V t = tw[r * k * TSTEP];  // r k TSTEP < N: no wrap needed
+                    if (SIGN > 0) t.y = -t.y;
+                    x = cmul(x, t);
+                }
+                v[r] = x;
+            }
+            radix_butterfly(v, R, SIGN);
+            const int idxD = (j / NS) * NS * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) dst[(idxD + r * NS) * kFixedLDS + l] = v[r];
+        }
+    }
+    __syncthreads();
+    if constexpr (sizeof...(Rest) == 0) {
+        return dst;
+    } else {
+        return fixed_stages<V, N, SIGN, NS * R, Rest...>(dst, src, tw);
+    }
+}
+
+template <class V, int N, int SIGN, int... R>
+__device__ __forceinline__ V* fixed_all(RadixList<R...>, V* src, V* dst, const V* __restrict__ tw) {
+    return fixed_stages<V, N, SIGN, 1, R...>(src, dst, tw);
+}
+
+template <class V, int N, int SIGN, bool CONTIG>
+__global__ void __launch_bounds__(kFixedThreads) fft_fixed_kernel(V* __restrict__ data, int A, int B,
+                                                                  const V* __restrict__ tw, int TA, int TB, int tilesB) {
+    __shared__ V sm[2 * N * kFixedLDS];
+    V* buf0 = sm;
+    V* buf1 = sm + N * kFixedLDS;
+    const int tile = blockIdx.x;
+    const long long gbase = (long long)blockIdx.y * A * N * B;
+    const int ta = tile / tilesB, tb = tile % tilesB;
+    const int a0 = ta * TA, b0 = tb * TB;
+    if (CONTIG) {  // B == 1: TA = LT whole lines, contiguous
+        constexpr int NEL = N * kFixedLT;
+#pragma unroll 4
+        for (int e = threadIdx.x; e < NEL; e += kFixedThreads) {
+            const int i = e % N, la = e / N;
+            const int a = a0 + la;
+            V x = cpack<V>(0.0, 0.0);
+            if (a < A) x = data[gbase + (long long)a * N + i];
+            buf0[i * kFixedLDS + la] = x;
+        }
+    } else {
+        const int nel = N * TA * TB;
+        for (int e = threadIdx.x; e < nel; e += kFixedThreads) {
+            const int lb = e % TB, rest = e / TB;
+            const int la = rest % TA, i = rest / TA;
+            const int a = a0 + la, b = b0 + lb;
+            V x = cpack<V>(0.0, 0.0);
+            if (a < A && b < B) x = data[gbase + ((long long)a * N + i) * B + b];
+            buf0[i * kFixedLDS + la * TB + lb] = x;
+        }
+    }
+    __syncthreads();
+    V* out = fixed_all<V, N, SIGN>(typename Factor<N>::type{}, buf0, buf1, tw);
+    if (CONTIG) {
+        constexpr int NEL = N * kFixedLT;
+#pragma unroll 4
+        for (int e = threadIdx.x; e < NEL; e += kFixedThreads) {
+            const int i = e % N, la = e / N;
+            const int a = a0 + la;
+            if (a < A) data[gbase + (long long)a * N + i] = out[i * kFixedLDS + la];
+        }
+    } else {
+        const int nel = N * TA * TB;
+        for (int e = threadIdx.x; e < nel; e += kFixedThreads) {
+            const int lb = e % TB, rest = e / TB;
+            const int la = rest % TA, i = rest / TA;
+            const int a = a0 + la, b = b0 + lb;
+            if (a < A && b < B) data[gbase + ((long long)a * N + i) * B + b] = out[i * kFixedLDS + la * TB + lb];
+        }
+    }
+}
+
+// launches the compile-time pass for size n if it is one of the listed sizes; returns false otherwise
+template <class V, int N>
+static bool launch_fixed_n(V* data, int A, int B, const V* tw, int sign, int nb, cudaStream_t st) {
+    if constexpr (sizeof(V) * 2 * N * kFixedLDS > 48 * 1024) {
+        return false;  // beyond static shared memory: the runtime-size pass takes it
+    }
+    int TB = B < kFixedLT ? B : kFixedLT;
+    int TA = kFixedLT / TB;
+    if (TA < 1) TA = 1;
+    const int tilesA = (A + TA - 1) / TA, tilesB = (B + TB - 1) / TB;
+    dim3 grid(tilesA * tilesB, nb);
+    if (B == 1) {
+        if (sign > 0) fft_fixed_kernel<V, N, 1, true><<<grid, kFixedThreads, 0, st>>>(data, A, B, tw, TA, TB, tilesB);
+        else fft_fixed_kernel<V, N, -1, true><<<grid, kFixedThreads, 0, st>>>(data, A, B, tw, TA, TB, tilesB);
+    } else {
+        if (sign > 0) fft_fixed_kernel<V, N, 1, false><<<grid, kFixedThreads, 0, st>>>(data, A, B, tw, TA, TB, tilesB);
+        else fft_fixed_kernel<V, N, -1, false><<<grid, kFixedThreads, 0, st>>>(data, A, B, tw, TA, TB, tilesB);
+    }
+    return true;
+}
+
+template <class V>
+static bool launch_fixed(int n, V* data, int A, int B, const V* tw, int sign, int nb, cudaStream_t st) {
+    switch (n) {
+#define HP_FIXED(NN) \
+    case NN: return launch_fixed_n<V, NN>(data, A, B, tw, sign, nb, st);
+        HP_FIXED(8) HP_FIXED(9) HP_FIXED(10) HP_FIXED(12) HP_FIXED(15) HP_FIXED(16) HP_FIXED(18) HP_FIXED(20)
+        HP_FIXED(24) HP_FIXED(25) HP_FIXED(27) HP_FIXED(30) HP_FIXED(32) HP_FIXED(36) HP_FIXED(40) HP_FIXED(45)
+        HP_FIXED(48) HP_FIXED(50) HP_FIXED(54) HP_FIXED(60) HP_FIXED(64) HP_FIXED(72) HP_FIXED(75) HP_FIXED(80)
+        HP_FIXED(90) HP_FIXED(96)
+#undef HP_FIXED
+        default: return false;
+    }
+}
+
 cudaError_t fft_plan_create(FftPlan& p, const int N[3]) {
     for (int d = 0; d < 3; ++d) {
         p.N[d] = N[d];
@@ -257,8 +426,9 @@ static cudaError_t fft3d_impl(const FftPlan& p, V* data, int nb, int sign, cudaS
             cudaEventCreate(&e1);
             cudaEventRecord(e0, st);
         }
-        fft_axis_kernel<kLT, V><<<grid, 128, smem, st>>>(data, A, B, p.ax[d].rad, twiddles<V>(p.ax[d]), sign, TA, TB,
-                                                         tilesA, tilesB);
+        if (!launch_fixed<V>(n, data, A, B, twiddles<V>(p.ax[d]), sign, nb, st))
+            fft_axis_kernel<kLT, V><<<grid, 128, smem, st>>>(data, A, B, p.ax[d].rad, twiddles<V>(p.ax[d]), sign, TA, TB,
+                                                             tilesA, tilesB);
         HP_LAUNCHED();
         if (g_prof.on) {
             cudaEventRecord(e1, st);
