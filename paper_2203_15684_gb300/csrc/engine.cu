@@ -62,7 +62,7 @@ void cross(const double* a, const double* b, double* o) {
     o[2] = a[0] * b[1] - a[1] * b[0];
 }
 
-// enumerate the sphere |k + m.B|^2 <= ecut, ordered by (|k+G|^2, m)
+// enumerate the sphere |k + m.B|^2 <= ecut, ordered by Miller index (column by column)
 void build_sphere(const hp_ctx* c, const double kfrac[3], KSphere& s) {
     for (int i = 0; i < 3; ++i) {
         s.kfrac[i] = kfrac[i];
@@ -86,9 +86,8 @@ void build_sphere(const hp_ctx* c, const double kfrac[3], KSphere& s) {
                 const double g2 = K[0] * K[0] + K[1] * K[1] + K[2] * K[2];
                 if (g2 <= c->ecut) v.push_back({g2, {a, b, d}});
             }
+    // column by column (m0, m1), then m2: the points of one z-column of the FFT grid are contiguous
     std::sort(v.begin(), v.end(), [](const E& x, const E& y) {
-        const double rx = std::round(x.g2 * 1e12), ry = std::round(y.g2 * 1e12);
-        if (rx != ry) return rx < ry;
         if (x.m[0] != y.m[0]) return x.m[0] < y.m[0];
         if (x.m[1] != y.m[1]) return x.m[1] < y.m[1];
         return x.m[2] < y.m[2];
@@ -130,14 +129,60 @@ hp_status upload_sphereset(hp_ctx* c, const std::vector<const KSphere*>& sph, co
             g2[(size_t)k * ld + i] = s.g2[i];
         }
     }
+    // columns: runs of points with the same grid (x, y)
+    std::vector<std::vector<int>> cs(nk), cl(nk), cxy(nk);
+    std::vector<int> iz((size_t)nk * ld, 0), ncol(nk);
+    int ncmax = 0;
+    for (int k = 0; k < nk; ++k) {
+        const int npw = S.npw[k];
+        for (int i = 0; i < npw; ++i) {
+            const int gi = idx[(size_t)k * ld + i];
+            const int xy = gi / c->N[2];
+            iz[(size_t)k * ld + i] = gi % c->N[2];
+            if (i == 0 || xy != idx[(size_t)k * ld + i - 1] / c->N[2]) {
+                cs[k].push_back(i);
+                cl[k].push_back(0);
+                cxy[k].push_back(xy);
+            }
+            cl[k].back() += 1;
+        }
+        ncol[k] = (int)cs[k].size();
+        ncmax = std::max(ncmax, ncol[k]);
+    }
+    std::vector<int> hs((size_t)nk * ncmax, 0), hl((size_t)nk * ncmax, 0), hxy((size_t)nk * ncmax, 0);
+    for (int k = 0; k < nk; ++k)
+        for (int j = 0; j < ncol[k]; ++j) {
+            hs[(size_t)k * ncmax + j] = cs[k][j];
+            hl[(size_t)k * ncmax + j] = cl[k][j];
+            hxy[(size_t)k * ncmax + j] = cxy[k][j];
+        }
     if (!S.d_npw) {
         CK(dalloc(c, &S.d_npw, nk));
         CK(dalloc(c, &S.d_idx, (size_t)nk * ld));
         CK(dalloc(c, &S.d_g2, (size_t)nk * ld));
+        CK(dalloc(c, &S.d_iz, (size_t)nk * ld));
+        CK(dalloc(c, &S.d_ncol, nk));
+    }
+    if (ncmax > S.ncmax) {
+        for (void* p : {(void*)S.d_col_start, (void*)S.d_col_len, (void*)S.d_col_xy}) dfree(c, p);
+        CK(dalloc(c, &S.d_col_start, (size_t)nk * ncmax));
+        CK(dalloc(c, &S.d_col_len, (size_t)nk * ncmax));
+        CK(dalloc(c, &S.d_col_xy, (size_t)nk * ncmax));
+    }
+    S.ncmax = ncmax;
+    for (int k = 0; k < nk && c->fused; ++k) {  // the fused transforms need one buffer slot per grid column
+        std::vector<int> xs(cxy[k]);
+        std::sort(xs.begin(), xs.end());
+        if (std::adjacent_find(xs.begin(), xs.end()) != xs.end()) c->fused = false;
     }
     CK(h2d(S.d_npw, S.npw.data(), nk, c->st));
     CK(h2d(S.d_idx, idx.data(), idx.size(), c->st));
     CK(h2d(S.d_g2, g2.data(), g2.size(), c->st));
+    CK(h2d(S.d_iz, iz.data(), iz.size(), c->st));
+    CK(h2d(S.d_ncol, ncol.data(), nk, c->st));
+    CK(h2d(S.d_col_start, hs.data(), hs.size(), c->st));
+    CK(h2d(S.d_col_len, hl.data(), hl.size(), c->st));
+    CK(h2d(S.d_col_xy, hxy.data(), hxy.size(), c->st));
     CK(cudaStreamSynchronize(c->st));
     return HP_OK;
 }
@@ -247,6 +292,63 @@ hp_status apply_local(hp_ctx* c, const SphereSet& S, const BandList& L, const do
         CK(k_mul_rpot(c->d_grid, nc, c->nr, veff, L, c0, c->st));
         CK(fft3d(c->fft, c->d_grid, nc, -1, c->st));
         CK(k_gather_h(S, L, c0, nc, c->d_grid, c->nr, X, Y, c->ld, c->st));
+    }
+    return HP_OK;
+}
+
+hp_status ensure_colbuf(hp_ctx* c, size_t bytes) {
+    if (bytes <= c->col_cap) return HP_OK;
+    dfree(c, c->d_colA);
+    dfree(c, c->d_colB);
+    c->d_colA = c->d_colB = nullptr;
+    unsigned char *a = nullptr, *b = nullptr;
+    CK(dalloc(c, &a, bytes));
+    CK(dalloc(c, &b, bytes));
+    c->d_colA = a;
+    c->d_colB = b;
+    c->col_cap = bytes;
+    return HP_OK;
+}
+
+// bands per batch of the fused transforms (two column buffers and, for real-space output, grids)
+int fused_batch(const hp_ctx* c, const SphereSet& S, int nb) {
+    const size_t per = sizeof(double2) * (size_t)c->N[2] * std::max(1, S.ncmax);
+    int b = (int)std::min<size_t>(32768, std::max<size_t>(1, ((size_t)512 << 20) / per));
+    return std::max(1, std::min(nb, std::min(b, band_batch(c, nb))));
+}
+
+FusedArgs fused_args(hp_ctx* c, const SphereSet& S, const BandList& L) {
+    FusedArgs a;
+    a.S = &S;
+    a.L = &L;
+    a.fft = &c->fft;
+    a.N0 = c->N[0];
+    a.N1 = c->N[1];
+    a.N2 = c->N[2];
+    a.colA = c->d_colA;
+    a.colB = c->d_colB;
+    a.vt = c->d_vt;
+    a.inv_n = 1.0 / c->nr;
+    a.st = c->st;
+    return a;
+}
+
+// Y = (T + V - shift) X through the fused column/plane transforms
+hp_status apply_local_fused(hp_ctx* c, const SphereSet& S, const BandList& L, const double2* X, double2* Y, bool fp32) {
+    if (L.nb == 0) return HP_OK;
+    const int chunk = fused_batch(c, S, L.nb);
+    hp_status s = ensure_colbuf(c, sizeof(double2) * (size_t)chunk * c->N[2] * S.ncmax);
+    if (s != HP_OK) return s;
+    for (int c0 = 0; c0 < L.nb; c0 += chunk) {
+        FusedArgs a = fused_args(c, S, L);
+        a.c0 = c0;
+        a.nc = std::min(chunk, L.nb - c0);
+        a.X = X;
+        a.Y = Y;
+        a.mode = 0;
+        CK(fused_col(fp32, true, a));
+        CK(fused_plane(fp32, 0, a));
+        CK(fused_col(fp32, false, a));
     }
     return HP_OK;
 }
@@ -413,6 +515,7 @@ static hp_status setup_impl(hp_ctx* c, const double cell[9], int nspecies, const
     if (c->nproj > kPStride || c->nhub > kPStride) return fail(c, HP_EINVAL, "hp_setup: more than 128 projector rows");
     if (c->hub_atoms.empty()) return fail(c, HP_EINVAL, "hp_setup: no Hubbard species");
     // device data
+    c->fused = fused_supported(c->N) && !getenv("HP_NO_FUSED");
     CK(fft_plan_create(c->fft, c->N));
     CK(dalloc(c, &c->d_bvec, 9));
     CK(h2d(c->d_bvec, c->bvec, 9, c->st));
@@ -759,8 +862,48 @@ hp_status prepare_resp(hp_ctx* c) {
     s = upload_list(c, L);
     if (s != HP_OK) return s;
     // u_k(r): scatter straight into the cache and transform in place
+    if (c->fused) {
+        // plane-major V_eff (FP64 or FP32) and the real-space occupied bands through the fused path
+        dfree(c, c->d_vt);
+        dfree(c, c->d_dvt);
+        dfree(c, c->d_drho_pm);
+        c->d_vt = c->d_dvt = nullptr;
+        double* tmp;
+        CK(dalloc(c, &tmp, (size_t)nspin * nr));
+        CK(k_to_planes_real(c->d_veff, tmp, c->N, nspin, c->st));
+        if (mixed) {
+            float* v32;
+            float2* dv32;
+            CK(dalloc(c, &v32, (size_t)nspin * nr));
+            CK(k_to_f32(tmp, v32, (long long)nspin * nr, c->st));
+            CK(dalloc(c, &dv32, (size_t)nspin * nr));
+            c->d_vt = v32;
+            c->d_dvt = dv32;
+            CK(cudaStreamSynchronize(c->st));
+            dfree(c, tmp);
+        } else {
+            double2* dv64;
+            CK(dalloc(c, &dv64, (size_t)nspin * nr));
+            c->d_vt = tmp;
+            c->d_dvt = dv64;
+        }
+        CK(dalloc(c, &c->d_drho_pm, (size_t)nspin * nr));
+        const int chunk = fused_batch(c, c->kset, rows);
+        s = ensure_colbuf(c, sizeof(double2) * (size_t)chunk * c->N[2] * c->kset.ncmax);
+        if (s != HP_OK) return s;
+        for (int c0 = 0; c0 < rows; c0 += chunk) {
+            FusedArgs a = fused_args(c, c->kset, L);
+            a.c0 = c0;
+            a.nc = std::min(chunk, rows - c0);
+            a.X = c->d_psi;
+            a.out = mixed ? (void*)(c->d_ur32 + (size_t)c0 * nr) : (void*)(c->d_ur + (size_t)c0 * nr);
+            CK(fused_col(mixed, true, a));
+            CK(fused_plane(mixed, 1, a));
+        }
+    }
+    c->ur_planes = c->fused;
     const int chunk = std::max(1, band_batch(c, rows));
-    for (int c0 = 0; c0 < rows; c0 += chunk) {
+    for (int c0 = 0; c0 < rows && !c->fused; c0 += chunk) {
         const int nc = std::min(chunk, rows - c0);
         if (mixed) {
             CK(k_scatter32(c->kset, L, c0, nc, c->d_psi, c->d_ur32 + (size_t)c0 * nr, nr, c->st));
@@ -858,7 +1001,7 @@ hp_status apply_sternheimer(hp_ctx* c, const BandList& L, const double2* X, doub
     const SphereSet& S = c->qc.set;
     const int* kmap = c->qc.d_miller;
     const bool fp32 = c->opt.precision == HP_PRECISION_MIXED;
-    hp_status s = apply_local(c, S, L, X, Y, c->d_veff, fp32);
+    hp_status s = (c->fused && c->d_vt) ? apply_local_fused(c, S, L, X, Y, fp32) : apply_local(c, S, L, X, Y, c->d_veff, fp32);
     if (s != HP_OK) return s;
     s = apply_nonlocal(c, S, L, X, Y, c->d_Pbuf, kmap, fp32);
     if (s != HP_OK) return s;
@@ -897,6 +1040,10 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
     std::vector<int> kprime;
     s = prepare_q(c, iq, kprime);
     if (s != HP_OK) return s;
+    if (c->ur_planes != c->fused) {  // the k+q spheres turned the fused path off: rebuild the caches
+        c->resp_ready = false;
+        if ((s = prepare_resp(c)) != HP_OK) return s;
+    }
     const int nspin = c->nspin, nk = c->nk, nocc = c->nocc, nr = c->nr, ld = c->ld;
     const int rows = nspin * nk * nocc;
     const int nh = (int)c->hub_atoms.size();
@@ -949,7 +1096,26 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
         } else {
             s = ensure_grid(c, band_batch(c, rows));
             if (s != HP_OK) return s;
-            if (mixed) {
+            if (c->fused) {
+                // plane-major Delta V, then u_k(r) Delta V(r) -> forward transform onto the k+q sphere
+                CK(k_to_planes_c(c->d_dv, c->d_drho_pm, c->N, nspin, c->st));
+                if (mixed) CK(k_to_c32(c->d_drho_pm, (float2*)c->d_dvt, ndv, c->st));
+                else CK(cudaMemcpyAsync(c->d_dvt, c->d_drho_pm, sizeof(double2) * ndv, cudaMemcpyDeviceToDevice, c->st));
+                const int chunk = fused_batch(c, Sq, rows);
+                if ((s = ensure_colbuf(c, sizeof(double2) * (size_t)chunk * c->N[2] * Sq.ncmax)) != HP_OK) return s;
+                for (int c0 = 0; c0 < rows; c0 += chunk) {
+                    FusedArgs a = fused_args(c, Sq, Lall);
+                    a.c0 = c0;
+                    a.nc = std::min(chunk, rows - c0);
+                    a.ur = mixed ? (const void*)c->d_ur32 : (const void*)c->d_ur;
+                    a.dvt = c->d_dvt;
+                    a.Y = c->d_b;
+                    a.mode = 1;
+                    a.scale = -1.0;
+                    CK(fused_plane(mixed, 2, a));
+                    CK(fused_col(mixed, false, a));
+                }
+            } else if (mixed) {
                 float2* g32 = (float2*)c->d_grid;
                 const int cap = 2 * c->grid_cap;
                 CK(k_to_c32(c->d_dv, c->d_dv32, ndv, c->st));
@@ -1011,7 +1177,27 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
         CK(cudaMemsetAsync(c->d_drho, 0, sizeof(double2) * ndv, c->st));
         s = ensure_grid(c, band_batch(c, rows));
         if (s != HP_OK) return s;
-        if (mixed) {
+        if (c->fused) {
+            // x -> real space (plane-major) through the fused path, then conj(u) x accumulated per spin
+            CK(cudaMemsetAsync(c->d_drho_pm, 0, sizeof(double2) * ndv, c->st));
+            const int chunk = std::min(fused_batch(c, Sq, rows), mixed ? 2 * c->grid_cap : c->grid_cap);
+            if ((s = ensure_colbuf(c, sizeof(double2) * (size_t)chunk * c->N[2] * Sq.ncmax)) != HP_OK) return s;
+            for (int c0 = 0; c0 < rows; c0 += chunk) {
+                FusedArgs a = fused_args(c, Sq, Lall);
+                a.c0 = c0;
+                a.nc = std::min(chunk, rows - c0);
+                a.X = c->d_x;
+                a.out = c->d_grid;
+                CK(fused_col(mixed, true, a));
+                CK(fused_plane(mixed, 1, a));
+                if (mixed)
+                    CK(k_drho_acc32(c->d_ur32, Lall.d_row, (const float2*)c->d_grid, a.nc, nr, Lall, c0, wrho, nspin,
+                                    c->d_drho_pm, c->st));
+                else
+                    CK(k_drho_acc(c->d_ur, Lall.d_row, c->d_grid, a.nc, nr, Lall, c0, wrho, nspin, c->d_drho_pm, c->st));
+            }
+            CK(k_from_planes_c(c->d_drho_pm, c->d_drho, c->N, nspin, c->st));
+        } else if (mixed) {
             float2* g32 = (float2*)c->d_grid;
             const int cap = 2 * c->grid_cap;
             for (int c0 = 0; c0 < rows; c0 += cap) {

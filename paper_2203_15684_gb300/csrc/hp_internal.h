@@ -96,6 +96,15 @@ struct SphereSet {          // device arrays, nk spheres of at most ld points
     int* d_idx = nullptr;   // [nk][ld] flat grid index of each coefficient
     double* d_g2 = nullptr; // [nk][ld] |k+G|^2
     std::vector<int> npw;   // host copy
+    // column structure (the sphere is stored column by column, z fastest): for each k, ncol
+    // columns (x, y) of the grid that hold sphere points, their first point and length, and the
+    // z index of every point
+    int ncmax = 0;
+    int* d_ncol = nullptr;      // [nk]
+    int* d_col_start = nullptr; // [nk][ncmax]
+    int* d_col_len = nullptr;   // [nk][ncmax]
+    int* d_col_xy = nullptr;    // [nk][ncmax] x * N1 + y
+    int* d_iz = nullptr;        // [nk][ld]
 };
 
 struct BandList {
@@ -225,6 +234,32 @@ struct QCache {                    // per-q data: k+q spheres, projectors and oc
     int* d_miller = nullptr;
 };
 
+// fused.cu: sphere-sparse column/plane transforms
+struct FusedArgs {
+    const SphereSet* S = nullptr;
+    const BandList* L = nullptr;
+    const FftPlan* fft = nullptr;
+    int c0 = 0, nc = 0, N0 = 0, N1 = 0, N2 = 0;
+    const double2* X = nullptr;
+    double2* Y = nullptr;
+    int mode = 0;
+    double scale = 1.0;
+    void* colA = nullptr;        // column buffer written by col_inv, read by plane
+    void* colB = nullptr;        // column buffer written by plane, read by col_fwd
+    const void* vt = nullptr;    // plane-major real potential [spin][z][y][x]
+    const void* ur = nullptr;    // plane-major real-space bands [row][z][y][x]
+    const void* dvt = nullptr;   // plane-major complex Delta V [spin][z][y][x]
+    void* out = nullptr;         // plane-major real-space output [c][z][y][x]
+    double inv_n = 1.0;
+    cudaStream_t st = nullptr;
+};
+bool fused_supported(const int N[3]);
+cudaError_t fused_col(bool fp32, bool inv, const FusedArgs& a);
+cudaError_t fused_plane(bool fp32, int op, const FusedArgs& a);
+cudaError_t k_to_planes_real(const double* a, double* b, const int N[3], int nvec, cudaStream_t st);
+cudaError_t k_to_planes_c(const double2* a, double2* b, const int N[3], int nvec, cudaStream_t st);
+cudaError_t k_from_planes_c(const double2* b, double2* a, const int N[3], int nvec, cudaStream_t st);
+
 // engine.cu helpers shared with the ground-state driver
 hp_status fail(hp_ctx* c, hp_status s, const std::string& msg);
 hp_status cuda_fail(hp_ctx* c, cudaError_t e, const char* what);
@@ -295,6 +330,15 @@ struct hp_ctx {
     float2* d_ur32 = nullptr;          // mixed precision: [nspin][nk][nocc][nr] FP32 u_k(r)
     float* d_veff32 = nullptr;         // mixed precision: FP32 copy of V_loc + V_Hxc
     float2* d_dv32 = nullptr;          // mixed precision: FP32 copy of Delta V_Hxc
+    // sphere-sparse fused transforms (when the grid sizes are supported)
+    bool fused = false;
+    bool ur_planes = false;            // the real-space band cache is plane-major (built by the fused path)
+    void* d_vt = nullptr;              // plane-major V_eff [nspin][z][y][x] (double or float)
+    void* d_dvt = nullptr;             // plane-major Delta V (double2 or float2)
+    double2* d_drho_pm = nullptr;      // plane-major Delta rho accumulation
+    void* d_colA = nullptr;
+    void* d_colB = nullptr;
+    size_t col_cap = 0;                // bytes of each column buffer
     double alpha_pv = 0;
     hp::QCache qc;
     // response work arrays
