@@ -179,17 +179,25 @@ def reference_arm(args, rank):
 # ------------------------------------------------------------------------------------------------
 # our arm
 # ------------------------------------------------------------------------------------------------
-def ncu_traffic():
-    """Per-launch DRAM bytes of the FFT pass kernel from the committed ncu summary, if the kernel
-    source is unchanged since the capture."""
-    path = os.path.join(ROOT, "profiles", "fft_axis_kernel_fp32_medium.json")
+FAMILY_KERNELS = {"fft_pass": ("fft_fixed_kernel / fft_axis_kernel (FP32 Stockham pass)", "fft.cu"),
+                  "column": ("col_inv_kernel + col_fwd_kernel (fused z-column transforms)", "fused.cu"),
+                  "plane": ("plane_kernel (fused x/y plane transforms + real-space product)", "fused.cu"),
+                  "project": ("proj_kernel + proj_reduce_kernel (FP32 projections)", "kernels.cu"),
+                  "expand": ("expand_kernel (FP32 projector expansion)", "kernels.cu")}
+
+
+def ncu_traffic(family, alg_bytes_per_launch):
+    """DRAM bytes per launch of a kernel family: the DRAM/algorithmic byte ratio of a committed ncu
+    capture (profiles/traffic_<family>_medium.json) times this run's algorithmic bytes per launch;
+    None when the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic_%s_medium.json" % family)
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
-    src = open(os.path.join(ROOT, "paper_2203_15684_gb300", "csrc", "fft.cu"), "rb").read()
-    if d.get("fft_cu_sha256") != hashlib.sha256(src).hexdigest():
+    src = open(os.path.join(ROOT, "paper_2203_15684_gb300", "csrc", FAMILY_KERNELS[family][1]), "rb").read()
+    if d.get("source_sha256") != hashlib.sha256(src).hexdigest():
         return None
-    return d.get("dram_bytes_per_launch_full_batch")
+    return d["dram_over_algorithmic"] * alg_bytes_per_launch
 
 
 def measured_peaks():
@@ -315,15 +323,23 @@ def main():
             dist.destroy_process_group()
         return
 
+    # roofline of the dominant kernel family (largest summed event time in the timed region)
     prof = mix["prof"]
     peak, peak_src = measured_peaks()
-    avg_s = prof["ms"] / prof["launches"] / 1000.0
-    achieved = prof["bytes"] / prof["launches"] / avg_s / 1e9
+    fam = max(prof, key=lambda f: prof[f]["ms"])
+    p = prof[fam]
+    avg_s = p["ms"] / p["launches"] / 1000.0
+    alg = p["bytes"] / p["launches"]
+    achieved = alg / avg_s / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": ncu_traffic(), "kernel": "fft_axis_kernel (FP32 Stockham pass)", "peak_source": peak_src,
-                "launches": prof["launches"], "avg_launch_ms": avg_s * 1000.0,
-                "algorithmic_bytes_per_launch": prof["bytes"] / prof["launches"],
-                "achieved_tflops": prof["flops"] / prof["ms"] * 1e-9, "share_of_step": prof["ms"] / 1000.0 / mix["elapsed"]}
+                "traffic": ncu_traffic(fam, alg), "kernel": FAMILY_KERNELS[fam][0], "peak_source": peak_src,
+                "launches": p["launches"], "avg_launch_ms": avg_s * 1000.0, "algorithmic_bytes_per_launch": alg,
+                "achieved_tflops": p["flops"] / p["ms"] * 1e-9, "share_of_step": p["ms"] / 1000.0 / mix["elapsed"],
+                "families": {f: {"share_of_step": round(q["ms"] / 1000.0 / mix["elapsed"], 4),
+                                 "launches": q["launches"],
+                                 "gbs": round(q["bytes"] / q["ms"] * 1e-6, 1) if q["ms"] else None,
+                                 "tflops": round(q["flops"] / q["ms"] * 1e-9, 3) if q["ms"] else None}
+                             for f, q in prof.items()}}
     line = {"metric": METRIC, "value": mix["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": mix["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64 (mixed: FP32 grids and projections, FP64 vectors and scalars)",

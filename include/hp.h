@@ -207,13 +207,39 @@ const char* hp_last_error(const hp_ctx* ctx);
 /* Frees the context and all device memory it owns.  NULL is ignored. */
 void hp_destroy(hp_ctx* ctx);
 
-/* Live timing of the FFT passes (the dominant kernel of H.psi): between hp_profile_begin and
- * hp_profile_end every FFT pass launch is bracketed by CUDA events recorded on its launch stream;
- * hp_profile_end waits for them and returns the summed kernel time (ms), the number of pass
- * launches, and their algorithmic flops (5 n log2 n per transformed line of n points) and bytes
- * (every grid point read and written once per pass).  Process-wide, not per context. */
+/* Live timing of the hot kernel families.  Between hp_profile_begin and hp_profile_end every
+ * launch of a timed family is bracketed by CUDA events recorded on its own launch stream and adds
+ * its algorithmic flops and bytes (counted on the host from the sizes the launch processes):
+ *   HP_KF_FFT_PASS  one pass of the batched 3D FFT: every grid point read and written once;
+ *                   5 n log2 n flops per line of n points.
+ *   HP_KF_COLUMN    fused column transform (z-FFT between the wavefunction sphere and the compact
+ *                   column buffer): sphere coefficients read or written in FP64 (plus the input
+ *                   vector for the kinetic term, and the zeroed padding), column buffer once.
+ *   HP_KF_PLANE     fused plane transform (x/y-FFTs of one z-plane of one band in shared memory and
+ *                   the real-space product): column buffer in and out, real-space grids read or
+ *                   written once per band, the potential once per spin.
+ *   HP_KF_PROJECT   <beta|psi> projections: band vectors and projector rows read once, partial sums
+ *                   and results written; 8 flops per complex multiply-add.
+ *   HP_KF_EXPAND    psi += beta P: projector rows and coefficients read, band vectors read and written.
+ * hp_profile_end waits for the events and fills stats[0 .. HP_KF_COUNT-1] with the summed kernel
+ * time (ms), launches, flops and bytes of each family.  Process-wide (one host thread), not per
+ * context.  Errors: HP_ECUDA if an event could not be read. */
+enum {
+    HP_KF_FFT_PASS = 0,
+    HP_KF_COLUMN = 1,
+    HP_KF_PLANE = 2,
+    HP_KF_PROJECT = 3,
+    HP_KF_EXPAND = 4,
+    HP_KF_COUNT = 5
+};
+typedef struct {
+    double ms;
+    long long launches;
+    double flops;
+    double bytes;
+} hp_kernel_stats;
 void hp_profile_begin(void);
-hp_status hp_profile_end(double* fft_ms, long long* fft_launches, double* fft_flops, double* fft_bytes);
+hp_status hp_profile_end(hp_kernel_stats* stats);
 
 /* Number of CUDA kernels this library has launched in this process (monotonic counter). */
 long long hp_launch_count(void);

@@ -58,6 +58,13 @@ class RespInfo(C.Structure):
                 ("residual", C.c_double), ("dchi", C.c_double), ("seconds", C.c_double)]
 
 
+class KernelStats(C.Structure):
+    _fields_ = [("ms", C.c_double), ("launches", C.c_longlong), ("flops", C.c_double), ("bytes", C.c_double)]
+
+
+# kernel families timed by profile_begin/profile_end, in the order of HP_KF_*
+KERNEL_FAMILIES = ("fft_pass", "column", "plane", "project", "expand")
+
 _lib = None
 
 SYMBOLS = ["hp_default_options", "hp_setup", "hp_query_sizes", "hp_sphere", "hp_hubbard_atoms", "hp_ground_state",
@@ -97,7 +104,7 @@ def lib():
     L.hp_get_wavefunctions.argtypes = [V, P(D)]
     L.hp_profile_begin.argtypes = []
     L.hp_profile_begin.restype = None
-    L.hp_profile_end.argtypes = [P(D), P(C.c_longlong), P(D), P(D)]
+    L.hp_profile_end.argtypes = [P(KernelStats)]
     L.hp_launch_count.argtypes = []
     L.hp_apply_h_noalloc.argtypes = [V, I, I, I, V, V, V]
     L.hp_set_precision.argtypes = [V, I]
@@ -159,13 +166,14 @@ def profile_begin():
 
 
 def profile_end():
-    """-> dict(ms, launches, flops, bytes) of the FFT passes since profile_begin()."""
-    ms, fl, by = C.c_double(), C.c_double(), C.c_double()
-    n = C.c_longlong()
-    st = lib().hp_profile_end(C.byref(ms), C.byref(n), C.byref(fl), C.byref(by))
+    """-> {family: dict(ms, launches, flops, bytes)} for the kernel families timed since
+    profile_begin() (names in KERNEL_FAMILIES)."""
+    stats = (KernelStats * len(KERNEL_FAMILIES))()
+    st = lib().hp_profile_end(stats)
     if st != HP_OK:
         raise HPError(st, "hp_profile_end")
-    return dict(ms=ms.value, launches=n.value, flops=fl.value, bytes=by.value)
+    return {name: dict(ms=x.ms, launches=x.launches, flops=x.flops, bytes=x.bytes)
+            for name, x in zip(KERNEL_FAMILIES, stats)}
 
 
 def launch_count():

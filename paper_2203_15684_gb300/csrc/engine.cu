@@ -170,6 +170,40 @@ hp_status upload_sphereset(hp_ctx* c, const std::vector<const KSphere*>& sph, co
         CK(dalloc(c, &S.d_col_xy, (size_t)nk * ncmax));
     }
     S.ncmax = ncmax;
+    S.ncol = ncol;
+    // whether each column is one run of consecutive z, and the run of columns of each grid x
+    const int N0 = c->N[0], N1 = c->N[1], N2 = c->N[2];
+    bool contig = true, xruns = true;
+    std::vector<int> xt((size_t)nk * N0 * 3, 0);
+    for (int k = 0; k < nk; ++k)
+        for (int j = 0; j < ncol[k]; ++j) {
+            const int st = cs[k][j];
+            for (int p = 1; p < cl[k][j]; ++p)
+                if (iz[(size_t)k * ld + st + p] != (iz[(size_t)k * ld + st] + p) % N2) contig = false;
+            const int x = cxy[k][j] / N1, y = cxy[k][j] % N1;
+            int* t = &xt[((size_t)k * N0 + x) * 3];
+            if (t[1] == 0) {
+                t[0] = j;
+                t[2] = y;
+            } else if (t[0] + t[1] != j || (t[2] + t[1]) % N1 != y) {
+                xruns = false;
+            }
+            t[1] += 1;
+        }
+    S.contig = contig;
+    if (S.d_xtab && S.xtab_n0 != N0) {
+        dfree(c, S.d_xtab);
+        S.d_xtab = nullptr;
+    }
+    if (xruns) {
+        if (!S.d_xtab) CK(dalloc(c, &S.d_xtab, xt.size()));
+        CK(h2d(S.d_xtab, xt.data(), xt.size(), c->st));
+        S.xtab_n0 = N0;
+    } else if (S.d_xtab) {
+        dfree(c, S.d_xtab);
+        S.d_xtab = nullptr;
+        S.xtab_n0 = 0;
+    }
     for (int k = 0; k < nk && c->fused; ++k) {  // the fused transforms need one buffer slot per grid column
         std::vector<int> xs(cxy[k]);
         std::sort(xs.begin(), xs.end());
@@ -329,6 +363,7 @@ FusedArgs fused_args(hp_ctx* c, const SphereSet& S, const BandList& L) {
     a.colB = c->d_colB;
     a.vt = c->d_vt;
     a.inv_n = 1.0 / c->nr;
+    a.reg = c->fused_reg;
     a.st = c->st;
     return a;
 }
@@ -355,7 +390,7 @@ hp_status apply_local_fused(hp_ctx* c, const SphereSet& S, const BandList& L, co
 
 hp_status project(hp_ctx* c, const SphereSet& S, const BandList& L, const ProjMat& A, const double2* X, double2* P,
                   bool fp32) {
-    hp_status s = ensure_scratch(c, (size_t)8 * std::max(1, L.nb) * kPStride);
+    hp_status s = ensure_scratch(c, (size_t)16 * std::max(1, L.nb) * kPStride);
     if (s != HP_OK) return s;
     CK(k_proj(L, S, A, X, c->ld, P, c->d_scratch, c->scratch_elems, c->st, fp32));
     return HP_OK;
@@ -516,6 +551,7 @@ static hp_status setup_impl(hp_ctx* c, const double cell[9], int nspecies, const
     if (c->hub_atoms.empty()) return fail(c, HP_EINVAL, "hp_setup: no Hubbard species");
     // device data
     c->fused = fused_supported(c->N) && !getenv("HP_NO_FUSED");
+    c->fused_reg = !getenv("HP_FUSED_SMEM");  // HP_FUSED_SMEM: shared-memory line FFTs instead
     CK(fft_plan_create(c->fft, c->N));
     CK(dalloc(c, &c->d_bvec, 9));
     CK(h2d(c->d_bvec, c->bvec, 9, c->st));
@@ -1177,6 +1213,7 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
         CK(cudaMemsetAsync(c->d_drho, 0, sizeof(double2) * ndv, c->st));
         s = ensure_grid(c, band_batch(c, rows));
         if (s != HP_OK) return s;
+        if ((s = ensure_scratch(c, (size_t)64 * nr)) != HP_OK) return s;  // band-slice partial sums
         if (c->fused) {
             // x -> real space (plane-major) through the fused path, then conj(u) x accumulated per spin
             CK(cudaMemsetAsync(c->d_drho_pm, 0, sizeof(double2) * ndv, c->st));
@@ -1192,9 +1229,9 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
                 CK(fused_plane(mixed, 1, a));
                 if (mixed)
                     CK(k_drho_acc32(c->d_ur32, Lall.d_row, (const float2*)c->d_grid, a.nc, nr, Lall, c0, wrho, nspin,
-                                    c->d_drho_pm, c->st));
+                                    c->d_drho_pm, c->d_scratch, c->scratch_elems, c->st));
                 else
-                    CK(k_drho_acc(c->d_ur, Lall.d_row, c->d_grid, a.nc, nr, Lall, c0, wrho, nspin, c->d_drho_pm, c->st));
+                    CK(k_drho_acc(c->d_ur, Lall.d_row, c->d_grid, a.nc, nr, Lall, c0, wrho, nspin, c->d_drho_pm, c->d_scratch, c->scratch_elems, c->st));
             }
             CK(k_from_planes_c(c->d_drho_pm, c->d_drho, c->N, nspin, c->st));
         } else if (mixed) {
@@ -1204,14 +1241,16 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
                 const int nc = std::min(cap, rows - c0);
                 CK(k_scatter32(Sq, Lall, c0, nc, c->d_x, g32, nr, c->st));
                 CK(fft3d(c->fft, g32, nc, +1, c->st));
-                CK(k_drho_acc32(c->d_ur32, Lall.d_row, g32, nc, nr, Lall, c0, wrho, nspin, c->d_drho, c->st));
+                CK(k_drho_acc32(c->d_ur32, Lall.d_row, g32, nc, nr, Lall, c0, wrho, nspin, c->d_drho, c->d_scratch,
+                                   c->scratch_elems, c->st));
             }
         } else {
             for (int c0 = 0; c0 < rows; c0 += c->grid_cap) {
                 const int nc = std::min(c->grid_cap, rows - c0);
                 CK(k_scatter(Sq, Lall, c0, nc, c->d_x, ld, c->d_grid, nr, c->st));
                 CK(fft3d(c->fft, c->d_grid, nc, +1, c->st));
-                CK(k_drho_acc(c->d_ur, Lall.d_row, c->d_grid, nc, nr, Lall, c0, wrho, nspin, c->d_drho, c->st));
+                CK(k_drho_acc(c->d_ur, Lall.d_row, c->d_grid, nc, nr, Lall, c0, wrho, nspin, c->d_drho, c->d_scratch,
+                                   c->scratch_elems, c->st));
             }
         }
         // ---- response occupations

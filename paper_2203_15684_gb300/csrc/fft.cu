@@ -357,40 +357,6 @@ void fft_plan_destroy(FftPlan& p) {
 
 static constexpr int kLT = 16;
 
-// live timing of the FFT passes with CUDA events recorded on the launch stream (hp_profile_*)
-struct FftProfile {
-    bool on = false;
-    std::vector<cudaEvent_t> ev;   // start/stop pairs
-    long long launches = 0;
-    double flops = 0, bytes = 0;
-};
-static FftProfile g_prof;
-
-void fft_profile_begin() {
-    for (auto e : g_prof.ev) cudaEventDestroy(e);
-    g_prof = FftProfile();
-    g_prof.on = true;
-}
-
-cudaError_t fft_profile_end(double* ms, long long* launches, double* flops, double* bytes) {
-    double tot = 0.0;
-    cudaError_t err = cudaSuccess;
-    for (size_t i = 0; i + 1 < g_prof.ev.size(); i += 2) {
-        cudaError_t e = cudaEventSynchronize(g_prof.ev[i + 1]);
-        float t = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, g_prof.ev[i], g_prof.ev[i + 1]);
-        if (e != cudaSuccess) err = e;
-        tot += t;
-    }
-    if (ms) *ms = tot;
-    if (launches) *launches = g_prof.launches;
-    if (flops) *flops = g_prof.flops;
-    if (bytes) *bytes = g_prof.bytes;
-    for (auto e : g_prof.ev) cudaEventDestroy(e);
-    g_prof = FftProfile();
-    return err;
-}
-
 template <class V>
 static const V* twiddles(const FftAxis& a);
 template <>
@@ -420,24 +386,15 @@ static cudaError_t fft3d_impl(const FftPlan& p, V* data, int nb, int sign, cudaS
             if (e != cudaSuccess) return e;
         }
         dim3 grid(tilesA * tilesB, nb);
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        if (g_prof.on) {
-            cudaEventCreate(&e0);
-            cudaEventCreate(&e1);
-            cudaEventRecord(e0, st);
-        }
+        const ProfMark pm = prof_start(st);
         if (!launch_fixed<V>(n, data, A, B, twiddles<V>(p.ax[d]), sign, nb, st))
             fft_axis_kernel<kLT, V><<<grid, 128, smem, st>>>(data, A, B, p.ax[d].rad, twiddles<V>(p.ax[d]), sign, TA, TB,
                                                              tilesA, tilesB);
         HP_LAUNCHED();
-        if (g_prof.on) {
-            cudaEventRecord(e1, st);
-            g_prof.ev.push_back(e0);
-            g_prof.ev.push_back(e1);
-            g_prof.launches += 1;
+        if (prof_on()) {
             const double nrg = (double)N0 * N1 * N2 * nb;
-            g_prof.flops += nrg * 5.0 * std::log2((double)n);   // 5 n log2 n per line of n points
-            g_prof.bytes += nrg * 2.0 * sizeof(V);               // every point read and written once
+            // 5 n log2 n flops per line of n points; every point read and written once
+            prof_stop(pm, HP_KF_FFT_PASS, st, nrg * 5.0 * std::log2((double)n), nrg * 2.0 * sizeof(V));
         }
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -474,12 +431,6 @@ void fft_host_lines(const Radices& rad, const std::vector<double2>& tw, int nlin
 }
 
 }  // namespace hp
-
-extern "C" void hp_profile_begin(void) { hp::fft_profile_begin(); }
-
-extern "C" hp_status hp_profile_end(double* fft_ms, long long* fft_launches, double* fft_flops, double* fft_bytes) {
-    return hp::fft_profile_end(fft_ms, fft_launches, fft_flops, fft_bytes) == cudaSuccess ? HP_OK : HP_ECUDA;
-}
 
 extern "C" long long hp_launch_count(void) { return hp::g_launches.load(); }
 

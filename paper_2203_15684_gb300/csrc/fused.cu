@@ -10,7 +10,10 @@
 //   col_fwd   : forward z-FFT of the columns and the gather onto the sphere, with the kinetic term.
 // Real-space band grids use the plane-major layout [z][y][x] so that a plane is contiguous.
 // HBM traffic per band drops from ~6 full-grid round trips to two compact column buffers.
+#include <cmath>
+#include <mutex>
 #include <type_traits>
+#include <vector>
 
 #include "hp_internal.h"
 
@@ -124,6 +127,341 @@ __device__ __forceinline__ V* lines(V* src, V* dst, const V* __restrict__ tw) {
 template <class V>
 __device__ __forceinline__ V from64(double2 x) {
     return cpack<V>(x.x, x.y);
+}
+
+// ------------------------------------------------------------------------------------------------
+// register-resident FFTs: one thread holds a whole line of N points in registers and runs the
+// Stockham stages with every index and twiddle position known at compile time; twiddles
+// W_N^e = exp(-2 pi i e / N) come from constant memory.
+// ------------------------------------------------------------------------------------------------
+template <int N> struct TwOff;
+template <> struct TwOff<10> { static constexpr int v = 0; };
+template <> struct TwOff<12> { static constexpr int v = 10; };
+template <> struct TwOff<15> { static constexpr int v = 22; };
+template <> struct TwOff<16> { static constexpr int v = 37; };
+template <> struct TwOff<18> { static constexpr int v = 53; };
+template <> struct TwOff<20> { static constexpr int v = 71; };
+template <> struct TwOff<24> { static constexpr int v = 91; };
+template <> struct TwOff<36> { static constexpr int v = 115; };
+template <> struct TwOff<45> { static constexpr int v = 151; };
+template <> struct TwOff<72> { static constexpr int v = 196; };
+constexpr int kTwTotal = 268;
+constexpr int kTwSizes[] = {10, 12, 15, 16, 18, 20, 24, 36, 45, 72};
+__constant__ float2 c_tw32[kTwTotal];
+__constant__ double2 c_tw64[kTwTotal];
+
+template <class V>
+__device__ __forceinline__ V ctw(int i);
+template <>
+__device__ __forceinline__ float2 ctw<float2>(int i) { return c_tw32[i]; }
+template <>
+__device__ __forceinline__ double2 ctw<double2>(int i) { return c_tw64[i]; }
+
+template <class V, int N, int SIGN, int NS, int R, int... Rest>
+__device__ __forceinline__ void rstages(V (&a)[N]) {
+    constexpr int NR = N / R;
+    constexpr int TSTEP = N / (NS * R);
+    V b[N];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+        const int k = j % NS;
+        V v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            V x = a[j + r * NR];
+            if (r > 0 && k > 0) {
+                V t = ctw<V>(TwOff<N>::v + r * k * TSTEP);
+                if (SIGN > 0) t.y = -t.y;
+                x = cmul(x, t);
+            }
+            v[r] = x;
+        }
+        bfly(v, R, SIGN);
+        const int d = (j / NS) * NS * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) b[d + r * NS] = v[r];
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) a[i] = b[i];
+    if constexpr (sizeof...(Rest) > 0) rstages<V, N, SIGN, NS * R, Rest...>(a);
+}
+
+template <class V, int N, int SIGN, int... R>
+__device__ __forceinline__ void rfft_(Radices_<R...>, V (&a)[N]) {
+    rstages<V, N, SIGN, 1, R...>(a);
+}
+
+template <class V, int N, int SIGN>
+__device__ __forceinline__ void rfft(V (&a)[N]) {
+    rfft_<V, N, SIGN>(typename FactorF<N>::type{}, a);
+}
+
+// line lengths a thread can hold: 72 complex FP32 or 36 complex FP64 values
+template <class V>
+constexpr int reg_nmax() { return sizeof(V) == 8 ? 72 : 36; }
+
+static cudaError_t regfft_init() {
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, [] {
+        std::vector<float2> t32(kTwTotal);
+        std::vector<double2> t64(kTwTotal);
+        int off = 0;
+        for (int n : kTwSizes) {
+            for (int e = 0; e < n; ++e) {
+                const double a = -2.0 * M_PI * (double)e / (double)n;
+                t64[off + e] = cmk(std::cos(a), std::sin(a));
+                t32[off + e] = cmkf((float)std::cos(a), (float)std::sin(a));
+            }
+            off += n;
+        }
+        err = cudaMemcpyToSymbol(c_tw32, t32.data(), sizeof(float2) * kTwTotal);
+        if (err == cudaSuccess) err = cudaMemcpyToSymbol(c_tw64, t64.data(), sizeof(double2) * kTwTotal);
+    });
+    return err;
+}
+
+// column transforms with one thread per (band, column): the column's sphere points are one run of
+// consecutive z (wrapping at N2), so every register index is a compile-time z.
+constexpr int kColRegThreads = 128;
+
+template <class V, int N2>
+__global__ void __launch_bounds__(kColRegThreads) col_inv_reg_kernel(
+    const double2* __restrict__ X, int ld, const int* __restrict__ row, const int* __restrict__ kk, int c0,
+    const int* __restrict__ ncol, const int* __restrict__ col_start, const int* __restrict__ col_len,
+    const int* __restrict__ iz, int ncmax, V* __restrict__ colbuf) {
+    const int c = blockIdx.y;
+    const int k = kk[c0 + c];
+    const int j = blockIdx.x * kColRegThreads + threadIdx.x;
+    if (j >= ncol[k]) return;
+    const int st = col_start[(long long)k * ncmax + j], len = col_len[(long long)k * ncmax + j];
+    const int z0 = iz[(long long)k * ld + st];
+    const double2* x = X + (long long)row[c0 + c] * ld + st;
+    V a[N2];
+#pragma unroll
+    for (int z = 0; z < N2; ++z) {
+        int p = z - z0;
+        if (p < 0) p += N2;
+        a[z] = p < len ? from64<V>(x[p]) : cpack<V>(0.0, 0.0);
+    }
+    rfft<V, N2, +1>(a);
+    V* dst = colbuf + (long long)c * N2 * ncmax + j;
+#pragma unroll
+    for (int z = 0; z < N2; ++z) dst[(long long)z * ncmax] = a[z];
+}
+
+template <class V, int N2>
+__global__ void __launch_bounds__(kColRegThreads) col_fwd_reg_kernel(
+    const V* __restrict__ colbuf, int ncmax, const int* __restrict__ row, const int* __restrict__ kk, int c0,
+    const int* __restrict__ npw, const int* __restrict__ ncol, const int* __restrict__ col_start,
+    const int* __restrict__ col_len, const int* __restrict__ iz, const double* __restrict__ g2,
+    const double* __restrict__ shift, const double2* __restrict__ X, double2* __restrict__ Y, int ld, int mode,
+    double scale) {
+    const int c = blockIdx.y;
+    const int k = kk[c0 + c];
+    const long long ro = (long long)row[c0 + c] * ld;
+    if (blockIdx.x == 0)
+        for (int g = npw[k] + threadIdx.x; g < ld; g += kColRegThreads) Y[ro + g] = cmk(0.0, 0.0);
+    const int j = blockIdx.x * kColRegThreads + threadIdx.x;
+    if (j >= ncol[k]) return;
+    const int st = col_start[(long long)k * ncmax + j], len = col_len[(long long)k * ncmax + j];
+    const int z0 = iz[(long long)k * ld + st];
+    const V* src = colbuf + (long long)c * N2 * ncmax + j;
+    V a[N2];
+#pragma unroll
+    for (int z = 0; z < N2; ++z) a[z] = src[(long long)z * ncmax];
+    rfft<V, N2, -1>(a);
+    const double sh = mode == 0 ? shift[c0 + c] : 0.0;
+#pragma unroll
+    for (int z = 0; z < N2; ++z) {
+        int p = z - z0;
+        if (p < 0) p += N2;
+        if (p < len) {
+            const long long g = ro + st + p;
+            double2 y;
+            if (mode == 0) {
+                const double d = 0.5 * g2[(long long)k * ld + st + p] - sh;
+                const double2 xv = X[g];
+                y = cmk((double)a[z].x + d * xv.x, (double)a[z].y + d * xv.y);
+            } else {
+                y = cmk((double)a[z].x * scale, (double)a[z].y * scale);
+            }
+            Y[g] = y;
+        }
+    }
+}
+
+// plane transforms with one thread per line: P (band, z) planes per CTA, each [y][x] in shared
+// memory with row stride N0 + 1.  The columns with one grid x form one run of consecutive column
+// indices and consecutive y (mod N1), given per (k, x) by xtab = (first column, count, first y), so
+// the y-line threads read and write their column values straight from and to the column buffers:
+//   op 0: y-inverse (columns -> smem) | x: inverse, * V, forward | y-forward (smem -> columns)
+//   op 1: y-inverse | x-inverse | coalesced copy of the real-space planes
+//   op 2: x-forward of u(r) Delta V(r) read row by row | y-forward
+template <class V, int N0, int N1>
+struct PlaneCfg {
+    static constexpr int L = N0 > N1 ? N0 : N1;
+    static constexpr int LD = N0 + 1;
+    static constexpr int kSmemMax = 227 * 1024;
+    static constexpr int per_plane = N1 * LD * (int)sizeof(V);
+    static constexpr int P0 = 256 / L > 0 ? 256 / L : 1;
+    static constexpr int P = P0 * per_plane <= kSmemMax ? P0 : (kSmemMax / per_plane > 0 ? kSmemMax / per_plane : 1);
+    static constexpr int NT = ((P * L + 31) / 32) * 32;
+    static constexpr bool ok = N0 <= reg_nmax<V>() && N1 <= reg_nmax<V>() && P * per_plane <= kSmemMax;
+    // resident CTAs per SM asked of the compiler (register budget 65536 / (NT * MINB) per thread):
+    // three for the inverse-only form of FP32 lines up to 36 points, which fits 80 registers
+    // without spilling, two for the forms that also hold the forward transform
+    template <int OP>
+    static constexpr int minb() {
+        return (sizeof(V) == 8 && L <= 36) ? (OP == 1 && 3 * P * per_plane <= 228 * 1024 ? 3 : 2) : 1;
+    }
+};
+
+// row of N real or complex values from global memory into registers, 16-byte loads where aligned
+template <class E, int N>
+__device__ __forceinline__ void load_row(const E* __restrict__ p, E (&a)[N]) {
+    constexpr int W = 16 / (int)sizeof(E);
+    if constexpr (W > 1 && N % W == 0) {
+        if ((reinterpret_cast<size_t>(p) & 15) == 0) {
+            const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+            for (int i = 0; i < N / W; ++i) {
+                const float4 v = __ldg(q + i);
+                const E* e = reinterpret_cast<const E*>(&v);
+#pragma unroll
+                for (int w = 0; w < W; ++w) a[i * W + w] = e[w];
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) a[i] = p[i];
+}
+
+// a[x] *= row[x] for a row of N real or complex values in global memory, read in 16-byte pieces
+// where aligned (multiplied as they arrive, so no second row is held in registers)
+template <class V, class E, int N>
+__device__ __forceinline__ void mul_row(const E* __restrict__ p, V (&a)[N]) {
+    constexpr int W = 16 / (int)sizeof(E);
+    if constexpr (W > 1 && N % W == 0) {
+        if ((reinterpret_cast<size_t>(p) & 15) == 0) {
+            const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+            for (int i = 0; i < N / W; ++i) {
+                const float4 v = __ldg(q + i);
+                const E* e = reinterpret_cast<const E*>(&v);
+#pragma unroll
+                for (int w = 0; w < W; ++w) {
+                    if constexpr (sizeof(E) == sizeof(V)) a[i * W + w] = cmul(a[i * W + w], e[w]);
+                    else a[i * W + w] = cscale(a[i * W + w], e[w]);
+                }
+            }
+            return;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        if constexpr (sizeof(E) == sizeof(V)) a[i] = cmul(a[i], p[i]);
+        else a[i] = cscale(a[i], p[i]);
+    }
+}
+
+template <class V, int N0, int N1, int OP>
+__global__ void __launch_bounds__(PlaneCfg<V, N0, N1>::NT, PlaneCfg<V, N0, N1>::template minb<OP>()) plane_reg_kernel(
+    const V* __restrict__ colin, V* __restrict__ colout, int ncmax, const int* __restrict__ kk,
+    const int* __restrict__ spin, int c0, int nc, const int* __restrict__ xtab, int N2,
+    const typename Scalar<V>::type* __restrict__ vt, const V* __restrict__ ur, const int* __restrict__ ur_row,
+    const V* __restrict__ dvt, V* __restrict__ out, double inv_n) {
+    using Cfg = PlaneCfg<V, N0, N1>;
+    using T = typename Scalar<V>::type;
+    constexpr int P = Cfg::P, NT = Cfg::NT, LD = Cfg::LD, NP = N0 * N1, PS = N1 * LD;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V* S = (V*)smraw;  // [P][N1][LD]
+    const long long q0 = (long long)blockIdx.x * P;
+    const long long npairs = (long long)nc * N2;
+    const int tid = threadIdx.x;
+    // ---- y-inverse: line x of plane p from its run of columns (zero where x has none)
+    if (OP != 2) {
+        if (tid < P * N0) {
+            const int p = tid / N0, x = tid % N0;
+            const long long q = q0 + p;
+            if (q < npairs) {
+                const int k = kk[c0 + (int)(q / N2)];
+                const int* t = xtab + ((long long)k * N0 + x) * 3;
+                const int j0 = t[0], cnt = t[1], y0 = t[2];
+                V a[N1];
+                const V* src = colin + q * ncmax + j0;  // pair q = c * N2 + z: plane z of chunk band c
+#pragma unroll
+                for (int y = 0; y < N1; ++y) {
+                    int i = y - y0;
+                    if (i < 0) i += N1;
+                    a[y] = i < cnt ? src[i] : cpack<V>(0.0, 0.0);
+                }
+                if (cnt > 0) rfft<V, N1, +1>(a);
+                V* col = S + p * PS + x;
+#pragma unroll
+                for (int y = 0; y < N1; ++y) col[y * LD] = a[y];
+            }
+        }
+        __syncthreads();
+    }
+    // ---- along x
+    if (tid < P * N1) {
+        const int p = tid / N1, y = tid % N1;
+        const long long q = q0 + p;
+        if (q < npairs) {
+            const int c = (int)(q / N2), z = (int)(q % N2);
+            V* rowp = S + p * PS + y * LD;
+            V a[N0];
+            if (OP == 2) {
+                load_row<V, N0>(ur + ((long long)ur_row[c0 + c] * N2 + z) * NP + y * N0, a);
+                mul_row<V, V, N0>(dvt + ((long long)spin[c0 + c] * N2 + z) * NP + y * N0, a);
+            } else {
+#pragma unroll
+                for (int x = 0; x < N0; ++x) a[x] = rowp[x];
+                rfft<V, N0, +1>(a);
+            }
+            if (OP == 0) mul_row<V, T, N0>(vt + ((long long)spin[c0 + c] * N2 + z) * NP + y * N0, a);
+            if (OP != 1) rfft<V, N0, -1>(a);
+#pragma unroll
+            for (int x = 0; x < N0; ++x) rowp[x] = a[x];
+        }
+    }
+    __syncthreads();
+    if (OP == 1) {
+        for (int p = 0; p < P; ++p) {
+            const long long q = q0 + p;
+            if (q >= npairs) break;
+            V* o = out + q * NP;
+            for (int e = tid; e < NP; e += NT) o[e] = S[p * PS + (e / N0) * LD + e % N0];
+        }
+        return;
+    }
+    // ---- y-forward on the x-lines that hold columns, written straight to the column buffer
+    if (tid < P * N0) {
+        const int p = tid / N0, x = tid % N0;
+        const long long q = q0 + p;
+        if (q < npairs) {
+            const int k = kk[c0 + (int)(q / N2)];
+            const int* t = xtab + ((long long)k * N0 + x) * 3;
+            const int j0 = t[0], cnt = t[1], y0 = t[2];
+            if (cnt > 0) {
+                const V* col = S + p * PS + x;
+                V a[N1];
+#pragma unroll
+                for (int y = 0; y < N1; ++y) a[y] = col[y * LD];
+                rfft<V, N1, -1>(a);
+                const T sc = (T)inv_n;
+                V* dst = colout + q * ncmax + j0;
+#pragma unroll
+                for (int y = 0; y < N1; ++y) {
+                    int i = y - y0;
+                    if (i < 0) i += N1;
+                    if (i < cnt) dst[i] = cscale(a[y], sc);
+                }
+            }
+        }
+    }
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -318,8 +656,23 @@ template <class V, int N2>
 static cudaError_t col_launch(bool inv, const FusedArgs& a) {
     const SphereSet& S = *a.S;
     const BandList& L = *a.L;
-    dim3 g(cdivf(S.ncmax, kCT), a.nc);
-    if (inv) {
+    const bool reg = a.reg && S.contig && N2 <= reg_nmax<V>();
+    if (reg) {
+        cudaError_t e = regfft_init();
+        if (e != cudaSuccess) return e;
+    }
+    dim3 g(cdivf(S.ncmax, reg ? kColRegThreads : kCT), a.nc);
+    const ProfMark pm = prof_start(a.st);
+    if (reg && inv) {
+        col_inv_reg_kernel<V, N2><<<g, kColRegThreads, 0, a.st>>>(a.X, S.ld, L.d_row, L.d_k, a.c0, S.d_ncol,
+                                                                  S.d_col_start, S.d_col_len, S.d_iz, S.ncmax,
+                                                                  (V*)a.colA);
+    } else if (reg) {
+        col_fwd_reg_kernel<V, N2><<<g, kColRegThreads, 0, a.st>>>((const V*)a.colB, S.ncmax, L.d_row, L.d_k, a.c0,
+                                                                  S.d_npw, S.d_ncol, S.d_col_start, S.d_col_len,
+                                                                  S.d_iz, S.d_g2, L.d_shift, a.X, a.Y, S.ld, a.mode,
+                                                                  a.scale);
+    } else if (inv) {
         col_inv_kernel<V, N2><<<g, kColThreads, 0, a.st>>>(a.X, S.ld, L.d_row, L.d_k, a.c0, S.d_ncol, S.d_col_start,
                                                            S.d_col_len, S.d_iz, S.ncmax, (V*)a.colA,
                                                            tw_of<V>(a.fft->ax[2]));
@@ -330,11 +683,66 @@ static cudaError_t col_launch(bool inv, const FusedArgs& a) {
                                                            tw_of<V>(a.fft->ax[2]));
     }
     HP_LAUNCHED();
+    if (prof_on() && L.k.size() >= (size_t)(a.c0 + a.nc) && !S.ncol.empty()) {
+        // sphere coefficients (FP64) once, column buffer once; forward: input vector for the kinetic
+        // term and the zeroed padding as well
+        double bytes = 0.0, flops = 0.0;
+        for (int b = a.c0; b < a.c0 + a.nc; ++b) {
+            const int k = L.k[b];
+            const double col = (double)sizeof(V) * N2 * S.ncol[k];
+            bytes += col + 16.0 * S.npw[k];
+            if (!inv) bytes += 16.0 * (S.ld - S.npw[k]) + (a.mode == 0 ? 16.0 * S.npw[k] : 0.0);
+            flops += 5.0 * N2 * std::log2((double)N2) * S.ncol[k];
+        }
+        prof_stop(pm, HP_KF_COLUMN, a.st, flops, bytes);
+    }
+    return cudaGetLastError();
+}
+
+template <class V, int N0, int N1, int OP>
+static cudaError_t plane_reg_launch(const FusedArgs& a) {
+    using Cfg = PlaneCfg<V, N0, N1>;
+    using T = typename Scalar<V>::type;
+    const SphereSet& S = *a.S;
+    const BandList& L = *a.L;
+    cudaError_t e = regfft_init();
+    if (e != cudaSuccess) return e;
+    const size_t smem = (size_t)Cfg::P * Cfg::per_plane;
+    static bool attr = false;
+    if (!attr) {
+        e = cudaFuncSetAttribute(plane_reg_kernel<V, N0, N1, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const long long npairs = (long long)a.nc * a.N2;
+    const int grid = cdivf(npairs, Cfg::P);
+    const ProfMark pm = prof_start(a.st);
+    plane_reg_kernel<V, N0, N1, OP><<<grid, Cfg::NT, smem, a.st>>>(
+        (const V*)a.colA, (V*)a.colB, S.ncmax, L.d_k, L.d_spin, a.c0, a.nc, S.d_xtab, a.N2, (const T*)a.vt,
+        (const V*)a.ur, L.d_row, (const V*)a.dvt, (V*)a.out, a.inv_n);
+    HP_LAUNCHED();
+    if (prof_on() && L.k.size() >= (size_t)(a.c0 + a.nc) && L.spin.size() >= (size_t)(a.c0 + a.nc) && !S.ncol.empty()) {
+        const double nr = (double)N0 * N1 * a.N2;
+        double bytes = 0.0;
+        bool spin_seen[2] = {false, false};
+        for (int b = a.c0; b < a.c0 + a.nc; ++b) {
+            const double col = (double)sizeof(V) * a.N2 * S.ncol[L.k[b]];
+            bytes += OP == 0 ? 2.0 * col : col + (double)sizeof(V) * nr;
+            spin_seen[L.spin[b] & 1] = true;
+        }
+        const double pot = OP == 0 ? (double)sizeof(T) * nr : OP == 2 ? (double)sizeof(V) * nr : 0.0;
+        bytes += pot * ((int)spin_seen[0] + (int)spin_seen[1]);
+        const double flops = (OP == 0 ? 2.0 : 1.0) * 5.0 * nr * std::log2((double)N0 * N1) * a.nc;
+        prof_stop(pm, HP_KF_PLANE, a.st, flops, bytes);
+    }
     return cudaGetLastError();
 }
 
 template <class V, int N0, int N1, int OP>
 static cudaError_t plane_launch(const FusedArgs& a) {
+    if constexpr (PlaneCfg<V, N0, N1>::ok) {
+        if (a.reg && a.S->d_xtab && a.S->xtab_n0 == N0) return plane_reg_launch<V, N0, N1, OP>(a);
+    }
     const SphereSet& S = *a.S;
     const BandList& L = *a.L;
     const size_t smem = 2 * sizeof(V) * N1 * (N0 + 1);
@@ -347,10 +755,26 @@ static cudaError_t plane_launch(const FusedArgs& a) {
     }
     dim3 g(a.N2, a.nc);
     using T = typename Scalar<V>::type;
+    const ProfMark pm = prof_start(a.st);
     plane_kernel<V, N0, N1, OP><<<g, kPlaneThreads, smem, a.st>>>(
         (const V*)a.colA, (V*)a.colB, S.ncmax, L.d_k, L.d_spin, a.c0, S.d_ncol, S.d_col_xy, a.N2, (const T*)a.vt,
         (const V*)a.ur, L.d_row, (const V*)a.dvt, (V*)a.out, a.inv_n, tw_of<V>(a.fft->ax[0]), tw_of<V>(a.fft->ax[1]));
     HP_LAUNCHED();
+    if (prof_on() && L.k.size() >= (size_t)(a.c0 + a.nc) && L.spin.size() >= (size_t)(a.c0 + a.nc) && !S.ncol.empty()) {
+        // column buffer in and/or out per band, real-space grids once per band, potential once per spin
+        const double nr = (double)N0 * N1 * a.N2;
+        double bytes = 0.0;
+        bool spin_seen[2] = {false, false};
+        for (int b = a.c0; b < a.c0 + a.nc; ++b) {
+            const double col = (double)sizeof(V) * a.N2 * S.ncol[L.k[b]];
+            bytes += OP == 0 ? 2.0 * col : col + (double)sizeof(V) * nr;
+            spin_seen[L.spin[b] & 1] = true;
+        }
+        const double pot = OP == 0 ? (double)sizeof(T) * nr : OP == 2 ? (double)sizeof(V) * nr : 0.0;
+        bytes += pot * ((int)spin_seen[0] + (int)spin_seen[1]);
+        const double flops = (OP == 0 ? 2.0 : 1.0) * 5.0 * nr * std::log2((double)N0 * N1) * a.nc;
+        prof_stop(pm, HP_KF_PLANE, a.st, flops, bytes);
+    }
     return cudaGetLastError();
 }
 

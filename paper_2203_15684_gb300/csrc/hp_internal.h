@@ -105,6 +105,12 @@ struct SphereSet {          // device arrays, nk spheres of at most ld points
     int* d_col_len = nullptr;   // [nk][ncmax]
     int* d_col_xy = nullptr;    // [nk][ncmax] x * N1 + y
     int* d_iz = nullptr;        // [nk][ld]
+    std::vector<int> ncol;      // host copy of d_ncol
+    // per (k, x): the columns with grid x are columns j0 .. j0 + cnt - 1 with y = y0, y0 + 1, ...
+    // (mod N1); [nk][xtab_n0][3] = (j0, cnt, y0); null when some x does not form such a run
+    int* d_xtab = nullptr;
+    int xtab_n0 = 0;
+    bool contig = false;        // every column is one run of consecutive z (mod N2)
 };
 
 struct BandList {
@@ -155,7 +161,8 @@ cudaError_t k_gather_scaled32(const SphereSet& S, const BandList& L, int c0, int
 cudaError_t k_mul_cpot32(float2* grid, const float2* src_rows, const int* src_row_of_item, int nc, int nr,
                          const float2* v, const BandList& L, int c0, cudaStream_t st);
 cudaError_t k_drho_acc32(const float2* ur, const int* ur_row_of_item, const float2* xr, int nc, int nr,
-                         const BandList& L, int c0, double weight, int nspin, double2* drho, cudaStream_t st);
+                         const BandList& L, int c0, double weight, int nspin, double2* drho, double2* part,
+                         size_t part_elems, cudaStream_t st);
 cudaError_t k_to_f32(const double* a, float* b, long long n, cudaStream_t st);
 cudaError_t k_to_c32(const double2* a, float2* b, long long n, cudaStream_t st);
 cudaError_t k_band_dot(const BandList& L, const SphereSet& S, const double2* X, const double2* Y, int ld,
@@ -176,7 +183,8 @@ cudaError_t k_formfactor(const double* kcart, int nk, const int* miller, const i
                          const double* row_width, const double* row_pref, const double* tau, double2* out,
                          cudaStream_t st);
 cudaError_t k_drho_acc(const double2* ur, const int* ur_row_of_item, const double2* xr, int nc, int nr,
-                       const BandList& L, int c0, double weight, int nspin, double2* drho, cudaStream_t st);
+                       const BandList& L, int c0, double weight, int nspin, double2* drho, double2* part,
+                         size_t part_elems, cudaStream_t st);
 cudaError_t k_density_acc(const double2* ur, int nc, int nr, const BandList& L, int c0, double weight, int nspin,
                           double* rho, cudaStream_t st);
 cudaError_t k_hartree_q(double2* rho_g, const int N[3], const double* bvec, const double qfrac[3], double ecut4,
@@ -251,8 +259,18 @@ struct FusedArgs {
     const void* dvt = nullptr;   // plane-major complex Delta V [spin][z][y][x]
     void* out = nullptr;         // plane-major real-space output [c][z][y][x]
     double inv_n = 1.0;
+    bool reg = true;             // register-resident line FFTs where the sizes allow
     cudaStream_t st = nullptr;
 };
+// live kernel timing (hp_profile_*): mark before a launch, stop after it with its family and its
+// algorithmic flops and bytes; both are no-ops while profiling is off
+struct ProfMark {
+    cudaEvent_t e0 = nullptr;
+};
+bool prof_on();
+ProfMark prof_start(cudaStream_t st);
+void prof_stop(const ProfMark& m, int fam, cudaStream_t st, double flops, double bytes);
+
 bool fused_supported(const int N[3]);
 cudaError_t fused_col(bool fp32, bool inv, const FusedArgs& a);
 cudaError_t fused_plane(bool fp32, int op, const FusedArgs& a);
@@ -332,6 +350,7 @@ struct hp_ctx {
     float2* d_dv32 = nullptr;          // mixed precision: FP32 copy of Delta V_Hxc
     // sphere-sparse fused transforms (when the grid sizes are supported)
     bool fused = false;
+    bool fused_reg = true;             // fused transforms with register-resident line FFTs
     bool ur_planes = false;            // the real-space band cache is plane-major (built by the fused path)
     void* d_vt = nullptr;              // plane-major V_eff [nspin][z][y][x] (double or float)
     void* d_dvt = nullptr;             // plane-major Delta V (double2 or float2)

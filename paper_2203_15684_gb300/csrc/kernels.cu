@@ -268,32 +268,6 @@ cudaError_t k_mul_cpot32(float2* grid, const float2* src_rows, const int* src_ro
 }
 
 // drho[s][r] += weight * sum_c conj(ur[ur_row[c]][r]) xr[c][r]  (FP32 inputs, FP64 accumulation)
-__global__ void drho_acc32_kernel(const float2* __restrict__ ur, const int* __restrict__ ur_row,
-                                  const float2* __restrict__ xr, int nc, int nr, const int* __restrict__ spin, int c0,
-                                  double weight, int nspin, double2* __restrict__ drho) {
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += gridDim.x * blockDim.x) {
-        double a0r = 0.0, a0i = 0.0, a1r = 0.0, a1i = 0.0;
-        for (int c = 0; c < nc; ++c) {
-            const float2 u = ur[(long long)ur_row[c0 + c] * nr + r];
-            const float2 x = xr[(long long)c * nr + r];
-            const double tr = (double)u.x * x.x + (double)u.y * x.y;
-            const double ti = (double)u.x * x.y - (double)u.y * x.x;
-            if (spin[c0 + c] == 0) { a0r += tr; a0i += ti; }
-            else { a1r += tr; a1i += ti; }
-        }
-        drho[r] = cadd(drho[r], cmk(a0r * weight, a0i * weight));
-        if (nspin == 2) drho[(long long)nr + r] = cadd(drho[(long long)nr + r], cmk(a1r * weight, a1i * weight));
-    }
-}
-
-cudaError_t k_drho_acc32(const float2* ur, const int* ur_row_of_item, const float2* xr, int nc, int nr,
-                         const BandList& L, int c0, double weight, int nspin, double2* drho, cudaStream_t st) {
-    if (nc <= 0) return cudaSuccess;
-    drho_acc32_kernel<<<cdiv(nr, 256), 256, 0, st>>>(ur, ur_row_of_item, xr, nc, nr, L.d_spin, c0, weight, nspin, drho);
-    HP_LAUNCHED();
-    return cudaGetLastError();
-}
-
 __global__ void to_f32_kernel(const double* __restrict__ a, float* __restrict__ b, long long n) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         b[i] = (float)a[i];
@@ -405,11 +379,13 @@ cudaError_t k_proj(const BandList& L, const SphereSet& S, const ProjMat& A, cons
                    double2* scratch, size_t scratch_elems, cudaStream_t st, bool fp32) {
     if (L.nb <= 0 || A.nrow <= 0) return cudaSuccess;
     if (A.nrow > kPStride) return cudaErrorInvalidValue;
-    int ksplit = std::max(1, 2 * 152 / std::max(1, L.nseg));
-    ksplit = std::min(ksplit, std::max(1, S.ld / 128));
+    // about one wave of 8 resident CTAs per SM, at least two 32-point tiles per split
+    int ksplit = std::max(1, cdiv(152 * 8, std::max(1, L.nseg)));
+    ksplit = std::min(ksplit, std::max(1, S.ld / (2 * TG)));
     while (ksplit > 1 && (size_t)ksplit * L.nb * kPStride > scratch_elems) --ksplit;
     if ((size_t)ksplit * L.nb * kPStride > scratch_elems) return cudaErrorMemoryAllocation;
     dim3 g(L.nseg, ksplit);
+    const ProfMark pm = prof_start(st);
     if (fp32)
         proj_kernel<float><<<g, 256, 0, st>>>(A.base, A.stride_s, A.stride_k, A.row0, A.nrow, ld, X, L.d_row,
                                               L.d_seg_start, L.d_seg_k, L.d_seg_s, S.d_npw, A.kmap, ksplit, scratch, L.nb);
@@ -421,10 +397,21 @@ cudaError_t k_proj(const BandList& L, const SphereSet& S, const ProjMat& A, cons
     if (e != cudaSuccess) return e;
     proj_reduce_kernel<<<cdiv((long long)L.nb * A.nrow, 256), 256, 0, st>>>(scratch, ksplit, L.nb, A.nrow, P);
     HP_LAUNCHED();
+    if (prof_on() && L.k.size() >= (size_t)L.nb && L.seg_k.size() >= (size_t)L.nseg) {
+        // band vectors once, projector rows once per (k, spin) segment, partial sums written and
+        // read, results written; 8 flops per complex multiply-add
+        double bytes = 2.0 * 16.0 * ksplit * L.nb * A.nrow + 16.0 * L.nb * A.nrow, flops = 0.0;
+        for (int b = 0; b < L.nb; ++b) {
+            bytes += 16.0 * S.npw[L.k[b]];
+            flops += 8.0 * A.nrow * S.npw[L.k[b]];
+        }
+        for (int sg = 0; sg < L.nseg; ++sg) bytes += 16.0 * A.nrow * S.npw[L.seg_k[sg]];
+        prof_stop(pm, HP_KF_PROJECT, st, flops, bytes);
+    }
     return cudaGetLastError();
 }
 
-constexpr int kExpC = 8;
+constexpr int kExpC = 16;
 
 template <class S>
 __global__ void __launch_bounds__(128) expand_kernel(const double2* __restrict__ Abase, long long sa_s, long long sa_k,
@@ -488,6 +475,7 @@ cudaError_t k_expand(const BandList& L, const SphereSet& S, const ProjMat& A, co
     if (L.nb <= 0 || A.nrow <= 0) return cudaSuccess;
     if (A.nrow > kPStride) return cudaErrorInvalidValue;
     dim3 g(cdiv(ld, 128), L.nseg);
+    const ProfMark pm = prof_start(st);
     if (fp32)
         expand_kernel<float><<<g, 128, 0, st>>>(A.base, A.stride_s, A.stride_k, A.row0, A.nrow, ld, P, pscale, alpha, Y,
                                                 L.d_row, L.d_seg_start, L.d_seg_k, L.d_seg_s, S.d_npw, A.kmap);
@@ -495,6 +483,16 @@ cudaError_t k_expand(const BandList& L, const SphereSet& S, const ProjMat& A, co
         expand_kernel<double><<<g, 128, 0, st>>>(A.base, A.stride_s, A.stride_k, A.row0, A.nrow, ld, P, pscale, alpha, Y,
                                                  L.d_row, L.d_seg_start, L.d_seg_k, L.d_seg_s, S.d_npw, A.kmap);
     HP_LAUNCHED();
+    if (prof_on() && L.k.size() >= (size_t)L.nb && L.seg_k.size() >= (size_t)L.nseg) {
+        // band vectors read and written, coefficients read, projector rows once per segment
+        double bytes = 16.0 * L.nb * A.nrow, flops = 0.0;
+        for (int b = 0; b < L.nb; ++b) {
+            bytes += 2.0 * 16.0 * S.npw[L.k[b]];
+            flops += 8.0 * A.nrow * S.npw[L.k[b]];
+        }
+        for (int sg = 0; sg < L.nseg; ++sg) bytes += 16.0 * A.nrow * S.npw[L.seg_k[sg]];
+        prof_stop(pm, HP_KF_EXPAND, st, flops, bytes);
+    }
     return cudaGetLastError();
 }
 
@@ -755,29 +753,89 @@ cudaError_t k_formfactor(const double* kcart, int nk, const int* miller, const i
 // densities
 // ------------------------------------------------------------------------------------------------
 // drho[s][r] += weight * sum_c conj(ur[ur_row[c]][r]) xr[c][r]   (items of spin s), fixed order
-__global__ void drho_acc_kernel(const double2* __restrict__ ur, const int* __restrict__ ur_row,
-                                const double2* __restrict__ xr, int nc, int nr, const int* __restrict__ spin, int c0,
-                                double weight, int nspin, double2* __restrict__ drho) {
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nr; r += gridDim.x * blockDim.x) {
-        double2 acc0 = cmk(0.0, 0.0), acc1 = cmk(0.0, 0.0);
-        for (int c = 0; c < nc; ++c) {
-            const double2 u = ur[(long long)ur_row[c0 + c] * nr + r];
-            const double2 x = xr[(long long)c * nr + r];
-            const double2 t = cmulc(u, x);
-            if (spin[c0 + c] == 0) acc0 = cadd(acc0, t);
-            else acc1 = cadd(acc1, t);
+// Delta rho[s][r] += weight * sum_c conj(ur[row(c)][r]) xr[c][r], split over band slices: each CTA
+// sums one slice of bands for 256 points (tiles of 16 bands in the compute precision, FP64 across
+// tiles) into part[slice][spin][r]; the slices are then added in fixed order.
+constexpr int kDrhoTile = 16;
+
+template <class V>
+__global__ void __launch_bounds__(256) drho_part_kernel(const V* __restrict__ ur, const int* __restrict__ ur_row,
+                                                        const V* __restrict__ xr, int nc, int nr,
+                                                        const int* __restrict__ spin, int c0, int slice,
+                                                        double2* __restrict__ part) {
+    using T = typename Scalar<V>::type;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int sl = blockIdx.y;
+    const int cb = sl * slice, ce = min(nc, cb + slice);
+    if (r >= nr) return;
+    double a0r = 0.0, a0i = 0.0, a1r = 0.0, a1i = 0.0;
+    for (int t = cb; t < ce; t += kDrhoTile) {
+        const int te = min(ce, t + kDrhoTile);
+        T t0r = 0, t0i = 0, t1r = 0, t1i = 0;
+#pragma unroll 4
+        for (int c = t; c < te; ++c) {
+            const V u = ur[(long long)ur_row[c0 + c] * nr + r];
+            const V x = xr[(long long)c * nr + r];
+            const T tr = u.x * x.x + u.y * x.y;
+            const T ti = u.x * x.y - u.y * x.x;
+            if (spin[c0 + c] == 0) {
+                t0r += tr;
+                t0i += ti;
+            } else {
+                t1r += tr;
+                t1i += ti;
+            }
         }
-        drho[r] = cadd(drho[r], cscale(acc0, weight));
-        if (nspin == 2) drho[(long long)nr + r] = cadd(drho[(long long)nr + r], cscale(acc1, weight));
+        a0r += (double)t0r;
+        a0i += (double)t0i;
+        a1r += (double)t1r;
+        a1i += (double)t1i;
     }
+    part[((long long)sl * 2) * nr + r] = cmk(a0r, a0i);
+    part[((long long)sl * 2 + 1) * nr + r] = cmk(a1r, a1i);
+}
+
+__global__ void drho_reduce_kernel(const double2* __restrict__ part, int nsplit, int nr, int nspin, double weight,
+                                   double2* __restrict__ drho) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)nspin * nr) return;
+    const int s = (int)(e / nr), r = (int)(e % nr);
+    double2 acc = cmk(0.0, 0.0);
+    for (int sl = 0; sl < nsplit; ++sl) acc = cadd(acc, part[((long long)sl * 2 + s) * nr + r]);
+    drho[e] = cadd(drho[e], cscale(acc, weight));
+}
+
+template <class V>
+static cudaError_t drho_acc_launch(const V* ur, const int* ur_row, const V* xr, int nc, int nr, const BandList& L,
+                                   int c0, double weight, int nspin, double2* drho, double2* part, size_t part_elems,
+                                   cudaStream_t st) {
+    if (nc <= 0) return cudaSuccess;
+    const int bx = cdiv(nr, 256);
+    // about two waves of 8 resident CTAs per SM, slices of at least one tile, partials within the scratch
+    int nsplit = std::max(1, std::min(cdiv(2 * 152 * 8, bx), cdiv(nc, kDrhoTile)));
+    while (nsplit > 1 && (size_t)nsplit * 2 * nr > part_elems) --nsplit;
+    if ((size_t)nsplit * 2 * nr > part_elems) return cudaErrorMemoryAllocation;
+    const int slice = cdiv(nc, nsplit);
+    nsplit = cdiv(nc, slice);
+    drho_part_kernel<V><<<dim3(bx, nsplit), 256, 0, st>>>(ur, ur_row, xr, nc, nr, L.d_spin, c0, slice, part);
+    HP_LAUNCHED();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    drho_reduce_kernel<<<cdiv((long long)nspin * nr, 256), 256, 0, st>>>(part, nsplit, nr, nspin, weight, drho);
+    HP_LAUNCHED();
+    return cudaGetLastError();
 }
 
 cudaError_t k_drho_acc(const double2* ur, const int* ur_row_of_item, const double2* xr, int nc, int nr,
-                       const BandList& L, int c0, double weight, int nspin, double2* drho, cudaStream_t st) {
-    if (nc <= 0) return cudaSuccess;
-    drho_acc_kernel<<<cdiv(nr, 256), 256, 0, st>>>(ur, ur_row_of_item, xr, nc, nr, L.d_spin, c0, weight, nspin, drho);
-    HP_LAUNCHED();
-    return cudaGetLastError();
+                       const BandList& L, int c0, double weight, int nspin, double2* drho, double2* part,
+                       size_t part_elems, cudaStream_t st) {
+    return drho_acc_launch<double2>(ur, ur_row_of_item, xr, nc, nr, L, c0, weight, nspin, drho, part, part_elems, st);
+}
+
+cudaError_t k_drho_acc32(const float2* ur, const int* ur_row_of_item, const float2* xr, int nc, int nr,
+                         const BandList& L, int c0, double weight, int nspin, double2* drho, double2* part,
+                         size_t part_elems, cudaStream_t st) {
+    return drho_acc_launch<float2>(ur, ur_row_of_item, xr, nc, nr, L, c0, weight, nspin, drho, part, part_elems, st);
 }
 
 // rho[s][r] += weight * sum_c |ur[c][r]|^2
