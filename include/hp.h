@@ -254,6 +254,13 @@ hp_status hp_selftest_fft_host(int n, int nlines, int sign, const double* in, do
  * Allocates its own device buffers.  Errors: HP_EINVAL, HP_ECUDA. */
 hp_status hp_selftest_eigh(int n, int nbatch, const double* A, double* w, double* V);
 
+/* Device self-test of the integer-operation FP64 <-> FP32 conversions used in the FP32 form's hot
+ * loops (no counterpart in the paper).  For n host values in[i]: f[i] = FP64 -> FP32 rounded to
+ * nearest even (results below the FP32 normal range flushed to signed zero), back[i] = f[i]
+ * widened exactly to FP64; f_ref and back_ref are the hardware conversions of the same values.
+ * Allocates its own device buffers.  Errors: HP_EINVAL (n < 1 or a NULL pointer), HP_ECUDA. */
+hp_status hp_selftest_convert(long long n, const double* in, float* f, double* back, float* f_ref, double* back_ref);
+
 #ifdef __cplusplus
 }
 #endif

@@ -70,7 +70,7 @@ _lib = None
 SYMBOLS = ["hp_default_options", "hp_setup", "hp_query_sizes", "hp_sphere", "hp_hubbard_atoms", "hp_ground_state",
            "hp_set_ground_state", "hp_get_ground_state", "hp_apply_h", "hp_response", "hp_hubbard", "hp_last_error",
            "hp_destroy", "hp_selftest_fft_host", "hp_selftest_eigh", "hp_get_wavefunctions", "hp_profile_begin",
-           "hp_profile_end", "hp_launch_count", "hp_apply_h_noalloc", "hp_set_precision"]
+           "hp_profile_end", "hp_launch_count", "hp_apply_h_noalloc", "hp_set_precision", "hp_selftest_convert"]
 
 
 def lib():
@@ -108,6 +108,7 @@ def lib():
     L.hp_launch_count.argtypes = []
     L.hp_apply_h_noalloc.argtypes = [V, I, I, I, V, V, V]
     L.hp_set_precision.argtypes = [V, I]
+    L.hp_selftest_convert.argtypes = [C.c_longlong, P(D), P(C.c_float), P(D), P(C.c_float), P(D)]
     for n in SYMBOLS:
         f = getattr(L, n)
         if n == "hp_launch_count":
@@ -159,6 +160,20 @@ def selftest_eigh(A):
     if st != HP_OK:
         raise HPError(st, "hp_selftest_eigh")
     return w, V
+
+
+def selftest_convert(x):
+    """-> (f, back, f_ref, back_ref): the library's integer-operation FP64 -> FP32 -> FP64
+    conversions of the float64 array x and the hardware conversions, computed on the GPU."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    n = x.size
+    f, fr = np.zeros(n, np.float32), np.zeros(n, np.float32)
+    b, br = np.zeros(n), np.zeros(n)
+    fp = lambda a: a.ctypes.data_as(C.POINTER(C.c_float))
+    st = lib().hp_selftest_convert(n, _dptr(x), fp(f), _dptr(b), fp(fr), _dptr(br))
+    if st != HP_OK:
+        raise HPError(st, "hp_selftest_convert")
+    return f, b, fr, br
 
 
 def profile_begin():

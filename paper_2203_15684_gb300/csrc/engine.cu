@@ -879,11 +879,27 @@ hp_status prepare_resp(hp_ctx* c) {
     c->d_ur32 = nullptr;
     dfree(c, c->d_aphi);
     dfree(c, c->d_fxc);
+    for (float2** p : {&c->d_psi32, &c->d_beta32, &c->d_phi32}) {
+        dfree(c, *p);
+        *p = nullptr;
+    }
     if (mixed) {
         CK(dalloc(c, &c->d_ur32, (size_t)rows * nr));
         CK(dalloc(c, &c->d_veff32, (size_t)nspin * nr));
         CK(dalloc(c, &c->d_dv32, (size_t)nspin * nr));
         CK(k_to_f32(c->d_veff, c->d_veff32, (long long)nspin * nr, c->st));
+        const size_t npsi = (size_t)nspin * nk * c->nbnd * c->ld, nbeta = (size_t)nk * c->nproj * c->ld,
+                     nphi = (size_t)nk * c->nhub * c->ld;
+        CK(dalloc(c, &c->d_psi32, npsi));
+        CK(k_to_c32(c->d_psi, c->d_psi32, (long long)npsi, c->st));
+        if (nbeta) {
+            CK(dalloc(c, &c->d_beta32, nbeta));
+            CK(k_to_c32(c->d_beta_k, c->d_beta32, (long long)nbeta, c->st));
+        }
+        if (nphi) {
+            CK(dalloc(c, &c->d_phi32, nphi));
+            CK(k_to_c32(c->d_phi_k, c->d_phi32, (long long)nphi, c->st));
+        }
     } else {
         CK(dalloc(c, &c->d_ur, (size_t)rows * nr));
     }
@@ -1039,12 +1055,19 @@ hp_status apply_sternheimer(hp_ctx* c, const BandList& L, const double2* X, doub
     const bool fp32 = c->opt.precision == HP_PRECISION_MIXED;
     hp_status s = (c->fused && c->d_vt) ? apply_local_fused(c, S, L, X, Y, fp32) : apply_local(c, S, L, X, Y, c->d_veff, fp32);
     if (s != HP_OK) return s;
-    s = apply_nonlocal(c, S, L, X, Y, c->d_Pbuf, kmap, fp32);
+    // V_NL and alpha P_v in one projection and one expansion: rows 0 .. nproj-1 are beta (weights
+    // D), rows nproj .. nproj+nocc-1 the occupied states at k+q (weight alpha)
+    ProjMat A = beta_family(c, kmap);
+    A.base32 = c->d_beta32;
+    A.base2 = c->d_psi;
+    A.base2_32 = c->d_psi32;
+    A.stride2_s = (long long)c->nk * c->nbnd * c->ld;
+    A.stride2_k = (long long)c->nbnd * c->ld;
+    A.nrow2 = c->nocc;
+    A.scale2 = c->alpha_pv;
+    s = project(c, S, L, A, X, c->d_Pbuf, fp32);
     if (s != HP_OK) return s;
-    ProjMat U{c->d_psi, (long long)c->nk * c->nbnd * c->ld, (long long)c->nbnd * c->ld, c->nocc, 0, kmap};
-    s = project(c, S, L, U, X, c->d_Pbuf, fp32);
-    if (s != HP_OK) return s;
-    CK(k_expand(L, S, U, c->d_Pbuf, nullptr, c->alpha_pv, Y, c->ld, c->st, fp32));
+    CK(k_expand(L, S, A, c->d_Pbuf, c->d_projD, 1.0, Y, c->ld, c->st, fp32));
     return HP_OK;
 }
 
@@ -1105,8 +1128,8 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
     const int mJ = c->hub_mdim[jj], oJ = c->hub_off[jj];
     ProjMat phiJk{c->d_phi_k, 0, (long long)c->nhub * ld, mJ, oJ, nullptr};
     ProjMat phiJkq{c->d_phi_k, 0, (long long)c->nhub * ld, mJ, oJ, kmap};
-    ProjMat phikq{c->d_phi_k, 0, (long long)c->nhub * ld, c->nhub, 0, kmap};
-    ProjMat Ukq{c->d_psi, (long long)nk * c->nbnd * ld, (long long)c->nbnd * ld, nocc, 0, kmap};
+    ProjMat phikq{c->d_phi_k, 0, (long long)c->nhub * ld, c->nhub, 0, kmap, c->d_phi32};
+    ProjMat Ukq{c->d_psi, (long long)nk * c->nbnd * ld, (long long)c->nbnd * ld, nocc, 0, kmap, c->d_psi32};
     if ((s = project(c, c->kset, Lpsi, phiJk, c->d_psi, c->d_Pbuf)) != HP_OK) return s;
     CK(cudaMemsetAsync(c->d_vpu, 0, sizeof(double2) * nvec, c->st));
     CK(k_expand(Lall, Sq, phiJkq, c->d_Pbuf, nullptr, 1.0, c->d_vpu, ld, c->st));

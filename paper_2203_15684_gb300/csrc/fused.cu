@@ -126,7 +126,14 @@ __device__ __forceinline__ V* lines(V* src, V* dst, const V* __restrict__ tw) {
 
 template <class V>
 __device__ __forceinline__ V from64(double2 x) {
-    return cpack<V>(x.x, x.y);
+    if constexpr (sizeof(V) == 8) return cmkf(d2f_bits(x.x), d2f_bits(x.y));
+    else return x;
+}
+
+template <class V>
+__device__ __forceinline__ double2 to64(V x) {
+    if constexpr (sizeof(V) == 8) return cmk(f2d_bits(x.x), f2d_bits(x.y));
+    else return x;
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -278,13 +285,14 @@ __global__ void __launch_bounds__(kColRegThreads) col_fwd_reg_kernel(
         if (p < 0) p += N2;
         if (p < len) {
             const long long g = ro + st + p;
+            const double2 v = to64<V>(a[z]);
             double2 y;
             if (mode == 0) {
                 const double d = 0.5 * g2[(long long)k * ld + st + p] - sh;
                 const double2 xv = X[g];
-                y = cmk((double)a[z].x + d * xv.x, (double)a[z].y + d * xv.y);
+                y = cmk(v.x + d * xv.x, v.y + d * xv.y);
             } else {
-                y = cmk((double)a[z].x * scale, (double)a[z].y * scale);
+                y = cscale(v, scale);
             }
             Y[g] = y;
         }

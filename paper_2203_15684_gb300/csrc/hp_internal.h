@@ -48,6 +48,34 @@ template <class V> HD V cpack(double r, double i);
 template <> HD double2 cpack<double2>(double r, double i) { return cmk(r, i); }
 template <> HD float2 cpack<float2>(double r, double i) { return cmkf((float)r, (float)i); }
 
+#if defined(__CUDACC__)
+// FP64 <-> FP32 conversions with integer operations on the IEEE 754 bit patterns, for hot loops:
+// the FP64 pipe that runs the hardware conversions is narrow on this part.
+// d2f_bits: round to nearest, ties to even; results below the FP32 normal range flush to a signed
+// zero and results above it become infinity (NaN inputs are not expected).
+__device__ __forceinline__ float d2f_bits(double d) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const unsigned sign = hi & 0x80000000u;
+    const int fe = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;  // FP32 biased exponent
+    if (fe <= 0) return __uint_as_float(sign);
+    if (fe >= 255) return __uint_as_float(sign | 0x7F800000u);
+    unsigned f = ((unsigned)fe << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    const unsigned rem = lo & 0x1FFFFFFFu;  // the 29 dropped mantissa bits
+    f += (rem > 0x10000000u) | ((rem == 0x10000000u) & (f & 1u));
+    return __uint_as_float(sign | f);
+}
+// f2d_bits: exact widening; FP32 subnormals become zero (infinity and NaN are not expected).
+__device__ __forceinline__ double f2d_bits(float x) {
+    const unsigned u = __float_as_uint(x);
+    const unsigned e = (u >> 23) & 0xFFu;
+    const unsigned sign = u & 0x80000000u;
+    const unsigned hi = e ? (sign | ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3)) : sign;
+    const unsigned lo = e ? (u << 29) : 0u;
+    return __hiloint2double((int)hi, (int)lo);
+}
+#endif
+
 // every kernel launch of the library increments this counter (read by hp_launch_count)
 extern std::atomic<long long> g_launches;
 #define HP_LAUNCHED() (hp::g_launches.fetch_add(1, std::memory_order_relaxed))
@@ -130,9 +158,16 @@ struct BandList {
 struct ProjMat {            // a family of projector matrices: base + s*stride_s + k*stride_k
     const double2* base;
     long long stride_s, stride_k;
-    int nrow;               // rows used (<= 128)
+    int nrow;               // rows used (nrow + nrow2 <= 128)
     int row0;               // first row inside each matrix
     const int* kmap;        // optional device map: matrix of list sphere k is kmap[k]
+    const float2* base32 = nullptr;     // FP32 copy of the family (same layout), read by the FP32 form
+    // optional second family, rows nrow .. nrow + nrow2 - 1 of the projection (same kmap)
+    const double2* base2 = nullptr;
+    const float2* base2_32 = nullptr;
+    long long stride2_s = 0, stride2_k = 0;
+    int nrow2 = 0, row02 = 0;
+    double scale2 = 1.0;    // expansion weight of the second family's rows
 };
 
 // kernels.cu
@@ -340,6 +375,11 @@ struct hp_ctx {
     double* d_rho = nullptr;           // [nspin][nr]
     double* d_veff = nullptr;          // [nspin][nr] V_loc + V_Hxc
     double2* d_psi = nullptr;          // [nspin][nk][nbnd][ld]
+    // FP32 copies of the projector families for the mixed form (same layouts), built with the
+    // response caches
+    float2* d_psi32 = nullptr;
+    float2* d_beta32 = nullptr;
+    float2* d_phi32 = nullptr;
     // response caches (built on first use after a ground state)
     bool resp_ready = false;
     double2* d_ur = nullptr;           // [nspin][nk][nocc][nr]

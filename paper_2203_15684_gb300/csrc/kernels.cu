@@ -286,82 +286,148 @@ cudaError_t k_to_c32(const double2* a, float2* b, long long n, cudaStream_t st) 
 }
 
 // ------------------------------------------------------------------------------------------------
-// segmented projector contractions
-//   proj:   P[c][p]  = sum_G conj(A_seg[row0 + p][G]) X[row[c]][G]          (p < nrow)
-//   expand: Y[row[c]][G] += alpha sum_p A_seg[row0 + p][G] pscale[p] P[c][p]
-// P is indexed by list item c with a row stride of 128.
+// segmented projector contractions over one or two projector families (rows 0 .. n0-1 from the
+// first, n0 .. n0+n1-1 from the second):
+//   proj:   P[c][p]  = sum_G conj(A_seg[p][G]) X[row[c]][G]
+//   expand: Y[row[c]][G] += alpha sum_p A_seg[p][G] w_p P[c][p],  w_p = pscale[p] (first family)
+//           or scale2 (second family)
+// P is indexed by list item c with a row stride of 128.  In the FP32 form the families are read
+// from their FP32 copies when present, and FP64 band data is rounded with integer operations.
 // ------------------------------------------------------------------------------------------------
 constexpr int kPStride = 128;
-constexpr int TP = 32, TC = 32, TG = 32;
+constexpr int TC = 32, TG = 32;
 
-template <class S>
-__global__ void __launch_bounds__(256) proj_kernel(const double2* __restrict__ Abase, long long sa_s, long long sa_k,
-                                                   int row0, int nrow, int ld, const double2* __restrict__ X,
+struct ProjDev {
+    const void* a0;
+    const void* a1;
+    long long s0_s, s0_k, s1_s, s1_k;
+    int n0, r0, n1, r1;
+    const int* kmap;
+};
+
+template <class AT>
+__device__ __forceinline__ const AT* proj_row(const ProjDev& d, int s, int mk, int p, int ld) {
+    if (p < d.n0) return (const AT*)d.a0 + s * d.s0_s + mk * d.s0_k + (long long)(d.r0 + p) * ld;
+    return (const AT*)d.a1 + s * d.s1_s + mk * d.s1_k + (long long)(d.r1 + p - d.n0) * ld;
+}
+
+template <class V>
+__device__ __forceinline__ V load_as(const double2& x) {
+    if constexpr (sizeof(V) == 8) return cmkf(d2f_bits(x.x), d2f_bits(x.y));
+    else return x;
+}
+template <class V>
+__device__ __forceinline__ V load_as(const float2& x) {
+    if constexpr (sizeof(V) == 8) return x;
+    else return cmk((double)x.x, (double)x.y);
+}
+
+template <class V>
+__device__ __forceinline__ double2 widen(const V& x) {
+    if constexpr (sizeof(V) == 8) return cmk(f2d_bits(x.x), f2d_bits(x.y));
+    else return x;
+}
+
+// CTA (segment, G split): rows in NPT tiles of 32 (lane = row), bands in one tile of 32 (4 per
+// warp); 32-point tiles summed in the compute precision, eight tiles in the compute precision,
+// then FP64.
+// CTA (segment, G split): rows in NPT tiles of 32 (lane = row), bands in one tile of 32 (4 per
+// warp); G tiles (32 points FP32, 16 FP64) summed in the compute precision, eight tiles in the
+// compute precision, then FP64.
+template <class S, class AT, int NPT>
+__global__ void __launch_bounds__(256) proj_kernel(ProjDev d, int ld, const double2* __restrict__ X,
                                                    const int* __restrict__ row, const int* __restrict__ seg_start,
                                                    const int* __restrict__ seg_k, const int* __restrict__ seg_s,
-                                                   const int* __restrict__ npw_of_k, const int* __restrict__ kmap,
-                                                   int ksplit, double2* __restrict__ part, int nb) {
+                                                   const int* __restrict__ npw_of_k, int ksplit,
+                                                   double2* __restrict__ part, int nb) {
     using V = typename std::conditional<std::is_same<S, float>::value, float2, double2>::type;
-    __shared__ V As[TG][TP + 1];
-    __shared__ V Xs[TG][TC + 1];
+    constexpr int TP = 32 * NPT;
+    constexpr int TGV = sizeof(V) == 16 ? 16 : 32;  // G tile (keeps static shared memory under 48 KB)
+    __shared__ V As[TGV][TP + 1];
+    __shared__ V Xs[TGV][TC + 1];
     const int seg = blockIdx.x, ks = blockIdx.y;
     const int cbeg = seg_start[seg], cend = seg_start[seg + 1];
-    const int k = seg_k[seg];
+    const int k = seg_k[seg], sp = seg_s[seg];
     const int npw = npw_of_k[k];
-    const int chunk = ((npw + ksplit - 1) / ksplit + TG - 1) / TG * TG;
+    const int chunk = ((npw + ksplit - 1) / ksplit + TGV - 1) / TGV * TGV;
     const int g0 = ks * chunk;
     const int g1 = min(npw, g0 + chunk);
-    const int mk = kmap ? kmap[k] : k;
-    const double2* A = Abase + seg_s[seg] * sa_s + mk * sa_k + (long long)row0 * ld;
+    const int mk = d.kmap ? d.kmap[k] : k;
+    const int nrow = d.n0 + d.n1;
     const int tid = threadIdx.x;
     const int tp = tid & 31, tc = tid >> 5;  // 8 warps
-    for (int pt = 0; pt < nrow; pt += TP) {
-        for (int ct = cbeg; ct < cend; ct += TC) {
-            double2 acc[4];  // FP64 across tiles; each 32-point tile summed in the compute precision
+    for (int ct = cbeg; ct < cend; ct += TC) {
+        double2 acc[NPT][4];
+        V macc[NPT][4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) acc[i] = cmk(0.0, 0.0);
-            for (int gt = g0; gt < g1; gt += TG) {
-                // load A tile [TG][TP] and X tile [TG][TC]
-                for (int e = tid; e < TG * TP; e += 256) {
-                    const int gg = e & 31, pp = e >> 5;
-                    const int p = pt + pp, G = gt + gg;
-                    const double2 a = (p < nrow && G < g1) ? A[(long long)p * ld + G] : cmk(0.0, 0.0);
-                    As[gg][pp] = cpack<V>(a.x, a.y);
-                }
-                for (int e = tid; e < TG * TC; e += 256) {
-                    const int gg = e & 31, cc = e >> 5;
-                    const int c = ct + cc, G = gt + gg;
-                    const double2 x = (c < cend && G < g1) ? X[(long long)row[c] * ld + G] : cmk(0.0, 0.0);
-                    Xs[gg][cc] = cpack<V>(x.x, x.y);
-                }
-                __syncthreads();
-                V tacc[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) tacc[i] = cpack<V>(0.0, 0.0);
-#pragma unroll 8
-                for (int gg = 0; gg < TG; ++gg) {
-                    const V a = As[gg][tp];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const V x = Xs[gg][tc + 8 * i];
-                        tacc[i].x += a.x * x.x + a.y * x.y;
-                        tacc[i].y += a.x * x.y - a.y * x.x;
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    acc[i].x += (double)tacc[i].x;
-                    acc[i].y += (double)tacc[i].y;
-                }
-                __syncthreads();
-            }
-            const int p = pt + tp;
+        for (int r = 0; r < NPT; ++r)
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const int c = ct + tc + 8 * i;
-                if (p < nrow && c < cend) part[((long long)ks * nb + c) * kPStride + p] = acc[i];
+                acc[r][i] = cmk(0.0, 0.0);
+                macc[r][i] = cpack<V>(0.0, 0.0);
             }
+        int ntile = 0;
+        for (int gt = g0; gt < g1; gt += TGV) {
+            for (int e = tid; e < TGV * TP; e += 256) {
+                const int gg = e % TGV, pp = e / TGV;
+                const int G = gt + gg;
+                V a = cpack<V>(0.0, 0.0);
+                if (pp < nrow && G < g1) a = load_as<V>(proj_row<AT>(d, sp, mk, pp, ld)[G]);
+                As[gg][pp] = a;
+            }
+            for (int e = tid; e < TGV * TC; e += 256) {
+                const int gg = e % TGV, cc = e / TGV;
+                const int c = ct + cc, G = gt + gg;
+                V x = cpack<V>(0.0, 0.0);
+                if (c < cend && G < g1) x = load_as<V>(X[(long long)row[c] * ld + G]);
+                Xs[gg][cc] = x;
+            }
+            __syncthreads();
+            V tacc[NPT][4];
+#pragma unroll
+            for (int r = 0; r < NPT; ++r)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) tacc[r][i] = cpack<V>(0.0, 0.0);
+#pragma unroll 4
+            for (int gg = 0; gg < TGV; ++gg) {
+                V x[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) x[i] = Xs[gg][tc + 8 * i];
+#pragma unroll
+                for (int r = 0; r < NPT; ++r) {
+                    const V a = As[gg][tp + 32 * r];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        tacc[r][i].x += a.x * x[i].x + a.y * x[i].y;
+                        tacc[r][i].y += a.x * x[i].y - a.y * x[i].x;
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < NPT; ++r)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) macc[r][i] = cadd(macc[r][i], tacc[r][i]);
+            if (++ntile == 8) {
+                ntile = 0;
+#pragma unroll
+                for (int r = 0; r < NPT; ++r)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        acc[r][i] = cadd(acc[r][i], widen<V>(macc[r][i]));
+                        macc[r][i] = cpack<V>(0.0, 0.0);
+                    }
+            }
+            __syncthreads();
         }
+#pragma unroll
+        for (int r = 0; r < NPT; ++r)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                acc[r][i] = cadd(acc[r][i], widen<V>(macc[r][i]));
+                const int p = tp + 32 * r;
+                const int c = ct + tc + 8 * i;
+                if (p < nrow && c < cend) part[((long long)ks * nb + c) * kPStride + p] = acc[r][i];
+            }
     }
 }
 
@@ -375,37 +441,76 @@ __global__ void proj_reduce_kernel(const double2* __restrict__ part, int ksplit,
     P[(long long)c * kPStride + p] = s;
 }
 
+static bool fam32(const ProjMat& A) {
+    return (A.nrow == 0 || A.base32) && (A.nrow2 == 0 || !A.base2 || A.base2_32);
+}
+
+static ProjDev proj_dev(const ProjMat& A, bool use32) {
+    ProjDev d;
+    d.a0 = use32 ? (const void*)A.base32 : (const void*)A.base;
+    d.a1 = use32 ? (const void*)A.base2_32 : (const void*)A.base2;
+    d.s0_s = A.stride_s;
+    d.s0_k = A.stride_k;
+    d.s1_s = A.stride2_s;
+    d.s1_k = A.stride2_k;
+    d.n0 = A.nrow;
+    d.r0 = A.row0;
+    d.n1 = A.base2 ? A.nrow2 : 0;
+    d.r1 = A.row02;
+    d.kmap = A.kmap;
+    return d;
+}
+
+template <class S, class AT>
+static void proj_launch(int npt, dim3 g, cudaStream_t st, const ProjDev& d, int ld, const double2* X, const BandList& L,
+                        const SphereSet& Sp, int ksplit, double2* scratch) {
+    if (npt == 1)
+        proj_kernel<S, AT, 1><<<g, 256, 0, st>>>(d, ld, X, L.d_row, L.d_seg_start, L.d_seg_k, L.d_seg_s, Sp.d_npw,
+                                                 ksplit, scratch, L.nb);
+    else if (npt == 2)
+        proj_kernel<S, AT, 2><<<g, 256, 0, st>>>(d, ld, X, L.d_row, L.d_seg_start, L.d_seg_k, L.d_seg_s, Sp.d_npw,
+                                                 ksplit, scratch, L.nb);
+    else
+        proj_kernel<S, AT, 4><<<g, 256, 0, st>>>(d, ld, X, L.d_row, L.d_seg_start, L.d_seg_k, L.d_seg_s, Sp.d_npw,
+                                                 ksplit, scratch, L.nb);
+}
+
 cudaError_t k_proj(const BandList& L, const SphereSet& S, const ProjMat& A, const double2* X, int ld, double2* P,
                    double2* scratch, size_t scratch_elems, cudaStream_t st, bool fp32) {
-    if (L.nb <= 0 || A.nrow <= 0) return cudaSuccess;
-    if (A.nrow > kPStride) return cudaErrorInvalidValue;
+    const int nrow = A.nrow + (A.base2 ? A.nrow2 : 0);
+    if (L.nb <= 0 || nrow <= 0) return cudaSuccess;
+    if (nrow > kPStride) return cudaErrorInvalidValue;
     // about one wave of 8 resident CTAs per SM, at least two 32-point tiles per split
     int ksplit = std::max(1, cdiv(152 * 8, std::max(1, L.nseg)));
     ksplit = std::min(ksplit, std::max(1, S.ld / (2 * TG)));
     while (ksplit > 1 && (size_t)ksplit * L.nb * kPStride > scratch_elems) --ksplit;
     if ((size_t)ksplit * L.nb * kPStride > scratch_elems) return cudaErrorMemoryAllocation;
+    const int npt = nrow <= 32 ? 1 : nrow <= 64 ? 2 : 4;
     dim3 g(L.nseg, ksplit);
+    const bool use32 = fp32 && fam32(A);
+    const ProjDev d = proj_dev(A, use32);
     const ProfMark pm = prof_start(st);
-    if (fp32)
-        proj_kernel<float><<<g, 256, 0, st>>>(A.base, A.stride_s, A.stride_k, A.row0, A.nrow, ld, X, L.d_row,
-                                              L.d_seg_start, L.d_seg_k, L.d_seg_s, S.d_npw, A.kmap, ksplit, scratch, L.nb);
+    if (!fp32)
+        proj_launch<double, double2>(npt, g, st, d, ld, X, L, S, ksplit, scratch);
+    else if (use32)
+        proj_launch<float, float2>(npt, g, st, d, ld, X, L, S, ksplit, scratch);
     else
-        proj_kernel<double><<<g, 256, 0, st>>>(A.base, A.stride_s, A.stride_k, A.row0, A.nrow, ld, X, L.d_row,
-                                               L.d_seg_start, L.d_seg_k, L.d_seg_s, S.d_npw, A.kmap, ksplit, scratch, L.nb);
+        proj_launch<float, double2>(npt, g, st, d, ld, X, L, S, ksplit, scratch);
     HP_LAUNCHED();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    proj_reduce_kernel<<<cdiv((long long)L.nb * A.nrow, 256), 256, 0, st>>>(scratch, ksplit, L.nb, A.nrow, P);
+    proj_reduce_kernel<<<cdiv((long long)L.nb * nrow, 256), 256, 0, st>>>(scratch, ksplit, L.nb, nrow, P);
     HP_LAUNCHED();
     if (prof_on() && L.k.size() >= (size_t)L.nb && L.seg_k.size() >= (size_t)L.nseg) {
         // band vectors once, projector rows once per (k, spin) segment, partial sums written and
         // read, results written; 8 flops per complex multiply-add
-        double bytes = 2.0 * 16.0 * ksplit * L.nb * A.nrow + 16.0 * L.nb * A.nrow, flops = 0.0;
+        const double ab = use32 ? 8.0 : 16.0;
+        double bytes = 2.0 * 16.0 * ksplit * L.nb * nrow + 16.0 * L.nb * nrow, flops = 0.0;
         for (int b = 0; b < L.nb; ++b) {
             bytes += 16.0 * S.npw[L.k[b]];
-            flops += 8.0 * A.nrow * S.npw[L.k[b]];
+            flops += 8.0 * nrow * S.npw[L.k[b]];
         }
-        for (int sg = 0; sg < L.nseg; ++sg) bytes += 16.0 * A.nrow * S.npw[L.seg_k[sg]];
+        for (int sg = 0; sg < L.nseg; ++sg) bytes += ab * nrow * S.npw[L.seg_k[sg]];
         prof_stop(pm, HP_KF_PROJECT, st, flops, bytes);
     }
     return cudaGetLastError();
@@ -413,34 +518,31 @@ cudaError_t k_proj(const BandList& L, const SphereSet& S, const ProjMat& A, cons
 
 constexpr int kExpC = 16;
 
-template <class S>
-__global__ void __launch_bounds__(128) expand_kernel(const double2* __restrict__ Abase, long long sa_s, long long sa_k,
-                                                     int row0, int nrow, int ld, const double2* __restrict__ P,
-                                                     const double* __restrict__ pscale, double alpha,
+template <class S, class AT>
+__global__ void __launch_bounds__(128) expand_kernel(ProjDev d, int ld, const double2* __restrict__ P,
+                                                     const double* __restrict__ pscale, double alpha, double scale2,
                                                      double2* __restrict__ Y, const int* __restrict__ row,
                                                      const int* __restrict__ seg_start, const int* __restrict__ seg_k,
-                                                     const int* __restrict__ seg_s, const int* __restrict__ npw_of_k,
-                                                     const int* __restrict__ kmap) {
+                                                     const int* __restrict__ seg_s, const int* __restrict__ npw_of_k) {
     using V = typename std::conditional<std::is_same<S, float>::value, float2, double2>::type;
     __shared__ V Ps[kExpC][kPStride];
     const int seg = blockIdx.y;
     const int cbeg = seg_start[seg], cend = seg_start[seg + 1];
-    const int k = seg_k[seg];
+    const int k = seg_k[seg], sp = seg_s[seg];
     const int npw = npw_of_k[k];
     const int G = blockIdx.x * blockDim.x + threadIdx.x;
-    const int mk = kmap ? kmap[k] : k;
-    const double2* A = Abase + seg_s[seg] * sa_s + mk * sa_k + (long long)row0 * ld;
+    const int mk = d.kmap ? d.kmap[k] : k;
+    const int nrow = d.n0 + d.n1;
     for (int ct = cbeg; ct < cend; ct += kExpC) {
         for (int e = threadIdx.x; e < kExpC * nrow; e += blockDim.x) {
             const int cc = e / nrow, p = e % nrow;
             const int c = ct + cc;
             double2 v = cmk(0.0, 0.0);
             if (c < cend) {
-                v = P[(long long)c * kPStride + p];
-                const double s = alpha * (pscale ? pscale[p] : 1.0);
-                v = cscale(v, s);
+                const double w = p < d.n0 ? (pscale ? pscale[p] : 1.0) : scale2;
+                v = cscale(P[(long long)c * kPStride + p], alpha * w);
             }
-            Ps[cc][p] = cpack<V>(v.x, v.y);
+            Ps[cc][p] = load_as<V>(v);
         }
         __syncthreads();
         if (G < npw) {
@@ -448,8 +550,7 @@ __global__ void __launch_bounds__(128) expand_kernel(const double2* __restrict__
 #pragma unroll
             for (int i = 0; i < kExpC; ++i) acc[i] = cpack<V>(0.0, 0.0);
             for (int p = 0; p < nrow; ++p) {
-                const double2 a64 = A[(long long)p * ld + G];
-                const V a = cpack<V>(a64.x, a64.y);
+                const V a = load_as<V>(proj_row<AT>(d, sp, mk, p, ld)[G]);
 #pragma unroll
                 for (int i = 0; i < kExpC; ++i) {
                     const V q = Ps[i][p];
@@ -462,7 +563,7 @@ __global__ void __launch_bounds__(128) expand_kernel(const double2* __restrict__
                 const int c = ct + i;
                 if (c < cend) {
                     const long long o = (long long)row[c] * ld + G;
-                    Y[o] = cadd(Y[o], cmk((double)acc[i].x, (double)acc[i].y));
+                    Y[o] = cadd(Y[o], widen<V>(acc[i]));
                 }
             }
         }
@@ -472,25 +573,32 @@ __global__ void __launch_bounds__(128) expand_kernel(const double2* __restrict__
 
 cudaError_t k_expand(const BandList& L, const SphereSet& S, const ProjMat& A, const double2* P, const double* pscale,
                      double alpha, double2* Y, int ld, cudaStream_t st, bool fp32) {
-    if (L.nb <= 0 || A.nrow <= 0) return cudaSuccess;
-    if (A.nrow > kPStride) return cudaErrorInvalidValue;
+    const int nrow = A.nrow + (A.base2 ? A.nrow2 : 0);
+    if (L.nb <= 0 || nrow <= 0) return cudaSuccess;
+    if (nrow > kPStride) return cudaErrorInvalidValue;
     dim3 g(cdiv(ld, 128), L.nseg);
+    const bool use32 = fp32 && fam32(A);
+    const ProjDev d = proj_dev(A, use32);
     const ProfMark pm = prof_start(st);
-    if (fp32)
-        expand_kernel<float><<<g, 128, 0, st>>>(A.base, A.stride_s, A.stride_k, A.row0, A.nrow, ld, P, pscale, alpha, Y,
-                                                L.d_row, L.d_seg_start, L.d_seg_k, L.d_seg_s, S.d_npw, A.kmap);
+    if (!fp32)
+        expand_kernel<double, double2><<<g, 128, 0, st>>>(d, ld, P, pscale, alpha, A.scale2, Y, L.d_row, L.d_seg_start,
+                                                          L.d_seg_k, L.d_seg_s, S.d_npw);
+    else if (use32)
+        expand_kernel<float, float2><<<g, 128, 0, st>>>(d, ld, P, pscale, alpha, A.scale2, Y, L.d_row, L.d_seg_start,
+                                                        L.d_seg_k, L.d_seg_s, S.d_npw);
     else
-        expand_kernel<double><<<g, 128, 0, st>>>(A.base, A.stride_s, A.stride_k, A.row0, A.nrow, ld, P, pscale, alpha, Y,
-                                                 L.d_row, L.d_seg_start, L.d_seg_k, L.d_seg_s, S.d_npw, A.kmap);
+        expand_kernel<float, double2><<<g, 128, 0, st>>>(d, ld, P, pscale, alpha, A.scale2, Y, L.d_row, L.d_seg_start,
+                                                         L.d_seg_k, L.d_seg_s, S.d_npw);
     HP_LAUNCHED();
     if (prof_on() && L.k.size() >= (size_t)L.nb && L.seg_k.size() >= (size_t)L.nseg) {
         // band vectors read and written, coefficients read, projector rows once per segment
-        double bytes = 16.0 * L.nb * A.nrow, flops = 0.0;
+        const double ab = use32 ? 8.0 : 16.0;
+        double bytes = 16.0 * L.nb * nrow, flops = 0.0;
         for (int b = 0; b < L.nb; ++b) {
             bytes += 2.0 * 16.0 * S.npw[L.k[b]];
-            flops += 8.0 * A.nrow * S.npw[L.k[b]];
+            flops += 8.0 * nrow * S.npw[L.k[b]];
         }
-        for (int sg = 0; sg < L.nseg; ++sg) bytes += 16.0 * A.nrow * S.npw[L.seg_k[sg]];
+        for (int sg = 0; sg < L.nseg; ++sg) bytes += ab * nrow * S.npw[L.seg_k[sg]];
         prof_stop(pm, HP_KF_EXPAND, st, flops, bytes);
     }
     return cudaGetLastError();
@@ -1418,3 +1526,48 @@ cudaError_t k_add_real(const double* a, const double* b, double* out, int n, cud
 }
 
 }  // namespace hp
+
+namespace {
+__global__ void convert_selftest_kernel(const double* __restrict__ in, long long n, float* __restrict__ f,
+                                        double* __restrict__ back, float* __restrict__ f_ref,
+                                        double* __restrict__ back_ref) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float a = hp::d2f_bits(in[i]);
+        f[i] = a;
+        back[i] = hp::f2d_bits(a);
+        const float r = __double2float_rn(in[i]);
+        f_ref[i] = r;
+        back_ref[i] = (double)r;
+    }
+}
+}  // namespace
+
+extern "C" hp_status hp_selftest_convert(long long n, const double* in, float* f, double* back, float* f_ref,
+                                         double* back_ref) {
+    if (n < 1 || !in || !f || !back || !f_ref || !back_ref) return HP_EINVAL;
+    double *d_in = nullptr, *d_back = nullptr, *d_back_ref = nullptr;
+    float *d_f = nullptr, *d_f_ref = nullptr;
+    const size_t n8 = sizeof(double) * (size_t)n, n4 = sizeof(float) * (size_t)n;
+    cudaError_t e = cudaMalloc(&d_in, n8);
+    if (e == cudaSuccess) e = cudaMalloc(&d_back, n8);
+    if (e == cudaSuccess) e = cudaMalloc(&d_back_ref, n8);
+    if (e == cudaSuccess) e = cudaMalloc(&d_f, n4);
+    if (e == cudaSuccess) e = cudaMalloc(&d_f_ref, n4);
+    if (e == cudaSuccess) e = cudaMemcpy(d_in, in, n8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        convert_selftest_kernel<<<(int)std::min<long long>((n + 255) / 256, 4096), 256>>>(d_in, n, d_f, d_back, d_f_ref,
+                                                                                       d_back_ref);
+        hp::g_launches.fetch_add(1, std::memory_order_relaxed);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(f, d_f, n4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(back, d_back, n8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(f_ref, d_f_ref, n4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(back_ref, d_back_ref, n8, cudaMemcpyDeviceToHost);
+    cudaFree(d_in);
+    cudaFree(d_back);
+    cudaFree(d_back_ref);
+    cudaFree(d_f);
+    cudaFree(d_f_ref);
+    return e == cudaSuccess ? HP_OK : HP_ECUDA;
+}
