@@ -295,7 +295,7 @@ cudaError_t k_to_c32(const double2* a, float2* b, long long n, cudaStream_t st) 
 // from their FP32 copies when present, and FP64 band data is rounded with integer operations.
 // ------------------------------------------------------------------------------------------------
 constexpr int kPStride = 128;
-constexpr int TC = 32, TG = 32;
+constexpr int TG = 32;
 
 struct ProjDev {
     const void* a0;
@@ -328,13 +328,11 @@ __device__ __forceinline__ double2 widen(const V& x) {
     else return x;
 }
 
-// CTA (segment, G split): rows in NPT tiles of 32 (lane = row), bands in one tile of 32 (4 per
-// warp); 32-point tiles summed in the compute precision, eight tiles in the compute precision,
-// then FP64.
-// CTA (segment, G split): rows in NPT tiles of 32 (lane = row), bands in one tile of 32 (4 per
-// warp); G tiles (32 points FP32, 16 FP64) summed in the compute precision, eight tiles in the
-// compute precision, then FP64.
-template <class S, class AT, int NPT>
+// CTA (segment, G split): rows in NPT tiles of 32 (lane = row), bands in tiles of 8 NBI (NBI per
+// warp, sized to the largest segment of the list).  G tiles (32 points FP32, 16 FP64) go through
+// shared memory with the next tile's global loads issued before the current tile is used; each
+// tile is summed in the compute precision, eight tiles in the compute precision, then FP64.
+template <class S, class AT, int NPT, int NBI>
 __global__ void __launch_bounds__(256) proj_kernel(ProjDev d, int ld, const double2* __restrict__ X,
                                                    const int* __restrict__ row, const int* __restrict__ seg_start,
                                                    const int* __restrict__ seg_k, const int* __restrict__ seg_s,
@@ -343,8 +341,12 @@ __global__ void __launch_bounds__(256) proj_kernel(ProjDev d, int ld, const doub
     using V = typename std::conditional<std::is_same<S, float>::value, float2, double2>::type;
     constexpr int TP = 32 * NPT;
     constexpr int TGV = sizeof(V) == 16 ? 16 : 32;  // G tile (keeps static shared memory under 48 KB)
+    constexpr int TCB = 8 * NBI;                    // bands per tile
+    constexpr int RS = 256 / TGV;                   // rows (or bands) advanced per load step
+    constexpr int AE = TP / RS;                     // A elements per thread per tile
+    constexpr int XE = (TCB + RS - 1) / RS;         // X elements per thread per tile
     __shared__ V As[TGV][TP + 1];
-    __shared__ V Xs[TGV][TC + 1];
+    __shared__ V Xs[TGV][TCB + 1];
     const int seg = blockIdx.x, ks = blockIdx.y;
     const int cbeg = seg_start[seg], cend = seg_start[seg + 1];
     const int k = seg_k[seg], sp = seg_s[seg];
@@ -352,52 +354,73 @@ __global__ void __launch_bounds__(256) proj_kernel(ProjDev d, int ld, const doub
     const int chunk = ((npw + ksplit - 1) / ksplit + TGV - 1) / TGV * TGV;
     const int g0 = ks * chunk;
     const int g1 = min(npw, g0 + chunk);
+    if (g0 >= g1) {
+        // empty split: its partial sums are zero
+        const int nrow = d.n0 + d.n1;
+        for (int e = threadIdx.x; e < (cend - cbeg) * nrow; e += 256)
+            part[((long long)ks * nb + cbeg + e / nrow) * kPStride + e % nrow] = cmk(0.0, 0.0);
+        return;
+    }
     const int mk = d.kmap ? d.kmap[k] : k;
     const int nrow = d.n0 + d.n1;
     const int tid = threadIdx.x;
-    const int tp = tid & 31, tc = tid >> 5;  // 8 warps
-    for (int ct = cbeg; ct < cend; ct += TC) {
-        double2 acc[NPT][4];
-        V macc[NPT][4];
+    const int tp = tid & 31, tc = tid >> 5;  // compute mapping: lane = row, warp = band
+    const int lg = tid % TGV, lr = tid / TGV;  // load mapping: G within the tile, first row / band
+    const AT* arow[AE];
+#pragma unroll
+    for (int j = 0; j < AE; ++j) {
+        const int p = lr + j * RS;
+        arow[j] = p < nrow ? proj_row<AT>(d, sp, mk, p, ld) : nullptr;
+    }
+    for (int ct = cbeg; ct < cend; ct += TCB) {
+        const double2* xrow[XE];
+#pragma unroll
+        for (int j = 0; j < XE; ++j) {
+            const int cc = lr + j * RS;
+            xrow[j] = (cc < TCB && ct + cc < cend) ? X + (long long)row[ct + cc] * ld : nullptr;
+        }
+        V ra[AE], rx[XE];
+        auto fetch = [&](int gt) {
+            const int G = gt + lg;
+#pragma unroll
+            for (int j = 0; j < AE; ++j) ra[j] = (arow[j] && G < g1) ? load_as<V>(arow[j][G]) : cpack<V>(0.0, 0.0);
+#pragma unroll
+            for (int j = 0; j < XE; ++j) rx[j] = (xrow[j] && G < g1) ? load_as<V>(xrow[j][G]) : cpack<V>(0.0, 0.0);
+        };
+        double2 acc[NPT][NBI];
+        V macc[NPT][NBI];
 #pragma unroll
         for (int r = 0; r < NPT; ++r)
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
+            for (int i = 0; i < NBI; ++i) {
                 acc[r][i] = cmk(0.0, 0.0);
                 macc[r][i] = cpack<V>(0.0, 0.0);
             }
         int ntile = 0;
+        fetch(g0);
         for (int gt = g0; gt < g1; gt += TGV) {
-            for (int e = tid; e < TGV * TP; e += 256) {
-                const int gg = e % TGV, pp = e / TGV;
-                const int G = gt + gg;
-                V a = cpack<V>(0.0, 0.0);
-                if (pp < nrow && G < g1) a = load_as<V>(proj_row<AT>(d, sp, mk, pp, ld)[G]);
-                As[gg][pp] = a;
-            }
-            for (int e = tid; e < TGV * TC; e += 256) {
-                const int gg = e % TGV, cc = e / TGV;
-                const int c = ct + cc, G = gt + gg;
-                V x = cpack<V>(0.0, 0.0);
-                if (c < cend && G < g1) x = load_as<V>(X[(long long)row[c] * ld + G]);
-                Xs[gg][cc] = x;
-            }
+#pragma unroll
+            for (int j = 0; j < AE; ++j) As[lg][lr + j * RS] = ra[j];
+#pragma unroll
+            for (int j = 0; j < XE; ++j)
+                if (lr + j * RS < TCB) Xs[lg][lr + j * RS] = rx[j];
             __syncthreads();
-            V tacc[NPT][4];
+            if (gt + TGV < g1) fetch(gt + TGV);  // next tile's loads overlap this tile's arithmetic
+            V tacc[NPT][NBI];
 #pragma unroll
             for (int r = 0; r < NPT; ++r)
 #pragma unroll
-                for (int i = 0; i < 4; ++i) tacc[r][i] = cpack<V>(0.0, 0.0);
-#pragma unroll 4
+                for (int i = 0; i < NBI; ++i) tacc[r][i] = cpack<V>(0.0, 0.0);
+#pragma unroll 8
             for (int gg = 0; gg < TGV; ++gg) {
-                V x[4];
+                V x[NBI];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) x[i] = Xs[gg][tc + 8 * i];
+                for (int i = 0; i < NBI; ++i) x[i] = Xs[gg][tc + 8 * i];
 #pragma unroll
                 for (int r = 0; r < NPT; ++r) {
                     const V a = As[gg][tp + 32 * r];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
+                    for (int i = 0; i < NBI; ++i) {
                         tacc[r][i].x += a.x * x[i].x + a.y * x[i].y;
                         tacc[r][i].y += a.x * x[i].y - a.y * x[i].x;
                     }
@@ -406,13 +429,13 @@ __global__ void __launch_bounds__(256) proj_kernel(ProjDev d, int ld, const doub
 #pragma unroll
             for (int r = 0; r < NPT; ++r)
 #pragma unroll
-                for (int i = 0; i < 4; ++i) macc[r][i] = cadd(macc[r][i], tacc[r][i]);
+                for (int i = 0; i < NBI; ++i) macc[r][i] = cadd(macc[r][i], tacc[r][i]);
             if (++ntile == 8) {
                 ntile = 0;
 #pragma unroll
                 for (int r = 0; r < NPT; ++r)
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
+                    for (int i = 0; i < NBI; ++i) {
                         acc[r][i] = cadd(acc[r][i], widen<V>(macc[r][i]));
                         macc[r][i] = cpack<V>(0.0, 0.0);
                     }
@@ -422,7 +445,7 @@ __global__ void __launch_bounds__(256) proj_kernel(ProjDev d, int ld, const doub
 #pragma unroll
         for (int r = 0; r < NPT; ++r)
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
+            for (int i = 0; i < NBI; ++i) {
                 acc[r][i] = cadd(acc[r][i], widen<V>(macc[r][i]));
                 const int p = tp + 32 * r;
                 const int c = ct + tc + 8 * i;
@@ -461,18 +484,34 @@ static ProjDev proj_dev(const ProjMat& A, bool use32) {
     return d;
 }
 
-template <class S, class AT>
-static void proj_launch(int npt, dim3 g, cudaStream_t st, const ProjDev& d, int ld, const double2* X, const BandList& L,
-                        const SphereSet& Sp, int ksplit, double2* scratch) {
+template <class S, class AT, int NBI>
+static void proj_launch_b(int npt, dim3 g, cudaStream_t st, const ProjDev& d, int ld, const double2* X,
+                          const BandList& L, const SphereSet& Sp, int ksplit, double2* scratch) {
     if (npt == 1)
-        proj_kernel<S, AT, 1><<<g, 256, 0, st>>>(d, ld, X, L.d_row, L.d_seg_start, L.d_seg_k, L.d_seg_s, Sp.d_npw,
-                                                 ksplit, scratch, L.nb);
+        proj_kernel<S, AT, 1, NBI><<<g, 256, 0, st>>>(d, ld, X, L.d_row, L.d_seg_start, L.d_seg_k, L.d_seg_s,
+                                                      Sp.d_npw, ksplit, scratch, L.nb);
     else if (npt == 2)
-        proj_kernel<S, AT, 2><<<g, 256, 0, st>>>(d, ld, X, L.d_row, L.d_seg_start, L.d_seg_k, L.d_seg_s, Sp.d_npw,
-                                                 ksplit, scratch, L.nb);
+        proj_kernel<S, AT, 2, NBI><<<g, 256, 0, st>>>(d, ld, X, L.d_row, L.d_seg_start, L.d_seg_k, L.d_seg_s,
+                                                      Sp.d_npw, ksplit, scratch, L.nb);
     else
-        proj_kernel<S, AT, 4><<<g, 256, 0, st>>>(d, ld, X, L.d_row, L.d_seg_start, L.d_seg_k, L.d_seg_s, Sp.d_npw,
-                                                 ksplit, scratch, L.nb);
+        proj_kernel<S, AT, 4, NBI><<<g, 256, 0, st>>>(d, ld, X, L.d_row, L.d_seg_start, L.d_seg_k, L.d_seg_s,
+                                                      Sp.d_npw, ksplit, scratch, L.nb);
+}
+
+template <class S, class AT>
+static void proj_launch(int npt, int nbi, dim3 g, cudaStream_t st, const ProjDev& d, int ld, const double2* X,
+                        const BandList& L, const SphereSet& Sp, int ksplit, double2* scratch) {
+    if (nbi == 1) proj_launch_b<S, AT, 1>(npt, g, st, d, ld, X, L, Sp, ksplit, scratch);
+    else if (nbi == 2) proj_launch_b<S, AT, 2>(npt, g, st, d, ld, X, L, Sp, ksplit, scratch);
+    else if (nbi == 3) proj_launch_b<S, AT, 3>(npt, g, st, d, ld, X, L, Sp, ksplit, scratch);
+    else proj_launch_b<S, AT, 4>(npt, g, st, d, ld, X, L, Sp, ksplit, scratch);
+}
+
+// largest number of list items in one (k, spin) segment
+static int max_seg(const BandList& L) {
+    int m = 0;
+    for (int i = 0; i + 1 < (int)L.seg_start.size(); ++i) m = std::max(m, L.seg_start[i + 1] - L.seg_start[i]);
+    return L.seg_start.size() < 2 ? L.nb : m;
 }
 
 cudaError_t k_proj(const BandList& L, const SphereSet& S, const ProjMat& A, const double2* X, int ld, double2* P,
@@ -486,16 +525,18 @@ cudaError_t k_proj(const BandList& L, const SphereSet& S, const ProjMat& A, cons
     while (ksplit > 1 && (size_t)ksplit * L.nb * kPStride > scratch_elems) --ksplit;
     if ((size_t)ksplit * L.nb * kPStride > scratch_elems) return cudaErrorMemoryAllocation;
     const int npt = nrow <= 32 ? 1 : nrow <= 64 ? 2 : 4;
+    const int ms = max_seg(L);
+    const int nbi = ms <= 8 ? 1 : ms <= 16 ? 2 : ms <= 24 ? 3 : 4;
     dim3 g(L.nseg, ksplit);
     const bool use32 = fp32 && fam32(A);
     const ProjDev d = proj_dev(A, use32);
     const ProfMark pm = prof_start(st);
     if (!fp32)
-        proj_launch<double, double2>(npt, g, st, d, ld, X, L, S, ksplit, scratch);
+        proj_launch<double, double2>(npt, nbi, g, st, d, ld, X, L, S, ksplit, scratch);
     else if (use32)
-        proj_launch<float, float2>(npt, g, st, d, ld, X, L, S, ksplit, scratch);
+        proj_launch<float, float2>(npt, nbi, g, st, d, ld, X, L, S, ksplit, scratch);
     else
-        proj_launch<float, double2>(npt, g, st, d, ld, X, L, S, ksplit, scratch);
+        proj_launch<float, double2>(npt, nbi, g, st, d, ld, X, L, S, ksplit, scratch);
     HP_LAUNCHED();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -516,9 +557,8 @@ cudaError_t k_proj(const BandList& L, const SphereSet& S, const ProjMat& A, cons
     return cudaGetLastError();
 }
 
-constexpr int kExpC = 16;
-
-template <class S, class AT>
+// bands per pass kExpC (4 to 24), sized to the largest segment of the list
+template <class S, class AT, int kExpC>
 __global__ void __launch_bounds__(128) expand_kernel(ProjDev d, int ld, const double2* __restrict__ P,
                                                      const double* __restrict__ pscale, double alpha, double scale2,
                                                      double2* __restrict__ Y, const int* __restrict__ row,
@@ -571,6 +611,21 @@ __global__ void __launch_bounds__(128) expand_kernel(ProjDev d, int ld, const do
     }
 }
 
+template <int KC>
+static void expand_launch(bool fp32, bool use32, dim3 g, cudaStream_t st, const ProjDev& d, int ld, const double2* P,
+                          const double* pscale, double alpha, double scale2, double2* Y, const BandList& L,
+                          const SphereSet& S) {
+    if (!fp32)
+        expand_kernel<double, double2, KC><<<g, 128, 0, st>>>(d, ld, P, pscale, alpha, scale2, Y, L.d_row,
+                                                              L.d_seg_start, L.d_seg_k, L.d_seg_s, S.d_npw);
+    else if (use32)
+        expand_kernel<float, float2, KC><<<g, 128, 0, st>>>(d, ld, P, pscale, alpha, scale2, Y, L.d_row,
+                                                            L.d_seg_start, L.d_seg_k, L.d_seg_s, S.d_npw);
+    else
+        expand_kernel<float, double2, KC><<<g, 128, 0, st>>>(d, ld, P, pscale, alpha, scale2, Y, L.d_row,
+                                                             L.d_seg_start, L.d_seg_k, L.d_seg_s, S.d_npw);
+}
+
 cudaError_t k_expand(const BandList& L, const SphereSet& S, const ProjMat& A, const double2* P, const double* pscale,
                      double alpha, double2* Y, int ld, cudaStream_t st, bool fp32) {
     const int nrow = A.nrow + (A.base2 ? A.nrow2 : 0);
@@ -580,15 +635,13 @@ cudaError_t k_expand(const BandList& L, const SphereSet& S, const ProjMat& A, co
     const bool use32 = fp32 && fam32(A);
     const ProjDev d = proj_dev(A, use32);
     const ProfMark pm = prof_start(st);
-    if (!fp32)
-        expand_kernel<double, double2><<<g, 128, 0, st>>>(d, ld, P, pscale, alpha, A.scale2, Y, L.d_row, L.d_seg_start,
-                                                          L.d_seg_k, L.d_seg_s, S.d_npw);
-    else if (use32)
-        expand_kernel<float, float2><<<g, 128, 0, st>>>(d, ld, P, pscale, alpha, A.scale2, Y, L.d_row, L.d_seg_start,
-                                                        L.d_seg_k, L.d_seg_s, S.d_npw);
-    else
-        expand_kernel<float, double2><<<g, 128, 0, st>>>(d, ld, P, pscale, alpha, A.scale2, Y, L.d_row, L.d_seg_start,
-                                                         L.d_seg_k, L.d_seg_s, S.d_npw);
+    const int ms = max_seg(L);
+    if (ms <= 4) expand_launch<4>(fp32, use32, g, st, d, ld, P, pscale, alpha, A.scale2, Y, L, S);
+    else if (ms <= 8) expand_launch<8>(fp32, use32, g, st, d, ld, P, pscale, alpha, A.scale2, Y, L, S);
+    else if (ms <= 12) expand_launch<12>(fp32, use32, g, st, d, ld, P, pscale, alpha, A.scale2, Y, L, S);
+    else if (ms <= 16 || !fp32) expand_launch<16>(fp32, use32, g, st, d, ld, P, pscale, alpha, A.scale2, Y, L, S);
+    else if (ms <= 20) expand_launch<20>(fp32, use32, g, st, d, ld, P, pscale, alpha, A.scale2, Y, L, S);
+    else expand_launch<24>(fp32, use32, g, st, d, ld, P, pscale, alpha, A.scale2, Y, L, S);
     HP_LAUNCHED();
     if (prof_on() && L.k.size() >= (size_t)L.nb && L.seg_k.size() >= (size_t)L.nseg) {
         // band vectors read and written, coefficients read, projector rows once per segment
