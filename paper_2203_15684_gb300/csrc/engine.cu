@@ -160,6 +160,7 @@ hp_status upload_sphereset(hp_ctx* c, const std::vector<const KSphere*>& sph, co
         CK(dalloc(c, &S.d_npw, nk));
         CK(dalloc(c, &S.d_idx, (size_t)nk * ld));
         CK(dalloc(c, &S.d_g2, (size_t)nk * ld));
+        CK(dalloc(c, &S.d_prec, (size_t)nk * ld));
         CK(dalloc(c, &S.d_iz, (size_t)nk * ld));
         CK(dalloc(c, &S.d_ncol, nk));
     }
@@ -212,6 +213,10 @@ hp_status upload_sphereset(hp_ctx* c, const std::vector<const KSphere*>& sph, co
     CK(h2d(S.d_npw, S.npw.data(), nk, c->st));
     CK(h2d(S.d_idx, idx.data(), idx.size(), c->st));
     CK(h2d(S.d_g2, g2.data(), g2.size(), c->st));
+    std::vector<double> prec(g2.size(), 0.0);
+    for (int k = 0; k < nk; ++k)
+        for (int i = 0; i < S.npw[k]; ++i) prec[(size_t)k * ld + i] = 1.0 / (1.0 + 0.5 * g2[(size_t)k * ld + i]);
+    CK(h2d(S.d_prec, prec.data(), prec.size(), c->st));
     CK(h2d(S.d_iz, iz.data(), iz.size(), c->st));
     CK(h2d(S.d_ncol, ncol.data(), nk, c->st));
     CK(h2d(S.d_col_start, hs.data(), hs.size(), c->st));
@@ -1126,13 +1131,13 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
     if ((s = upload_list(c, Lpsi)) != HP_OK) return s;
     // V_pert u_k = sum_m phi^J_m,k+q <phi^J_m,k|u_k>
     const int mJ = c->hub_mdim[jj], oJ = c->hub_off[jj];
-    ProjMat phiJk{c->d_phi_k, 0, (long long)c->nhub * ld, mJ, oJ, nullptr};
-    ProjMat phiJkq{c->d_phi_k, 0, (long long)c->nhub * ld, mJ, oJ, kmap};
+    ProjMat phiJk{c->d_phi_k, 0, (long long)c->nhub * ld, mJ, oJ, nullptr, c->d_phi32};
+    ProjMat phiJkq{c->d_phi_k, 0, (long long)c->nhub * ld, mJ, oJ, kmap, c->d_phi32};
     ProjMat phikq{c->d_phi_k, 0, (long long)c->nhub * ld, c->nhub, 0, kmap, c->d_phi32};
     ProjMat Ukq{c->d_psi, (long long)nk * c->nbnd * ld, (long long)c->nbnd * ld, nocc, 0, kmap, c->d_psi32};
-    if ((s = project(c, c->kset, Lpsi, phiJk, c->d_psi, c->d_Pbuf)) != HP_OK) return s;
+    if ((s = project(c, c->kset, Lpsi, phiJk, c->d_psi, c->d_Pbuf, mixed)) != HP_OK) return s;
     CK(cudaMemsetAsync(c->d_vpu, 0, sizeof(double2) * nvec, c->st));
-    CK(k_expand(Lall, Sq, phiJkq, c->d_Pbuf, nullptr, 1.0, c->d_vpu, ld, c->st));
+    CK(k_expand(Lall, Sq, phiJkq, c->d_Pbuf, nullptr, 1.0, c->d_vpu, ld, c->st, mixed));
     CK(cudaMemsetAsync(c->d_x, 0, sizeof(double2) * nvec, c->st));
     CK(cudaMemsetAsync(c->d_dv, 0, sizeof(double2) * ndv, c->st));
     const double f = nspin == 1 ? 2.0 : 1.0;
@@ -1226,9 +1231,7 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
             if ((s = upload_list(c, La)) != HP_OK) return s;
             if ((s = apply_sternheimer(c, La, c->d_p, c->d_ap)) != HP_OK) return s;
             hpsi += La.nb;
-            CK(k_band_dot(La, Sq, c->d_p, c->d_ap, ld, c->d_pap, c->st));
-            CK(k_cg_update(La, Sq, c->d_pap, c->d_x, c->d_r, c->d_p, c->d_ap, ld, c->d_rz, c->d_rr, c->d_rzold, c->st));
-            CK(k_cg_direction(La, Sq, c->d_rz, c->d_rzold, c->d_r, c->d_p, ld, c->st));
+            CK(k_cg_step(La, Sq, c->d_x, c->d_r, c->d_p, c->d_ap, ld, c->d_pap, c->d_rz, c->d_rr, c->st));
             cg_total += La.nb;
             ++cgit;
         }

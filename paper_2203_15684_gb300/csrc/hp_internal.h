@@ -123,6 +123,7 @@ struct SphereSet {          // device arrays, nk spheres of at most ld points
     int* d_npw = nullptr;   // [nk]
     int* d_idx = nullptr;   // [nk][ld] flat grid index of each coefficient
     double* d_g2 = nullptr; // [nk][ld] |k+G|^2
+    double* d_prec = nullptr;  // [nk][ld] CG preconditioner 1 / (1 + |k+G|^2 / 2), 0 beyond npw
     std::vector<int> npw;   // host copy
     // column structure (the sphere is stored column by column, z fastest): for each k, ncol
     // columns (x, y) of the grid that hold sphere points, their first point and length, and the
@@ -204,11 +205,8 @@ cudaError_t k_band_dot(const BandList& L, const SphereSet& S, const double2* X, 
                        double* out, cudaStream_t st);
 cudaError_t k_cg_init(const BandList& L, const SphereSet& S, const double2* r, double2* p, int ld,
                       double* rz, double* rr, cudaStream_t st);
-cudaError_t k_cg_update(const BandList& L, const SphereSet& S, const double* pap, double2* x, double2* r,
-                        const double2* p, const double2* ap, int ld, double* rz, double* rr, double* rz_old,
-                        cudaStream_t st);
-cudaError_t k_cg_direction(const BandList& L, const SphereSet& S, const double* rz, const double* rz_old,
-                           const double2* r, double2* p, int ld, cudaStream_t st);
+cudaError_t k_cg_step(const BandList& L, const SphereSet& S, double2* x, double2* r, double2* p, const double2* ap,
+                      int ld, double* pap, double* rz, double* rr, cudaStream_t st);
 cudaError_t k_rows_axpby(const BandList& L, const SphereSet& S, double a, const double2* X, double b,
                          double2* Y, int ld, cudaStream_t st);
 cudaError_t k_gather_kq(const int* map, const int* npw_kq, const int* kprime, int nk, int nspin, int nocc,

@@ -29,6 +29,16 @@ __device__ double block_sum(double v, double* sh) {
     return v;
 }
 
+// the same sum, returned to every thread of the block (sh holds at least 33 doubles)
+__device__ double block_allsum(double v, double* sh) {
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0) sh[32] = v;
+    __syncthreads();
+    v = sh[32];
+    __syncthreads();
+    return v;
+}
+
 // ------------------------------------------------------------------------------------------------
 // sphere <-> grid
 // ------------------------------------------------------------------------------------------------
@@ -687,7 +697,7 @@ cudaError_t k_band_dot(const BandList& L, const SphereSet& S, const double2* X, 
 
 // p = M r; rz = <r, M r>; rr = <r, r>
 __global__ void cg_init_kernel(const int* __restrict__ row, const int* __restrict__ kk, const int* __restrict__ npw,
-                               const double* __restrict__ g2, const double2* __restrict__ r, double2* __restrict__ p,
+                               const double* __restrict__ prec, const double2* __restrict__ r, double2* __restrict__ p,
                                int ld, double* __restrict__ rz, double* __restrict__ rr) {
     __shared__ double sh[32];
     const int c = blockIdx.x, k = kk[c];
@@ -695,7 +705,7 @@ __global__ void cg_init_kernel(const int* __restrict__ row, const int* __restric
     const long long o = (long long)row[c] * ld;
     double s1 = 0.0, s2 = 0.0;
     for (int G = threadIdx.x; G < n; G += blockDim.x) {
-        const double m = 1.0 / (1.0 + 0.5 * g2[(long long)k * ld + G]);
+        const double m = prec[(long long)k * ld + G];
         const double2 x = r[o + G];
         const double q = x.x * x.x + x.y * x.y;
         p[o + G] = cscale(x, m);
@@ -713,76 +723,112 @@ __global__ void cg_init_kernel(const int* __restrict__ row, const int* __restric
 cudaError_t k_cg_init(const BandList& L, const SphereSet& S, const double2* r, double2* p, int ld, double* rz,
                       double* rr, cudaStream_t st) {
     if (L.nb <= 0) return cudaSuccess;
-    cg_init_kernel<<<L.nb, 256, 0, st>>>(L.d_row, L.d_k, S.d_npw, S.d_g2, r, p, ld, rz, rr);
+    cg_init_kernel<<<L.nb, 256, 0, st>>>(L.d_row, L.d_k, S.d_npw, S.d_prec, r, p, ld, rz, rr);
     HP_LAUNCHED();
     return cudaGetLastError();
 }
 
-// a = rz / pAp; x += a p; r -= a Ap; rz_old = rz; rz = <r, M r>; rr = <r, r>
-__global__ void cg_update_kernel(const int* __restrict__ row, const int* __restrict__ kk, const int* __restrict__ npw,
-                                 const double* __restrict__ g2, const double* __restrict__ pap, double2* __restrict__ x,
-                                 double2* __restrict__ r, const double2* __restrict__ p, const double2* __restrict__ ap,
-                                 int ld, double* __restrict__ rz, double* __restrict__ rr, double* __restrict__ rz_old) {
-    __shared__ double sh[32];
+// One CG step per band, fused: pAp = <p, Ap>; a = rz / pAp; x += a p; r -= a Ap;
+// rz' = <r, M r>, rr = <r, r>; p = M r + (rz' / rz) p.  One CTA per band; with E > 0 the band's p
+// and Ap (then r) stay in registers (E elements per thread, npw <= 256 E), with E = 0 they are
+// read again.  Reductions in a fixed order.
+template <int E>
+__global__ void __launch_bounds__(256) cg_step_kernel(const int* __restrict__ row, const int* __restrict__ kk,
+                                                      const int* __restrict__ npw, const double* __restrict__ prec,
+                                                      double2* __restrict__ x, double2* __restrict__ r,
+                                                      double2* __restrict__ p, const double2* __restrict__ ap, int ld,
+                                                      double* __restrict__ pap, double* __restrict__ rz,
+                                                      double* __restrict__ rr) {
+    __shared__ double sh[33];
     const int c = blockIdx.x, k = kk[c];
     const int b = row[c];
     const int n = npw[k];
     const long long o = (long long)b * ld;
-    const double a = rz[b] / pap[b];
+    const double* m = prec + (long long)k * ld;
+    const double rz0 = rz[b];
+    constexpr int EC = E > 0 ? E : 1;
+    double2 pv[EC], av[EC];
+    double s = 0.0;
+    if (E > 0) {
+#pragma unroll
+        for (int e = 0; e < EC; ++e) {
+            const int G = threadIdx.x + 256 * e;
+            if (G < n) {
+                pv[e] = p[o + G];
+                av[e] = ap[o + G];
+                s += pv[e].x * av[e].x + pv[e].y * av[e].y;
+            }
+        }
+    } else {
+        for (int G = threadIdx.x; G < n; G += 256) {
+            const double2 a = p[o + G], q = ap[o + G];
+            s += a.x * q.x + a.y * q.y;
+        }
+    }
+    const double pAp = block_allsum(s, sh);
+    const double alpha = rz0 / pAp;
     double s1 = 0.0, s2 = 0.0;
-    for (int G = threadIdx.x; G < n; G += blockDim.x) {
-        const double2 pv = p[o + G], av = ap[o + G];
+    auto upd = [&](int G, const double2& pg, const double2& ag) {
         double2 xv = x[o + G], rv = r[o + G];
-        xv.x += a * pv.x;
-        xv.y += a * pv.y;
-        rv.x -= a * av.x;
-        rv.y -= a * av.y;
+        xv.x += alpha * pg.x;
+        xv.y += alpha * pg.y;
+        rv.x -= alpha * ag.x;
+        rv.y -= alpha * ag.y;
         x[o + G] = xv;
         r[o + G] = rv;
-        const double m = 1.0 / (1.0 + 0.5 * g2[(long long)k * ld + G]);
         const double q = rv.x * rv.x + rv.y * rv.y;
-        s1 += m * q;
+        s1 += m[G] * q;
         s2 += q;
+        return rv;
+    };
+    if (E > 0) {
+#pragma unroll
+        for (int e = 0; e < EC; ++e) {
+            const int G = threadIdx.x + 256 * e;
+            if (G < n) av[e] = upd(G, pv[e], av[e]);
+        }
+    } else {
+        for (int G = threadIdx.x; G < n; G += 256) upd(G, p[o + G], ap[o + G]);
     }
-    s1 = block_sum(s1, sh);
-    s2 = block_sum(s2, sh);
+    s1 = block_allsum(s1, sh);
+    s2 = block_allsum(s2, sh);
+    const double beta = s1 / rz0;
+    if (E > 0) {
+#pragma unroll
+        for (int e = 0; e < EC; ++e) {
+            const int G = threadIdx.x + 256 * e;
+            if (G < n) {
+                const double mm = m[G];
+                p[o + G] = cmk(mm * av[e].x + beta * pv[e].x, mm * av[e].y + beta * pv[e].y);
+            }
+        }
+    } else {
+        for (int G = threadIdx.x; G < n; G += 256) {
+            const double mm = m[G];
+            const double2 rv = r[o + G], q = p[o + G];
+            p[o + G] = cmk(mm * rv.x + beta * q.x, mm * rv.y + beta * q.y);
+        }
+    }
     if (threadIdx.x == 0) {
-        rz_old[b] = rz[b];
+        pap[b] = pAp;
         rz[b] = s1;
         rr[b] = s2;
     }
 }
 
-cudaError_t k_cg_update(const BandList& L, const SphereSet& S, const double* pap, double2* x, double2* r,
-                        const double2* p, const double2* ap, int ld, double* rz, double* rr, double* rz_old,
-                        cudaStream_t st) {
+cudaError_t k_cg_step(const BandList& L, const SphereSet& S, double2* x, double2* r, double2* p, const double2* ap,
+                      int ld, double* pap, double* rz, double* rr, cudaStream_t st) {
     if (L.nb <= 0) return cudaSuccess;
-    cg_update_kernel<<<L.nb, 256, 0, st>>>(L.d_row, L.d_k, S.d_npw, S.d_g2, pap, x, r, p, ap, ld, rz, rr, rz_old);
-    HP_LAUNCHED();
-    return cudaGetLastError();
-}
-
-// p = M r + (rz / rz_old) p
-__global__ void cg_dir_kernel(const int* __restrict__ row, const int* __restrict__ kk, const int* __restrict__ npw,
-                              const double* __restrict__ g2, const double* __restrict__ rz,
-                              const double* __restrict__ rz_old, const double2* __restrict__ r, double2* __restrict__ p,
-                              int ld) {
-    const int c = blockIdx.x, k = kk[c];
-    const int b = row[c];
-    const int n = npw[k];
-    const long long o = (long long)b * ld;
-    const double beta = rz[b] / rz_old[b];
-    for (int G = threadIdx.x; G < n; G += blockDim.x) {
-        const double m = 1.0 / (1.0 + 0.5 * g2[(long long)k * ld + G]);
-        const double2 rv = r[o + G], pv = p[o + G];
-        p[o + G] = cmk(m * rv.x + beta * pv.x, m * rv.y + beta * pv.y);
-    }
-}
-
-cudaError_t k_cg_direction(const BandList& L, const SphereSet& S, const double* rz, const double* rz_old,
-                           const double2* r, double2* p, int ld, cudaStream_t st) {
-    if (L.nb <= 0) return cudaSuccess;
-    cg_dir_kernel<<<L.nb, 256, 0, st>>>(L.d_row, L.d_k, S.d_npw, S.d_g2, rz, rz_old, r, p, ld);
+    int nmax = 0;
+    for (int v : S.npw) nmax = std::max(nmax, v);
+    const int e = (nmax + 255) / 256;
+#define HP_CGS(EE) cg_step_kernel<EE><<<L.nb, 256, 0, st>>>(L.d_row, L.d_k, S.d_npw, S.d_prec, x, r, p, ap, ld, pap, rz, rr)
+    if (e <= 3) HP_CGS(3);
+    else if (e <= 6) HP_CGS(6);
+    else if (e <= 9) HP_CGS(9);
+    else if (e <= 12) HP_CGS(12);
+    else HP_CGS(0);
+#undef HP_CGS
     HP_LAUNCHED();
     return cudaGetLastError();
 }
