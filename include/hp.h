@@ -83,6 +83,10 @@ typedef struct {
     int fft_grid[3];        /* FFT grid; 0 = smallest alias-free 2-3-5 grid */
     int band_batch;         /* bands per FFT batch (0 = automatic) */
     void* cuda_stream;      /* cudaStream_t to issue work on; NULL = legacy default stream */
+    double cg_adapt;        /* outer iterations after the first stop each band's CG at
+                             * ||r|| <= max(cg_tol, theta ||b||), theta = min(1e-2, cg_adapt x the
+                             * previous iteration's relative Hxc residual); 0 = always cg_tol
+                             * (default 0.01).  The first iteration (chi_0) always uses cg_tol. */
 } hp_options;
 
 /* Fills *opt with the defaults listed above. */

@@ -40,7 +40,7 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("cg_tol", C.c_double), ("cg_maxiter", C.c_int), ("scf_tol", C.c_double),
                 ("conv_thr_chi", C.c_double), ("niter_max", C.c_int), ("nmix", C.c_int), ("alpha_mix", C.c_double),
                 ("gs_tol", C.c_double), ("gs_maxiter", C.c_int), ("fft_grid", C.c_int * 3), ("band_batch", C.c_int),
-                ("cuda_stream", C.c_void_p)]
+                ("cuda_stream", C.c_void_p), ("cg_adapt", C.c_double)]
 
 
 class Sizes(C.Structure):

@@ -432,6 +432,7 @@ extern "C" void hp_default_options(hp_options* o) {
     o->cg_tol = 1e-11;
     o->cg_maxiter = 400;
     o->scf_tol = 1e-10;
+    o->cg_adapt = 0.01;
     o->conv_thr_chi = 1e-10;
     o->niter_max = 100;
     o->nmix = 4;
@@ -1148,7 +1149,7 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
     std::vector<double> tr0, tr((size_t)2 * nh), tr_prev;
     long long cg_total = 0, hpsi = 0;
     int nhist = 0;
-    double res = INFINITY, dchi = INFINITY;
+    double res = INFINITY, dchi = INFINITY, res_rel = 1.0;
     bool converged = false, cg_ok = true;
     int it = 0;
     std::vector<double> res_hist;
@@ -1203,11 +1204,16 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
         CK(k_expand(Lall, Sq, Ukq, c->d_Pbuf, nullptr, -1.0, c->d_b, ld, c->st, mixed));
         // per-band stopping rule: ||r|| <= cg_tol, and in the mixed form also <= 1e-7 ||b|| (the FP32
         // operator is accurate to about 1e-7 relative; iterating below that buys nothing)
+        // Outer iterations after the first solve only as far as the response potential is known:
+        // theta = min(1e-2, cg_adapt x the previous relative Hxc residual) of ||b|| (the first
+        // iteration gives chi_0 and is solved to cg_tol).
         std::vector<double> tolb(rows, tol2);
-        if (mixed) {
+        const double theta = (it > 1 && c->opt.cg_adapt > 0) ? std::min(1e-2, c->opt.cg_adapt * res_rel) : 0.0;
+        if (mixed || theta > 0) {
             CK(k_band_dot(Lall, Sq, c->d_b, c->d_b, ld, c->d_pap, c->st));
             CK(d2h(rr.data(), c->d_pap, rows, c->st));
-            for (int i = 0; i < rows; ++i) tolb[i] = std::max(tol2, 1e-14 * rr[i]);
+            const double f2 = std::max(mixed ? 1e-14 : 0.0, theta * theta);
+            for (int i = 0; i < rows; ++i) tolb[i] = std::max(tol2, f2 * rr[i]);
         }
         // ---- CG on every band, warm start from the previous x
         if ((s = apply_sternheimer(c, Lall, c->d_x, c->d_ap)) != HP_OK) return s;
@@ -1310,11 +1316,10 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
         CK(k_hxc_combine(c->d_dvh, c->d_drho, c->d_fxc, nspin, nr, c->d_dvout, c->st));
         cudaError_t e;
         double scf_tol = c->opt.scf_tol, chi_tol = c->opt.conv_thr_chi;
-        double vrms = 0.0;
+        const double vv = dev_dot(c, c->d_dvout, c->d_dvout, ndv, &e);
+        if (e != cudaSuccess) return cuda_fail(c, e, "response norm");
+        const double vrms = std::sqrt(vv / (double)ndv);
         if (mixed) {  // FP32 noise floor: 3e-7 of the response potential and of the response traces
-            const double vv = dev_dot(c, c->d_dvout, c->d_dvout, ndv, &e);
-            if (e != cudaSuccess) return cuda_fail(c, e, "response norm");
-            vrms = std::sqrt(vv / (double)ndv);
             scf_tol = std::max(scf_tol, 3e-7 * vrms);
             double tmax = 0.0;
             for (int a = 0; a < 2 * nh; ++a) tmax = std::max(tmax, std::fabs(tr[a]));
@@ -1326,6 +1331,7 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
         if (e != cudaSuccess) return cuda_fail(c, e, "residual");
         if (!std::isfinite(ff)) return fail(c, HP_ENUMERIC, "hp_response: non-finite Hxc residual");
         res = std::sqrt(ff / (double)ndv);
+        res_rel = vrms > 0 ? res / vrms : 1.0;
         dchi = INFINITY;
         if (!tr_prev.empty()) {
             dchi = 0.0;
