@@ -180,10 +180,15 @@ def reference_arm(args, rank):
 # our arm
 # ------------------------------------------------------------------------------------------------
 FAMILY_KERNELS = {"fft_pass": ("fft_fixed_kernel / fft_axis_kernel (FP32 Stockham pass)", "fft.cu"),
-                  "column": ("col_inv_kernel + col_fwd_kernel (fused z-column transforms)", "fused.cu"),
-                  "plane": ("plane_kernel (fused x/y plane transforms + real-space product)", "fused.cu"),
+                  "column": ("col_inv_reg_kernel + col_fwd_reg_kernel (fused z-column transforms)", "fused.cu"),
+                  "plane": ("plane_reg_kernel (fused x/y plane transforms + real-space product)", "fused.cu"),
                   "project": ("proj_kernel + proj_reduce_kernel (FP32 projections)", "kernels.cu"),
                   "expand": ("expand_kernel (FP32 projector expansion)", "kernels.cu")}
+# what bounds each family on GB300 (ncu summaries under profiles/): FP32 instruction issue for the
+# in-register FFTs and the projector contractions, HBM for the data-movement passes
+FAMILY_BOUND = {"fft_pass": "hbm", "column": "hbm", "plane": "alu", "project": "alu", "expand": "alu"}
+# FP32 peak: 152 SMs x 128 FP32 lanes x 2 flops per FMA x 2.07 GHz (maximum SM clock)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 def ncu_traffic(family, alg_bytes_per_launch):
@@ -331,15 +336,28 @@ def main():
     avg_s = p["ms"] / p["launches"] / 1000.0
     alg = p["bytes"] / p["launches"]
     achieved = alg / avg_s / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": ncu_traffic(fam, alg), "kernel": FAMILY_KERNELS[fam][0], "peak_source": peak_src,
-                "launches": p["launches"], "avg_launch_ms": avg_s * 1000.0, "algorithmic_bytes_per_launch": alg,
-                "achieved_tflops": p["flops"] / p["ms"] * 1e-9, "share_of_step": p["ms"] / 1000.0 / mix["elapsed"],
+    bound = FAMILY_BOUND[fam]
+    tflops = p["flops"] / p["ms"] * 1e-9
+    if bound == "alu":
+        roofline = {"bound": "alu", "achieved": tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": tflops / FP32_PEAK_TFLOPS,
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (nominal flops: 5 n log2 n "
+                                   "per transformed line, 8 per complex multiply-add)",
+                    "hbm_achieved_gbs": achieved, "hbm_peak_gbs": peak, "hbm_frac": achieved / peak}
+    else:
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "peak_source": peak_src, "achieved_tflops": tflops}
+    roofline.update({"traffic": ncu_traffic(fam, alg), "kernel": FAMILY_KERNELS[fam][0],
+                     "launches": p["launches"], "avg_launch_ms": avg_s * 1000.0, "algorithmic_bytes_per_launch": alg,
+                     "share_of_step": p["ms"] / 1000.0 / mix["elapsed"]})
+    roofline.update({
                 "families": {f: {"share_of_step": round(q["ms"] / 1000.0 / mix["elapsed"], 4),
-                                 "launches": q["launches"],
+                                 "launches": q["launches"], "bound": FAMILY_BOUND[f],
                                  "gbs": round(q["bytes"] / q["ms"] * 1e-6, 1) if q["ms"] else None,
-                                 "tflops": round(q["flops"] / q["ms"] * 1e-9, 3) if q["ms"] else None}
-                             for f, q in prof.items()}}
+                                 "tflops": round(q["flops"] / q["ms"] * 1e-9, 3) if q["ms"] else None,
+                                 "traffic_per_launch": (ncu_traffic(f, q["bytes"] / q["launches"])
+                                                        if q["launches"] else None)}
+                             for f, q in prof.items()}})
     line = {"metric": METRIC, "value": mix["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": mix["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64 (mixed: FP32 grids and projections, FP64 vectors and scalars)",

@@ -227,7 +227,9 @@ void hp_destroy(hp_ctx* ctx);
  *   HP_KF_EXPAND    psi += beta P: projector rows and coefficients read, band vectors read and written.
  * hp_profile_end waits for the events and fills stats[0 .. HP_KF_COUNT-1] with the summed kernel
  * time (ms), launches, flops and bytes of each family.  Process-wide (one host thread), not per
- * context.  Errors: HP_ECUDA if an event could not be read. */
+ * context.  With the environment variable HP_PROF_LOG naming a file, every timed launch also
+ * appends one line "family kernel bytes flops" to it.  Errors: HP_ECUDA if an event could not be
+ * read. */
 enum {
     HP_KF_FFT_PASS = 0,
     HP_KF_COLUMN = 1,

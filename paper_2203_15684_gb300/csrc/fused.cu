@@ -702,7 +702,7 @@ static cudaError_t col_launch(bool inv, const FusedArgs& a) {
             if (!inv) bytes += 16.0 * (S.ld - S.npw[k]) + (a.mode == 0 ? 16.0 * S.npw[k] : 0.0);
             flops += 5.0 * N2 * std::log2((double)N2) * S.ncol[k];
         }
-        prof_stop(pm, HP_KF_COLUMN, a.st, flops, bytes);
+        prof_stop(pm, HP_KF_COLUMN, a.st, flops, bytes, inv ? (reg ? "col_inv_reg" : "col_inv") : (reg ? "col_fwd_reg" : "col_fwd"));
     }
     return cudaGetLastError();
 }
@@ -741,7 +741,7 @@ static cudaError_t plane_reg_launch(const FusedArgs& a) {
         const double pot = OP == 0 ? (double)sizeof(T) * nr : OP == 2 ? (double)sizeof(V) * nr : 0.0;
         bytes += pot * ((int)spin_seen[0] + (int)spin_seen[1]);
         const double flops = (OP == 0 ? 2.0 : 1.0) * 5.0 * nr * std::log2((double)N0 * N1) * a.nc;
-        prof_stop(pm, HP_KF_PLANE, a.st, flops, bytes);
+        prof_stop(pm, HP_KF_PLANE, a.st, flops, bytes, OP == 0 ? "plane_reg_op0" : OP == 1 ? "plane_reg_op1" : "plane_reg_op2");
     }
     return cudaGetLastError();
 }
@@ -781,7 +781,7 @@ static cudaError_t plane_launch(const FusedArgs& a) {
         const double pot = OP == 0 ? (double)sizeof(T) * nr : OP == 2 ? (double)sizeof(V) * nr : 0.0;
         bytes += pot * ((int)spin_seen[0] + (int)spin_seen[1]);
         const double flops = (OP == 0 ? 2.0 : 1.0) * 5.0 * nr * std::log2((double)N0 * N1) * a.nc;
-        prof_stop(pm, HP_KF_PLANE, a.st, flops, bytes);
+        prof_stop(pm, HP_KF_PLANE, a.st, flops, bytes, OP == 0 ? "plane_op0" : OP == 1 ? "plane_op1" : "plane_op2");
     }
     return cudaGetLastError();
 }

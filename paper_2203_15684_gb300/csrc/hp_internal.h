@@ -302,7 +302,10 @@ struct ProfMark {
 };
 bool prof_on();
 ProfMark prof_start(cudaStream_t st);
-void prof_stop(const ProfMark& m, int fam, cudaStream_t st, double flops, double bytes);
+// tag: kernel name written with the launch's bytes and flops to the file named by HP_PROF_LOG
+// (one line per timed launch), which lets a profiler capture of one launch be matched to its
+// algorithmic bytes
+void prof_stop(const ProfMark& m, int fam, cudaStream_t st, double flops, double bytes, const char* tag = nullptr);
 
 bool fused_supported(const int N[3]);
 cudaError_t fused_col(bool fp32, bool inv, const FusedArgs& a);

@@ -562,7 +562,7 @@ cudaError_t k_proj(const BandList& L, const SphereSet& S, const ProjMat& A, cons
             flops += 8.0 * nrow * S.npw[L.k[b]];
         }
         for (int sg = 0; sg < L.nseg; ++sg) bytes += ab * nrow * S.npw[L.seg_k[sg]];
-        prof_stop(pm, HP_KF_PROJECT, st, flops, bytes);
+        prof_stop(pm, HP_KF_PROJECT, st, flops, bytes, "proj");
     }
     return cudaGetLastError();
 }
@@ -662,7 +662,7 @@ cudaError_t k_expand(const BandList& L, const SphereSet& S, const ProjMat& A, co
             flops += 8.0 * nrow * S.npw[L.k[b]];
         }
         for (int sg = 0; sg < L.nseg; ++sg) bytes += ab * nrow * S.npw[L.seg_k[sg]];
-        prof_stop(pm, HP_KF_EXPAND, st, flops, bytes);
+        prof_stop(pm, HP_KF_EXPAND, st, flops, bytes, "expand");
     }
     return cudaGetLastError();
 }

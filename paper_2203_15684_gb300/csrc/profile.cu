@@ -5,6 +5,8 @@
 // events; each launch also adds its algorithmic flops and bytes, counted on the host from the sizes
 // it processes.  hp_profile_end waits for the events and returns per-family sums.  The profiler is
 // process-wide and meant for one host thread driving the library.
+#include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "hp_internal.h"
@@ -50,8 +52,16 @@ ProfMark prof_start(cudaStream_t st) {
     return m;
 }
 
-void prof_stop(const ProfMark& m, int fam, cudaStream_t st, double flops, double bytes) {
+void prof_stop(const ProfMark& m, int fam, cudaStream_t st, double flops, double bytes, const char* tag) {
     if (!g_prof.on || !m.e0 || fam < 0 || fam >= HP_KF_COUNT) return;
+    static FILE* log = [] {
+        const char* path = getenv("HP_PROF_LOG");
+        return path ? fopen(path, "a") : nullptr;
+    }();
+    if (log) {
+        fprintf(log, "%d %s %.0f %.0f\n", fam, tag ? tag : "-", bytes, flops);
+        fflush(log);
+    }
     cudaEvent_t e1 = take_event();
     if (!e1) return;
     cudaEventRecord(e1, st);
