@@ -1,9 +1,10 @@
 #!/usr/bin/env python3
 """Benchmark of the DFPT Hubbard-parameter hot path on GB300.
 
-Workload: the medium rocksalt-like cell (8.4 bohr cube, 4 H + 4 L, 40 electrons, collinear
-nspin = 2 with an antiferromagnetic start, 35 Ry, FFT 36^3, k 4x4x4, q 2x2x2).  The ground state
-is computed on the GPU before timing.  One step = one (q, J) self-consistent Sternheimer response
+Workload (--workload): "medium" (default), the rocksalt-like cell (8.4 bohr cube, 4 H + 4 L,
+40 electrons, collinear nspin = 2 with an antiferromagnetic start, 35 Ry, FFT 36^3, k 4x4x4,
+q 2x2x2); "precision", the same cell at 50 Ry (FFT 45^3).  The ground state is computed on the GPU
+before timing.  One step = one (q, J) self-consistent Sternheimer response
 (the per-q set-up a1 and a3-a10): every (spin, k, band) system of that pair, to the FP64
 tolerances the parity tests use.  The 64 (q, J) pairs of the full chi matrix are independent and
 alike, so the full-matrix wall time is reported as steps-per-matrix x time per step.  The headline
@@ -14,7 +15,7 @@ Metric: H.psi/s (single-band applications of the Sternheimer operator, summed ov
 N > 1 (torchrun): the (q, J) pairs are sharded round-robin over ranks (weak scaling, no collective
 on the data path); timing is the max over ranks between barriers.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload medium|precision]
 """
 
 from __future__ import annotations
@@ -35,8 +36,12 @@ sys.path.insert(0, ROOT)
 METRIC = "full χ-matrix wall time & H·ψ/s, mixed vs FP64 on 1 GB300 at |ΔU|≤1 meV"
 UNIT = "Hpsi/s"
 FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 rate (no measured FP64 peak is available; see DESIGN)
-WORKLOAD_DESC = ("medium: rocksalt cube a=8.4 bohr, 4 H + 4 L, 40 electrons, nspin=2 (AFM start), "
-                 "ecutwfc 35 Ry (npw<=2103), FFT 36^3, k 4x4x4, q 2x2x2")
+WORKLOADS = {
+    "medium": "medium: rocksalt cube a=8.4 bohr, 4 H + 4 L, 40 electrons, nspin=2 (AFM start), "
+              "ecutwfc 35 Ry (npw<=2103), FFT 36^3, k 4x4x4, q 2x2x2",
+    "precision": "precision: the medium cell at ecutwfc 50 Ry (npw<=3575), FFT 45^3, k 4x4x4, q 2x2x2, "
+                 "nspin=2 (AFM start)",
+}
 
 
 def parse():
@@ -50,6 +55,7 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--band-batch", type=int, default=0, help="grids per FFT batch (0 = automatic)")
+    p.add_argument("--workload", default="medium", choices=sorted(WORKLOADS))
     return p.parse_args()
 
 
@@ -108,7 +114,7 @@ class ClockSampler:
 # ------------------------------------------------------------------------------------------------
 # oracle timing (CPU baseline and the reference arm)
 # ------------------------------------------------------------------------------------------------
-def _oracle_sample(seconds):
+def _oracle_sample(seconds, workload="medium"):
     """The oracle's Sternheimer operator (H + alpha P_v - eps) applied to blocks of 20 bands on the
     workload's spheres and grid, with the oracle's own starting-density potential, for about
     ``seconds``; returns (H.psi count, elapsed)."""
@@ -119,7 +125,7 @@ def _oracle_sample(seconds):
     from oracle.hamiltonian import apply_h
     from oracle.model import Model
 
-    w = W.medium()
+    w = getattr(W, workload)()
     m = Model(w)
     vr = m.vloc_r() + G.hxc_potential(m, G.initial_density(m))[0]
     rng = np.random.default_rng(2203)
@@ -136,20 +142,20 @@ def _oracle_sample(seconds):
             return n, el, float(np.abs(Y).max())
 
 
-def run_oracle_subprocess(seconds):
+def run_oracle_subprocess(seconds, workload="medium"):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = ("import json,sys; sys.path.insert(0, %r); import bench; n, el, _ = bench._oracle_sample(%f); "
-            "print(json.dumps(dict(n=n, el=el)))" % (ROOT, seconds))
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; n, el, _ = bench._oracle_sample(%f, %r); "
+            "print(json.dumps(dict(n=n, el=el)))" % (ROOT, seconds, workload))
     r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
     d = json.loads(r.stdout.strip().splitlines()[-1])
     return d["n"], d["el"]
 
 
-def cpu_baseline(seconds):
-    n, el = run_oracle_subprocess(seconds)
+def cpu_baseline(seconds, workload="medium"):
+    n, el = run_oracle_subprocess(seconds, workload)
     return {"value": n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "oracle Sternheimer operator (H + alpha P_v - eps) on %d single-band vectors of the medium "
-                      "workload (20-band blocks cycling over its 64 k spheres, FFT 36^3), %.1f s, 1 thread" % (n, el)}
+            "sample": "oracle Sternheimer operator (H + alpha P_v - eps) on %d single-band vectors of the %s "
+                      "workload (20-band blocks cycling over its 64 k spheres), %.1f s, 1 thread" % (n, workload, el)}
 
 
 def reference_arm(args, rank):
@@ -158,9 +164,9 @@ def reference_arm(args, rank):
     vals = []
     n_tot, el_tot = 0, 0.0
     for _ in range(args.warmup):
-        run_oracle_subprocess(2.0)
+        run_oracle_subprocess(2.0, args.workload)
     for _ in range(args.steps):
-        n, el = run_oracle_subprocess(5.0)
+        n, el = run_oracle_subprocess(5.0, args.workload)
         vals.append(n / el)
         n_tot += n
         el_tot += el
@@ -168,7 +174,7 @@ def reference_arm(args, rank):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * el_tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD_DESC, "step": "about 5 s of the oracle's Sternheimer operator on the "
+            "config": {"workload": WORKLOADS[args.workload], "step": "about 5 s of the oracle's Sternheimer operator on the "
                                                           "workload's spheres (1 thread)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "%d H.psi in %.1f s over %d steps" % (n_tot, el_tot, args.steps)},
@@ -191,11 +197,11 @@ FAMILY_BOUND = {"fft_pass": "hbm", "column": "hbm", "plane": "alu", "project": "
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
-def ncu_traffic(family, alg_bytes_per_launch):
+def ncu_traffic(family, alg_bytes_per_launch, workload="medium"):
     """DRAM bytes per launch of a kernel family: the DRAM/algorithmic byte ratio of a committed ncu
-    capture (profiles/traffic_<family>_medium.json) times this run's algorithmic bytes per launch;
+    capture (profiles/traffic_<family>_<workload>.json) times this run's algorithmic bytes per launch;
     None when the kernel source changed since the capture."""
-    path = os.path.join(ROOT, "profiles", "traffic_%s_medium.json" % family)
+    path = os.path.join(ROOT, "profiles", "traffic_%s_%s.json" % (family, workload))
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
@@ -233,7 +239,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     stream = torch.cuda.current_stream()
-    w = W.medium()
+    w = getattr(W, args.workload)()
     ctx = P.Context.from_workload(w, cuda_stream=stream.cuda_stream, band_batch=args.band_batch)
     t0 = time.perf_counter()
     gs = ctx.ground_state(w["nelec"], w["nspin"], w["moments"])
@@ -347,7 +353,7 @@ def main():
     else:
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                     "peak_source": peak_src, "achieved_tflops": tflops}
-    roofline.update({"traffic": ncu_traffic(fam, alg), "kernel": FAMILY_KERNELS[fam][0],
+    roofline.update({"traffic": ncu_traffic(fam, alg, args.workload), "kernel": FAMILY_KERNELS[fam][0],
                      "launches": p["launches"], "avg_launch_ms": avg_s * 1000.0, "algorithmic_bytes_per_launch": alg,
                      "share_of_step": p["ms"] / 1000.0 / mix["elapsed"]})
     roofline.update({
@@ -355,14 +361,14 @@ def main():
                                  "launches": q["launches"], "bound": FAMILY_BOUND[f],
                                  "gbs": round(q["bytes"] / q["ms"] * 1e-6, 1) if q["ms"] else None,
                                  "tflops": round(q["flops"] / q["ms"] * 1e-9, 3) if q["ms"] else None,
-                                 "traffic_per_launch": (ncu_traffic(f, q["bytes"] / q["launches"])
+                                 "traffic_per_launch": (ncu_traffic(f, q["bytes"] / q["launches"], args.workload)
                                                         if q["launches"] else None)}
                              for f, q in prof.items()}})
     line = {"metric": METRIC, "value": mix["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": mix["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64 (mixed: FP32 grids and projections, FP64 vectors and scalars)",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD_DESC,
+            "config": {"workload": WORKLOADS[args.workload],
                        "step": "one (q, J) self-consistent Sternheimer response, %d band systems"
                                % (s["nspin"] * s["nk"] * s["nocc"]),
                        "pairs_per_chi_matrix": len(pairs),
@@ -383,7 +389,7 @@ def main():
             "e2e": {"value": hpsi_e / e2e_el, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": mix["launches"], "roofline": roofline}
     if args.cpu_seconds > 0:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, args.workload)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
