@@ -35,7 +35,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "full χ-matrix wall time & H·ψ/s, mixed vs FP64 on 1 GB300 at |ΔU|≤1 meV"
 UNIT = "Hpsi/s"
-FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 rate (no measured FP64 peak is available; see DESIGN)
 WORKLOADS = {
     "medium": "medium: rocksalt cube a=8.4 bohr, 4 H + 4 L, 40 electrons, nspin=2 (AFM start), "
               "ecutwfc 35 Ry (npw<=2103), FFT 36^3, k 4x4x4, q 2x2x2",
