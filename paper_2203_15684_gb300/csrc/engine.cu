@@ -161,6 +161,8 @@ hp_status upload_sphereset(hp_ctx* c, const std::vector<const KSphere*>& sph, co
         CK(dalloc(c, &S.d_idx, (size_t)nk * ld));
         CK(dalloc(c, &S.d_g2, (size_t)nk * ld));
         CK(dalloc(c, &S.d_prec, (size_t)nk * ld));
+        CK(dalloc(c, &S.d_prec32, (size_t)nk * ld));
+        CK(dalloc(c, &S.d_kin32, (size_t)nk * ld));
         CK(dalloc(c, &S.d_iz, (size_t)nk * ld));
         CK(dalloc(c, &S.d_ncol, nk));
     }
@@ -217,6 +219,10 @@ hp_status upload_sphereset(hp_ctx* c, const std::vector<const KSphere*>& sph, co
     for (int k = 0; k < nk; ++k)
         for (int i = 0; i < S.npw[k]; ++i) prec[(size_t)k * ld + i] = 1.0 / (1.0 + 0.5 * g2[(size_t)k * ld + i]);
     CK(h2d(S.d_prec, prec.data(), prec.size(), c->st));
+    std::vector<float> prec32(prec.begin(), prec.end()), kin32(g2.size(), 0.0f);
+    for (size_t i = 0; i < g2.size(); ++i) kin32[i] = (float)(0.5 * g2[i]);
+    CK(h2d(S.d_prec32, prec32.data(), prec32.size(), c->st));
+    CK(h2d(S.d_kin32, kin32.data(), kin32.size(), c->st));
     CK(h2d(S.d_iz, iz.data(), iz.size(), c->st));
     CK(h2d(S.d_ncol, ncol.data(), nk, c->st));
     CK(h2d(S.d_col_start, hs.data(), hs.size(), c->st));
@@ -374,7 +380,7 @@ FusedArgs fused_args(hp_ctx* c, const SphereSet& S, const BandList& L) {
 }
 
 // Y = (T + V - shift) X through the fused column/plane transforms
-hp_status apply_local_fused(hp_ctx* c, const SphereSet& S, const BandList& L, const double2* X, double2* Y, bool fp32) {
+hp_status apply_local_fused(hp_ctx* c, const SphereSet& S, const BandList& L, const void* X, void* Y, bool fp32) {
     if (L.nb == 0) return HP_OK;
     const int chunk = fused_batch(c, S, L.nb);
     hp_status s = ensure_colbuf(c, sizeof(double2) * (size_t)chunk * c->N[2] * S.ncmax);
@@ -385,6 +391,7 @@ hp_status apply_local_fused(hp_ctx* c, const SphereSet& S, const BandList& L, co
         a.nc = std::min(chunk, L.nb - c0);
         a.X = X;
         a.Y = Y;
+        a.vec32 = c->vec32;
         a.mode = 0;
         CK(fused_col(fp32, true, a));
         CK(fused_plane(fp32, 0, a));
@@ -394,6 +401,14 @@ hp_status apply_local_fused(hp_ctx* c, const SphereSet& S, const BandList& L, co
 }
 
 hp_status project(hp_ctx* c, const SphereSet& S, const BandList& L, const ProjMat& A, const double2* X, double2* P,
+                  bool fp32) {
+    hp_status s = ensure_scratch(c, (size_t)16 * std::max(1, L.nb) * kPStride);
+    if (s != HP_OK) return s;
+    CK(k_proj(L, S, A, X, c->ld, P, c->d_scratch, c->scratch_elems, c->st, fp32));
+    return HP_OK;
+}
+
+hp_status project(hp_ctx* c, const SphereSet& S, const BandList& L, const ProjMat& A, const float2* X, double2* P,
                   bool fp32) {
     hp_status s = ensure_scratch(c, (size_t)16 * std::max(1, L.nb) * kPStride);
     if (s != HP_OK) return s;
@@ -1060,6 +1075,7 @@ hp_status apply_sternheimer(hp_ctx* c, const BandList& L, const double2* X, doub
     const int* kmap = c->qc.d_miller;
     const bool fp32 = c->opt.precision == HP_PRECISION_MIXED;
     hp_status s = (c->fused && c->d_vt) ? apply_local_fused(c, S, L, X, Y, fp32) : apply_local(c, S, L, X, Y, c->d_veff, fp32);
+    // (FP32 band vectors are used only together with the fused transforms)
     if (s != HP_OK) return s;
     // V_NL and alpha P_v in one projection and one expansion: rows 0 .. nproj-1 are beta (weights
     // D), rows nproj .. nproj+nocc-1 the occupied states at k+q (weight alpha)
@@ -1071,9 +1087,15 @@ hp_status apply_sternheimer(hp_ctx* c, const BandList& L, const double2* X, doub
     A.stride2_k = (long long)c->nbnd * c->ld;
     A.nrow2 = c->nocc;
     A.scale2 = c->alpha_pv;
-    s = project(c, S, L, A, X, c->d_Pbuf, fp32);
-    if (s != HP_OK) return s;
-    CK(k_expand(L, S, A, c->d_Pbuf, c->d_projD, 1.0, Y, c->ld, c->st, fp32));
+    if (c->vec32) {
+        s = project(c, S, L, A, (const float2*)X, c->d_Pbuf, fp32);
+        if (s != HP_OK) return s;
+        CK(k_expand(L, S, A, c->d_Pbuf, c->d_projD, 1.0, (float2*)Y, c->ld, c->st, fp32));
+    } else {
+        s = project(c, S, L, A, X, c->d_Pbuf, fp32);
+        if (s != HP_OK) return s;
+        CK(k_expand(L, S, A, c->d_Pbuf, c->d_projD, 1.0, Y, c->ld, c->st, fp32));
+    }
     return HP_OK;
 }
 
@@ -1109,6 +1131,11 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
         c->resp_ready = false;
         if ((s = prepare_resp(c)) != HP_OK) return s;
     }
+    // Band vectors of the response (x, r, p, Ap, b, V_pert u) are FP32 in the mixed form with the
+    // fused transforms (step lengths, residual norms and every sum stay FP64), FP64 otherwise.
+    const bool v32 = mixed && c->fused;
+    c->vec32 = v32;
+    auto F32 = [](double2* p) { return reinterpret_cast<float2*>(p); };
     const int nspin = c->nspin, nk = c->nk, nocc = c->nocc, nr = c->nr, ld = c->ld;
     const int rows = nspin * nk * nocc;
     const int nh = (int)c->hub_atoms.size();
@@ -1138,7 +1165,8 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
     ProjMat Ukq{c->d_psi, (long long)nk * c->nbnd * ld, (long long)c->nbnd * ld, nocc, 0, kmap, c->d_psi32};
     if ((s = project(c, c->kset, Lpsi, phiJk, c->d_psi, c->d_Pbuf, mixed)) != HP_OK) return s;
     CK(cudaMemsetAsync(c->d_vpu, 0, sizeof(double2) * nvec, c->st));
-    CK(k_expand(Lall, Sq, phiJkq, c->d_Pbuf, nullptr, 1.0, c->d_vpu, ld, c->st, mixed));
+    if (v32) CK(k_expand(Lall, Sq, phiJkq, c->d_Pbuf, nullptr, 1.0, F32(c->d_vpu), ld, c->st, mixed));
+    else CK(k_expand(Lall, Sq, phiJkq, c->d_Pbuf, nullptr, 1.0, c->d_vpu, ld, c->st, mixed));
     CK(cudaMemsetAsync(c->d_x, 0, sizeof(double2) * nvec, c->st));
     CK(cudaMemsetAsync(c->d_dv, 0, sizeof(double2) * ndv, c->st));
     const double f = nspin == 1 ? 2.0 : 1.0;
@@ -1157,7 +1185,8 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
     for (it = 1; it <= c->opt.niter_max; ++it) {
         // ---- right-hand side b = -P_c (dV u + V_pert u)
         if (it == 1) {
-            CK(k_vec_scale_copy(c->d_b, c->d_vpu, -1.0, nvec, c->st));
+            if (v32) CK(k_vec_scale_copy(F32(c->d_b), F32(c->d_vpu), -1.0, nvec, c->st));
+            else CK(k_vec_scale_copy(c->d_b, c->d_vpu, -1.0, nvec, c->st));
         } else {
             s = ensure_grid(c, band_batch(c, rows));
             if (s != HP_OK) return s;
@@ -1175,6 +1204,7 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
                     a.ur = mixed ? (const void*)c->d_ur32 : (const void*)c->d_ur;
                     a.dvt = c->d_dvt;
                     a.Y = c->d_b;
+                    a.vec32 = v32;
                     a.mode = 1;
                     a.scale = -1.0;
                     CK(fused_plane(mixed, 2, a));
@@ -1198,10 +1228,16 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
                     CK(k_gather_scaled(Sq, Lall, c0, nc, c->d_grid, nr, -1.0 / nr, c->d_b, ld, 0, c->st));
                 }
             }
-            CK(k_vec_axpy(c->d_b, c->d_vpu, -1.0, nvec, c->st));
+            if (v32) CK(k_vec_axpy(F32(c->d_b), F32(c->d_vpu), -1.0, nvec, c->st));
+            else CK(k_vec_axpy(c->d_b, c->d_vpu, -1.0, nvec, c->st));
         }
-        if ((s = project(c, Sq, Lall, Ukq, c->d_b, c->d_Pbuf, mixed)) != HP_OK) return s;
-        CK(k_expand(Lall, Sq, Ukq, c->d_Pbuf, nullptr, -1.0, c->d_b, ld, c->st, mixed));
+        if (v32) {
+            if ((s = project(c, Sq, Lall, Ukq, F32(c->d_b), c->d_Pbuf, mixed)) != HP_OK) return s;
+            CK(k_expand(Lall, Sq, Ukq, c->d_Pbuf, nullptr, -1.0, F32(c->d_b), ld, c->st, mixed));
+        } else {
+            if ((s = project(c, Sq, Lall, Ukq, c->d_b, c->d_Pbuf, mixed)) != HP_OK) return s;
+            CK(k_expand(Lall, Sq, Ukq, c->d_Pbuf, nullptr, -1.0, c->d_b, ld, c->st, mixed));
+        }
         // per-band stopping rule: ||r|| <= cg_tol, and in the mixed form also <= 1e-7 ||b|| (the FP32
         // operator is accurate to about 1e-7 relative; iterating below that buys nothing)
         // Outer iterations after the first solve only as far as the response potential is known:
@@ -1210,7 +1246,8 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
         std::vector<double> tolb(rows, tol2);
         const double theta = (it > 1 && c->opt.cg_adapt > 0) ? std::min(1e-2, c->opt.cg_adapt * res_rel) : 0.0;
         if (mixed || theta > 0) {
-            CK(k_band_dot(Lall, Sq, c->d_b, c->d_b, ld, c->d_pap, c->st));
+            if (v32) CK(k_band_dot(Lall, Sq, F32(c->d_b), F32(c->d_b), ld, c->d_pap, c->st));
+            else CK(k_band_dot(Lall, Sq, c->d_b, c->d_b, ld, c->d_pap, c->st));
             CK(d2h(rr.data(), c->d_pap, rows, c->st));
             const double f2 = std::max(mixed ? 1e-14 : 0.0, theta * theta);
             for (int i = 0; i < rows; ++i) tolb[i] = std::max(tol2, f2 * rr[i]);
@@ -1218,8 +1255,13 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
         // ---- CG on every band, warm start from the previous x
         if ((s = apply_sternheimer(c, Lall, c->d_x, c->d_ap)) != HP_OK) return s;
         hpsi += rows;
-        CK(k_vec_sub(c->d_r, c->d_b, c->d_ap, nvec, c->st));
-        CK(k_cg_init(Lall, Sq, c->d_r, c->d_p, ld, c->d_rz, c->d_rr, c->st));
+        if (v32) {
+            CK(k_vec_sub(F32(c->d_r), F32(c->d_b), F32(c->d_ap), nvec, c->st));
+            CK(k_cg_init(Lall, Sq, F32(c->d_r), F32(c->d_p), ld, c->d_rz, c->d_rr, c->st));
+        } else {
+            CK(k_vec_sub(c->d_r, c->d_b, c->d_ap, nvec, c->st));
+            CK(k_cg_init(Lall, Sq, c->d_r, c->d_p, ld, c->d_rz, c->d_rr, c->st));
+        }
         int cgit = 0;
         BandList& La = c->L3;  // active (not yet converged) bands
         for (;;) {
@@ -1237,7 +1279,11 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
             if ((s = upload_list(c, La)) != HP_OK) return s;
             if ((s = apply_sternheimer(c, La, c->d_p, c->d_ap)) != HP_OK) return s;
             hpsi += La.nb;
-            CK(k_cg_step(La, Sq, c->d_x, c->d_r, c->d_p, c->d_ap, ld, c->d_pap, c->d_rz, c->d_rr, c->st));
+            if (v32)
+                CK(k_cg_step(La, Sq, F32(c->d_x), F32(c->d_r), F32(c->d_p), F32(c->d_ap), ld, c->d_pap, c->d_rz,
+                             c->d_rr, c->st));
+            else
+                CK(k_cg_step(La, Sq, c->d_x, c->d_r, c->d_p, c->d_ap, ld, c->d_pap, c->d_rz, c->d_rr, c->st));
             cg_total += La.nb;
             ++cgit;
         }
@@ -1256,6 +1302,7 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
                 a.c0 = c0;
                 a.nc = std::min(chunk, rows - c0);
                 a.X = c->d_x;
+                a.vec32 = v32;
                 a.out = c->d_grid;
                 CK(fused_col(mixed, true, a));
                 CK(fused_plane(mixed, 1, a));
@@ -1286,7 +1333,9 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
             }
         }
         // ---- response occupations
-        if ((s = project(c, Sq, Lall, phikq, c->d_x, c->d_Pbuf, mixed)) != HP_OK) return s;
+        if (v32) s = project(c, Sq, Lall, phikq, F32(c->d_x), c->d_Pbuf, mixed);
+        else s = project(c, Sq, Lall, phikq, c->d_x, c->d_Pbuf, mixed);
+        if (s != HP_OK) return s;
         CK(k_occ_response(c->d_Pbuf, c->d_aphi, nspin * nk, nocc, c->nhub, nk, nspin, c->d_M, c->st));
         {
             std::vector<int> off(c->hub_off), md(c->hub_mdim);

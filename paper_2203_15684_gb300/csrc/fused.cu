@@ -136,6 +136,46 @@ __device__ __forceinline__ double2 to64(V x) {
     else return x;
 }
 
+// band-vector element (FP64 or FP32 storage) to the compute type
+template <class V>
+__device__ __forceinline__ V from_vec(const double2& x) {
+    return from64<V>(x);
+}
+template <class V>
+__device__ __forceinline__ V from_vec(const float2& x) {
+    if constexpr (sizeof(V) == 8) return x;
+    else return cmk(f2d_bits(x.x), f2d_bits(x.y));
+}
+
+// Y[g] of the forward column transform: mode 0 adds the kinetic term (|k+G|^2/2 - shift) X[g], mode 1
+// scales.  FP64 storage forms the sum in FP64; FP32 storage (mixed form) in FP32.
+template <class V>
+__device__ __forceinline__ void fwd_store(double2* __restrict__ Y, const double2* __restrict__ X, long long g, V a,
+                                          int mode, double g2, float, double sh, float, double scale) {
+    const double2 v = to64<V>(a);
+    if (mode == 0) {
+        const double d = 0.5 * g2 - sh;
+        const double2 xv = X[g];
+        Y[g] = cmk(v.x + d * xv.x, v.y + d * xv.y);
+    } else {
+        Y[g] = cscale(v, scale);
+    }
+}
+template <class V>
+__device__ __forceinline__ void fwd_store(float2* __restrict__ Y, const float2* __restrict__ X, long long g, V a,
+                                          int mode, double, float kin, double, float sh32, double scale) {
+    const float2 v = sizeof(V) == 8 ? *reinterpret_cast<const float2*>(&a) : from64<float2>(*reinterpret_cast<const double2*>(&a));
+    if (mode == 0) {
+        const float d = kin - sh32;
+        const float2 xv = X[g];
+        Y[g] = cmkf(v.x + d * xv.x, v.y + d * xv.y);
+    } else {
+        Y[g] = cscale(v, (float)scale);
+    }
+}
+__device__ __forceinline__ void zero_el(double2& y) { y = cmk(0.0, 0.0); }
+__device__ __forceinline__ void zero_el(float2& y) { y = cmkf(0.f, 0.f); }
+
 // ------------------------------------------------------------------------------------------------
 // register-resident FFTs: one thread holds a whole line of N points in registers and runs the
 // Stockham stages with every index and twiddle position known at compile time; twiddles
@@ -232,9 +272,9 @@ static cudaError_t regfft_init() {
 // consecutive z (wrapping at N2), so every register index is a compile-time z.
 constexpr int kColRegThreads = 128;
 
-template <class V, int N2>
+template <class V, int N2, class VT>
 __global__ void __launch_bounds__(kColRegThreads) col_inv_reg_kernel(
-    const double2* __restrict__ X, int ld, const int* __restrict__ row, const int* __restrict__ kk, int c0,
+    const VT* __restrict__ X, int ld, const int* __restrict__ row, const int* __restrict__ kk, int c0,
     const int* __restrict__ ncol, const int* __restrict__ col_start, const int* __restrict__ col_len,
     const int* __restrict__ iz, int ncmax, V* __restrict__ colbuf) {
     const int c = blockIdx.y;
@@ -243,13 +283,13 @@ __global__ void __launch_bounds__(kColRegThreads) col_inv_reg_kernel(
     if (j >= ncol[k]) return;
     const int st = col_start[(long long)k * ncmax + j], len = col_len[(long long)k * ncmax + j];
     const int z0 = iz[(long long)k * ld + st];
-    const double2* x = X + (long long)row[c0 + c] * ld + st;
+    const VT* x = X + (long long)row[c0 + c] * ld + st;
     V a[N2];
 #pragma unroll
     for (int z = 0; z < N2; ++z) {
         int p = z - z0;
         if (p < 0) p += N2;
-        a[z] = p < len ? from64<V>(x[p]) : cpack<V>(0.0, 0.0);
+        a[z] = p < len ? from_vec<V>(x[p]) : cpack<V>(0.0, 0.0);
     }
     rfft<V, N2, +1>(a);
     V* dst = colbuf + (long long)c * N2 * ncmax + j;
@@ -257,18 +297,18 @@ __global__ void __launch_bounds__(kColRegThreads) col_inv_reg_kernel(
     for (int z = 0; z < N2; ++z) dst[(long long)z * ncmax] = a[z];
 }
 
-template <class V, int N2>
+template <class V, int N2, class VT>
 __global__ void __launch_bounds__(kColRegThreads) col_fwd_reg_kernel(
     const V* __restrict__ colbuf, int ncmax, const int* __restrict__ row, const int* __restrict__ kk, int c0,
     const int* __restrict__ npw, const int* __restrict__ ncol, const int* __restrict__ col_start,
     const int* __restrict__ col_len, const int* __restrict__ iz, const double* __restrict__ g2,
-    const double* __restrict__ shift, const double2* __restrict__ X, double2* __restrict__ Y, int ld, int mode,
-    double scale) {
+    const float* __restrict__ kin32, const double* __restrict__ shift, const VT* __restrict__ X,
+    VT* __restrict__ Y, int ld, int mode, double scale) {
     const int c = blockIdx.y;
     const int k = kk[c0 + c];
     const long long ro = (long long)row[c0 + c] * ld;
     if (blockIdx.x == 0)
-        for (int g = npw[k] + threadIdx.x; g < ld; g += kColRegThreads) Y[ro + g] = cmk(0.0, 0.0);
+        for (int g = npw[k] + threadIdx.x; g < ld; g += kColRegThreads) zero_el(Y[ro + g]);
     const int j = blockIdx.x * kColRegThreads + threadIdx.x;
     if (j >= ncol[k]) return;
     const int st = col_start[(long long)k * ncmax + j], len = col_len[(long long)k * ncmax + j];
@@ -279,22 +319,16 @@ __global__ void __launch_bounds__(kColRegThreads) col_fwd_reg_kernel(
     for (int z = 0; z < N2; ++z) a[z] = src[(long long)z * ncmax];
     rfft<V, N2, -1>(a);
     const double sh = mode == 0 ? shift[c0 + c] : 0.0;
+    const float sh32 = (float)sh;
+    const long long ko = (long long)k * ld + st;
 #pragma unroll
     for (int z = 0; z < N2; ++z) {
         int p = z - z0;
         if (p < 0) p += N2;
         if (p < len) {
-            const long long g = ro + st + p;
-            const double2 v = to64<V>(a[z]);
-            double2 y;
-            if (mode == 0) {
-                const double d = 0.5 * g2[(long long)k * ld + st + p] - sh;
-                const double2 xv = X[g];
-                y = cmk(v.x + d * xv.x, v.y + d * xv.y);
-            } else {
-                y = cscale(v, scale);
-            }
-            Y[g] = y;
+            const bool k32 = sizeof(VT) == 8;
+            fwd_store<V>(Y, X, ro + st + p, a[z], mode, (mode == 0 && !k32) ? g2[ko + p] : 0.0,
+                         (mode == 0 && k32) ? kin32[ko + p] : 0.f, sh, sh32, scale);
         }
     }
 }
@@ -478,8 +512,8 @@ __global__ void __launch_bounds__(PlaneCfg<V, N0, N1>::NT, PlaneCfg<V, N0, N1>::
 // ------------------------------------------------------------------------------------------------
 constexpr int kCT = 16, kCLD = kCT + 1, kColThreads = 128;
 
-template <class V, int N2>
-__global__ void __launch_bounds__(kColThreads) col_inv_kernel(const double2* __restrict__ X, int ld,
+template <class V, int N2, class VT>
+__global__ void __launch_bounds__(kColThreads) col_inv_kernel(const VT* __restrict__ X, int ld,
                                                               const int* __restrict__ row, const int* __restrict__ kk,
                                                               int c0, const int* __restrict__ ncol,
                                                               const int* __restrict__ col_start,
@@ -495,14 +529,14 @@ __global__ void __launch_bounds__(kColThreads) col_inv_kernel(const double2* __r
     if (cb >= nc) return;
     for (int e = threadIdx.x; e < N2 * kCLD; e += kColThreads) s0[e] = cpack<V>(0.0, 0.0);
     __syncthreads();
-    const double2* x = X + (long long)row[c0 + c] * ld;
+    const VT* x = X + (long long)row[c0 + c] * ld;
     for (int t = 0; t < kCT; ++t) {
         const int col = cb + t;
         if (col >= nc) break;
         const int st = col_start[(long long)k * ncmax + col], len = col_len[(long long)k * ncmax + col];
         for (int p = threadIdx.x; p < len; p += kColThreads) {
             const int g = st + p;
-            s0[iz[(long long)k * ld + g] * kCLD + t] = from64<V>(x[g]);
+            s0[iz[(long long)k * ld + g] * kCLD + t] = from_vec<V>(x[g]);
         }
     }
     __syncthreads();
@@ -518,7 +552,7 @@ __global__ void __launch_bounds__(kColThreads) col_inv_kernel(const double2* __r
 // col_fwd: column buffer -> forward z-FFT -> sphere.  mode 0: Y = col + (|k+G|^2/2 - shift) X;
 // mode 1: Y = scale * col.  Padding beyond npw is written as zero.
 // ------------------------------------------------------------------------------------------------
-template <class V, int N2>
+template <class V, int N2, class VT>
 __global__ void __launch_bounds__(kColThreads) col_fwd_kernel(const V* __restrict__ colbuf, int ncmax,
                                                               const int* __restrict__ row, const int* __restrict__ kk,
                                                               int c0, const int* __restrict__ npw,
@@ -526,8 +560,9 @@ __global__ void __launch_bounds__(kColThreads) col_fwd_kernel(const V* __restric
                                                               const int* __restrict__ col_start,
                                                               const int* __restrict__ col_len,
                                                               const int* __restrict__ iz, const double* __restrict__ g2,
+                                                              const float* __restrict__ kin32,
                                                               const double* __restrict__ shift,
-                                                              const double2* __restrict__ X, double2* __restrict__ Y,
+                                                              const VT* __restrict__ X, VT* __restrict__ Y,
                                                               int ld, int mode, double scale, const V* __restrict__ tw) {
     __shared__ V s0[N2 * kCLD];
     __shared__ V s1[N2 * kCLD];
@@ -537,7 +572,7 @@ __global__ void __launch_bounds__(kColThreads) col_fwd_kernel(const V* __restric
     const int cb = blockIdx.x * kCT;
     const long long ro = (long long)row[c0 + c] * ld;
     if (blockIdx.x == 0)
-        for (int g = npw[k] + threadIdx.x; g < ld; g += kColThreads) Y[ro + g] = cmk(0.0, 0.0);
+        for (int g = npw[k] + threadIdx.x; g < ld; g += kColThreads) zero_el(Y[ro + g]);
     if (cb >= nc) return;
     const V* src = colbuf + (long long)c * N2 * ncmax;
     for (int e = threadIdx.x; e < N2 * kCT; e += kColThreads) {
@@ -554,15 +589,9 @@ __global__ void __launch_bounds__(kColThreads) col_fwd_kernel(const V* __restric
         for (int p = threadIdx.x; p < len; p += kColThreads) {
             const int g = st + p;
             const V v = out[iz[(long long)k * ld + g] * kCLD + t];
-            double2 y;
-            if (mode == 0) {
-                const double d = 0.5 * g2[(long long)k * ld + g] - sh;
-                const double2 xv = X[ro + g];
-                y = cmk((double)v.x + d * xv.x, (double)v.y + d * xv.y);
-            } else {
-                y = cmk((double)v.x * scale, (double)v.y * scale);
-            }
-            Y[ro + g] = y;
+            const bool k32 = sizeof(VT) == 8;
+            fwd_store<V>(Y, X, ro + g, v, mode, (mode == 0 && !k32) ? g2[(long long)k * ld + g] : 0.0,
+                         (mode == 0 && k32) ? kin32[(long long)k * ld + g] : 0.f, sh, (float)sh, scale);
         }
     }
 }
@@ -660,6 +689,32 @@ const double2* tw_of<double2>(const FftAxis& a) { return a.d_tw; }
 template <>
 const float2* tw_of<float2>(const FftAxis& a) { return a.d_tw32; }
 
+template <class V, int N2, class VT>
+static void col_kernels(bool inv, bool reg, dim3 g, const FusedArgs& a) {
+    const SphereSet& S = *a.S;
+    const BandList& L = *a.L;
+    const VT* X = (const VT*)a.X;
+    VT* Y = (VT*)a.Y;
+    if (reg && inv) {
+        col_inv_reg_kernel<V, N2, VT><<<g, kColRegThreads, 0, a.st>>>(X, S.ld, L.d_row, L.d_k, a.c0, S.d_ncol,
+                                                                      S.d_col_start, S.d_col_len, S.d_iz, S.ncmax,
+                                                                      (V*)a.colA);
+    } else if (reg) {
+        col_fwd_reg_kernel<V, N2, VT><<<g, kColRegThreads, 0, a.st>>>(
+            (const V*)a.colB, S.ncmax, L.d_row, L.d_k, a.c0, S.d_npw, S.d_ncol, S.d_col_start, S.d_col_len, S.d_iz,
+            S.d_g2, S.d_kin32, L.d_shift, X, Y, S.ld, a.mode, a.scale);
+    } else if (inv) {
+        col_inv_kernel<V, N2, VT><<<g, kColThreads, 0, a.st>>>(X, S.ld, L.d_row, L.d_k, a.c0, S.d_ncol, S.d_col_start,
+                                                               S.d_col_len, S.d_iz, S.ncmax, (V*)a.colA,
+                                                               tw_of<V>(a.fft->ax[2]));
+    } else {
+        col_fwd_kernel<V, N2, VT><<<g, kColThreads, 0, a.st>>>((const V*)a.colB, S.ncmax, L.d_row, L.d_k, a.c0,
+                                                               S.d_npw, S.d_ncol, S.d_col_start, S.d_col_len, S.d_iz,
+                                                               S.d_g2, S.d_kin32, L.d_shift, X, Y, S.ld, a.mode,
+                                                               a.scale, tw_of<V>(a.fft->ax[2]));
+    }
+}
+
 template <class V, int N2>
 static cudaError_t col_launch(bool inv, const FusedArgs& a) {
     const SphereSet& S = *a.S;
@@ -669,27 +724,12 @@ static cudaError_t col_launch(bool inv, const FusedArgs& a) {
         cudaError_t e = regfft_init();
         if (e != cudaSuccess) return e;
     }
+    // FP32 band vectors only with FP32 transforms
+    if (a.vec32 && sizeof(V) != 8) return cudaErrorInvalidValue;
     dim3 g(cdivf(S.ncmax, reg ? kColRegThreads : kCT), a.nc);
     const ProfMark pm = prof_start(a.st);
-    if (reg && inv) {
-        col_inv_reg_kernel<V, N2><<<g, kColRegThreads, 0, a.st>>>(a.X, S.ld, L.d_row, L.d_k, a.c0, S.d_ncol,
-                                                                  S.d_col_start, S.d_col_len, S.d_iz, S.ncmax,
-                                                                  (V*)a.colA);
-    } else if (reg) {
-        col_fwd_reg_kernel<V, N2><<<g, kColRegThreads, 0, a.st>>>((const V*)a.colB, S.ncmax, L.d_row, L.d_k, a.c0,
-                                                                  S.d_npw, S.d_ncol, S.d_col_start, S.d_col_len,
-                                                                  S.d_iz, S.d_g2, L.d_shift, a.X, a.Y, S.ld, a.mode,
-                                                                  a.scale);
-    } else if (inv) {
-        col_inv_kernel<V, N2><<<g, kColThreads, 0, a.st>>>(a.X, S.ld, L.d_row, L.d_k, a.c0, S.d_ncol, S.d_col_start,
-                                                           S.d_col_len, S.d_iz, S.ncmax, (V*)a.colA,
-                                                           tw_of<V>(a.fft->ax[2]));
-    } else {
-        col_fwd_kernel<V, N2><<<g, kColThreads, 0, a.st>>>((const V*)a.colB, S.ncmax, L.d_row, L.d_k, a.c0, S.d_npw,
-                                                           S.d_ncol, S.d_col_start, S.d_col_len, S.d_iz, S.d_g2,
-                                                           L.d_shift, a.X, a.Y, S.ld, a.mode, a.scale,
-                                                           tw_of<V>(a.fft->ax[2]));
-    }
+    if (a.vec32) col_kernels<V, N2, float2>(inv, reg, g, a);
+    else col_kernels<V, N2, double2>(inv, reg, g, a);
     HP_LAUNCHED();
     if (prof_on() && L.k.size() >= (size_t)(a.c0 + a.nc) && !S.ncol.empty()) {
         // sphere coefficients (FP64) once, column buffer once; forward: input vector for the kinetic
@@ -698,8 +738,9 @@ static cudaError_t col_launch(bool inv, const FusedArgs& a) {
         for (int b = a.c0; b < a.c0 + a.nc; ++b) {
             const int k = L.k[b];
             const double col = (double)sizeof(V) * N2 * S.ncol[k];
-            bytes += col + 16.0 * S.npw[k];
-            if (!inv) bytes += 16.0 * (S.ld - S.npw[k]) + (a.mode == 0 ? 16.0 * S.npw[k] : 0.0);
+            const double vb = a.vec32 ? 8.0 : 16.0;  // band-vector element
+            bytes += col + vb * S.npw[k];
+            if (!inv) bytes += vb * (S.ld - S.npw[k]) + (a.mode == 0 ? vb * S.npw[k] : 0.0);
             flops += 5.0 * N2 * std::log2((double)N2) * S.ncol[k];
         }
         prof_stop(pm, HP_KF_COLUMN, a.st, flops, bytes, inv ? (reg ? "col_inv_reg" : "col_inv") : (reg ? "col_fwd_reg" : "col_fwd"));

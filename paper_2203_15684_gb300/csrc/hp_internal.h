@@ -124,6 +124,8 @@ struct SphereSet {          // device arrays, nk spheres of at most ld points
     int* d_idx = nullptr;   // [nk][ld] flat grid index of each coefficient
     double* d_g2 = nullptr; // [nk][ld] |k+G|^2
     double* d_prec = nullptr;  // [nk][ld] CG preconditioner 1 / (1 + |k+G|^2 / 2), 0 beyond npw
+    float* d_prec32 = nullptr; // the same in FP32
+    float* d_kin32 = nullptr;  // [nk][ld] |k+G|^2 / 2 in FP32
     std::vector<int> npw;   // host copy
     // column structure (the sphere is stored column by column, z fastest): for each k, ncol
     // columns (x, y) of the grid that hold sphere points, their first point and length, and the
@@ -184,8 +186,12 @@ cudaError_t k_mul_cpot(double2* grid, const double2* src_rows, const int* src_ro
                        const double2* v, const BandList& L, int c0, cudaStream_t st);
 cudaError_t k_proj(const BandList& L, const SphereSet& S, const ProjMat& A, const double2* X, int ld,
                    double2* P, double2* scratch, size_t scratch_elems, cudaStream_t st, bool fp32 = false);
+cudaError_t k_proj(const BandList& L, const SphereSet& S, const ProjMat& A, const float2* X, int ld,
+                   double2* P, double2* scratch, size_t scratch_elems, cudaStream_t st, bool fp32 = false);
 cudaError_t k_expand(const BandList& L, const SphereSet& S, const ProjMat& A, const double2* P,
                      const double* pscale, double alpha, double2* Y, int ld, cudaStream_t st, bool fp32 = false);
+cudaError_t k_expand(const BandList& L, const SphereSet& S, const ProjMat& A, const double2* P,
+                     const double* pscale, double alpha, float2* Y, int ld, cudaStream_t st, bool fp32 = false);
 // FP32 forms (mixed precision)
 cudaError_t k_scatter32(const SphereSet& S, const BandList& L, int c0, int nc, const double2* X, float2* grid, int nr,
                         cudaStream_t st);
@@ -203,9 +209,15 @@ cudaError_t k_to_f32(const double* a, float* b, long long n, cudaStream_t st);
 cudaError_t k_to_c32(const double2* a, float2* b, long long n, cudaStream_t st);
 cudaError_t k_band_dot(const BandList& L, const SphereSet& S, const double2* X, const double2* Y, int ld,
                        double* out, cudaStream_t st);
+cudaError_t k_band_dot(const BandList& L, const SphereSet& S, const float2* X, const float2* Y, int ld,
+                       double* out, cudaStream_t st);
 cudaError_t k_cg_init(const BandList& L, const SphereSet& S, const double2* r, double2* p, int ld,
                       double* rz, double* rr, cudaStream_t st);
+cudaError_t k_cg_init(const BandList& L, const SphereSet& S, const float2* r, float2* p, int ld,
+                      double* rz, double* rr, cudaStream_t st);
 cudaError_t k_cg_step(const BandList& L, const SphereSet& S, double2* x, double2* r, double2* p, const double2* ap,
+                      int ld, double* pap, double* rz, double* rr, cudaStream_t st);
+cudaError_t k_cg_step(const BandList& L, const SphereSet& S, float2* x, float2* r, float2* p, const float2* ap,
                       int ld, double* pap, double* rz, double* rr, cudaStream_t st);
 cudaError_t k_rows_axpby(const BandList& L, const SphereSet& S, double a, const double2* X, double b,
                          double2* Y, int ld, cudaStream_t st);
@@ -236,8 +248,11 @@ cudaError_t k_dn_traces(const double2* dn, int nh, int nspin, int mmax, double f
 cudaError_t k_vec_dot(const double2* a, const double2* b, long long n, double* out, double* partial,
                       cudaStream_t st);
 cudaError_t k_vec_axpy(double2* y, const double2* x, double a, long long n, cudaStream_t st);
+cudaError_t k_vec_axpy(float2* y, const float2* x, double a, long long n, cudaStream_t st);
 cudaError_t k_vec_sub(double2* out, const double2* a, const double2* b, long long n, cudaStream_t st);
+cudaError_t k_vec_sub(float2* out, const float2* a, const float2* b, long long n, cudaStream_t st);
 cudaError_t k_vec_scale_copy(double2* out, const double2* a, double s, long long n, cudaStream_t st);
+cudaError_t k_vec_scale_copy(float2* out, const float2* a, double s, long long n, cudaStream_t st);
 cudaError_t k_broyden_coef(const double* dots, int m, int ld, double w0, double* gamma, cudaStream_t st);
 cudaError_t k_broyden_apply(double2* x, const double2* f, const double2* const* dx, const double2* const* df,
                             const double* gamma, int m, double alpha, long long n, cudaStream_t st);
@@ -281,8 +296,9 @@ struct FusedArgs {
     const BandList* L = nullptr;
     const FftPlan* fft = nullptr;
     int c0 = 0, nc = 0, N0 = 0, N1 = 0, N2 = 0;
-    const double2* X = nullptr;
-    double2* Y = nullptr;
+    const void* X = nullptr;     // band vectors: double2, or float2 when vec32
+    void* Y = nullptr;
+    bool vec32 = false;
     int mode = 0;
     double scale = 1.0;
     void* colA = nullptr;        // column buffer written by col_inv, read by plane
@@ -326,6 +342,8 @@ int band_batch(const hp_ctx* c, int nb);
 hp_status apply_local(hp_ctx* c, const SphereSet& S, const BandList& L, const double2* X, double2* Y,
                       const double* veff, bool fp32 = false);
 hp_status project(hp_ctx* c, const SphereSet& S, const BandList& L, const ProjMat& A, const double2* X, double2* P,
+                  bool fp32 = false);
+hp_status project(hp_ctx* c, const SphereSet& S, const BandList& L, const ProjMat& A, const float2* X, double2* P,
                   bool fp32 = false);
 hp_status apply_nonlocal(hp_ctx* c, const SphereSet& S, const BandList& L, const double2* X, double2* Y, double2* P,
                          const int* kmap, bool fp32 = false);
@@ -391,6 +409,7 @@ struct hp_ctx {
     float2* d_dv32 = nullptr;          // mixed precision: FP32 copy of Delta V_Hxc
     // sphere-sparse fused transforms (when the grid sizes are supported)
     bool fused = false;
+    bool vec32 = false;                // response band vectors stored in FP32 (mixed form, fused path)
     bool fused_reg = true;             // fused transforms with register-resident line FFTs
     bool ur_planes = false;            // the real-space band cache is plane-major (built by the fused path)
     void* d_vt = nullptr;              // plane-major V_eff [nspin][z][y][x] (double or float)

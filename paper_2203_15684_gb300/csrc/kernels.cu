@@ -342,8 +342,8 @@ __device__ __forceinline__ double2 widen(const V& x) {
 // warp, sized to the largest segment of the list).  G tiles (32 points FP32, 16 FP64) go through
 // shared memory with the next tile's global loads issued before the current tile is used; each
 // tile is summed in the compute precision, eight tiles in the compute precision, then FP64.
-template <class S, class AT, int NPT, int NBI>
-__global__ void __launch_bounds__(256) proj_kernel(ProjDev d, int ld, const double2* __restrict__ X,
+template <class S, class AT, class XT, int NPT, int NBI>
+__global__ void __launch_bounds__(256) proj_kernel(ProjDev d, int ld, const XT* __restrict__ X,
                                                    const int* __restrict__ row, const int* __restrict__ seg_start,
                                                    const int* __restrict__ seg_k, const int* __restrict__ seg_s,
                                                    const int* __restrict__ npw_of_k, int ksplit,
@@ -383,7 +383,7 @@ __global__ void __launch_bounds__(256) proj_kernel(ProjDev d, int ld, const doub
         arow[j] = p < nrow ? proj_row<AT>(d, sp, mk, p, ld) : nullptr;
     }
     for (int ct = cbeg; ct < cend; ct += TCB) {
-        const double2* xrow[XE];
+        const XT* xrow[XE];
 #pragma unroll
         for (int j = 0; j < XE; ++j) {
             const int cc = lr + j * RS;
@@ -494,27 +494,27 @@ static ProjDev proj_dev(const ProjMat& A, bool use32) {
     return d;
 }
 
-template <class S, class AT, int NBI>
-static void proj_launch_b(int npt, dim3 g, cudaStream_t st, const ProjDev& d, int ld, const double2* X,
+template <class S, class AT, class XT, int NBI>
+static void proj_launch_b(int npt, dim3 g, cudaStream_t st, const ProjDev& d, int ld, const XT* X,
                           const BandList& L, const SphereSet& Sp, int ksplit, double2* scratch) {
     if (npt == 1)
-        proj_kernel<S, AT, 1, NBI><<<g, 256, 0, st>>>(d, ld, X, L.d_row, L.d_seg_start, L.d_seg_k, L.d_seg_s,
+        proj_kernel<S, AT, XT, 1, NBI><<<g, 256, 0, st>>>(d, ld, X, L.d_row, L.d_seg_start, L.d_seg_k, L.d_seg_s,
                                                       Sp.d_npw, ksplit, scratch, L.nb);
     else if (npt == 2)
-        proj_kernel<S, AT, 2, NBI><<<g, 256, 0, st>>>(d, ld, X, L.d_row, L.d_seg_start, L.d_seg_k, L.d_seg_s,
+        proj_kernel<S, AT, XT, 2, NBI><<<g, 256, 0, st>>>(d, ld, X, L.d_row, L.d_seg_start, L.d_seg_k, L.d_seg_s,
                                                       Sp.d_npw, ksplit, scratch, L.nb);
     else
-        proj_kernel<S, AT, 4, NBI><<<g, 256, 0, st>>>(d, ld, X, L.d_row, L.d_seg_start, L.d_seg_k, L.d_seg_s,
+        proj_kernel<S, AT, XT, 4, NBI><<<g, 256, 0, st>>>(d, ld, X, L.d_row, L.d_seg_start, L.d_seg_k, L.d_seg_s,
                                                       Sp.d_npw, ksplit, scratch, L.nb);
 }
 
-template <class S, class AT>
-static void proj_launch(int npt, int nbi, dim3 g, cudaStream_t st, const ProjDev& d, int ld, const double2* X,
+template <class S, class AT, class XT>
+static void proj_launch(int npt, int nbi, dim3 g, cudaStream_t st, const ProjDev& d, int ld, const XT* X,
                         const BandList& L, const SphereSet& Sp, int ksplit, double2* scratch) {
-    if (nbi == 1) proj_launch_b<S, AT, 1>(npt, g, st, d, ld, X, L, Sp, ksplit, scratch);
-    else if (nbi == 2) proj_launch_b<S, AT, 2>(npt, g, st, d, ld, X, L, Sp, ksplit, scratch);
-    else if (nbi == 3) proj_launch_b<S, AT, 3>(npt, g, st, d, ld, X, L, Sp, ksplit, scratch);
-    else proj_launch_b<S, AT, 4>(npt, g, st, d, ld, X, L, Sp, ksplit, scratch);
+    if (nbi == 1) proj_launch_b<S, AT, XT, 1>(npt, g, st, d, ld, X, L, Sp, ksplit, scratch);
+    else if (nbi == 2) proj_launch_b<S, AT, XT, 2>(npt, g, st, d, ld, X, L, Sp, ksplit, scratch);
+    else if (nbi == 3) proj_launch_b<S, AT, XT, 3>(npt, g, st, d, ld, X, L, Sp, ksplit, scratch);
+    else proj_launch_b<S, AT, XT, 4>(npt, g, st, d, ld, X, L, Sp, ksplit, scratch);
 }
 
 // largest number of list items in one (k, spin) segment
@@ -524,8 +524,9 @@ static int max_seg(const BandList& L) {
     return L.seg_start.size() < 2 ? L.nb : m;
 }
 
-cudaError_t k_proj(const BandList& L, const SphereSet& S, const ProjMat& A, const double2* X, int ld, double2* P,
-                   double2* scratch, size_t scratch_elems, cudaStream_t st, bool fp32) {
+template <class XT>
+static cudaError_t proj_t(const BandList& L, const SphereSet& S, const ProjMat& A, const XT* X, int ld, double2* P,
+                         double2* scratch, size_t scratch_elems, cudaStream_t st, bool fp32) {
     const int nrow = A.nrow + (A.base2 ? A.nrow2 : 0);
     if (L.nb <= 0 || nrow <= 0) return cudaSuccess;
     if (nrow > kPStride) return cudaErrorInvalidValue;
@@ -542,11 +543,11 @@ cudaError_t k_proj(const BandList& L, const SphereSet& S, const ProjMat& A, cons
     const ProjDev d = proj_dev(A, use32);
     const ProfMark pm = prof_start(st);
     if (!fp32)
-        proj_launch<double, double2>(npt, nbi, g, st, d, ld, X, L, S, ksplit, scratch);
+        proj_launch<double, double2, XT>(npt, nbi, g, st, d, ld, X, L, S, ksplit, scratch);
     else if (use32)
-        proj_launch<float, float2>(npt, nbi, g, st, d, ld, X, L, S, ksplit, scratch);
+        proj_launch<float, float2, XT>(npt, nbi, g, st, d, ld, X, L, S, ksplit, scratch);
     else
-        proj_launch<float, double2>(npt, nbi, g, st, d, ld, X, L, S, ksplit, scratch);
+        proj_launch<float, double2, XT>(npt, nbi, g, st, d, ld, X, L, S, ksplit, scratch);
     HP_LAUNCHED();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -558,7 +559,7 @@ cudaError_t k_proj(const BandList& L, const SphereSet& S, const ProjMat& A, cons
         const double ab = use32 ? 8.0 : 16.0;
         double bytes = 2.0 * 16.0 * ksplit * L.nb * nrow + 16.0 * L.nb * nrow, flops = 0.0;
         for (int b = 0; b < L.nb; ++b) {
-            bytes += 16.0 * S.npw[L.k[b]];
+            bytes += (double)sizeof(XT) * S.npw[L.k[b]];
             flops += 8.0 * nrow * S.npw[L.k[b]];
         }
         for (int sg = 0; sg < L.nseg; ++sg) bytes += ab * nrow * S.npw[L.seg_k[sg]];
@@ -567,11 +568,27 @@ cudaError_t k_proj(const BandList& L, const SphereSet& S, const ProjMat& A, cons
     return cudaGetLastError();
 }
 
+cudaError_t k_proj(const BandList& L, const SphereSet& S, const ProjMat& A, const double2* X, int ld, double2* P,
+                   double2* scratch, size_t scratch_elems, cudaStream_t st, bool fp32) {
+    return proj_t<double2>(L, S, A, X, ld, P, scratch, scratch_elems, st, fp32);
+}
+
+cudaError_t k_proj(const BandList& L, const SphereSet& S, const ProjMat& A, const float2* X, int ld, double2* P,
+                   double2* scratch, size_t scratch_elems, cudaStream_t st, bool fp32) {
+    return proj_t<float2>(L, S, A, X, ld, P, scratch, scratch_elems, st, fp32);
+}
+
+// y += a for a band-vector element of either storage type
+__device__ __forceinline__ void acc_into(double2& y, const double2& a) { y = cadd(y, a); }
+__device__ __forceinline__ void acc_into(double2& y, const float2& a) { y = cadd(y, widen<float2>(a)); }
+__device__ __forceinline__ void acc_into(float2& y, const float2& a) { y = cadd(y, a); }
+__device__ __forceinline__ void acc_into(float2& y, const double2& a) { y = cadd(y, cmkf(d2f_bits(a.x), d2f_bits(a.y))); }
+
 // bands per pass kExpC (4 to 24), sized to the largest segment of the list
-template <class S, class AT, int kExpC>
+template <class S, class AT, class YT, int kExpC>
 __global__ void __launch_bounds__(128) expand_kernel(ProjDev d, int ld, const double2* __restrict__ P,
                                                      const double* __restrict__ pscale, double alpha, double scale2,
-                                                     double2* __restrict__ Y, const int* __restrict__ row,
+                                                     YT* __restrict__ Y, const int* __restrict__ row,
                                                      const int* __restrict__ seg_start, const int* __restrict__ seg_k,
                                                      const int* __restrict__ seg_s, const int* __restrict__ npw_of_k) {
     using V = typename std::conditional<std::is_same<S, float>::value, float2, double2>::type;
@@ -613,7 +630,7 @@ __global__ void __launch_bounds__(128) expand_kernel(ProjDev d, int ld, const do
                 const int c = ct + i;
                 if (c < cend) {
                     const long long o = (long long)row[c] * ld + G;
-                    Y[o] = cadd(Y[o], widen<V>(acc[i]));
+                    acc_into(Y[o], acc[i]);
                 }
             }
         }
@@ -621,23 +638,24 @@ __global__ void __launch_bounds__(128) expand_kernel(ProjDev d, int ld, const do
     }
 }
 
-template <int KC>
+template <int KC, class YT>
 static void expand_launch(bool fp32, bool use32, dim3 g, cudaStream_t st, const ProjDev& d, int ld, const double2* P,
-                          const double* pscale, double alpha, double scale2, double2* Y, const BandList& L,
+                          const double* pscale, double alpha, double scale2, YT* Y, const BandList& L,
                           const SphereSet& S) {
     if (!fp32)
-        expand_kernel<double, double2, KC><<<g, 128, 0, st>>>(d, ld, P, pscale, alpha, scale2, Y, L.d_row,
-                                                              L.d_seg_start, L.d_seg_k, L.d_seg_s, S.d_npw);
+        expand_kernel<double, double2, YT, KC><<<g, 128, 0, st>>>(d, ld, P, pscale, alpha, scale2, Y, L.d_row,
+                                                                  L.d_seg_start, L.d_seg_k, L.d_seg_s, S.d_npw);
     else if (use32)
-        expand_kernel<float, float2, KC><<<g, 128, 0, st>>>(d, ld, P, pscale, alpha, scale2, Y, L.d_row,
-                                                            L.d_seg_start, L.d_seg_k, L.d_seg_s, S.d_npw);
+        expand_kernel<float, float2, YT, KC><<<g, 128, 0, st>>>(d, ld, P, pscale, alpha, scale2, Y, L.d_row,
+                                                                L.d_seg_start, L.d_seg_k, L.d_seg_s, S.d_npw);
     else
-        expand_kernel<float, double2, KC><<<g, 128, 0, st>>>(d, ld, P, pscale, alpha, scale2, Y, L.d_row,
-                                                             L.d_seg_start, L.d_seg_k, L.d_seg_s, S.d_npw);
+        expand_kernel<float, double2, YT, KC><<<g, 128, 0, st>>>(d, ld, P, pscale, alpha, scale2, Y, L.d_row,
+                                                                 L.d_seg_start, L.d_seg_k, L.d_seg_s, S.d_npw);
 }
 
-cudaError_t k_expand(const BandList& L, const SphereSet& S, const ProjMat& A, const double2* P, const double* pscale,
-                     double alpha, double2* Y, int ld, cudaStream_t st, bool fp32) {
+template <class YT>
+static cudaError_t expand_t(const BandList& L, const SphereSet& S, const ProjMat& A, const double2* P,
+                           const double* pscale, double alpha, YT* Y, int ld, cudaStream_t st, bool fp32) {
     const int nrow = A.nrow + (A.base2 ? A.nrow2 : 0);
     if (L.nb <= 0 || nrow <= 0) return cudaSuccess;
     if (nrow > kPStride) return cudaErrorInvalidValue;
@@ -658,7 +676,7 @@ cudaError_t k_expand(const BandList& L, const SphereSet& S, const ProjMat& A, co
         const double ab = use32 ? 8.0 : 16.0;
         double bytes = 16.0 * L.nb * nrow, flops = 0.0;
         for (int b = 0; b < L.nb; ++b) {
-            bytes += 2.0 * 16.0 * S.npw[L.k[b]];
+            bytes += 2.0 * (double)sizeof(YT) * S.npw[L.k[b]];
             flops += 8.0 * nrow * S.npw[L.k[b]];
         }
         for (int sg = 0; sg < L.nseg; ++sg) bytes += ab * nrow * S.npw[L.seg_k[sg]];
@@ -667,63 +685,102 @@ cudaError_t k_expand(const BandList& L, const SphereSet& S, const ProjMat& A, co
     return cudaGetLastError();
 }
 
+cudaError_t k_expand(const BandList& L, const SphereSet& S, const ProjMat& A, const double2* P, const double* pscale,
+                     double alpha, double2* Y, int ld, cudaStream_t st, bool fp32) {
+    return expand_t<double2>(L, S, A, P, pscale, alpha, Y, ld, st, fp32);
+}
+
+cudaError_t k_expand(const BandList& L, const SphereSet& S, const ProjMat& A, const double2* P, const double* pscale,
+                     double alpha, float2* Y, int ld, cudaStream_t st, bool fp32) {
+    return expand_t<float2>(L, S, A, P, pscale, alpha, Y, ld, st, fp32);
+}
+
 // ------------------------------------------------------------------------------------------------
 // per-band reductions and CG updates (one CTA per list item, fixed reduction order)
 // preconditioner M^-1 = 1 / (1 + |k+G|^2 / 2)
 // ------------------------------------------------------------------------------------------------
+// Band vectors are FP64 (double2) or, in the mixed form with the fused transforms, FP32 (float2).
+// With FP32 vectors the per-thread partial sums are FP32 (a few terms each) and the block sums FP64.
+template <class VT>
+__device__ __forceinline__ typename Scalar<VT>::type prec_at(const double* p64, const float* p32, long long i);
+template <>
+__device__ __forceinline__ double prec_at<double2>(const double* p64, const float*, long long i) { return p64[i]; }
+template <>
+__device__ __forceinline__ float prec_at<float2>(const double*, const float* p32, long long i) { return p32[i]; }
+
+template <class VT>
 __global__ void band_dot_kernel(const int* __restrict__ row, const int* __restrict__ kk, const int* __restrict__ npw,
-                               const double2* __restrict__ X, const double2* __restrict__ Y, int ld,
-                               double* __restrict__ out) {
+                                const VT* __restrict__ X, const VT* __restrict__ Y, int ld, double* __restrict__ out) {
+    using T = typename Scalar<VT>::type;
     __shared__ double sh[32];
     const int c = blockIdx.x;
     const int n = npw[kk[c]];
     const long long o = (long long)row[c] * ld;
-    double s = 0.0;
+    T s = 0;
     for (int G = threadIdx.x; G < n; G += blockDim.x) {
-        const double2 a = X[o + G], b = Y[o + G];
+        const VT a = X[o + G], b = Y[o + G];
         s += a.x * b.x + a.y * b.y;
     }
-    s = block_sum(s, sh);
-    if (threadIdx.x == 0) out[row[c]] = s;
+    const double t = block_sum((double)s, sh);
+    if (threadIdx.x == 0) out[row[c]] = t;
 }
 
 cudaError_t k_band_dot(const BandList& L, const SphereSet& S, const double2* X, const double2* Y, int ld, double* out,
                        cudaStream_t st) {
     if (L.nb <= 0) return cudaSuccess;
-    band_dot_kernel<<<L.nb, 256, 0, st>>>(L.d_row, L.d_k, S.d_npw, X, Y, ld, out);
+    band_dot_kernel<double2><<<L.nb, 256, 0, st>>>(L.d_row, L.d_k, S.d_npw, X, Y, ld, out);
     HP_LAUNCHED();
     return cudaGetLastError();
 }
 
-// p = M r; rz = <r, M r>; rr = <r, r>
+cudaError_t k_band_dot(const BandList& L, const SphereSet& S, const float2* X, const float2* Y, int ld, double* out,
+                       cudaStream_t st) {
+    if (L.nb <= 0) return cudaSuccess;
+    band_dot_kernel<float2><<<L.nb, 256, 0, st>>>(L.d_row, L.d_k, S.d_npw, X, Y, ld, out);
+    HP_LAUNCHED();
+    return cudaGetLastError();
+}
+
+// p = M r; rz = <r, M r>; rr = <r, r>   (M^-1 = 1 + |k+G|^2 / 2, precomputed per point)
+template <class VT>
 __global__ void cg_init_kernel(const int* __restrict__ row, const int* __restrict__ kk, const int* __restrict__ npw,
-                               const double* __restrict__ prec, const double2* __restrict__ r, double2* __restrict__ p,
-                               int ld, double* __restrict__ rz, double* __restrict__ rr) {
+                               const double* __restrict__ prec, const float* __restrict__ prec32,
+                               const VT* __restrict__ r, VT* __restrict__ p, int ld, double* __restrict__ rz,
+                               double* __restrict__ rr) {
+    using T = typename Scalar<VT>::type;
     __shared__ double sh[32];
     const int c = blockIdx.x, k = kk[c];
     const int n = npw[k];
     const long long o = (long long)row[c] * ld;
-    double s1 = 0.0, s2 = 0.0;
+    T s1 = 0, s2 = 0;
     for (int G = threadIdx.x; G < n; G += blockDim.x) {
-        const double m = prec[(long long)k * ld + G];
-        const double2 x = r[o + G];
-        const double q = x.x * x.x + x.y * x.y;
+        const T m = prec_at<VT>(prec, prec32, (long long)k * ld + G);
+        const VT x = r[o + G];
+        const T q = x.x * x.x + x.y * x.y;
         p[o + G] = cscale(x, m);
         s1 += m * q;
         s2 += q;
     }
-    s1 = block_sum(s1, sh);
-    s2 = block_sum(s2, sh);
+    const double t1 = block_sum((double)s1, sh);
+    const double t2 = block_sum((double)s2, sh);
     if (threadIdx.x == 0) {
-        rz[row[c]] = s1;
-        rr[row[c]] = s2;
+        rz[row[c]] = t1;
+        rr[row[c]] = t2;
     }
 }
 
 cudaError_t k_cg_init(const BandList& L, const SphereSet& S, const double2* r, double2* p, int ld, double* rz,
                       double* rr, cudaStream_t st) {
     if (L.nb <= 0) return cudaSuccess;
-    cg_init_kernel<<<L.nb, 256, 0, st>>>(L.d_row, L.d_k, S.d_npw, S.d_prec, r, p, ld, rz, rr);
+    cg_init_kernel<double2><<<L.nb, 256, 0, st>>>(L.d_row, L.d_k, S.d_npw, S.d_prec, S.d_prec32, r, p, ld, rz, rr);
+    HP_LAUNCHED();
+    return cudaGetLastError();
+}
+
+cudaError_t k_cg_init(const BandList& L, const SphereSet& S, const float2* r, float2* p, int ld, double* rz,
+                      double* rr, cudaStream_t st) {
+    if (L.nb <= 0) return cudaSuccess;
+    cg_init_kernel<float2><<<L.nb, 256, 0, st>>>(L.d_row, L.d_k, S.d_npw, S.d_prec, S.d_prec32, r, p, ld, rz, rr);
     HP_LAUNCHED();
     return cudaGetLastError();
 }
@@ -731,24 +788,25 @@ cudaError_t k_cg_init(const BandList& L, const SphereSet& S, const double2* r, d
 // One CG step per band, fused: pAp = <p, Ap>; a = rz / pAp; x += a p; r -= a Ap;
 // rz' = <r, M r>, rr = <r, r>; p = M r + (rz' / rz) p.  One CTA per band; with E > 0 the band's p
 // and Ap (then r) stay in registers (E elements per thread, npw <= 256 E), with E = 0 they are
-// read again.  Reductions in a fixed order.
-template <int E>
+// read again.  Reductions in a fixed order; step lengths in FP64.
+template <class VT, int E>
 __global__ void __launch_bounds__(256) cg_step_kernel(const int* __restrict__ row, const int* __restrict__ kk,
                                                       const int* __restrict__ npw, const double* __restrict__ prec,
-                                                      double2* __restrict__ x, double2* __restrict__ r,
-                                                      double2* __restrict__ p, const double2* __restrict__ ap, int ld,
-                                                      double* __restrict__ pap, double* __restrict__ rz,
-                                                      double* __restrict__ rr) {
+                                                      const float* __restrict__ prec32, VT* __restrict__ x,
+                                                      VT* __restrict__ r, VT* __restrict__ p,
+                                                      const VT* __restrict__ ap, int ld, double* __restrict__ pap,
+                                                      double* __restrict__ rz, double* __restrict__ rr) {
+    using T = typename Scalar<VT>::type;
     __shared__ double sh[33];
     const int c = blockIdx.x, k = kk[c];
     const int b = row[c];
     const int n = npw[k];
     const long long o = (long long)b * ld;
-    const double* m = prec + (long long)k * ld;
+    const long long mo = (long long)k * ld;
     const double rz0 = rz[b];
     constexpr int EC = E > 0 ? E : 1;
-    double2 pv[EC], av[EC];
-    double s = 0.0;
+    VT pv[EC], av[EC];
+    T s = 0;
     if (E > 0) {
 #pragma unroll
         for (int e = 0; e < EC; ++e) {
@@ -761,23 +819,23 @@ __global__ void __launch_bounds__(256) cg_step_kernel(const int* __restrict__ ro
         }
     } else {
         for (int G = threadIdx.x; G < n; G += 256) {
-            const double2 a = p[o + G], q = ap[o + G];
+            const VT a = p[o + G], q = ap[o + G];
             s += a.x * q.x + a.y * q.y;
         }
     }
-    const double pAp = block_allsum(s, sh);
-    const double alpha = rz0 / pAp;
-    double s1 = 0.0, s2 = 0.0;
-    auto upd = [&](int G, const double2& pg, const double2& ag) {
-        double2 xv = x[o + G], rv = r[o + G];
+    const double pAp = block_allsum((double)s, sh);
+    const T alpha = (T)(rz0 / pAp);
+    T s1 = 0, s2 = 0;
+    auto upd = [&](int G, const VT& pg, const VT& ag) {
+        VT xv = x[o + G], rv = r[o + G];
         xv.x += alpha * pg.x;
         xv.y += alpha * pg.y;
         rv.x -= alpha * ag.x;
         rv.y -= alpha * ag.y;
         x[o + G] = xv;
         r[o + G] = rv;
-        const double q = rv.x * rv.x + rv.y * rv.y;
-        s1 += m[G] * q;
+        const T q = rv.x * rv.x + rv.y * rv.y;
+        s1 += prec_at<VT>(prec, prec32, mo + G) * q;
         s2 += q;
         return rv;
     };
@@ -790,47 +848,67 @@ __global__ void __launch_bounds__(256) cg_step_kernel(const int* __restrict__ ro
     } else {
         for (int G = threadIdx.x; G < n; G += 256) upd(G, p[o + G], ap[o + G]);
     }
-    s1 = block_allsum(s1, sh);
-    s2 = block_allsum(s2, sh);
-    const double beta = s1 / rz0;
+    const double t1 = block_allsum((double)s1, sh);
+    const double t2 = block_allsum((double)s2, sh);
+    const T beta = (T)(t1 / rz0);
     if (E > 0) {
 #pragma unroll
         for (int e = 0; e < EC; ++e) {
             const int G = threadIdx.x + 256 * e;
             if (G < n) {
-                const double mm = m[G];
-                p[o + G] = cmk(mm * av[e].x + beta * pv[e].x, mm * av[e].y + beta * pv[e].y);
+                const T mm = prec_at<VT>(prec, prec32, mo + G);
+                VT q;
+                q.x = mm * av[e].x + beta * pv[e].x;
+                q.y = mm * av[e].y + beta * pv[e].y;
+                p[o + G] = q;
             }
         }
     } else {
         for (int G = threadIdx.x; G < n; G += 256) {
-            const double mm = m[G];
-            const double2 rv = r[o + G], q = p[o + G];
-            p[o + G] = cmk(mm * rv.x + beta * q.x, mm * rv.y + beta * q.y);
+            const T mm = prec_at<VT>(prec, prec32, mo + G);
+            const VT rv = r[o + G], q0 = p[o + G];
+            VT q;
+            q.x = mm * rv.x + beta * q0.x;
+            q.y = mm * rv.y + beta * q0.y;
+            p[o + G] = q;
         }
     }
     if (threadIdx.x == 0) {
         pap[b] = pAp;
-        rz[b] = s1;
-        rr[b] = s2;
+        rz[b] = t1;
+        rr[b] = t2;
     }
 }
 
-cudaError_t k_cg_step(const BandList& L, const SphereSet& S, double2* x, double2* r, double2* p, const double2* ap,
-                      int ld, double* pap, double* rz, double* rr, cudaStream_t st) {
+template <class VT>
+static cudaError_t cg_step_launch(const BandList& L, const SphereSet& S, VT* x, VT* r, VT* p, const VT* ap, int ld,
+                                  double* pap, double* rz, double* rr, cudaStream_t st) {
     if (L.nb <= 0) return cudaSuccess;
     int nmax = 0;
     for (int v : S.npw) nmax = std::max(nmax, v);
     const int e = (nmax + 255) / 256;
-#define HP_CGS(EE) cg_step_kernel<EE><<<L.nb, 256, 0, st>>>(L.d_row, L.d_k, S.d_npw, S.d_prec, x, r, p, ap, ld, pap, rz, rr)
+#define HP_CGS(EE)                                                                                                  \
+    cg_step_kernel<VT, EE><<<L.nb, 256, 0, st>>>(L.d_row, L.d_k, S.d_npw, S.d_prec, S.d_prec32, x, r, p, ap, ld, pap, \
+                                                 rz, rr)
     if (e <= 3) HP_CGS(3);
     else if (e <= 6) HP_CGS(6);
     else if (e <= 9) HP_CGS(9);
     else if (e <= 12) HP_CGS(12);
+    else if (sizeof(VT) == 8 && e <= 18) HP_CGS(18);
     else HP_CGS(0);
 #undef HP_CGS
     HP_LAUNCHED();
     return cudaGetLastError();
+}
+
+cudaError_t k_cg_step(const BandList& L, const SphereSet& S, double2* x, double2* r, double2* p, const double2* ap,
+                      int ld, double* pap, double* rz, double* rr, cudaStream_t st) {
+    return cg_step_launch<double2>(L, S, x, r, p, ap, ld, pap, rz, rr, st);
+}
+
+cudaError_t k_cg_step(const BandList& L, const SphereSet& S, float2* x, float2* r, float2* p, const float2* ap, int ld,
+                      double* pap, double* rz, double* rr, cudaStream_t st) {
+    return cg_step_launch<float2>(L, S, x, r, p, ap, ld, pap, rz, rr, st);
 }
 
 // Y = a X + b Y on the rows of the list (full padded rows)
@@ -1398,36 +1476,61 @@ cudaError_t k_sum_reduce(const double* partial, int nparts, double* out, cudaStr
     return cudaGetLastError();
 }
 
-__global__ void vec_axpy_kernel(double2* __restrict__ y, const double2* __restrict__ x, double a, long long n) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        y[i] = cmk(y[i].x + a * x[i].x, y[i].y + a * x[i].y);
+template <class VT>
+__global__ void vec_axpy_kernel(VT* __restrict__ y, const VT* __restrict__ x, typename Scalar<VT>::type a, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        VT v = y[i];
+        v.x += a * x[i].x;
+        v.y += a * x[i].y;
+        y[i] = v;
+    }
 }
 
-cudaError_t k_vec_axpy(double2* y, const double2* x, double a, long long n, cudaStream_t st) {
-    vec_axpy_kernel<<<std::min(cdiv(n, 256), 4096), 256, 0, st>>>(y, x, a, n);
-    HP_LAUNCHED();
-    return cudaGetLastError();
-}
-
-__global__ void vec_sub_kernel(double2* __restrict__ out, const double2* __restrict__ a, const double2* __restrict__ b,
-                               long long n) {
+template <class VT>
+__global__ void vec_sub_kernel(VT* __restrict__ out, const VT* __restrict__ a, const VT* __restrict__ b, long long n) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         out[i] = csub(a[i], b[i]);
 }
 
-cudaError_t k_vec_sub(double2* out, const double2* a, const double2* b, long long n, cudaStream_t st) {
-    vec_sub_kernel<<<std::min(cdiv(n, 256), 4096), 256, 0, st>>>(out, a, b, n);
-    HP_LAUNCHED();
-    return cudaGetLastError();
-}
-
-__global__ void vec_scale_copy_kernel(double2* __restrict__ out, const double2* __restrict__ a, double s, long long n) {
+template <class VT>
+__global__ void vec_scale_copy_kernel(VT* __restrict__ out, const VT* __restrict__ a, typename Scalar<VT>::type s,
+                                      long long n) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         out[i] = cscale(a[i], s);
 }
 
+cudaError_t k_vec_axpy(double2* y, const double2* x, double a, long long n, cudaStream_t st) {
+    vec_axpy_kernel<double2><<<std::min(cdiv(n, 256), 4096), 256, 0, st>>>(y, x, a, n);
+    HP_LAUNCHED();
+    return cudaGetLastError();
+}
+
+cudaError_t k_vec_axpy(float2* y, const float2* x, double a, long long n, cudaStream_t st) {
+    vec_axpy_kernel<float2><<<std::min(cdiv(n, 256), 4096), 256, 0, st>>>(y, x, (float)a, n);
+    HP_LAUNCHED();
+    return cudaGetLastError();
+}
+
+cudaError_t k_vec_sub(double2* out, const double2* a, const double2* b, long long n, cudaStream_t st) {
+    vec_sub_kernel<double2><<<std::min(cdiv(n, 256), 4096), 256, 0, st>>>(out, a, b, n);
+    HP_LAUNCHED();
+    return cudaGetLastError();
+}
+
+cudaError_t k_vec_sub(float2* out, const float2* a, const float2* b, long long n, cudaStream_t st) {
+    vec_sub_kernel<float2><<<std::min(cdiv(n, 256), 4096), 256, 0, st>>>(out, a, b, n);
+    HP_LAUNCHED();
+    return cudaGetLastError();
+}
+
 cudaError_t k_vec_scale_copy(double2* out, const double2* a, double s, long long n, cudaStream_t st) {
-    vec_scale_copy_kernel<<<std::min(cdiv(n, 256), 4096), 256, 0, st>>>(out, a, s, n);
+    vec_scale_copy_kernel<double2><<<std::min(cdiv(n, 256), 4096), 256, 0, st>>>(out, a, s, n);
+    HP_LAUNCHED();
+    return cudaGetLastError();
+}
+
+cudaError_t k_vec_scale_copy(float2* out, const float2* a, double s, long long n, cudaStream_t st) {
+    vec_scale_copy_kernel<float2><<<std::min(cdiv(n, 256), 4096), 256, 0, st>>>(out, a, (float)s, n);
     HP_LAUNCHED();
     return cudaGetLastError();
 }
