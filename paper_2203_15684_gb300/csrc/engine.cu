@@ -475,9 +475,6 @@ static hp_status setup_impl(hp_ctx* c, const double cell[9], int nspecies, const
         return fail(c, HP_EINVAL, "hp_setup: missing or non-positive argument");
     for (int i = 0; i < 3; ++i) {
         if (kmesh[i] < 1 || qmesh[i] < 1) return fail(c, HP_EINVAL, "hp_setup: mesh sizes must be >= 1");
-        if (kmesh[i] % qmesh[i] != 0)
-            return fail(c, HP_ENOTIMPL, "hp_setup: the q mesh must divide the k mesh (k+q off the k mesh needs a "
-                                        "non-self-consistent k+q calculation, not available)");
     }
     if (c->opt.nmix < 0 || c->opt.nmix > 8 || !(c->opt.cg_tol > 0) || c->opt.niter_max < 1 || c->opt.cg_maxiter < 1)
         return fail(c, HP_EINVAL, "hp_setup: options out of range (0 <= nmix <= 8, tolerances > 0)");
@@ -536,6 +533,23 @@ static hp_status setup_impl(hp_ctx* c, const double cell[9], int nspecies, const
                 build_sphere(c, kf, c->ks[ik]);
                 c->ld = std::max(c->ld, c->ks[ik].npw);
             }
+    // spheres at k+q where k+q is off the k mesh (Gamma-centred meshes: (k+q)_d kmesh_d is an
+    // integer for every d exactly when k+q is on the mesh)
+    c->kq_ks.assign((size_t)c->nq * c->nk, KSphere());
+    c->qfam.assign(c->nq, QFam());
+    for (int iq = 0; iq < c->nq; ++iq)
+        for (int ik = 0; ik < c->nk; ++ik) {
+            const int qi[3] = {iq / (qmesh[1] * qmesh[2]), (iq / qmesh[2]) % qmesh[1], iq % qmesh[2]};
+            const int ki[3] = {ik / (kmesh[1] * kmesh[2]), (ik / kmesh[2]) % kmesh[1], ik % kmesh[2]};
+            bool on = true;
+            for (int d = 0; d < 3; ++d) on = on && ((ki[d] * qmesh[d] + qi[d] * kmesh[d]) % qmesh[d] == 0);
+            if (on) continue;
+            double kf[3];
+            for (int d = 0; d < 3; ++d) kf[d] = (double)ki[d] / kmesh[d] + (double)qi[d] / qmesh[d];
+            KSphere& ks = c->kq_ks[(size_t)iq * c->nk + ik];
+            build_sphere(c, kf, ks);
+            c->ld = std::max(c->ld, ks.npw);
+        }
     // projector and Hubbard rows, with the K-independent prefactor
     //   (4 pi / sqrt(Omega)) N_R sqrt(pi/2) s^(2l+3),  N_R = sqrt(2 / (Gamma(l + 3/2) s^(2l+3)))
     auto pref = [&](int l, double s) {
@@ -746,6 +760,7 @@ void hp::invalidate_response(hp_ctx* c) {
     c->resp_ready = false;
     c->qc.iq = -1;
     c->cols.clear();
+    for (QFam& F : c->qfam) F.built = false;  // the states at k+q follow the ground state
 }
 
 extern "C" hp_status hp_set_ground_state(hp_ctx* c, int nspin, double nelec, const double* vhxc, const double* rho,
@@ -1040,51 +1055,216 @@ struct QState {
     int* d_kprime = nullptr;
 };
 
+void free_sphereset(hp_ctx* c, SphereSet& S) {
+    for (void* p : {(void*)S.d_npw, (void*)S.d_idx, (void*)S.d_g2, (void*)S.d_prec, (void*)S.d_prec32, (void*)S.d_kin32,
+                    (void*)S.d_iz, (void*)S.d_ncol, (void*)S.d_col_start, (void*)S.d_col_len, (void*)S.d_col_xy,
+                    (void*)S.d_xtab})
+        dfree(c, p);
+    S = SphereSet();
+}
+
+// projector (nrow0 = nproj) or Hubbard rows (nhub) at the given k points: kc [nk][3] Cartesian,
+// Miller indices [nk][ld][3] of the sphere set S
+hp_status family_rows(hp_ctx* c, const std::vector<double>& kc, const std::vector<int>& mil, const SphereSet& S,
+                      bool hub, double2* out) {
+    const int nk = (int)kc.size() / 3;
+    const int nrow_all = c->nproj + c->nhub;
+    const int nrow = hub ? c->nhub : c->nproj;
+    if (nrow == 0) return HP_OK;
+    const int o = hub ? c->nproj : 0;
+    int* d_mil;
+    double* d_kc;
+    CK(dalloc(c, &d_mil, mil.size()));
+    CK(dalloc(c, &d_kc, kc.size()));
+    CK(h2d(d_mil, mil.data(), mil.size(), c->st));
+    CK(h2d(d_kc, kc.data(), kc.size(), c->st));
+    CK(k_formfactor(d_kc, nk, d_mil, S.d_npw, c->ld, c->d_bvec, nrow, c->d_proj_int + o, c->d_proj_int + nrow_all + o,
+                    c->d_proj_int + 2 * nrow_all + o, c->d_proj_dbl + o, c->d_proj_dbl + nrow_all + o, c->d_tau, out,
+                    c->st));
+    CK(cudaStreamSynchronize(c->st));
+    dfree(c, d_mil);
+    dfree(c, d_kc);
+    return HP_OK;
+}
+
+// the families at k+q for a q with off-mesh points (QFam of iq)
+hp_status build_qfam(hp_ctx* c, int iq, const std::vector<const KSphere*>& sph, const std::vector<std::array<int, 3>>& g0,
+                     const std::vector<int>& kprime) {
+    QFam& F = c->qfam[iq];
+    const int nk = c->nk, ld = c->ld, nspin = c->nspin, nocc = c->nocc;
+    const size_t npsi = (size_t)nspin * nk * nocc * ld, nbeta = (size_t)nk * std::max(1, c->nproj) * ld,
+                 nphi = (size_t)nk * c->nhub * ld;
+    if (!F.beta) {
+        CK(dalloc(c, &F.beta, nbeta));
+        CK(dalloc(c, &F.phi, nphi));
+        CK(dalloc(c, &F.beta32, nbeta));
+        CK(dalloc(c, &F.phi32, nphi));
+    }
+    dfree(c, F.psi);
+    dfree(c, F.psi32);
+    CK(dalloc(c, &F.psi, npsi));
+    CK(dalloc(c, &F.psi32, npsi));
+    // Miller indices and Cartesian k+q of every k of this q (the q sphere set's order)
+    std::vector<int> mil((size_t)nk * ld * 3, 0);
+    std::vector<double> kc(3 * nk);
+    const int qi[3] = {iq / (c->qmesh[1] * c->qmesh[2]), (iq / c->qmesh[2]) % c->qmesh[1], iq % c->qmesh[2]};
+    for (int ik = 0; ik < nk; ++ik) {
+        const KSphere& s = *sph[ik];
+        for (int i = 0; i < s.npw; ++i)
+            for (int d = 0; d < 3; ++d) mil[((size_t)ik * ld + i) * 3 + d] = s.miller[3 * i + d] - g0[ik][d];
+        const int ki[3] = {ik / (c->kmesh[1] * c->kmesh[2]), (ik / c->kmesh[2]) % c->kmesh[1], ik % c->kmesh[2]};
+        double kf[3];
+        for (int d = 0; d < 3; ++d) kf[d] = (double)ki[d] / c->kmesh[d] + (double)qi[d] / c->qmesh[d];
+        for (int d = 0; d < 3; ++d)
+            kc[3 * ik + d] = kf[0] * c->bvec[0 * 3 + d] + kf[1] * c->bvec[1 * 3 + d] + kf[2] * c->bvec[2 * 3 + d];
+    }
+    hp_status s = family_rows(c, kc, mil, c->qc.set, false, F.beta);
+    if (s == HP_OK) s = family_rows(c, kc, mil, c->qc.set, true, F.phi);
+    if (s != HP_OK) return s;
+    // occupied states: rows of k' on the mesh, non-self-consistent states off it
+    std::vector<int> off;
+    for (int ik = 0; ik < nk; ++ik) {
+        if (kprime[ik] >= 0) {
+            for (int sp = 0; sp < nspin; ++sp)
+                CK(cudaMemcpyAsync(F.psi + ((size_t)sp * nk + ik) * nocc * ld,
+                                   c->d_psi + ((size_t)sp * nk + kprime[ik]) * c->nbnd * ld,
+                                   sizeof(double2) * (size_t)nocc * ld, cudaMemcpyDeviceToDevice, c->st));
+        } else {
+            off.push_back(ik);
+        }
+    }
+    if (!off.empty()) {
+        const int noff = (int)off.size();
+        std::vector<const KSphere*> so(noff);
+        std::vector<double> kco(3 * noff);
+        std::vector<int> milo((size_t)noff * ld * 3, 0);
+        for (int j = 0; j < noff; ++j) {
+            so[j] = sph[off[j]];
+            for (int d = 0; d < 3; ++d) kco[3 * j + d] = kc[3 * off[j] + d];
+            std::copy(mil.begin() + (size_t)off[j] * ld * 3, mil.begin() + (size_t)(off[j] + 1) * ld * 3,
+                      milo.begin() + (size_t)j * ld * 3);
+        }
+        SphereSet So;
+        const bool fused_before = c->fused;
+        s = upload_sphereset(c, so, nullptr, So);
+        c->fused = fused_before;  // the off-mesh set is not used by the fused transforms
+        if (s != HP_OK) return s;
+        double2 *beta_o = nullptr, *psi_o = nullptr;
+        CK(dalloc(c, &beta_o, (size_t)noff * std::max(1, c->nproj) * ld));
+        CK(dalloc(c, &psi_o, (size_t)nspin * noff * nocc * ld));
+        s = family_rows(c, kco, milo, So, false, beta_o);
+        std::vector<double> eps_o;
+        if (s == HP_OK) s = nscf_states(c, so, So, beta_o, psi_o, eps_o);
+        if (s != HP_OK) return s;
+        for (int j = 0; j < noff; ++j)
+            for (int sp = 0; sp < nspin; ++sp)
+                CK(cudaMemcpyAsync(F.psi + ((size_t)sp * nk + off[j]) * nocc * ld,
+                                   psi_o + ((size_t)sp * noff + j) * nocc * ld, sizeof(double2) * (size_t)nocc * ld,
+                                   cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaStreamSynchronize(c->st));
+        dfree(c, beta_o);
+        dfree(c, psi_o);
+        free_sphereset(c, So);
+    }
+    CK(k_to_c32(F.psi, F.psi32, (long long)npsi, c->st));
+    CK(k_to_c32(F.beta, F.beta32, (long long)nbeta, c->st));
+    if (nphi) CK(k_to_c32(F.phi, F.phi32, (long long)nphi, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    F.built = true;
+    return HP_OK;
+}
+
+// per q: spheres at k+q = k' + G0 (the k' sphere with Miller indices shifted by -G0) and kmap k -> k';
+// where k+q is off the mesh, its own sphere and the families materialised at k+q (QFam)
 hp_status prepare_q(hp_ctx* c, int iq, std::vector<int>& kprime) {
-    const int q1 = iq / (c->qmesh[1] * c->qmesh[2]), q2 = (iq / c->qmesh[2]) % c->qmesh[1], q3 = iq % c->qmesh[2];
-    const int qi[3] = {q1, q2, q3};
+    const int qi[3] = {iq / (c->qmesh[1] * c->qmesh[2]), (iq / c->qmesh[2]) % c->qmesh[1], iq % c->qmesh[2]};
     kprime.assign(c->nk, 0);
     std::vector<std::array<int, 3>> g0(c->nk);
     std::vector<const KSphere*> sph(c->nk);
-    for (int i1 = 0, ik = 0; i1 < c->kmesh[0]; ++i1)
-        for (int i2 = 0; i2 < c->kmesh[1]; ++i2)
-            for (int i3 = 0; i3 < c->kmesh[2]; ++i3, ++ik) {
-                const int ii[3] = {i1, i2, i3};
-                int j[3];
-                for (int d = 0; d < 3; ++d) {
-                    const int x = ii[d] + qi[d] * (c->kmesh[d] / c->qmesh[d]);  // (k+q) in units of 1/kmesh
-                    j[d] = x % c->kmesh[d];
-                    g0[ik][d] = x / c->kmesh[d];
-                }
-                kprime[ik] = (j[0] * c->kmesh[1] + j[1]) * c->kmesh[2] + j[2];
-                sph[ik] = &c->ks[kprime[ik]];
-            }
+    bool off = false;
+    for (int ik = 0; ik < c->nk; ++ik) {
+        const int ki[3] = {ik / (c->kmesh[1] * c->kmesh[2]), (ik / c->kmesh[2]) % c->kmesh[1], ik % c->kmesh[2]};
+        const KSphere& kq = c->kq_ks[(size_t)iq * c->nk + ik];
+        if (kq.npw > 0) {  // off the mesh
+            off = true;
+            kprime[ik] = -1;
+            g0[ik] = {0, 0, 0};
+            sph[ik] = &kq;
+            continue;
+        }
+        int j[3];
+        for (int d = 0; d < 3; ++d) {
+            const int x = (ki[d] * c->qmesh[d] + qi[d] * c->kmesh[d]) / c->qmesh[d];  // (k+q) in units of 1/kmesh
+            j[d] = x % c->kmesh[d];
+            g0[ik][d] = x / c->kmesh[d];
+        }
+        kprime[ik] = (j[0] * c->kmesh[1] + j[1]) * c->kmesh[2] + j[2];
+        sph[ik] = &c->ks[kprime[ik]];
+    }
     if (c->qc.iq == iq) return HP_OK;
     hp_status s = upload_sphereset(c, sph, &g0, c->qc.set);
     if (s != HP_OK) return s;
-    if (!c->qc.d_miller) CK(dalloc(c, &c->qc.d_miller, c->nk));  // holds kprime
-    CK(h2d(c->qc.d_miller, kprime.data(), c->nk, c->st));
+    std::vector<int> kmap(c->nk);
+    for (int ik = 0; ik < c->nk; ++ik) kmap[ik] = off ? ik : kprime[ik];
+    if (!c->qc.d_miller) CK(dalloc(c, &c->qc.d_miller, c->nk));  // holds the k map of the families
+    CK(h2d(c->qc.d_miller, kmap.data(), c->nk, c->st));
     CK(cudaStreamSynchronize(c->st));
+    c->qc.off = off;
+    if (off && !c->qfam[iq].built) {
+        s = build_qfam(c, iq, sph, g0, kprime);
+        if (s != HP_OK) return s;
+    }
     c->qc.iq = iq;
     return HP_OK;
+}
+
+// projector, Hubbard and occupied-state families at k+q for the current q (through the k map on
+// the mesh, or the materialised QFam)
+ProjMat fam_beta_kq(const hp_ctx* c) {
+    if (c->qc.off) {
+        const QFam& F = c->qfam[c->qc.iq];
+        return ProjMat{F.beta, 0, (long long)c->nproj * c->ld, c->nproj, 0, nullptr, F.beta32};
+    }
+    ProjMat A = beta_family(c, c->qc.d_miller);
+    A.base32 = c->d_beta32;
+    return A;
+}
+
+ProjMat fam_phi_kq(const hp_ctx* c, int nrow, int row0) {
+    if (c->qc.off) {
+        const QFam& F = c->qfam[c->qc.iq];
+        return ProjMat{F.phi, 0, (long long)c->nhub * c->ld, nrow, row0, nullptr, F.phi32};
+    }
+    return ProjMat{c->d_phi_k, 0, (long long)c->nhub * c->ld, nrow, row0, c->qc.d_miller, c->d_phi32};
+}
+
+// occupied states at k+q as a family: base, strides, FP32 copy
+void fam_psi_kq(const hp_ctx* c, const double2** base, const float2** base32, long long* ss, long long* sk) {
+    if (c->qc.off) {
+        const QFam& F = c->qfam[c->qc.iq];
+        *base = F.psi;
+        *base32 = F.psi32;
+        *ss = (long long)c->nk * c->nocc * c->ld;
+        *sk = (long long)c->nocc * c->ld;
+    } else {
+        *base = c->d_psi;
+        *base32 = c->d_psi32;
+        *ss = (long long)c->nk * c->nbnd * c->ld;
+        *sk = (long long)c->nbnd * c->ld;
+    }
 }
 
 // Y = A X = (H_k+q + alpha O_k+q - eps_v) X on the items of L
 hp_status apply_sternheimer(hp_ctx* c, const BandList& L, const double2* X, double2* Y) {
     const SphereSet& S = c->qc.set;
-    const int* kmap = c->qc.d_miller;
     const bool fp32 = c->opt.precision == HP_PRECISION_MIXED;
     hp_status s = (c->fused && c->d_vt) ? apply_local_fused(c, S, L, X, Y, fp32) : apply_local(c, S, L, X, Y, c->d_veff, fp32);
     // (FP32 band vectors are used only together with the fused transforms)
     if (s != HP_OK) return s;
     // V_NL and alpha P_v in one projection and one expansion: rows 0 .. nproj-1 are beta (weights
     // D), rows nproj .. nproj+nocc-1 the occupied states at k+q (weight alpha)
-    ProjMat A = beta_family(c, kmap);
-    A.base32 = c->d_beta32;
-    A.base2 = c->d_psi;
-    A.base2_32 = c->d_psi32;
-    A.stride2_s = (long long)c->nk * c->nbnd * c->ld;
-    A.stride2_k = (long long)c->nbnd * c->ld;
+    ProjMat A = fam_beta_kq(c);
+    fam_psi_kq(c, &A.base2, &A.base2_32, &A.stride2_s, &A.stride2_k);
     A.nrow2 = c->nocc;
     A.scale2 = c->alpha_pv;
     if (c->vec32) {
@@ -1142,7 +1322,6 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
     const long long nvec = (long long)rows * ld;
     const long long ndv = (long long)nspin * nr;
     const SphereSet& Sq = c->qc.set;
-    const int* kmap = c->qc.d_miller;
     // lists: Lall over response rows, Lpsi over the same (s, k, v) items with psi rows
     BandList& Lall = c->L1;
     BandList& Lpsi = c->L2;
@@ -1160,9 +1339,16 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
     // V_pert u_k = sum_m phi^J_m,k+q <phi^J_m,k|u_k>
     const int mJ = c->hub_mdim[jj], oJ = c->hub_off[jj];
     ProjMat phiJk{c->d_phi_k, 0, (long long)c->nhub * ld, mJ, oJ, nullptr, c->d_phi32};
-    ProjMat phiJkq{c->d_phi_k, 0, (long long)c->nhub * ld, mJ, oJ, kmap, c->d_phi32};
-    ProjMat phikq{c->d_phi_k, 0, (long long)c->nhub * ld, c->nhub, 0, kmap, c->d_phi32};
-    ProjMat Ukq{c->d_psi, (long long)nk * c->nbnd * ld, (long long)c->nbnd * ld, nocc, 0, kmap, c->d_psi32};
+    ProjMat phiJkq = fam_phi_kq(c, mJ, oJ);
+    ProjMat phikq = fam_phi_kq(c, c->nhub, 0);
+    ProjMat Ukq{nullptr, 0, 0, nocc, 0, nullptr};
+    {
+        const double2* b64;
+        const float2* b32;
+        long long ss, sk;
+        fam_psi_kq(c, &b64, &b32, &ss, &sk);
+        Ukq = ProjMat{b64, ss, sk, nocc, 0, c->qc.off ? nullptr : c->qc.d_miller, b32};
+    }
     if ((s = project(c, c->kset, Lpsi, phiJk, c->d_psi, c->d_Pbuf, mixed)) != HP_OK) return s;
     CK(cudaMemsetAsync(c->d_vpu, 0, sizeof(double2) * nvec, c->st));
     if (v32) CK(k_expand(Lall, Sq, phiJkq, c->d_Pbuf, nullptr, 1.0, F32(c->d_vpu), ld, c->st, mixed));

@@ -265,6 +265,14 @@ using namespace hp;
 
 namespace {
 
+// the band space an eigensolve works on: spheres, their k count, bands per (spin, k) and the
+// projector family at those k (rows of band (s, k, v) are (s * nk + k) * nbnd + v)
+struct EigSpace {
+    const SphereSet* S;
+    int nk, nbnd;
+    const double2* beta;  // [nk][nproj][ld]
+};
+
 struct GsWork {
     double2 *X = nullptr, *Y0 = nullptr, *Y1 = nullptr, *T = nullptr;
     double2 *Pb = nullptr, *Mb = nullptr, *Vb = nullptr, *Tmp = nullptr;
@@ -274,19 +282,25 @@ struct GsWork {
 };
 
 // Y = (H - shift) X for the list (shift taken from the list), including the nonlocal part
-hp_status apply_h_shift(hp_ctx* c, const BandList& L, const double2* X, double2* Y, double2* P) {
-    hp_status s = apply_local(c, c->kset, L, X, Y, c->d_veff);
+hp_status apply_h_shift(hp_ctx* c, const EigSpace& E, const BandList& L, const double2* X, double2* Y, double2* P) {
+    hp_status s = apply_local(c, *E.S, L, X, Y, c->d_veff);
+    if (s != HP_OK || c->nproj == 0) return s;
+    ProjMat B{E.beta, 0, (long long)c->nproj * c->ld, c->nproj, 0, nullptr};
+    s = project(c, *E.S, L, B, X, P);
     if (s != HP_OK) return s;
-    return apply_nonlocal(c, c->kset, L, X, Y, P, nullptr);
+    CK(k_expand(L, *E.S, B, P, c->d_projD, 1.0, Y, c->ld, c->st));
+    return HP_OK;
 }
 
 // Rayleigh-Ritz on the block Y (rows of L): X <- orthonormal Ritz vectors, eps <- Ritz values
-hp_status rayleigh_ritz(hp_ctx* c, BandList& L, BandList& L0, GsWork& W, double2* Y, double2* X, std::vector<double>& ritz) {
-    const int n = c->nbnd, nseg = L.nseg, ld = c->ld;
+hp_status rayleigh_ritz(hp_ctx* c, const EigSpace& E, BandList& L, BandList& L0, GsWork& W, double2* Y, double2* X,
+                        std::vector<double>& ritz) {
+    const int n = E.nbnd, nseg = L.nseg, ld = c->ld;
     const long long nvec = (long long)L.nb * ld;
-    ProjMat fam{nullptr, (long long)c->nk * n * ld, (long long)n * ld, n, 0, nullptr};
+    const SphereSet& S = *E.S;
+    ProjMat fam{nullptr, (long long)E.nk * n * ld, (long long)n * ld, n, 0, nullptr};
     // normalise columns, then overlap S = Y^H Y
-    CK(k_band_dot(L, c->kset, Y, Y, ld, W.nrm, c->st));
+    CK(k_band_dot(L, S, Y, Y, ld, W.nrm, c->st));
     {
         dim3 g(cdiv_(ld, 128), L.nb);
         rows_normalize_kernel<<<g, 128, 0, c->st>>>(L.d_row, W.nrm, Y, ld);
@@ -294,7 +308,7 @@ hp_status rayleigh_ritz(hp_ctx* c, BandList& L, BandList& L0, GsWork& W, double2
         CK(cudaGetLastError());
     }
     fam.base = Y;
-    hp_status s = project(c, c->kset, L, fam, Y, W.Pb);
+    hp_status s = project(c, S, L, fam, Y, W.Pb);
     if (s != HP_OK) return s;
     pack_seg_kernel<<<nseg, 256, 0, c->st>>>(W.Pb, L.d_seg_start, n, W.Mb);
     HP_LAUNCHED();
@@ -323,12 +337,12 @@ hp_status rayleigh_ritz(hp_ctx* c, BandList& L, BandList& L0, GsWork& W, double2
     HP_LAUNCHED();
     CK(cudaGetLastError());
     CK(cudaMemsetAsync(X, 0, sizeof(double2) * nvec, c->st));
-    CK(k_expand(L, c->kset, fam, W.Pb, nullptr, 1.0, X, ld, c->st));
+    CK(k_expand(L, S, fam, W.Pb, nullptr, 1.0, X, ld, c->st));
     // H in the orthonormal block
-    s = apply_h_shift(c, L0, X, W.T, W.Pb);
+    s = apply_h_shift(c, E, L0, X, W.T, W.Pb);
     if (s != HP_OK) return s;
     fam.base = X;
-    s = project(c, c->kset, L, fam, W.T, W.Pb);
+    s = project(c, S, L, fam, W.T, W.Pb);
     if (s != HP_OK) return s;
     pack_seg_kernel<<<nseg, 256, 0, c->st>>>(W.Pb, L.d_seg_start, n, W.Mb);
     HP_LAUNCHED();
@@ -340,7 +354,7 @@ hp_status rayleigh_ritz(hp_ctx* c, BandList& L, BandList& L0, GsWork& W, double2
     HP_LAUNCHED();
     CK(cudaGetLastError());
     CK(cudaMemsetAsync(Y, 0, sizeof(double2) * nvec, c->st));
-    CK(k_expand(L, c->kset, fam, W.Pb, nullptr, 1.0, Y, ld, c->st));
+    CK(k_expand(L, S, fam, W.Pb, nullptr, 1.0, Y, ld, c->st));
     CK(cudaMemcpyAsync(X, Y, sizeof(double2) * nvec, cudaMemcpyDeviceToDevice, c->st));
     ritz.resize((size_t)nseg * n);
     CK(d2h(ritz.data(), W.w, ritz.size(), c->st));
@@ -351,8 +365,8 @@ hp_status rayleigh_ritz(hp_ctx* c, BandList& L, BandList& L0, GsWork& W, double2
 }
 
 // Chebyshev filter of degree m damping [a, b]: X <- p_m(H) X
-hp_status cheb_filter(hp_ctx* c, BandList& L, GsWork& W, double2* X, int m, const std::vector<double>& a_seg, double b,
-                      BandList& Lc) {
+hp_status cheb_filter(hp_ctx* c, const EigSpace& E, BandList& L, GsWork& W, double2* X, int m,
+                      const std::vector<double>& a_seg, double b, BandList& Lc) {
     const int ld = c->ld;
     const long long nvec = (long long)L.nb * ld;
     // one interval for every segment: [a, b] with a the largest kept Ritz value over all segments
@@ -370,13 +384,13 @@ hp_status cheb_filter(hp_ctx* c, BandList& L, GsWork& W, double2* X, int m, cons
     if (s != HP_OK) return s;
     // Y0 = X ; Y1 = (H - c) X / e
     CK(cudaMemcpyAsync(W.Y0, X, sizeof(double2) * nvec, cudaMemcpyDeviceToDevice, c->st));
-    s = apply_h_shift(c, Lc, X, W.Y1, W.Pb);
+    s = apply_h_shift(c, E, Lc, X, W.Y1, W.Pb);
     if (s != HP_OK) return s;
     CK(k_vec_scale_copy(W.Y1, W.Y1, 1.0 / e, nvec, c->st));
     double2* ym1 = W.Y0;
     double2* y = W.Y1;
     for (int k = 2; k <= m; ++k) {
-        s = apply_h_shift(c, Lc, y, W.T, W.Pb);
+        s = apply_h_shift(c, E, Lc, y, W.T, W.Pb);
         if (s != HP_OK) return s;
         // y_{k} = 2/e (H - c) y_{k-1} - y_{k-2}, written over y_{k-2}
         vec_axmy_kernel<<<std::min(cdiv_(nvec, 256), 4096), 256, 0, c->st>>>(ym1, W.T, 2.0 / e, nvec);
@@ -391,6 +405,126 @@ hp_status cheb_filter(hp_ctx* c, BandList& L, GsWork& W, double2* X, int m, cons
 }
 
 }  // namespace
+
+// Non-self-consistent occupied states at k points off the k mesh (k + q): Chebyshev-filtered
+// subspace iteration with the ground-state potential V_eff held fixed, nocc + extra bands, until the
+// occupied residuals ||(H - eps) u|| are below 1e-11.  out: [nspin][nkq][nocc][ld]; eps_occ:
+// [nspin][nkq][nocc].
+hp_status hp::nscf_states(hp_ctx* c, const std::vector<const KSphere*>& sph, const SphereSet& S, const double2* beta,
+                          double2* out, std::vector<double>& eps_occ) {
+    const int nspin = c->nspin, nocc = c->nocc, ld = c->ld, nr = c->nr;
+    const int nkq = (int)sph.size();
+    int npw_min = ld;
+    for (const KSphere* k : sph) npw_min = std::min(npw_min, k->npw);
+    const int nbnd = std::min({kPS, nocc + std::max(6, nocc / 4), npw_min});
+    if (nbnd <= nocc) return fail(c, HP_EINVAL, "nscf: fewer plane waves at k+q than occupied bands plus a buffer");
+    const int rows = nspin * nkq * nbnd;
+    const long long nvec = (long long)rows * ld;
+    const long long ndv = (long long)nspin * nr;
+    const EigSpace E{&S, nkq, nbnd, beta};
+    GsWork W;
+    CK(dalloc(c, &W.X, nvec));
+    CK(dalloc(c, &W.Y0, nvec));
+    CK(dalloc(c, &W.Y1, nvec));
+    CK(dalloc(c, &W.T, nvec));
+    CK(dalloc(c, &W.Pb, (size_t)rows * kPS));
+    CK(dalloc(c, &W.Mb, (size_t)nspin * nkq * nbnd * nbnd));
+    CK(dalloc(c, &W.Vb, (size_t)nspin * nkq * nbnd * nbnd));
+    CK(dalloc(c, &W.Tmp, (size_t)nspin * nkq * nbnd * nbnd));
+    CK(dalloc(c, &W.w, (size_t)nspin * nkq * nbnd));
+    CK(dalloc(c, &W.nrm, rows));
+    CK(dalloc(c, &W.bad, 1));
+    auto release = [&]() {
+        for (void* p : {(void*)W.X, (void*)W.Y0, (void*)W.Y1, (void*)W.T, (void*)W.Pb, (void*)W.Mb, (void*)W.Vb,
+                        (void*)W.Tmp, (void*)W.w, (void*)W.nrm, (void*)W.bad})
+            dfree(c, p);
+    };
+    BandList& L = c->L1;
+    BandList& L0 = c->L2;
+    BandList& Lc = c->L3;
+    list_clear(L);
+    for (int sp = 0; sp < nspin; ++sp)
+        for (int k = 0; k < nkq; ++k)
+            for (int v = 0; v < nbnd; ++v) list_add(L, (sp * nkq + k) * nbnd + v, k, sp, 0.0);
+    hp_status st = upload_list(c, L);
+    if (st != HP_OK) return st;
+    L0.row = L.row;
+    L0.k = L.k;
+    L0.spin = L.spin;
+    L0.shift.assign(L.nb, 0.0);
+    if ((st = upload_list(c, L0)) != HP_OK) return st;
+    {   // random start (64-bit LCG + xorshift output, seed 2204), damped at large |k+G|
+        std::vector<double2> h(nvec, cmk(0.0, 0.0));
+        uint64_t state = 2204ULL * 6364136223846793005ULL + 1442695040888963407ULL;
+        auto next = [&]() {
+            state = state * 6364136223846793005ULL + 1442695040888963407ULL;
+            uint64_t x = state ^ (state >> 33);
+            x *= 0xff51afd7ed558ccdULL;
+            x ^= x >> 33;
+            return (double)(x >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+        };
+        for (int sp = 0; sp < nspin; ++sp)
+            for (int k = 0; k < nkq; ++k)
+                for (int v = 0; v < nbnd; ++v)
+                    for (int i = 0; i < sph[k]->npw; ++i) {
+                        const double damp = 1.0 / (1.0 + sph[k]->g2[i]);
+                        h[((size_t)(sp * nkq + k) * nbnd + v) * ld + i] = cmk(next() * damp, next() * damp);
+                    }
+        CK(h2d(W.X, h.data(), h.size(), c->st));
+        CK(cudaStreamSynchronize(c->st));
+    }
+    double dplus = 0.0;
+    for (int a = 0; a < (int)c->atom_species.size(); ++a) dplus += std::max(0.0, c->species[c->atom_species[a]].D);
+    if (!c->d_small) CK(dalloc(c, &c->d_small, 512));
+    vec_max_kernel<<<1, 256, 0, c->st>>>(c->d_veff, ndv, c->d_small + 100);
+    HP_LAUNCHED();
+    CK(cudaGetLastError());
+    double vmax = 0.0;
+    CK(d2h(&vmax, c->d_small + 100, 1, c->st));
+    const double b = 0.5 * c->ecut + vmax + 2.0 * dplus + 1.0;
+    const int nseg = nspin * nkq;
+    std::vector<double> ritz, aseg(nseg, 0.0);
+    if ((st = rayleigh_ritz(c, E, L, L0, W, W.X, W.Y0, ritz)) != HP_OK) return st;
+    CK(cudaMemcpyAsync(W.X, W.Y0, sizeof(double2) * nvec, cudaMemcpyDeviceToDevice, c->st));
+    double rmax = INFINITY;
+    for (int pass = 0; pass < 120 && !(rmax < 1e-11); ++pass) {
+        for (int gi = 0; gi < nseg; ++gi) aseg[gi] = ritz[(size_t)gi * nbnd + nbnd - 1];
+        if ((st = cheb_filter(c, E, L, W, W.X, 10, aseg, b, Lc)) != HP_OK) return st;
+        if ((st = rayleigh_ritz(c, E, L, L0, W, W.X, W.Y0, ritz)) != HP_OK) return st;
+        CK(cudaMemcpyAsync(W.X, W.Y0, sizeof(double2) * nvec, cudaMemcpyDeviceToDevice, c->st));
+        if (pass < 2) continue;
+        Lc.row = L.row;
+        Lc.k = L.k;
+        Lc.spin = L.spin;
+        Lc.shift.assign(ritz.begin(), ritz.end());
+        if ((st = upload_list(c, Lc)) != HP_OK) return st;
+        if ((st = apply_h_shift(c, E, Lc, W.X, W.T, W.Pb)) != HP_OK) return st;
+        CK(k_band_dot(Lc, S, W.T, W.T, ld, W.nrm, c->st));
+        std::vector<double> nr2(rows);
+        CK(d2h(nr2.data(), W.nrm, rows, c->st));
+        rmax = 0.0;
+        for (int sp = 0; sp < nspin; ++sp)
+            for (int k = 0; k < nkq; ++k)
+                for (int v = 0; v < nocc; ++v) rmax = std::max(rmax, std::sqrt(nr2[(size_t)(sp * nkq + k) * nbnd + v]));
+        if (getenv("HP_VERBOSE")) fprintf(stderr, "nscf: pass %d max occupied residual %.3e\n", pass, rmax);
+    }
+    if (!(rmax < 1e-9)) {
+        release();
+        return fail(c, HP_ENOTCONV, "nscf: occupied residuals at k+q did not converge");
+    }
+    for (int sp = 0; sp < nspin; ++sp)
+        for (int k = 0; k < nkq; ++k)
+            CK(cudaMemcpyAsync(out + (size_t)(sp * nkq + k) * nocc * ld, W.X + (size_t)(sp * nkq + k) * nbnd * ld,
+                               sizeof(double2) * (size_t)nocc * ld, cudaMemcpyDeviceToDevice, c->st));
+    eps_occ.assign((size_t)nspin * nkq * nocc, 0.0);
+    for (int sp = 0; sp < nspin; ++sp)
+        for (int k = 0; k < nkq; ++k)
+            for (int v = 0; v < nocc; ++v)
+                eps_occ[(size_t)(sp * nkq + k) * nocc + v] = ritz[(size_t)(sp * nkq + k) * nbnd + v];
+    CK(cudaStreamSynchronize(c->st));
+    release();
+    return HP_OK;
+}
 
 extern "C" hp_status hp_ground_state(hp_ctx* c, double nelec, int nspin, const int* init_moment, hp_gs_info* info) {
     if (!c) return HP_EINVAL;
@@ -419,6 +553,7 @@ extern "C" hp_status hp_ground_state(hp_ctx* c, double nelec, int nspin, const i
     CK(dalloc(c, &c->d_rho, ndv));
     CK(dalloc(c, &c->d_veff, ndv));
     CK(dalloc(c, &c->d_psi, nvec));
+    const EigSpace E{&c->kset, nk, nbnd, c->d_beta_k};
     GsWork W;
     CK(dalloc(c, &W.X, nvec));
     CK(dalloc(c, &W.Y0, nvec));
@@ -559,9 +694,9 @@ extern "C" hp_status hp_ground_state(hp_ctx* c, double nelec, int nspin, const i
         for (int pass = 0; pass < passes; ++pass) {
             if (!ritz.empty()) {
                 for (int g = 0; g < nseg; ++g) aseg[g] = ritz[(size_t)g * nbnd + nbnd - 1];
-                if ((st = cheb_filter(c, L, W, W.X, deg, aseg, b, Lc)) != HP_OK) return st;
+                if ((st = cheb_filter(c, E, L, W, W.X, deg, aseg, b, Lc)) != HP_OK) return st;
             }
-            if ((st = rayleigh_ritz(c, L, L0, W, W.X, W.Y0, ritz)) != HP_OK) return st;
+            if ((st = rayleigh_ritz(c, E, L, L0, W, W.X, W.Y0, ritz)) != HP_OK) return st;
             CK(cudaMemcpyAsync(W.X, W.Y0, sizeof(double2) * nvec, cudaMemcpyDeviceToDevice, c->st));
         }
         // density of the occupied Ritz vectors
@@ -647,8 +782,8 @@ extern "C" hp_status hp_ground_state(hp_ctx* c, double nelec, int nspin, const i
         CK(d2h(&vmax, c->d_small + 100, 1, c->st));
         const double b = 0.5 * c->ecut + vmax + 2.0 * dplus + 1.0;
         for (int g = 0; g < nseg; ++g) aseg[g] = ritz[(size_t)g * nbnd + nbnd - 1];
-        if ((st = cheb_filter(c, L, W, W.X, deg, aseg, b, Lc)) != HP_OK) return st;
-        if ((st = rayleigh_ritz(c, L, L0, W, W.X, W.Y0, ritz)) != HP_OK) return st;
+        if ((st = cheb_filter(c, E, L, W, W.X, deg, aseg, b, Lc)) != HP_OK) return st;
+        if ((st = rayleigh_ritz(c, E, L, L0, W, W.X, W.Y0, ritz)) != HP_OK) return st;
         CK(cudaMemcpyAsync(W.X, W.Y0, sizeof(double2) * nvec, cudaMemcpyDeviceToDevice, c->st));
         // residual norms ||(H - eps) x|| of the occupied bands
         Lc.row = L.row;
@@ -656,7 +791,7 @@ extern "C" hp_status hp_ground_state(hp_ctx* c, double nelec, int nspin, const i
         Lc.spin = L.spin;
         Lc.shift.assign(ritz.begin(), ritz.end());
         if ((st = upload_list(c, Lc)) != HP_OK) return st;
-        if ((st = apply_h_shift(c, Lc, W.X, W.T, W.Pb)) != HP_OK) return st;
+        if ((st = apply_h_shift(c, E, Lc, W.X, W.T, W.Pb)) != HP_OK) return st;
         CK(k_band_dot(Lc, c->kset, W.T, W.T, ld, W.nrm, c->st));
         std::vector<double> nr2(rows);
         CK(d2h(nr2.data(), W.nrm, rows, c->st));

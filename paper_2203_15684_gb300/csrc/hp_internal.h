@@ -279,8 +279,18 @@ struct RespCols {
     std::vector<double> tr0, tr;   // spin-summed traces per Hubbard atom
 };
 
+// families at k+q for a q with some k+q off the k mesh, materialised once per q: occupied states
+// (copied rows of k' where k+q = k' + G0, non-self-consistent states elsewhere) and the projector
+// and Hubbard rows evaluated at k+q, in FP64 and FP32
+struct QFam {
+    bool built = false;
+    double2 *psi = nullptr, *beta = nullptr, *phi = nullptr;  // [nspin][nk][nocc][ld], [nk][nproj][ld], [nk][nhub][ld]
+    float2 *psi32 = nullptr, *beta32 = nullptr, *phi32 = nullptr;
+};
+
 struct QCache {                    // per-q data: k+q spheres, projectors and occupied states at k+q
     int iq = -1;
+    bool off = false;              // some k+q of this q is off the k mesh: use the QFam of iq
     SphereSet set;
     std::vector<KSphere> ks;
     double2* d_beta = nullptr;     // [nk][nproj][ld]
@@ -348,6 +358,9 @@ hp_status project(hp_ctx* c, const SphereSet& S, const BandList& L, const ProjMa
 hp_status apply_nonlocal(hp_ctx* c, const SphereSet& S, const BandList& L, const double2* X, double2* Y, double2* P,
                          const int* kmap, bool fp32 = false);
 void invalidate_response(hp_ctx* c);
+// occupied states at k points off the k mesh with the ground-state potential fixed (groundstate.cu)
+hp_status nscf_states(hp_ctx* c, const std::vector<const KSphere*>& sph, const SphereSet& S, const double2* beta,
+                      double2* out, std::vector<double>& eps_occ);
 
 }  // namespace hp
 
@@ -365,6 +378,8 @@ struct hp_ctx {
     int N[3], nr = 0;
     int nk = 0, nq = 0;
     std::vector<hp::KSphere> ks;       // sphere per mesh k
+    std::vector<hp::KSphere> kq_ks;    // [nq][nk] spheres at k+q off the k mesh (npw 0 where on the mesh)
+    std::vector<hp::QFam> qfam;        // [nq]
     int ld = 0;                        // padded sphere length (max npw over k and every k+q)
     // projector rows and Hubbard rows
     int nproj = 0, nhub = 0;

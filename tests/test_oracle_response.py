@@ -161,3 +161,26 @@ def test_spin_polarised_sos_and_symmetry():
     for a in range(4):
         for b in range(4):
             assert abs(cols[m.hub_atoms[b]][a] - cols[m.hub_atoms[a]][b]) < 1e-8 * abs(diag[0])
+
+
+def test_off_mesh_branch_equals_mapped_states(monkeypatch):
+    """The non-self-consistent k+q branch (used when k+q is off the k mesh) forced on an on-mesh q
+    gives the same response column as the states mapped from k' = k+q - G0: same occupied
+    energies, and Delta n equal up to the gauge of the states (traces and the full matrices, which
+    do not depend on it)."""
+    w = W.tiny_q(ecut=8.0, grid=(12, 12, 12), kmesh=(2, 2, 2), qmesh=(2, 1, 1))
+    m = Model(w)
+    gs = G.scf(m, tol=1e-12)
+    J = m.hub_atoms[0]
+    mapped = R.solve_column(m, gs, 1, J, tol_cg=1e-13, scf_tol=1e-12, conv_chi=1e-13)
+    e_mapped = [G.kq_states(m, gs, ik, 1)[2] for ik in range(len(m.kpts))]
+    monkeypatch.setattr(Model, "kq_map", lambda self, ik, iq: (None, None))
+    e_nscf = [G.kq_states(m, gs, ik, 1)[2] for ik in range(len(m.kpts))]
+    nscf = R.solve_column(m, gs, 1, J, tol_cg=1e-13, scf_tol=1e-12, conv_chi=1e-13)
+    assert max(np.abs(a - b).max() for a, b in zip(e_mapped, e_nscf)) < 1e-9
+    for key in ("dn0", "dn"):
+        a, b = mapped[key], nscf[key]
+        assert set(a) == set(b)
+        scale = max(np.abs(np.asarray(v)).max() for v in a.values())
+        for atom in a:
+            assert np.abs(np.asarray(a[atom]) - np.asarray(b[atom])).max() < 1e-8 * scale
