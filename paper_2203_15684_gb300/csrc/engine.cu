@@ -1267,6 +1267,26 @@ hp_status apply_sternheimer(hp_ctx* c, const BandList& L, const double2* X, doub
     fam_psi_kq(c, &A.base2, &A.base2_32, &A.stride2_s, &A.stride2_k);
     A.nrow2 = c->nocc;
     A.scale2 = c->alpha_pv;
+    if (A.nrow + A.nrow2 > kPStride) {  // more rows than one projection holds: beta, then P_v
+        ProjMat U{A.base2, A.stride2_s, A.stride2_k, c->nocc, 0, A.kmap, A.base2_32};
+        A.base2 = nullptr;
+        A.base2_32 = nullptr;
+        A.nrow2 = 0;
+        for (int pass = 0; pass < 2; ++pass) {
+            const ProjMat& F = pass == 0 ? A : U;
+            const double* w = pass == 0 ? c->d_projD : nullptr;
+            const double al = pass == 0 ? 1.0 : c->alpha_pv;
+            if (F.nrow == 0) continue;
+            if (c->vec32) {
+                if ((s = project(c, S, L, F, (const float2*)X, c->d_Pbuf, fp32)) != HP_OK) return s;
+                CK(k_expand(L, S, F, c->d_Pbuf, w, al, (float2*)Y, c->ld, c->st, fp32));
+            } else {
+                if ((s = project(c, S, L, F, X, c->d_Pbuf, fp32)) != HP_OK) return s;
+                CK(k_expand(L, S, F, c->d_Pbuf, w, al, Y, c->ld, c->st, fp32));
+            }
+        }
+        return HP_OK;
+    }
     if (c->vec32) {
         s = project(c, S, L, A, (const float2*)X, c->d_Pbuf, fp32);
         if (s != HP_OK) return s;
