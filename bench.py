@@ -55,6 +55,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0)
     p.add_argument("--band-batch", type=int, default=0, help="grids per FFT batch (0 = automatic)")
     p.add_argument("--workload", default="medium", choices=sorted(WORKLOADS))
+    p.add_argument("--cg-adapt", type=float, default=None,
+                   help="CG threshold factor for outer iterations after the first (library default if omitted)")
     return p.parse_args()
 
 
@@ -239,7 +241,10 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     stream = torch.cuda.current_stream()
     w = getattr(W, args.workload)()
-    ctx = P.Context.from_workload(w, cuda_stream=stream.cuda_stream, band_batch=args.band_batch)
+    opts = dict(cuda_stream=stream.cuda_stream, band_batch=args.band_batch)
+    if args.cg_adapt is not None:
+        opts["cg_adapt"] = args.cg_adapt
+    ctx = P.Context.from_workload(w, **opts)
     t0 = time.perf_counter()
     gs = ctx.ground_state(w["nelec"], w["nspin"], w["moments"])
     gs_seconds = time.perf_counter() - t0

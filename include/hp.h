@@ -86,7 +86,7 @@ typedef struct {
     double cg_adapt;        /* outer iterations after the first stop each band's CG at
                              * ||r|| <= max(cg_tol, theta ||b||), theta = min(1e-2, cg_adapt x the
                              * previous iteration's relative Hxc residual); 0 = always cg_tol
-                             * (default 0.01).  The first iteration (chi_0) always uses cg_tol. */
+                             * (default 0.001).  The first iteration (chi_0) always uses cg_tol. */
 } hp_options;
 
 /* Fills *opt with the defaults listed above. */

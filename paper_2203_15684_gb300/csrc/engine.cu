@@ -447,7 +447,7 @@ extern "C" void hp_default_options(hp_options* o) {
     o->cg_tol = 1e-11;
     o->cg_maxiter = 400;
     o->scf_tol = 1e-10;
-    o->cg_adapt = 0.01;
+    o->cg_adapt = 0.001;
     o->conv_thr_chi = 1e-10;
     o->niter_max = 100;
     o->nmix = 4;
@@ -587,6 +587,9 @@ static hp_status setup_impl(hp_ctx* c, const double cell[9], int nspecies, const
     // device data
     c->fused = fused_supported(c->N) && !getenv("HP_NO_FUSED");
     c->fused_reg = !getenv("HP_FUSED_SMEM");  // HP_FUSED_SMEM: shared-memory line FFTs instead
+    // rows of one combined projection (at most the buffer's 128; HP_PROJ_ROWS lowers it)
+    c->proj_rows_max = kPStride;
+    if (const char* r = getenv("HP_PROJ_ROWS")) c->proj_rows_max = std::max(1, std::min(kPStride, atoi(r)));
     CK(fft_plan_create(c->fft, c->N));
     CK(dalloc(c, &c->d_bvec, 9));
     CK(h2d(c->d_bvec, c->bvec, 9, c->st));
@@ -1267,7 +1270,7 @@ hp_status apply_sternheimer(hp_ctx* c, const BandList& L, const double2* X, doub
     fam_psi_kq(c, &A.base2, &A.base2_32, &A.stride2_s, &A.stride2_k);
     A.nrow2 = c->nocc;
     A.scale2 = c->alpha_pv;
-    if (A.nrow + A.nrow2 > kPStride) {  // more rows than one projection holds: beta, then P_v
+    if (A.nrow + A.nrow2 > c->proj_rows_max) {  // more rows than one projection holds: beta, then P_v
         ProjMat U{A.base2, A.stride2_s, A.stride2_k, c->nocc, 0, A.kmap, A.base2_32};
         A.base2 = nullptr;
         A.base2_32 = nullptr;

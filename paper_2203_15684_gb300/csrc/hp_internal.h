@@ -424,6 +424,7 @@ struct hp_ctx {
     float2* d_dv32 = nullptr;          // mixed precision: FP32 copy of Delta V_Hxc
     // sphere-sparse fused transforms (when the grid sizes are supported)
     bool fused = false;
+    int proj_rows_max = 128;           // rows of one combined beta / P_v projection
     bool vec32 = false;                // response band vectors stored in FP32 (mixed form, fused path)
     bool fused_reg = true;             // fused transforms with register-resident line FFTs
     bool ur_planes = false;            // the real-space band cache is plane-major (built by the fused path)

@@ -64,3 +64,17 @@ def test_mixed_routes_agree_with_fp64(monkeypatch, route):
     _, dn, _ = ctx.response(1, J)
     r1 = oracle_dn_padded(m, ref["dn"])
     assert np.abs(dn - r1).max() < 1e-5 * np.abs(r1).max()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_two_pass_projection_matches_oracle(monkeypatch, precision):
+    """beta and P_v rows projected in two passes (as when nproj + nocc exceeds one projection's
+    128 rows), forced here with HP_PROJ_ROWS on the small cell: FP64 at 1e-8, mixed at 1e-5."""
+    w, m, gs, J, ref = _reference(GRIDS[0])
+    monkeypatch.setenv("HP_PROJ_ROWS", "4")
+    kw = dict(cg_tol=1e-12, scf_tol=1e-11, conv_thr_chi=1e-11) if precision == 0 else {}
+    ctx = P.Context.from_workload(w, precision=precision, **kw)
+    import_ground_state(ctx, m, gs)
+    _, dn, _ = ctx.response(1, J)
+    r1 = oracle_dn_padded(m, ref["dn"])
+    assert np.abs(dn - r1).max() < (1e-8 if precision == 0 else 1e-5) * np.abs(r1).max()
