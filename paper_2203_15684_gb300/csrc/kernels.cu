@@ -592,7 +592,7 @@ __global__ void __launch_bounds__(128) expand_kernel(ProjDev d, int ld, const do
                                                      const int* __restrict__ seg_start, const int* __restrict__ seg_k,
                                                      const int* __restrict__ seg_s, const int* __restrict__ npw_of_k) {
     using V = typename std::conditional<std::is_same<S, float>::value, float2, double2>::type;
-    __shared__ V Ps[kExpC][kPStride];
+    __shared__ __align__(16) V Ps[kPStride][kExpC];  // [row][band]: two FP32 bands per 16-byte read
     const int seg = blockIdx.y;
     const int cbeg = seg_start[seg], cend = seg_start[seg + 1];
     const int k = seg_k[seg], sp = seg_s[seg];
@@ -600,6 +600,9 @@ __global__ void __launch_bounds__(128) expand_kernel(ProjDev d, int ld, const do
     const int G = blockIdx.x * blockDim.x + threadIdx.x;
     const int mk = d.kmap ? d.kmap[k] : k;
     const int nrow = d.n0 + d.n1;
+    // row p of the first family at G is a0[p * ld], of the second a1[(p - n0) * ld]
+    const AT* a0 = (const AT*)d.a0 + sp * d.s0_s + mk * d.s0_k + (long long)d.r0 * ld + G;
+    const AT* a1 = d.n1 > 0 ? (const AT*)d.a1 + sp * d.s1_s + mk * d.s1_k + (long long)d.r1 * ld + G : nullptr;
     for (int ct = cbeg; ct < cend; ct += kExpC) {
         for (int e = threadIdx.x; e < kExpC * nrow; e += blockDim.x) {
             const int cc = e / nrow, p = e % nrow;
@@ -609,22 +612,48 @@ __global__ void __launch_bounds__(128) expand_kernel(ProjDev d, int ld, const do
                 const double w = p < d.n0 ? (pscale ? pscale[p] : 1.0) : scale2;
                 v = cscale(P[(long long)c * kPStride + p], alpha * w);
             }
-            Ps[cc][p] = load_as<V>(v);
+            Ps[p][cc] = load_as<V>(v);
         }
         __syncthreads();
         if (G < npw) {
             V acc[kExpC];
 #pragma unroll
             for (int i = 0; i < kExpC; ++i) acc[i] = cpack<V>(0.0, 0.0);
-            for (int p = 0; p < nrow; ++p) {
-                const V a = load_as<V>(proj_row<AT>(d, sp, mk, p, ld)[G]);
+            auto mac = [&](const V a, int p) {
+                if constexpr (sizeof(V) == 8 && kExpC % 2 == 0) {
+                    const float4* q4 = reinterpret_cast<const float4*>(&Ps[p][0]);
 #pragma unroll
-                for (int i = 0; i < kExpC; ++i) {
-                    const V q = Ps[i][p];
-                    acc[i].x += a.x * q.x - a.y * q.y;
-                    acc[i].y += a.x * q.y + a.y * q.x;
+                    for (int i = 0; i < kExpC / 2; ++i) {
+                        const float4 q = q4[i];
+                        acc[2 * i].x += a.x * q.x - a.y * q.y;
+                        acc[2 * i].y += a.x * q.y + a.y * q.x;
+                        acc[2 * i + 1].x += a.x * q.z - a.y * q.w;
+                        acc[2 * i + 1].y += a.x * q.w + a.y * q.z;
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < kExpC; ++i) {
+                        const V q = Ps[p][i];
+                        acc[i].x += a.x * q.x - a.y * q.y;
+                        acc[i].y += a.x * q.y + a.y * q.x;
+                    }
                 }
+            };
+            int p = 0;
+            for (; p + 1 < d.n0; p += 2) {  // first family, two rows at a time (both loads in flight)
+                const V x0 = load_as<V>(a0[(long long)p * ld]);
+                const V x1 = load_as<V>(a0[(long long)(p + 1) * ld]);
+                mac(x0, p);
+                mac(x1, p + 1);
             }
+            for (; p < d.n0; ++p) mac(load_as<V>(a0[(long long)p * ld]), p);
+            for (; p + 1 < nrow; p += 2) {
+                const V x0 = load_as<V>(a1[(long long)(p - d.n0) * ld]);
+                const V x1 = load_as<V>(a1[(long long)(p + 1 - d.n0) * ld]);
+                mac(x0, p);
+                mac(x1, p + 1);
+            }
+            for (; p < nrow; ++p) mac(load_as<V>(a1[(long long)(p - d.n0) * ld]), p);
 #pragma unroll
             for (int i = 0; i < kExpC; ++i) {
                 const int c = ct + i;
