@@ -1052,11 +1052,6 @@ hp_status prepare_resp(hp_ctx* c) {
     return HP_OK;
 }
 
-// per q: spheres at k+q = k' + G0 (the k' sphere with Miller indices shifted by -G0), kmap k -> k'
-struct QState {
-    std::vector<int> kprime;
-    int* d_kprime = nullptr;
-};
 
 void free_sphereset(hp_ctx* c, SphereSet& S) {
     for (void* p : {(void*)S.d_npw, (void*)S.d_idx, (void*)S.d_g2, (void*)S.d_prec, (void*)S.d_prec32, (void*)S.d_kin32,

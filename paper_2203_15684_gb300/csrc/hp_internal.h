@@ -288,16 +288,11 @@ struct QFam {
     float2 *psi32 = nullptr, *beta32 = nullptr, *phi32 = nullptr;
 };
 
-struct QCache {                    // per-q data: k+q spheres, projectors and occupied states at k+q
+struct QCache {                    // per-q data: the k+q sphere set and the k map of the families
     int iq = -1;
     bool off = false;              // some k+q of this q is off the k mesh: use the QFam of iq
     SphereSet set;
-    std::vector<KSphere> ks;
-    double2* d_beta = nullptr;     // [nk][nproj][ld]
-    double2* d_phi = nullptr;      // [nk][nhub][ld]
-    double2* d_u = nullptr;        // [nspin][nk][nocc][ld]
-    double* d_kcart = nullptr;
-    int* d_miller = nullptr;
+    int* d_miller = nullptr;       // [nk] family index of each k+q (k' on the mesh, k itself off it)
 };
 
 // fused.cu: sphere-sparse column/plane transforms
@@ -340,7 +335,7 @@ cudaError_t k_to_planes_real(const double* a, double* b, const int N[3], int nve
 cudaError_t k_to_planes_c(const double2* a, double2* b, const int N[3], int nvec, cudaStream_t st);
 cudaError_t k_from_planes_c(const double2* b, double2* a, const int N[3], int nvec, cudaStream_t st);
 
-// engine.cu helpers shared with the ground-state driver
+// engine.cu helpers shared with the ground-state code
 hp_status fail(hp_ctx* c, hp_status s, const std::string& msg);
 hp_status cuda_fail(hp_ctx* c, cudaError_t e, const char* what);
 void dfree(hp_ctx* c, void* p);
