@@ -212,6 +212,25 @@ def ncu_traffic(family, alg_bytes_per_launch, workload="medium"):
     return d["dram_over_algorithmic"] * alg_bytes_per_launch
 
 
+def shard_pairs(pairs, rank, world):
+    """The (q, J) pairs one rank runs: round-robin over ranks, disjoint, together all pairs."""
+    return pairs[rank::world]
+
+
+def reduce_over_ranks(elapsed, units, dist, device):
+    """Whole-job timing: (max elapsed over ranks, sum of the units all ranks processed).  dist is
+    torch.distributed (or None for one process)."""
+    if dist is None:
+        return elapsed, float(units)
+    import torch
+
+    t = torch.tensor([elapsed, float(units)], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
+    dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(t[1])
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -251,7 +270,7 @@ def main():
     atoms, _ = ctx.hubbard_atoms()
     s = ctx.query_sizes()
     pairs = [(iq, int(J)) for J in atoms for iq in range(s["nq"])]
-    mine = pairs[rank::world]
+    mine = shard_pairs(pairs, rank, world)
 
     def barrier():
         if dist is not None:
@@ -293,14 +312,7 @@ def main():
         out = dict(launches=P.launch_count() - l0, prof=P.profile_end() if profile else None,
                    clocks=clocks.stop() if clocks else None, elapsed=e0.elapsed_time(e1) / 1000.0,
                    hpsi=hpsi, iters=iters, traces=traces, k=k)
-        t = torch.tensor([out["elapsed"], float(hpsi)], dtype=torch.float64, device="cuda")
-        if dist is not None:
-            tmax = t.clone()
-            dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
-            dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
-            out["elapsed"], out["hpsi_all"] = float(tmax[0]), float(t[1])
-        else:
-            out["hpsi_all"] = float(hpsi)
+        out["elapsed"], out["hpsi_all"] = reduce_over_ranks(out["elapsed"], hpsi, dist, "cuda")
         out["value"] = out["hpsi_all"] / out["elapsed"] if steps else None
         out["ms_per_step"] = 1000.0 * out["elapsed"] / steps if steps else None
         return out
