@@ -40,6 +40,8 @@ WORKLOADS = {
               "ecutwfc 35 Ry (npw<=2103), FFT 36^3, k 4x4x4, q 2x2x2",
     "precision": "precision: the medium cell at ecutwfc 50 Ry (npw<=3575), FFT 45^3, k 4x4x4, q 2x2x2, "
                  "nspin=2 (AFM start)",
+    "batch": "batch: 6 small insulating cells of uneven sizes (two-atom cube at 8/10/20 Ry, q meshes of 1-8 "
+             "points, rocksalt cell at 6 Ry with nspin=2), mixed form",
 }
 
 
@@ -239,8 +241,70 @@ def measured_peaks():
     return 6800.0, "fallback (no MEASURED_PEAKS.json)"
 
 
+def batch_arm(args):
+    """Batching form: the full chi matrices of a batch of small cells, one cell after the other and
+    all at once (hp_batch_run: one host thread and CUDA stream per cell); cells per hour of each."""
+    import torch
+
+    import paper_2203_15684_gb300 as P
+    import workloads as W
+
+    cells = W.batch_small()
+
+    def ready(w):
+        stream = torch.cuda.Stream()
+        ctx = P.Context.from_workload(w, cuda_stream=stream.cuda_stream, precision=1)
+        ctx.ground_state(w["nelec"], w["nspin"], w.get("moments"))
+        return ctx, stream
+
+    def alone(ctxs):
+        for ctx, _ in ctxs:
+            atoms, _ = ctx.hubbard_atoms()
+            for J in atoms:
+                for iq in range(ctx.query_sizes()["nq"]):
+                    ctx.response(iq, int(J))
+            ctx.hubbard()
+
+    times_a, times_b = [], []
+    l0 = P.launch_count()
+    for rep in range(args.warmup + args.steps):
+        ctxs = [ready(w) for w in cells]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        alone(ctxs)
+        torch.cuda.synchronize()
+        ta = time.perf_counter() - t0
+        ctxs = [ready(w) for w in cells]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        P.batch_run([c for c, _ in ctxs])
+        torch.cuda.synchronize()
+        tb = time.perf_counter() - t0
+        if rep >= args.warmup:
+            times_a.append(ta)
+            times_b.append(tb)
+    ta, tb = sum(times_a) / len(times_a), sum(times_b) / len(times_b)
+    n = len(cells)
+    line = {"metric": "cells/hour, batch of small cells (full chi and U/V per cell, mixed form)",
+            "value": n * 3600.0 / tb, "unit": "cells/h", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * tb, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64 (mixed)", "data": "synthetic",
+            "config": {"workload": WORKLOADS["batch"], "step": "one batch: every (q, J) response and chi/U/V of every "
+                                                                "cell, ground states computed before timing",
+                       "one_after_another_cells_per_hour": n * 3600.0 / ta,
+                       "speedup_batch_vs_one_after_another": ta / tb},
+            "gpu_launches": P.launch_count() - l0}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "batch":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the batch mode has no reference arm"}))
+            return
+        batch_arm(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

@@ -205,6 +205,18 @@ hp_status hp_response(hp_ctx* ctx, int iq, int atom, double* dn0, double* dn, hp
  * Errors: HP_ESINGULAR. */
 hp_status hp_hubbard(hp_ctx* ctx, double* chi0, double* chi, double* hub);
 
+/* Several independent cells at once (the batching form; the paper's code runs one system per job,
+ * so there is no counterpart there).  For every context cells[0 .. ncells-1], each set up with its
+ * own CUDA stream (hp_options.cuda_stream) and holding a ground state, runs every (q, J) response
+ * (hp_response) and then hp_hubbard, one host thread per cell, so that the cells' kernels overlap
+ * on the GPU; returns when all cells are done.  chi0[i], chi[i], hub[i]: cell i's outputs as for
+ * hp_hubbard (the arrays of pointers, or any entry, may be NULL).  status[i] receives cell i's
+ * result (caller-owned, ncells entries).  Returns HP_OK when every cell succeeded, else the first
+ * failing status in cell order.  Errors: HP_EINVAL (ncells < 1, a NULL or repeated context).
+ * While it runs, no other thread may use these contexts; contexts on the same stream serialise. */
+hp_status hp_batch_run(int ncells, hp_ctx* const* cells, double* const* chi0, double* const* chi, double* const* hub,
+                       hp_status* status);
+
 /* Message of the last failure on this context ("" if none).  Valid until the next call. */
 const char* hp_last_error(const hp_ctx* ctx);
 

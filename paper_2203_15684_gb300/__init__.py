@@ -70,7 +70,8 @@ _lib = None
 SYMBOLS = ["hp_default_options", "hp_setup", "hp_query_sizes", "hp_sphere", "hp_hubbard_atoms", "hp_ground_state",
            "hp_set_ground_state", "hp_get_ground_state", "hp_apply_h", "hp_response", "hp_hubbard", "hp_last_error",
            "hp_destroy", "hp_selftest_fft_host", "hp_selftest_eigh", "hp_get_wavefunctions", "hp_profile_begin",
-           "hp_profile_end", "hp_launch_count", "hp_apply_h_noalloc", "hp_set_precision", "hp_selftest_convert"]
+           "hp_profile_end", "hp_launch_count", "hp_apply_h_noalloc", "hp_set_precision", "hp_selftest_convert",
+           "hp_batch_run"]
 
 
 def lib():
@@ -109,6 +110,7 @@ def lib():
     L.hp_apply_h_noalloc.argtypes = [V, I, I, I, V, V, V]
     L.hp_set_precision.argtypes = [V, I]
     L.hp_selftest_convert.argtypes = [C.c_longlong, P(D), P(C.c_float), P(D), P(C.c_float), P(D)]
+    L.hp_batch_run.argtypes = [I, P(V), P(P(D)), P(P(D)), P(P(D)), P(I)]
     for n in SYMBOLS:
         f = getattr(L, n)
         if n == "hp_launch_count":
@@ -343,3 +345,22 @@ class Context:
         hub = np.zeros((n, n))
         self._check(lib().hp_hubbard(self._ptr, _dptr(chi0), _dptr(chi), _dptr(hub)), "hp_hubbard")
         return chi0, chi, hub
+
+
+def batch_run(contexts):
+    """Every (q, J) response and chi0, chi, U/V of several independent cells at once, one host
+    thread per cell inside the library (each context should carry its own CUDA stream).
+    -> list of (chi0, chi, hub) per context."""
+    n = len(contexts)
+    dims = [c.query_sizes()["nchi"] for c in contexts]
+    out = [tuple(np.zeros((m, m)) for _ in range(3)) for m in dims]
+    PD = C.POINTER(C.c_double)
+    arr = [(PD * n)(*[_dptr(o[j]) for o in out]) for j in range(3)]
+    ptrs = (C.c_void_p * n)(*[c._ptr for c in contexts])
+    status = np.zeros(n, dtype=np.int32)
+    st = lib().hp_batch_run(n, ptrs, arr[0], arr[1], arr[2], _iptr(status))
+    if st != HP_OK:
+        bad = int(np.nonzero(status)[0][0]) if np.any(status) else 0
+        raise HPError(st, "hp_batch_run (cell %d)" % bad, contexts[bad].last_error())
+    return out
+

@@ -13,6 +13,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <thread>
 #include <cstring>
 
 #include "hp_internal.h"
@@ -686,6 +687,7 @@ extern "C" hp_status hp_setup(const double cell[9], int nspecies, const hp_speci
     if (opt) c->opt = *opt;
     else hp_default_options(&c->opt);
     c->st = (cudaStream_t)c->opt.cuda_stream;
+    if (cudaGetDevice(&c->device) != cudaSuccess) c->device = 0;
     hp_status s = setup_impl(c, cell, nspecies, sp, natoms, species_of, frac_pos, ecutwfc_ry, kmesh, qmesh);
     if (s != HP_OK) {
         fprintf(stderr, "hp_setup: %s\n", c->err.c_str());
@@ -1747,5 +1749,37 @@ extern "C" hp_status hp_hubbard(hp_ctx* c, double* chi0_out, double* chi_out, do
     if (chi0_out) memcpy(chi0_out, h.data(), sizeof(double) * n * n);
     if (chi_out) memcpy(chi_out, h.data() + (size_t)2 * n * n, sizeof(double) * n * n);
     if (hub_out) memcpy(hub_out, h.data() + (size_t)6 * n * n, sizeof(double) * n * n);
+    return HP_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// several independent cells at once: one host thread per cell, each on its context's stream
+// ------------------------------------------------------------------------------------------------
+extern "C" hp_status hp_batch_run(int ncells, hp_ctx* const* cells, double* const* chi0, double* const* chi,
+                                  double* const* hub, hp_status* status) {
+    if (ncells < 1 || !cells || !status) return HP_EINVAL;
+    for (int i = 0; i < ncells; ++i) {
+        if (!cells[i]) return HP_EINVAL;
+        for (int j = 0; j < i; ++j)
+            if (cells[j] == cells[i]) return HP_EINVAL;  // a context serves one thread
+    }
+    auto run = [&](int i) {
+        hp_ctx* c = cells[i];
+        if (cudaSetDevice(c->device) != cudaSuccess) {
+            status[i] = fail(c, HP_ECUDA, "hp_batch_run: cannot select the context's device");
+            return;
+        }
+        hp_status s = HP_OK;
+        for (size_t a = 0; a < c->hub_atoms.size() && s == HP_OK; ++a)
+            for (int iq = 0; iq < c->nq && s == HP_OK; ++iq) s = hp_response(c, iq, c->hub_atoms[a], nullptr, nullptr, nullptr);
+        if (s == HP_OK) s = hp_hubbard(c, chi0 ? chi0[i] : nullptr, chi ? chi[i] : nullptr, hub ? hub[i] : nullptr);
+        status[i] = s;
+    };
+    std::vector<std::thread> th;
+    th.reserve(ncells);
+    for (int i = 0; i < ncells; ++i) th.emplace_back(run, i);
+    for (auto& t : th) t.join();
+    for (int i = 0; i < ncells; ++i)
+        if (status[i] != HP_OK) return status[i];
     return HP_OK;
 }

@@ -757,12 +757,10 @@ static cudaError_t plane_reg_launch(const FusedArgs& a) {
     cudaError_t e = regfft_init();
     if (e != cudaSuccess) return e;
     const size_t smem = (size_t)Cfg::P * Cfg::per_plane;
-    static bool attr = false;
-    if (!attr) {
-        e = cudaFuncSetAttribute(plane_reg_kernel<V, N0, N1, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    // set once per kernel (a function-local static is initialised once, also with several host threads)
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(plane_reg_kernel<V, N0, N1, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (attr != cudaSuccess) return attr;
     const long long npairs = (long long)a.nc * a.N2;
     const int grid = cdivf(npairs, Cfg::P);
     const ProfMark pm = prof_start(a.st);
@@ -795,13 +793,9 @@ static cudaError_t plane_launch(const FusedArgs& a) {
     const SphereSet& S = *a.S;
     const BandList& L = *a.L;
     const size_t smem = 2 * sizeof(V) * N1 * (N0 + 1);
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(plane_kernel<V, N0, N1, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(plane_kernel<V, N0, N1, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (attr != cudaSuccess) return attr;
     dim3 g(a.N2, a.nc);
     using T = typename Scalar<V>::type;
     const ProfMark pm = prof_start(a.st);

@@ -362,6 +362,7 @@ hp_status nscf_states(hp_ctx* c, const std::vector<const KSphere*>& sph, const S
 struct hp_ctx {
     hp_options opt;
     cudaStream_t st = nullptr;
+    int device = 0;                    // CUDA device current at hp_setup
     std::string err;
     // cell
     double cell[9], bvec[9], omega = 0;

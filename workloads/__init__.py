@@ -242,3 +242,16 @@ def random_coefficients(seed, shape):
     """Seeded complex normal array (PCG64), used as trial vectors in parity tests."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def batch_small():
+    """A batch of small insulating cells of uneven sizes for the batching form's timing: the two-atom
+    cube at 8, 10 and 20 Ry on different q meshes and the spin-polarised rocksalt cell at 6 Ry
+    (stand-ins with known gaps; the seeded generator batch_cells leaves the electron count open)."""
+    return [tiny_q(ecut=8.0, grid=(12, 12, 12), kmesh=(2, 2, 2), qmesh=(2, 1, 1)),
+            tiny_lowcut(ecut=10.0, grid=(12, 12, 12), kmesh=(2, 2, 2), qmesh=(2, 2, 1)),
+            medium_small(ecut=6.0, grid=(16, 16, 16), kmesh=(2, 1, 1), qmesh=(2, 1, 1)),
+            tiny_q(ecut=8.0, grid=(12, 12, 12), kmesh=(2, 2, 2), qmesh=(2, 2, 2)),
+            tiny_lowcut(ecut=10.0, grid=(12, 12, 12), kmesh=(2, 2, 2), qmesh=(1, 1, 1)),
+            tiny()]
+
