@@ -122,7 +122,9 @@ typedef struct {
 /* Set-up (a1 of the hot path: the cell, spheres, grid maps, closed-form form factors).
  * cell: lattice vectors as rows (bohr), 9 doubles.  sp: nspecies species.  species_of: natoms
  * indices into sp.  frac_pos: natoms x 3 crystal coordinates.  kmesh, qmesh: Gamma-centred mesh
- * sizes; every q-mesh size must divide the k-mesh size along its axis (k+q stays on the k mesh).
+ * sizes.  Where k+q lies on the k mesh (k+q = k' + G0) the response reuses the states of k'; where
+ * it does not, hp_response computes the occupied states at k+q non-self-consistently at the
+ * ground-state potential (once per q) and evaluates the projector and Hubbard rows there.
  * opt may be NULL (defaults).  *out receives a new context owned by the caller (hp_destroy).
  * Errors: HP_EINVAL (bad sizes, a grid too small for the sphere, l out of range), HP_ECUDA,
  * HP_ENOMEM.  On error *out is NULL. */
