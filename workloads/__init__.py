@@ -195,7 +195,7 @@ def batch_cells(ncells=16, seed=BATCH_SEED):
     in {2, 3, 4}, q mesh per axis in {1, 2} dividing the k mesh.  Generator: numpy PCG64.
 
     The number of occupied bands is not drawn here (it depends on the band structure); each cell
-    carries ``nelec = None`` and the caller chooses it."""
+    carries ``nelec = 0`` and the caller chooses it."""
     rng = np.random.Generator(np.random.PCG64(seed))
     cells = []
     for ic in range(ncells):
