@@ -27,6 +27,15 @@
  *   - A lattice-periodic function u(r) = sum_G c(G) exp(iG.r) with sum |c|^2 = 1.
  *   - Work is issued on the stream given in hp_options.cuda_stream (0 = legacy default stream);
  *     every call synchronises that stream before returning host results.
+ *
+ * Environment (read at hp_setup unless noted; for tests and diagnostics, results are the same
+ * within the stated tolerances):
+ *   HP_NO_FUSED     use the batched 3D FFT with scatter/gather instead of the fused column/plane
+ *                   transforms (the fallback taken anyway for grids the fused kernels do not cover)
+ *   HP_FUSED_SMEM   fused transforms with shared-memory line FFTs instead of register-resident ones
+ *   HP_PROJ_ROWS    at most this many rows (<= 128) in one combined beta / P_v projection
+ *   HP_PROF_LOG     file receiving one line per timed launch while profiling (hp_profile_begin)
+ *   HP_VERBOSE      progress of the ground state, the k+q eigensolver and the response on stderr
  */
 #ifndef HP_H
 #define HP_H
