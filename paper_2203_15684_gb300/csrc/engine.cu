@@ -1503,7 +1503,28 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
             CK(cudaMemsetAsync(c->d_drho_pm, 0, sizeof(double2) * ndv, c->st));
             const int chunk = std::min(fused_batch(c, Sq, rows), mixed ? 2 * c->grid_cap : c->grid_cap);
             if ((s = ensure_colbuf(c, sizeof(double2) * (size_t)chunk * c->N[2] * Sq.ncmax)) != HP_OK) return s;
-            for (int c0 = 0; c0 < rows; c0 += chunk) {
+            FusedArgs probe = fused_args(c, Sq, Lall);
+            const bool fdrho = v32 && fused_drho_supported(probe);
+            if (fdrho) {
+                // FP32 form: Delta u(r) stays on chip; group sums of conj(u) Delta u, then the groups in order
+                int ng = 0;
+                for (int c0 = 0; c0 < rows; c0 += chunk) ng += fused_drho_groups(std::min(chunk, rows - c0));
+                if ((s = ensure_scratch(c, (size_t)ng * 2 * nr)) != HP_OK) return s;
+                int g0 = 0;
+                for (int c0 = 0; c0 < rows; c0 += chunk) {
+                    FusedArgs a = fused_args(c, Sq, Lall);
+                    a.c0 = c0;
+                    a.nc = std::min(chunk, rows - c0);
+                    a.X = c->d_x;
+                    a.vec32 = true;
+                    a.ur = c->d_ur32;
+                    CK(fused_col(true, true, a));
+                    CK(fused_drho(a, c->d_scratch, g0));
+                    g0 += fused_drho_groups(a.nc);
+                }
+                CK(k_drho_reduce(c->d_scratch, ng, nr, nspin, wrho, c->d_drho_pm, c->st));
+            }
+            for (int c0 = 0; c0 < rows && !fdrho; c0 += chunk) {
                 FusedArgs a = fused_args(c, Sq, Lall);
                 a.c0 = c0;
                 a.nc = std::min(chunk, rows - c0);

@@ -847,6 +847,150 @@ static cudaError_t plane_dispatch(int n0, int n1, const FusedArgs& a) {
     return cudaErrorInvalidValue;
 }
 
+// ------------------------------------------------------------------------------------------------
+// Delta rho with the inverse transform of Delta u fused in (FP32 form): CTA (z-plane, group of
+// kDrhoGroup bands).  Rounds of P bands: y- and x-inverse transforms of the bands' z-plane as in
+// op 1, then conj(u(r)) Delta u(r) per point; the group's sum per spin is kept in FP32 in shared memory and
+// written as FP64 to part[group][spin][z][y][x]; the groups are added in a fixed order afterwards.
+// Delta u(r) never goes to HBM.
+// ------------------------------------------------------------------------------------------------
+constexpr int kDrhoGroup = 32;
+
+// two resident CTAs per SM asked of the compiler for lines up to 36 points (no spills there)
+template <int N0, int N1>
+constexpr int drho_minb() { return (N0 <= 36 && N1 <= 36) ? 2 : 1; }
+
+template <int N0, int N1>
+__global__ void __launch_bounds__(PlaneCfg<float2, N0, N1>::NT, drho_minb<N0, N1>()) drho_plane_kernel(
+    const float2* __restrict__ colin, int ncmax, const int* __restrict__ kk, const int* __restrict__ spin,
+    const int* __restrict__ ur_row, int c0, int nc, const int* __restrict__ xtab, int N2,
+    const float2* __restrict__ ur, double2* __restrict__ part, int group0) {
+    using V = float2;
+    using Cfg = PlaneCfg<V, N0, N1>;
+    constexpr int P = Cfg::P, NT = Cfg::NT, LD = Cfg::LD, NP = N0 * N1, PS = N1 * LD;
+    constexpr int EPT = (NP + NT - 1) / NT;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    V* S = (V*)smraw;          // [P][N1][LD]
+    V* A = S + P * PS;         // [2][NP] the group's sums per spin (each point owned by one thread)
+    __shared__ int sp_of[P];
+    const int z = blockIdx.x, grp = blockIdx.y;
+    const int b0 = grp * kDrhoGroup, b1 = min(nc, b0 + kDrhoGroup);
+    const int tid = threadIdx.x;
+    for (int e = tid; e < 2 * NP; e += NT) A[e] = cmkf(0.f, 0.f);
+    for (int r0 = b0; r0 < b1; r0 += P) {
+        if (tid < P) sp_of[tid] = (r0 + tid < b1) ? spin[c0 + r0 + tid] : -1;
+        // y-inverse on the x-lines of each band's column runs (zero elsewhere)
+        if (tid < P * N0) {
+            const int p = tid / N0, x = tid % N0;
+            const int c = r0 + p;
+            if (c < b1) {
+                const int k = kk[c0 + c];
+                const int* t = xtab + ((long long)k * N0 + x) * 3;
+                const int j0 = t[0], cnt = t[1], y0 = t[2];
+                const V* src = colin + ((long long)c * N2 + z) * ncmax + j0;
+                V a[N1];
+#pragma unroll
+                for (int y = 0; y < N1; ++y) {
+                    int i = y - y0;
+                    if (i < 0) i += N1;
+                    a[y] = i < cnt ? src[i] : cmkf(0.f, 0.f);
+                }
+                if (cnt > 0) rfft<V, N1, +1>(a);
+                V* col = S + p * PS + x;
+#pragma unroll
+                for (int y = 0; y < N1; ++y) col[y * LD] = a[y];
+            }
+        }
+        __syncthreads();
+        // x-inverse, then conj(u(r)) Delta u(r) written back in place
+        if (tid < P * N1) {
+            const int p = tid / N1, y = tid % N1;
+            const int c = r0 + p;
+            if (c < b1) {
+                V* rowp = S + p * PS + y * LD;
+                V a[N0];
+#pragma unroll
+                for (int x = 0; x < N0; ++x) a[x] = rowp[x];
+                rfft<V, N0, +1>(a);
+                const V* u = ur + ((long long)ur_row[c0 + c] * N2 + z) * NP + y * N0;
+#pragma unroll
+                for (int x = 0; x < N0; ++x) {
+                    const V uv = u[x];
+                    rowp[x] = cmkf(uv.x * a[x].x + uv.y * a[x].y, uv.x * a[x].y - uv.y * a[x].x);
+                }
+            }
+        }
+        __syncthreads();
+        // the round's bands into the per-spin sums, in band order
+#pragma unroll
+        for (int j = 0; j < EPT; ++j) {
+            const int e = tid + j * NT;
+            if (e < NP) {
+                const int o = (e / N0) * LD + e % N0;
+                for (int p = 0; p < P; ++p) {
+                    const int sp = sp_of[p];
+                    if (sp < 0) break;
+                    A[sp * NP + e] = cadd(A[sp * NP + e], S[p * PS + o]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+    const long long nr = (long long)NP * N2;
+#pragma unroll
+    for (int j = 0; j < EPT; ++j) {
+        const int e = tid + j * NT;
+        if (e < NP) {
+            const long long r = (long long)z * NP + e;
+            const V s0 = A[e], s1 = A[NP + e];
+            part[((long long)(group0 + grp) * 2) * nr + r] = cmk((double)s0.x, (double)s0.y);
+            part[((long long)(group0 + grp) * 2 + 1) * nr + r] = cmk((double)s1.x, (double)s1.y);
+        }
+    }
+}
+
+template <int N0, int N1>
+static cudaError_t drho_plane_launch(const FusedArgs& a, double2* part, int group0) {
+    using Cfg = PlaneCfg<float2, N0, N1>;
+    if constexpr (!Cfg::ok) {
+        return cudaErrorInvalidValue;
+    } else {
+        const SphereSet& S = *a.S;
+        const BandList& L = *a.L;
+        cudaError_t e = regfft_init();
+        if (e != cudaSuccess) return e;
+        const size_t smem = ((size_t)Cfg::P * N1 * Cfg::LD + 2 * (size_t)N0 * N1) * sizeof(float2);
+        static const cudaError_t attr =
+            cudaFuncSetAttribute(drho_plane_kernel<N0, N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (attr != cudaSuccess) return attr;
+        dim3 g(a.N2, (a.nc + kDrhoGroup - 1) / kDrhoGroup);
+        drho_plane_kernel<N0, N1><<<g, Cfg::NT, smem, a.st>>>((const float2*)a.colA, S.ncmax, L.d_k, L.d_spin, L.d_row,
+                                                               a.c0, a.nc, S.d_xtab, a.N2, (const float2*)a.ur, part,
+                                                               group0);
+        HP_LAUNCHED();
+        return cudaGetLastError();
+    }
+}
+
+int fused_drho_groups(int nc) { return (nc + kDrhoGroup - 1) / kDrhoGroup; }
+
+bool fused_drho_supported(const FusedArgs& a) {
+    const int n0 = a.N0, n1 = a.N1;
+    const bool sizes = (n0 == n1 && (n0 == 10 || n0 == 12 || n0 == 15 || n0 == 16 || n0 == 18 || n0 == 20 ||
+                                     n0 == 24 || n0 == 36 || n0 == 45)) ||
+                       (n0 == 72 && n1 == 45);
+    return sizes && a.reg && a.S->d_xtab && a.S->xtab_n0 == n0;
+}
+
+cudaError_t fused_drho(const FusedArgs& a, double2* part, int group0) {
+#define HP_DR(A0, A1) \
+    if (a.N0 == A0 && a.N1 == A1) return drho_plane_launch<A0, A1>(a, part, group0);
+    HP_DR(10, 10) HP_DR(12, 12) HP_DR(15, 15) HP_DR(16, 16) HP_DR(18, 18) HP_DR(20, 20) HP_DR(24, 24)
+    HP_DR(36, 36) HP_DR(45, 45) HP_DR(72, 45)
+#undef HP_DR
+    return cudaErrorInvalidValue;
+}
+
 bool fused_supported(const int N[3]) {
     auto colok = [](int n) { return n == 10 || n == 12 || n == 15 || n == 16 || n == 18 || n == 20 || n == 24 || n == 36 || n == 45; };
     auto plok = [](int a, int b) {

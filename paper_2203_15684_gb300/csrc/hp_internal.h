@@ -227,6 +227,9 @@ cudaError_t k_formfactor(const double* kcart, int nk, const int* miller, const i
                          const double* bvec, int nrow, const int* row_atom, const int* row_l, const int* row_m,
                          const double* row_width, const double* row_pref, const double* tau, double2* out,
                          cudaStream_t st);
+// drho[s][r] += weight * sum over the nsplit partial sums part[slice][s][r] (fixed order)
+cudaError_t k_drho_reduce(const double2* part, int nsplit, int nr, int nspin, double weight, double2* drho,
+                          cudaStream_t st);
 cudaError_t k_drho_acc(const double2* ur, const int* ur_row_of_item, const double2* xr, int nc, int nr,
                        const BandList& L, int c0, double weight, int nspin, double2* drho, double2* part,
                          size_t part_elems, cudaStream_t st);
@@ -331,6 +334,11 @@ void prof_stop(const ProfMark& m, int fam, cudaStream_t st, double flops, double
 bool fused_supported(const int N[3]);
 cudaError_t fused_col(bool fp32, bool inv, const FusedArgs& a);
 cudaError_t fused_plane(bool fp32, int op, const FusedArgs& a);
+// Delta rho of the FP32 form with the inverse plane transform fused in: partial sums of groups of
+// bands, part[group0 + g][spin][z][y][x] (FP64); the groups are then added by k_drho_reduce
+bool fused_drho_supported(const FusedArgs& a);
+int fused_drho_groups(int nc);
+cudaError_t fused_drho(const FusedArgs& a, double2* part, int group0);
 cudaError_t k_to_planes_real(const double* a, double* b, const int N[3], int nvec, cudaStream_t st);
 cudaError_t k_to_planes_c(const double2* a, double2* b, const int N[3], int nvec, cudaStream_t st);
 cudaError_t k_from_planes_c(const double2* b, double2* a, const int N[3], int nvec, cudaStream_t st);

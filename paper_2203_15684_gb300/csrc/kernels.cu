@@ -1140,6 +1140,13 @@ static cudaError_t drho_acc_launch(const V* ur, const int* ur_row, const V* xr, 
     return cudaGetLastError();
 }
 
+cudaError_t k_drho_reduce(const double2* part, int nsplit, int nr, int nspin, double weight, double2* drho,
+                          cudaStream_t st) {
+    drho_reduce_kernel<<<cdiv((long long)nspin * nr, 256), 256, 0, st>>>(part, nsplit, nr, nspin, weight, drho);
+    HP_LAUNCHED();
+    return cudaGetLastError();
+}
+
 cudaError_t k_drho_acc(const double2* ur, const int* ur_row_of_item, const double2* xr, int nc, int nr,
                        const BandList& L, int c0, double weight, int nspin, double2* drho, double2* part,
                        size_t part_elems, cudaStream_t st) {

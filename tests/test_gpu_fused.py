@@ -52,7 +52,7 @@ def test_route_matches_oracle(monkeypatch, grid, route):
     assert info["iterations"] > 2
 
 
-@pytest.mark.parametrize("route", ["register", "shared"])
+@pytest.mark.parametrize("route", ["register", "shared", "fft3d"])
 def test_mixed_routes_agree_with_fp64(monkeypatch, route):
     """Mixed form through both fused routes: Delta n within 1e-5 of max|Delta n| of the FP64
     oracle, the bar the mixed form's chi is held to."""
