@@ -219,10 +219,6 @@ cudaError_t k_cg_step(const BandList& L, const SphereSet& S, double2* x, double2
                       int ld, double* pap, double* rz, double* rr, cudaStream_t st);
 cudaError_t k_cg_step(const BandList& L, const SphereSet& S, float2* x, float2* r, float2* p, const float2* ap,
                       int ld, double* pap, double* rz, double* rr, cudaStream_t st);
-cudaError_t k_rows_axpby(const BandList& L, const SphereSet& S, double a, const double2* X, double b,
-                         double2* Y, int ld, cudaStream_t st);
-cudaError_t k_gather_kq(const int* map, const int* npw_kq, const int* kprime, int nk, int nspin, int nocc,
-                        int ld, const double2* psi, int nbnd, double2* ukq, cudaStream_t st);
 cudaError_t k_formfactor(const double* kcart, int nk, const int* miller, const int* npw, int ld,
                          const double* bvec, int nrow, const int* row_atom, const int* row_l, const int* row_m,
                          const double* row_width, const double* row_pref, const double* tau, double2* out,

@@ -940,53 +940,7 @@ cudaError_t k_cg_step(const BandList& L, const SphereSet& S, float2* x, float2* 
     return cg_step_launch<float2>(L, S, x, r, p, ap, ld, pap, rz, rr, st);
 }
 
-// Y = a X + b Y on the rows of the list (full padded rows)
-__global__ void rows_axpby_kernel(const int* __restrict__ row, double a, const double2* __restrict__ X, double b,
-                                  double2* __restrict__ Y, int ld) {
-    const int c = blockIdx.y;
-    const int G = blockIdx.x * blockDim.x + threadIdx.x;
-    if (G >= ld) return;
-    const long long o = (long long)row[c] * ld + G;
-    const double2 x = X ? X[o] : cmk(0.0, 0.0);
-    const double2 y = Y[o];
-    Y[o] = cmk(a * x.x + b * y.x, a * x.y + b * y.y);
-}
 
-cudaError_t k_rows_axpby(const BandList& L, const SphereSet& S, double a, const double2* X, double b, double2* Y,
-                         int ld, cudaStream_t st) {
-    if (L.nb <= 0) return cudaSuccess;
-    dim3 g(cdiv(ld, 128), L.nb);
-    rows_axpby_kernel<<<g, 128, 0, st>>>(L.d_row, a, X, b, Y, ld);
-    HP_LAUNCHED();
-    (void)S;
-    return cudaGetLastError();
-}
-
-// u_{k+q}[s][k][v][G] = psi[s][k'][v][map[k][G]]  (k+q = k' + G0 re-indexing), zero padding
-__global__ void gather_kq_kernel(const int* __restrict__ map, const int* __restrict__ npw_kq,
-                                 const int* __restrict__ kprime, int nk, int nocc, int ld,
-                                 const double2* __restrict__ psi, int nbnd, double2* __restrict__ ukq) {
-    const int item = blockIdx.y;  // (s * nk + k) * nocc + v
-    const int v = item % nocc;
-    const int sk = item / nocc;
-    const int k = sk % nk, s = sk / nk;
-    const int G = blockIdx.x * blockDim.x + threadIdx.x;
-    if (G >= ld) return;
-    double2 z = cmk(0.0, 0.0);
-    if (G < npw_kq[k]) {
-        const long long src = ((long long)(s * nk + kprime[k]) * nbnd + v) * ld + map[(long long)k * ld + G];
-        z = psi[src];
-    }
-    ukq[(long long)item * ld + G] = z;
-}
-
-cudaError_t k_gather_kq(const int* map, const int* npw_kq, const int* kprime, int nk, int nspin, int nocc, int ld,
-                        const double2* psi, int nbnd, double2* ukq, cudaStream_t st) {
-    dim3 g(cdiv(ld, 128), nspin * nk * nocc);
-    gather_kq_kernel<<<g, 128, 0, st>>>(map, npw_kq, kprime, nk, nocc, ld, psi, nbnd, ukq);
-    HP_LAUNCHED();
-    return cudaGetLastError();
-}
 
 // ------------------------------------------------------------------------------------------------
 // closed-form atomic form factors <k+G|f_lm>:
