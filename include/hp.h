@@ -40,6 +40,8 @@
 #ifndef HP_H
 #define HP_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -54,8 +56,8 @@ typedef enum {
     HP_ENOTCONV = 4,    /* an iteration hit its cap; partial results are filled in */
     HP_ENUMERIC = 5,    /* NaN/Inf met in an FP64 scalar */
     HP_ECUDA = 6,       /* a CUDA runtime call failed (message in hp_last_error) */
-    HP_ETIMEOUT = 7,    /* reserved: a bounded device wait ran out */
-    HP_ESINGULAR = 8,   /* chi_0 or chi could not be inverted (condition number > 1e12) */
+    HP_ETIMEOUT = 7,    /* a bounded device-side wait ran out (hp_options.wait_timeout_s) */
+    HP_ESINGULAR = 8,   /* chi_0 or chi is singular or its 1-norm condition number exceeds 1e10 */
     HP_ENOGAP = 9,      /* the ground state has no gap (<= 1e-4 Ha) at the fixed band count */
     HP_ENOTIMPL = 10    /* the requested form is not available */
 } hp_status;
@@ -96,6 +98,21 @@ typedef struct {
                              * ||r|| <= max(cg_tol, theta ||b||), theta = min(1e-2, cg_adapt x the
                              * previous iteration's relative Hxc residual); 0 = always cg_tol
                              * (default 0.001).  The first iteration (chi_0) always uses cg_tol. */
+    double mixed_floor;     /* mixed form only: the response SCF also stops once the residual and the
+                             * change of the traces are below mixed_floor x the response potential and
+                             * x the largest trace (the FP32 noise floor; default 3e-7) */
+    double wait_timeout_s;  /* bound on every device-side wait of the library's kernels (mbarrier polls
+                             * of the tensor-core contractions): a wait that runs this long (about; it
+                             * is counted in polls) makes the kernel record an error flag and return,
+                             * and the call fails with HP_ETIMEOUT.  Default 2 s. */
+    /* Device memory.  When dev_alloc is set every device buffer of the context comes from
+     * dev_alloc(bytes, alloc_user) (NULL = out of memory) and goes back through
+     * dev_free(ptr, alloc_user); the Python binding registers PyTorch's caching allocator here.
+     * Both NULL: cudaMalloc / cudaFree.  The library frees a buffer only after the work that uses
+     * it has finished on the context's stream. */
+    void* (*dev_alloc)(size_t bytes, void* user);
+    void (*dev_free)(void* ptr, void* user);
+    void* alloc_user;
 } hp_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -125,10 +142,25 @@ typedef struct {
     double residual;        /* final rms of dV_out - dV_in */
     double dchi;            /* final change of the response traces */
     double seconds;
+    int stagnated;          /* mixed form: 1 when the SCF stopped because its residual had not fallen for
+                             * three iterations while below 1e-5 of the response potential (the FP32
+                             * noise floor) rather than on the mixed_floor test; 0 otherwise */
 } hp_resp_info;
 
+/* One inter-site pair of hp_hubbard's V list: Hubbard atom s of the primitive cell (index into the
+ * Hubbard-atom list) and its neighbour (l', s') of the q-mesh supercell (chi index l' * nhub_atoms
+ * + s'), their distance in bohr and V in eV. */
+typedef struct {
+    int s, jchi;
+    double dist;
+    double V;
+} hp_pairV;
+
 /* ------------------------------------------------------------------------------------------ */
-/* Set-up (a1 of the hot path: the cell, spheres, grid maps, closed-form form factors).
+/* Set-up (a1 of the hot path: the cell, spheres, grid maps, closed-form form factors).  The paper's
+ * method starts from the cell, the pseudopotentials (here the model species), the cutoff and the
+ * k and q meshes of the ground-state and linear-response runs (Sec. 3.1-3.2; the q mesh images the
+ * supercell of Eq. occ_matrix_response_lp_1).
  * cell: lattice vectors as rows (bohr), 9 doubles.  sp: nspecies species.  species_of: natoms
  * indices into sp.  frac_pos: natoms x 3 crystal coordinates.  kmesh, qmesh: Gamma-centred mesh
  * sizes.  Where k+q lies on the k mesh (k+q = k' + G0) the response reuses the states of k'; where
@@ -141,6 +173,9 @@ hp_status hp_setup(const double cell[9], int nspecies, const hp_species* sp, int
                    const int* species_of, const double* frac_pos, double ecutwfc_ry,
                    const int kmesh[3], const int qmesh[3], const hp_options* opt, hp_ctx** out);
 
+/* Sizes of the context: meshes, bands, grid, Hubbard atoms, and the dimension N_H N_q of chi and
+ * chi_0 (Sec. 3.2: the response matrices are N_H^sc x N_H^sc with N_H^sc = N_H N_q).  Output
+ * buffers of hp_response / hp_hubbard are sized from it.  Errors: HP_EINVAL (NULL pointer). */
 hp_status hp_query_sizes(const hp_ctx* ctx, hp_sizes* out);
 
 /* Switches the precision form of later hp_response calls (HP_PRECISION_FP64 or _MIXED) without
@@ -155,12 +190,17 @@ hp_status hp_sphere(const hp_ctx* ctx, int ik, int* npw, int* miller);
  * nhub_atoms Hubbard atoms in order.  Either pointer may be NULL. */
 hp_status hp_hubbard_atoms(const hp_ctx* ctx, int* atom_index, int* mdim);
 
-/* Ground state by the library: fixed-occupation SCF on the GPU (LDA/LSDA), nelec electrons,
- * nspin 1 or 2; init_moment: natoms signs (+1, -1, 0) of the starting magnetisation, NULL for
- * none.  Starting density: uniform nelec/Omega, for nspin = 2 split as rho0/2 (1 +- s(r)),
+/* Ground state by the library (the unperturbed state the response starts from, Sec. 3.1: occupied
+ * u_vk, eps_vk, the spin densities and the Hubbard occupations of Eq. occ_matrix_0): fixed-occupation
+ * SCF on the GPU (LDA/LSDA), nelec electrons, nspin 1 or 2; init_moment: natoms signs (+1, -1, 0)
+ * of the starting magnetisation, NULL for none.  tot_mag: the fixed total magnetisation (occupied
+ * bands per spin (nelec +- tot_mag) / 2, the paper's tot_magnetization of a magnetic insulator,
+ * Sec. 5.2); only tot_mag = 0 (equal band counts) is built, any other value returns HP_ENOTIMPL.
+ * Starting density: uniform nelec/Omega, for nspin = 2 split as rho0/2 (1 +- s(r)),
  * s(r) = clip(sum_I m_I 0.9 exp(-|r - tau_I|^2 / 2), -0.9, 0.9).
- * Errors: HP_EINVAL, HP_ENOTCONV, HP_ENOGAP (the state is kept; hp_response refuses it). */
-hp_status hp_ground_state(hp_ctx* ctx, double nelec, int nspin, const int* init_moment,
+ * Errors: HP_EINVAL, HP_ENOTIMPL, HP_ENOTCONV, HP_ENOGAP (the state is kept; hp_response refuses
+ * it). */
+hp_status hp_ground_state(hp_ctx* ctx, double nelec, int nspin, const int* init_moment, double tot_mag,
                           hp_gs_info* info);
 
 /* Imports a ground state (so that the response can be checked on identical inputs).
@@ -188,8 +228,10 @@ hp_status hp_get_ground_state(const hp_ctx* ctx, double* eps, double* rho, doubl
  * that device current (cudaGetSymbolAddress) and caches it.  Every call reuses the same array and
  * leaves its contents behind; the call clears what it needs cleared.  Calls whose work overlaps on
  * the GPU (other streams, other host threads) race on the array and must be serialised by the
- * caller.  Errors: HP_EINVAL (bad arguments, or nb too large for the fixed scratch on this grid:
- * call it on fewer bands), HP_ESTATE (no ground state), HP_ECUDA. */
+ * caller.  The current device must be the context's device (the one current at hp_setup) and the
+ * stream must belong to it.  Errors: HP_EINVAL (bad arguments, another device current, or nb too
+ * large for the fixed scratch on this grid: call it on fewer bands), HP_ESTATE (no ground state),
+ * HP_ECUDA. */
 hp_status hp_apply_h_noalloc(hp_ctx* ctx, int ik, int spin, int nb, const double* psi_dev, double* out_dev,
                              void* stream);
 
@@ -202,6 +244,22 @@ hp_status hp_get_wavefunctions(const hp_ctx* ctx, double* psi);
  * hp_sphere order): out = H psi with H = T + V_loc + V_Hxc,s + V_NL (needs a ground state). */
 hp_status hp_apply_h(hp_ctx* ctx, int ik, int spin, int nb, const double* psi, double* out);
 
+/* Wavefunction sphere at k+q for mesh point ik and q point iq, in the coefficient order the
+ * response (hp_response, hp_apply_sternheimer) uses for vectors at k+q: *npw receives its size; if
+ * miller != NULL it receives npw x 3 Miller indices G with |k+q+G|^2 <= ecutwfc.  Where k+q = k' + G0
+ * lies on the k mesh this is the sphere of k' shifted by -G0 in the order of k'.  Errors: HP_EINVAL. */
+hp_status hp_sphere_kq(const hp_ctx* ctx, int iq, int ik, int* npw, int* miller);
+
+/* The operator of the q-specific Sternheimer equation (Eq. LRKSeq_lp, left-hand side),
+ * out_b = (H_k+q,spin + alpha O_k+q,spin - eps_b) psi_b, with O the projector on the occupied states
+ * at k+q (Eq. proj_v) and alpha = 2 (max - min) of the occupied ground-state energies, applied to
+ * nb host vectors of hp_sphere_kq(iq, ik) size (complex, packed) through exactly the kernels and
+ * the precision form hp_response uses (fused column/plane transforms where the grid allows them,
+ * FP32 vectors and projections in the mixed form).  eps: nb shifts (Ha).  Needs a ground state.
+ * Allocates its device buffers per call.  Errors: HP_EINVAL, HP_ESTATE, HP_ECUDA. */
+hp_status hp_apply_sternheimer(hp_ctx* ctx, int iq, int ik, int spin, int nb, const double* eps,
+                               const double* psi, double* out);
+
 /* One (q, J) response (hot path a1-a10): iq indexes the q mesh, atom is the index of the
  * perturbed Hubbard atom in the set-up atom list.  dn0 / dn (may be NULL) receive the bare and
  * self-consistent Delta_q n^{s sigma}_{m1 m2} as complex [nhub_atoms][nspin][mmax][mmax]
@@ -210,11 +268,20 @@ hp_status hp_apply_h(hp_ctx* ctx, int ik, int spin, int nb, const double* psi, d
  * HP_ENOTCONV (partial data written), HP_ENUMERIC. */
 hp_status hp_response(hp_ctx* ctx, int iq, int atom, double* dn0, double* dn, hp_resp_info* info);
 
-/* Post-processing (a11): chi0, chi: real nchi x nchi (row-major, index (l, s) -> l*nhub_atoms+s,
- * l the supercell cell (l1*n2 + l2)*n3 + l3); hub: (chi0^-1 - chi^-1) in eV (U on the diagonal,
- * V off it).  Any pointer may be NULL.  Needs every (q, J) column (HP_ESTATE otherwise).
- * Errors: HP_ESINGULAR. */
-hp_status hp_hubbard(hp_ctx* ctx, double* chi0, double* chi, double* hub);
+/* Post-processing (a11): the q-sum with phases (Eq. occ_matrix_response_lp_1) into chi_0 and chi
+ * (Eq. chi), their inverses and U, V (Eqs. U_def, V_def).
+ * chi0, chi: real nchi x nchi (row-major, index (l, s) -> l*nhub_atoms+s, l the supercell cell
+ * (l1*n2 + l2)*n3 + l3); hub: (chi0^-1 - chi^-1) in eV (U on the diagonal, V off it).
+ * U: nhub_atoms on-site values U^s = hub[s][s] in eV.  V, nV: the inter-site V of every Hubbard atom
+ * s of the primitive cell to its nearest Hubbard neighbours of another species in the q-mesh
+ * supercell: every (l', s') at the shortest minimum-image distance d_min of that species class or
+ * within d_min + 6e-4 bohr of it (the paper's dist_thr default, Appendix B); *nV is the capacity
+ * of V on input and the number of pairs on output (all pairs are counted even when they do not fit;
+ * HP_EINVAL then).  Any output pointer may be NULL (nV with V).  Needs every (q, J) column
+ * (HP_ESTATE otherwise).  chi0 and chi are written even when one of them is singular or has a
+ * 1-norm condition number above 1e10; U, V and hub are then not written and the call returns
+ * HP_ESINGULAR. */
+hp_status hp_hubbard(hp_ctx* ctx, double* chi0, double* chi, double* hub, double* U, hp_pairV* V, int* nV);
 
 /* Several independent cells at once (the batching form; the paper's code runs one system per job,
  * so there is no counterpart there).  For every context cells[0 .. ncells-1], each set up with its
@@ -273,6 +340,10 @@ hp_status hp_profile_end(hp_kernel_stats* stats);
 /* Number of CUDA kernels this library has launched in this process (monotonic counter). */
 long long hp_launch_count(void);
 
+/* Number of device allocations this library has made in this process, through cudaMalloc or a
+ * registered dev_alloc (monotonic counter; no counterpart in the paper). */
+long long hp_alloc_count(void);
+
 /* Host-only self-test of the FFT engine's stage logic (runs the same Stockham code on the CPU).
  * in/out: nlines x n complex; sign -1 forward exp(-2 pi i jk/n), +1 backward (unnormalised). */
 hp_status hp_selftest_fft_host(int n, int nlines, int sign, const double* in, double* out);
@@ -282,6 +353,14 @@ hp_status hp_selftest_fft_host(int n, int nlines, int sign, const double* in, do
  * w: nbatch x n eigenvalues ascending; V: nbatch n x n, eigenvectors in the columns.  n <= 512.
  * Allocates its own device buffers.  Errors: HP_EINVAL, HP_ECUDA. */
 hp_status hp_selftest_eigh(int n, int nbatch, const double* A, double* w, double* V);
+
+/* Device self-test of the LDA kernel of the ground state and the response (Slater exchange +
+ * Perdew-Zunger 1981 correlation, von Barth-Hedin spin interpolation): for n grid points and spin
+ * densities rho (nspin x n), vxc receives nspin x n potentials and fxc the kernel f_xc (n values
+ * for nspin = 1; 3 x n for nspin = 2: f_up,up, f_up,down, f_down,down), the same kernel as the
+ * response's Delta V_xc = sum_s' f_ss' Delta rho_s' (Sec. 2.3, the response Hxc potential).
+ * Allocates its own device buffers.  Errors: HP_EINVAL, HP_ECUDA. */
+hp_status hp_selftest_xc(int n, int nspin, const double* rho, double* vxc, double* fxc);
 
 /* Device self-test of the integer-operation FP64 <-> FP32 conversions used in the FP32 form's hot
  * loops (no counterpart in the paper).  For n host values in[i]: f[i] = FP64 -> FP32 rounded to

@@ -37,6 +37,15 @@ from .hamiltonian import apply_h, from_grid, hartree_r, to_grid
 from .mixing import Broyden
 
 
+def sternheimer_operator(model, kdq, vr, Cq, alpha, eps_v, X):
+    """Left-hand side of Eq. LRKSeq_lp on the columns of X (npw_k+q, nb):
+    (H_k+q + alpha O_k+q - eps_v) X with O_k+q = Cq Cq^H the projector on the occupied states at
+    k+q (Eq. proj_v, Cq (npw_k+q, nocc)), ``vr`` the spin's local potential on the grid and eps_v
+    one shift per column."""
+    HX = apply_h(model, kdq, vr, X)
+    return HX + alpha * (Cq @ (Cq.conj().T @ X)) - X * np.asarray(eps_v)[None, :]
+
+
 class ResponseContext:
     """Everything a (q, J) solve needs that does not depend on J: k+q states, real-space u_k,
     f_xc, alpha."""
@@ -62,11 +71,8 @@ class ResponseContext:
 
     def apply_A(self, s, ik, X, eps_v):
         """(H_k+q + alpha O_k+q - eps_v) X for the columns of X (per-column eps_v)."""
-        m, gs = self.model, self.gs
         kdq, Cq, _ = self.kq[ik]
-        HX = apply_h(m, kdq, gs.vr(s), X)
-        Cqs = Cq[s]
-        return HX + self.alpha * (Cqs @ (Cqs.conj().T @ X)) - X * eps_v[None, :]
+        return sternheimer_operator(self.model, kdq, self.gs.vr(s), Cq[s], self.alpha, eps_v, X)
 
     def dv_times_u(self, s, ik, dv):
         """Delta V_Hxc,q(r) u_k(r), taken to the k+q sphere."""

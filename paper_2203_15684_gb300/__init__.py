@@ -36,11 +36,17 @@ class Species(C.Structure):
                 ("proj_width", C.c_double), ("l_hub", C.c_int), ("hub_width", C.c_double)]
 
 
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("cg_tol", C.c_double), ("cg_maxiter", C.c_int), ("scf_tol", C.c_double),
                 ("conv_thr_chi", C.c_double), ("niter_max", C.c_int), ("nmix", C.c_int), ("alpha_mix", C.c_double),
                 ("gs_tol", C.c_double), ("gs_maxiter", C.c_int), ("fft_grid", C.c_int * 3), ("band_batch", C.c_int),
-                ("cuda_stream", C.c_void_p), ("cg_adapt", C.c_double)]
+                ("cuda_stream", C.c_void_p), ("cg_adapt", C.c_double), ("mixed_floor", C.c_double),
+                ("wait_timeout_s", C.c_double), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
+                ("alloc_user", C.c_void_p)]
 
 
 class Sizes(C.Structure):
@@ -55,7 +61,11 @@ class GsInfo(C.Structure):
 
 class RespInfo(C.Structure):
     _fields_ = [("iterations", C.c_int), ("cg_iterations", C.c_longlong), ("hpsi", C.c_longlong),
-                ("residual", C.c_double), ("dchi", C.c_double), ("seconds", C.c_double)]
+                ("residual", C.c_double), ("dchi", C.c_double), ("seconds", C.c_double), ("stagnated", C.c_int)]
+
+
+class PairV(C.Structure):
+    _fields_ = [("s", C.c_int), ("jchi", C.c_int), ("dist", C.c_double), ("V", C.c_double)]
 
 
 class KernelStats(C.Structure):
@@ -71,7 +81,7 @@ SYMBOLS = ["hp_default_options", "hp_setup", "hp_query_sizes", "hp_sphere", "hp_
            "hp_set_ground_state", "hp_get_ground_state", "hp_apply_h", "hp_response", "hp_hubbard", "hp_last_error",
            "hp_destroy", "hp_selftest_fft_host", "hp_selftest_eigh", "hp_get_wavefunctions", "hp_profile_begin",
            "hp_profile_end", "hp_launch_count", "hp_apply_h_noalloc", "hp_set_precision", "hp_selftest_convert",
-           "hp_batch_run"]
+           "hp_batch_run", "hp_alloc_count", "hp_sphere_kq", "hp_apply_sternheimer", "hp_selftest_xc"]
 
 
 def lib():
@@ -90,12 +100,12 @@ def lib():
     L.hp_query_sizes.argtypes = [V, P(Sizes)]
     L.hp_sphere.argtypes = [V, I, P(I), P(I)]
     L.hp_hubbard_atoms.argtypes = [V, P(I), P(I)]
-    L.hp_ground_state.argtypes = [V, D, I, P(I), P(GsInfo)]
+    L.hp_ground_state.argtypes = [V, D, I, P(I), D, P(GsInfo)]
     L.hp_set_ground_state.argtypes = [V, I, D, P(D), P(D), P(D), P(D)]
     L.hp_get_ground_state.argtypes = [V, P(D), P(D), P(D)]
     L.hp_apply_h.argtypes = [V, I, I, I, P(D), P(D)]
     L.hp_response.argtypes = [V, I, I, P(D), P(D), P(RespInfo)]
-    L.hp_hubbard.argtypes = [V, P(D), P(D), P(D)]
+    L.hp_hubbard.argtypes = [V, P(D), P(D), P(D), P(D), P(PairV), P(I)]
     L.hp_last_error.argtypes = [V]
     L.hp_last_error.restype = C.c_char_p
     L.hp_destroy.argtypes = [V]
@@ -111,9 +121,13 @@ def lib():
     L.hp_set_precision.argtypes = [V, I]
     L.hp_selftest_convert.argtypes = [C.c_longlong, P(D), P(C.c_float), P(D), P(C.c_float), P(D)]
     L.hp_batch_run.argtypes = [I, P(V), P(P(D)), P(P(D)), P(P(D)), P(I)]
+    L.hp_alloc_count.argtypes = []
+    L.hp_sphere_kq.argtypes = [V, I, I, P(I), P(I)]
+    L.hp_apply_sternheimer.argtypes = [V, I, I, I, I, P(D), P(D), P(D)]
+    L.hp_selftest_xc.argtypes = [I, I, P(D), P(D), P(D)]
     for n in SYMBOLS:
         f = getattr(L, n)
-        if n == "hp_launch_count":
+        if n in ("hp_launch_count", "hp_alloc_count"):
             f.restype = C.c_longlong
         elif n not in ("hp_default_options", "hp_last_error", "hp_destroy", "hp_profile_begin"):
             f.restype = I
@@ -197,12 +211,60 @@ def launch_count():
     return int(lib().hp_launch_count())
 
 
+def alloc_count():
+    """Device allocations the library has made in this process."""
+    return int(lib().hp_alloc_count())
+
+
+def selftest_xc(rho):
+    """LDA potential and kernel of the library on the GPU: rho (nspin, n) -> (vxc (nspin, n),
+    fxc (1 or 3, n))."""
+    rho = np.ascontiguousarray(rho, dtype=np.float64)
+    nspin, n = rho.shape
+    v = np.zeros_like(rho)
+    f = np.zeros((1 if nspin == 1 else 3, n))
+    st = lib().hp_selftest_xc(n, nspin, _dptr(rho), _dptr(v), _dptr(f))
+    if st != HP_OK:
+        raise HPError(st, "hp_selftest_xc")
+    return v, f
+
+
+class TorchAllocator:
+    """dev_alloc / dev_free callbacks that take the library's device buffers from PyTorch's caching
+    allocator on a given CUDA stream (argument marshalling only; the library decides what to
+    allocate)."""
+
+    def __init__(self, stream=None, device=None):
+        import torch
+
+        self._torch = torch
+        self.device = torch.cuda.current_device() if device is None else device
+        self.stream = stream
+        self.alloc_fn = ALLOC_FN(self._alloc)
+        self.free_fn = FREE_FN(self._free)
+
+    def _alloc(self, nbytes, user):
+        try:
+            return int(self._torch.cuda.caching_allocator_alloc(int(nbytes), self.device, self.stream))
+        except Exception:
+            return None
+
+    def _free(self, ptr, user):
+        try:
+            self._torch.cuda.caching_allocator_delete(int(ptr))
+        except Exception:
+            pass
+
+
 class Context:
     """An hp_ctx: one crystal, its ground state and its response columns."""
 
-    def __init__(self, cell, species, atoms, ecutwfc, kmesh, qmesh, options=None):
+    def __init__(self, cell, species, atoms, ecutwfc, kmesh, qmesh, options=None, torch_alloc=None):
+        """torch_alloc: take device memory from PyTorch's caching allocator (on the options' CUDA
+        stream); None = whenever torch sees a GPU."""
         L = lib()
         self._ptr = C.c_void_p()
+        self._alloc = None
         cell = np.ascontiguousarray(np.asarray(cell, dtype=np.float64).reshape(9))
         sp = (Species * len(species))()
         for i, s in enumerate(species):
@@ -213,15 +275,27 @@ class Context:
         km = np.ascontiguousarray(kmesh, dtype=np.int32)
         qm = np.ascontiguousarray(qmesh, dtype=np.int32)
         opt = options if options is not None else default_options()
+        if torch_alloc is None:
+            try:
+                import torch
+
+                torch_alloc = torch.cuda.is_available()
+            except ImportError:
+                torch_alloc = False
+        if torch_alloc:
+            self._alloc = TorchAllocator(stream=opt.cuda_stream or 0)
+            opt.dev_alloc = self._alloc.alloc_fn
+            opt.dev_free = self._alloc.free_fn
         st = L.hp_setup(_dptr(cell), len(species), sp, len(kinds), _iptr(kinds), _dptr(frac), float(ecutwfc),
                         _iptr(km), _iptr(qm), C.byref(opt), C.byref(self._ptr))
         if st != HP_OK:
             raise HPError(st, "hp_setup")
 
     @classmethod
-    def from_workload(cls, w, **opts):
+    def from_workload(cls, w, torch_alloc=None, **opts):
         opts.setdefault("fft_grid", w.get("grid"))
-        return cls(w["cell"], w["species"], w["atoms"], w["ecutwfc"], w["kmesh"], w["qmesh"], default_options(**opts))
+        return cls(w["cell"], w["species"], w["atoms"], w["ecutwfc"], w["kmesh"], w["qmesh"], default_options(**opts),
+                   torch_alloc=torch_alloc)
 
     # -------------------------------------------------------------------------------------------
     def _check(self, st, where, ok=(HP_OK,)):
@@ -234,7 +308,11 @@ class Context:
 
     def destroy(self):
         if self._ptr:
-            lib().hp_destroy(self._ptr)
+            import sys
+
+            # at interpreter exit PyTorch may already be gone: leave the buffers to the process exit
+            if not (self._alloc is not None and sys.is_finalizing()):
+                lib().hp_destroy(self._ptr)
             self._ptr = C.c_void_p()
 
     def __del__(self):
@@ -268,13 +346,13 @@ class Context:
         self._check(lib().hp_hubbard_atoms(self._ptr, _iptr(a), _iptr(m)), "hp_hubbard_atoms")
         return a, m
 
-    def ground_state(self, nelec, nspin, moments=None):
+    def ground_state(self, nelec, nspin, moments=None, tot_mag=0.0):
         info = GsInfo()
         mom = None
         if moments is not None:
             mom_a = np.ascontiguousarray(moments, dtype=np.int32)
             mom = _iptr(mom_a)
-        st = lib().hp_ground_state(self._ptr, float(nelec), int(nspin), mom, C.byref(info))
+        st = lib().hp_ground_state(self._ptr, float(nelec), int(nspin), mom, float(tot_mag), C.byref(info))
         self._check(st, "hp_ground_state")
         return {n: getattr(info, n) for n, _ in GsInfo._fields_}
 
@@ -339,12 +417,40 @@ class Context:
         return dn0, dn, {n: getattr(info, n) for n, _ in RespInfo._fields_}
 
     def hubbard(self):
-        n = self.query_sizes()["nchi"]
-        chi0 = np.zeros((n, n))
-        chi = np.zeros((n, n))
-        hub = np.zeros((n, n))
-        self._check(lib().hp_hubbard(self._ptr, _dptr(chi0), _dptr(chi), _dptr(hub)), "hp_hubbard")
-        return chi0, chi, hub
+        """-> (chi0, chi, hub): the supercell response matrices and (chi0^-1 - chi^-1) in eV."""
+        r = self.hubbard_parameters()
+        return r["chi0"], r["chi"], r["hub"]
+
+    def hubbard_parameters(self):
+        """-> dict(chi0, chi, hub, U (eV per Hubbard atom), V: list of (s, jchi, dist_bohr, V_eV))."""
+        s = self.query_sizes()
+        n, nh = s["nchi"], s["nhub_atoms"]
+        chi0, chi, hub, U = np.zeros((n, n)), np.zeros((n, n)), np.zeros((n, n)), np.zeros(nh)
+        cap = C.c_int(0)
+        self._check(lib().hp_hubbard(self._ptr, _dptr(chi0), _dptr(chi), _dptr(hub), _dptr(U), None, C.byref(cap)),
+                    "hp_hubbard")
+        pairs = (PairV * max(1, cap.value))()
+        self._check(lib().hp_hubbard(self._ptr, None, None, None, None, pairs, C.byref(cap)), "hp_hubbard")
+        V = [(p.s, p.jchi, p.dist, p.V) for p in pairs[: cap.value]]
+        return dict(chi0=chi0, chi=chi, hub=hub, U=U, V=V)
+
+    def sphere_kq(self, iq, ik):
+        """Miller indices (npw, 3) of the k+q sphere in the response's coefficient order."""
+        n = C.c_int()
+        self._check(lib().hp_sphere_kq(self._ptr, int(iq), int(ik), C.byref(n), None), "hp_sphere_kq")
+        m = np.zeros((n.value, 3), dtype=np.int32)
+        self._check(lib().hp_sphere_kq(self._ptr, int(iq), int(ik), C.byref(n), _iptr(m)), "hp_sphere_kq")
+        return m
+
+    def apply_sternheimer(self, iq, ik, spin, eps, psi):
+        """(H_k+q + alpha O_k+q - eps_b) psi_b through the response's own kernels; psi (nb, npw_k+q)."""
+        x = np.ascontiguousarray(psi, dtype=np.complex128)
+        e = np.ascontiguousarray(eps, dtype=np.float64).reshape(-1)
+        out = np.empty_like(x)
+        self._check(lib().hp_apply_sternheimer(self._ptr, int(iq), int(ik), int(spin), x.shape[0], _dptr(e),
+                                               _dptr(x.view(np.float64)), _dptr(out.view(np.float64))),
+                    "hp_apply_sternheimer")
+        return out
 
 
 def batch_run(contexts):

@@ -23,6 +23,7 @@ using namespace hp;
 namespace hp {
 
 std::atomic<long long> g_launches{0};
+std::atomic<long long> g_allocs{0};
 
 constexpr double kHaToEv = 27.211386245988;
 constexpr int kMmax = 5;
@@ -45,7 +46,7 @@ void dfree(hp_ctx* c, void* p) {
     if (!p) return;
     auto it = std::find(c->owned.begin(), c->owned.end(), p);
     if (it != c->owned.end()) c->owned.erase(it);
-    cudaFree(p);
+    dev_free_raw(c, p);
 }
 
 int good_fft_size(int n) {
@@ -457,13 +458,20 @@ extern "C" void hp_default_options(hp_options* o) {
     o->gs_maxiter = 200;
     o->band_batch = 0;
     o->cuda_stream = nullptr;
+    o->mixed_floor = 3e-7;
+    o->wait_timeout_s = 2.0;
+    o->dev_alloc = nullptr;
+    o->dev_free = nullptr;
+    o->alloc_user = nullptr;
 }
 
 extern "C" const char* hp_last_error(const hp_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
 extern "C" void hp_destroy(hp_ctx* c) {
     if (!c) return;
-    for (void* p : c->owned) cudaFree(p);
+    if (c->st) cudaStreamSynchronize(c->st);  // nothing of this context may still run on its buffers
+    else cudaDeviceSynchronize();
+    for (void* p : c->owned) dev_free_raw(c, p);
     c->owned.clear();
     fft_plan_destroy(c->fft);
     delete c;
@@ -477,8 +485,11 @@ static hp_status setup_impl(hp_ctx* c, const double cell[9], int nspecies, const
     for (int i = 0; i < 3; ++i) {
         if (kmesh[i] < 1 || qmesh[i] < 1) return fail(c, HP_EINVAL, "hp_setup: mesh sizes must be >= 1");
     }
-    if (c->opt.nmix < 0 || c->opt.nmix > 8 || !(c->opt.cg_tol > 0) || c->opt.niter_max < 1 || c->opt.cg_maxiter < 1)
-        return fail(c, HP_EINVAL, "hp_setup: options out of range (0 <= nmix <= 8, tolerances > 0)");
+    if (c->opt.nmix < 0 || c->opt.nmix > 8 || !(c->opt.cg_tol > 0) || c->opt.niter_max < 1 || c->opt.cg_maxiter < 1 ||
+        !(c->opt.mixed_floor >= 0) || !(c->opt.wait_timeout_s > 0))
+        return fail(c, HP_EINVAL, "hp_setup: options out of range (0 <= nmix <= 8, tolerances > 0, wait_timeout_s > 0)");
+    if ((c->opt.dev_alloc == nullptr) != (c->opt.dev_free == nullptr))
+        return fail(c, HP_EINVAL, "hp_setup: dev_alloc and dev_free must be given together");
     for (int s = 0; s < nspecies; ++s) {
         if (sp[s].l_proj < 0 || sp[s].l_proj > 2 || sp[s].l_hub > 2 || !(sp[s].width > 0) || !(sp[s].proj_width > 0) ||
             (sp[s].l_hub >= 0 && !(sp[s].hub_width > 0)))
@@ -591,7 +602,7 @@ static hp_status setup_impl(hp_ctx* c, const double cell[9], int nspecies, const
     // rows of one combined projection (at most the buffer's 128; HP_PROJ_ROWS lowers it)
     c->proj_rows_max = kPStride;
     if (const char* r = getenv("HP_PROJ_ROWS")) c->proj_rows_max = std::max(1, std::min(kPStride, atoi(r)));
-    CK(fft_plan_create(c->fft, c->N));
+    CK(fft_plan_create(c, c->fft, c->N));
     CK(dalloc(c, &c->d_bvec, 9));
     CK(h2d(c->d_bvec, c->bvec, 9, c->st));
     CK(dalloc(c, &c->d_tau, 3 * natoms));
@@ -1309,6 +1320,90 @@ double dev_dot(hp_ctx* c, const double2* a, const double2* b, long long n, cudaE
 
 }  // namespace
 
+// k+q for mesh point ik and q point iq: on the k mesh k+q = k' + G0 (kp >= 0), else kp = -1
+static void kq_point(const hp_ctx* c, int iq, int ik, int* kp, int g0[3]) {
+    const int qi[3] = {iq / (c->qmesh[1] * c->qmesh[2]), (iq / c->qmesh[2]) % c->qmesh[1], iq % c->qmesh[2]};
+    const int ki[3] = {ik / (c->kmesh[1] * c->kmesh[2]), (ik / c->kmesh[2]) % c->kmesh[1], ik % c->kmesh[2]};
+    if (c->kq_ks[(size_t)iq * c->nk + ik].npw > 0) {
+        *kp = -1;
+        g0[0] = g0[1] = g0[2] = 0;
+        return;
+    }
+    int j[3];
+    for (int d = 0; d < 3; ++d) {
+        const int x = (ki[d] * c->qmesh[d] + qi[d] * c->kmesh[d]) / c->qmesh[d];
+        j[d] = x % c->kmesh[d];
+        g0[d] = x / c->kmesh[d];
+    }
+    *kp = (j[0] * c->kmesh[1] + j[1]) * c->kmesh[2] + j[2];
+}
+
+extern "C" hp_status hp_sphere_kq(const hp_ctx* c, int iq, int ik, int* npw, int* miller) {
+    if (!c || !npw || iq < 0 || iq >= c->nq || ik < 0 || ik >= c->nk) return HP_EINVAL;
+    int kp, g0[3];
+    kq_point(c, iq, ik, &kp, g0);
+    const KSphere& s = kp >= 0 ? c->ks[kp] : c->kq_ks[(size_t)iq * c->nk + ik];
+    *npw = s.npw;
+    if (miller)
+        for (int i = 0; i < s.npw; ++i)
+            for (int d = 0; d < 3; ++d) miller[3 * i + d] = s.miller[3 * i + d] - g0[d];
+    return HP_OK;
+}
+
+extern "C" hp_status hp_apply_sternheimer(hp_ctx* c, int iq, int ik, int spin, int nb, const double* eps,
+                                          const double* psi, double* out) {
+    if (!c) return HP_EINVAL;
+    if (!c->have_gs) return fail(c, HP_ESTATE, "hp_apply_sternheimer: no ground state");
+    if (iq < 0 || iq >= c->nq || ik < 0 || ik >= c->nk || spin < 0 || spin >= c->nspin || nb < 1 || !eps || !psi || !out)
+        return fail(c, HP_EINVAL, "hp_apply_sternheimer: bad arguments");
+    const bool mixed = c->opt.precision == HP_PRECISION_MIXED;
+    hp_status s = prepare_resp(c);
+    if (s != HP_OK) return s;
+    std::vector<int> kprime;
+    if ((s = prepare_q(c, iq, kprime)) != HP_OK) return s;
+    if (c->ur_planes != c->fused) {
+        c->resp_ready = false;
+        if ((s = prepare_resp(c)) != HP_OK) return s;
+    }
+    const bool v32 = mixed && c->fused;
+    c->vec32 = v32;
+    const int ld = c->ld, npw = c->qc.set.npw[ik];
+    const int chunk = std::min(nb, c->resp_rows);
+    double2 *dX64, *dX, *dY;
+    CK(dalloc(c, &dX64, (size_t)chunk * ld));
+    CK(dalloc(c, &dX, (size_t)chunk * ld));
+    CK(dalloc(c, &dY, (size_t)chunk * ld));
+    std::vector<double2> h((size_t)chunk * ld);
+    for (int b0 = 0; b0 < nb && s == HP_OK; b0 += chunk) {
+        const int nc = std::min(chunk, nb - b0);
+        std::fill(h.begin(), h.end(), cmk(0.0, 0.0));
+        for (int b = 0; b < nc; ++b)
+            for (int i = 0; i < npw; ++i)
+                h[(size_t)b * ld + i] = cmk(psi[2 * ((size_t)(b0 + b) * npw + i)], psi[2 * ((size_t)(b0 + b) * npw + i) + 1]);
+        CK(h2d(dX64, h.data(), (size_t)nc * ld, c->st));
+        CK(cudaMemsetAsync(dY, 0, sizeof(double2) * (size_t)chunk * ld, c->st));
+        if (v32) CK(k_to_c32(dX64, reinterpret_cast<float2*>(dX), (long long)nc * ld, c->st));
+        else CK(cudaMemcpyAsync(dX, dX64, sizeof(double2) * (size_t)nc * ld, cudaMemcpyDeviceToDevice, c->st));
+        BandList& L = c->L3;
+        list_clear(L);
+        for (int b = 0; b < nc; ++b) list_add(L, b, ik, spin, eps[b0 + b]);
+        if ((s = upload_list(c, L)) != HP_OK) break;
+        if ((s = apply_sternheimer(c, L, dX, dY)) != HP_OK) break;
+        if (v32) CK(k_to_c64(reinterpret_cast<const float2*>(dY), dX64, (long long)nc * ld, c->st));
+        else CK(cudaMemcpyAsync(dX64, dY, sizeof(double2) * (size_t)nc * ld, cudaMemcpyDeviceToDevice, c->st));
+        CK(d2h(h.data(), dX64, (size_t)nc * ld, c->st));
+        for (int b = 0; b < nc; ++b)
+            for (int i = 0; i < npw; ++i) {
+                out[2 * ((size_t)(b0 + b) * npw + i)] = h[(size_t)b * ld + i].x;
+                out[2 * ((size_t)(b0 + b) * npw + i) + 1] = h[(size_t)b * ld + i].y;
+            }
+    }
+    dfree(c, dX64);
+    dfree(c, dX);
+    dfree(c, dY);
+    return s;
+}
+
 extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, double* dn_out, hp_resp_info* info) {
     if (!c) return HP_EINVAL;
     if (!c->have_gs) return fail(c, HP_ESTATE, "hp_response: no ground state");
@@ -1384,7 +1479,7 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
     long long cg_total = 0, hpsi = 0;
     int nhist = 0;
     double res = INFINITY, dchi = INFINITY, res_rel = 1.0;
-    bool converged = false, cg_ok = true;
+    bool converged = false, cg_ok = true, stagnated = false;
     int it = 0;
     std::vector<double> res_hist;
     const bool verbose = getenv("HP_VERBOSE") != nullptr;
@@ -1595,11 +1690,11 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
         const double vv = dev_dot(c, c->d_dvout, c->d_dvout, ndv, &e);
         if (e != cudaSuccess) return cuda_fail(c, e, "response norm");
         const double vrms = std::sqrt(vv / (double)ndv);
-        if (mixed) {  // FP32 noise floor: 3e-7 of the response potential and of the response traces
-            scf_tol = std::max(scf_tol, 3e-7 * vrms);
-            double tmax = 0.0;
-            for (int a = 0; a < 2 * nh; ++a) tmax = std::max(tmax, std::fabs(tr[a]));
-            chi_tol = std::max(chi_tol, 3e-7 * tmax);
+        double tmax = 0.0;
+        for (int a = 0; a < 2 * nh; ++a) tmax = std::max(tmax, std::fabs(tr[a]));
+        if (mixed) {  // FP32 noise floor: mixed_floor (3e-7) of the response potential and of the traces
+            scf_tol = std::max(scf_tol, c->opt.mixed_floor * vrms);
+            chi_tol = std::max(chi_tol, c->opt.mixed_floor * tmax);
         }
         // residual F = dV_out - dV_in (kept in d_dvout)
         CK(k_vec_sub(c->d_dvout, c->d_dvout, c->d_dv, ndv, c->st));
@@ -1627,8 +1722,9 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
         if (mixed && it >= 6 && res < 1e-5 * vrms) {
             const size_t n = res_hist.size();
             const double lo = std::min(res_hist[n - 1], std::min(res_hist[n - 2], res_hist[n - 3]));
-            if (lo > 0.5 * res_hist[n - 4] && dchi < 1e-5 * std::max(1e-300, chi_tol / 3e-7)) {
+            if (lo > 0.5 * res_hist[n - 4] && dchi < 1e-5 * tmax) {
                 converged = true;
+                stagnated = true;
                 break;
             }
         }
@@ -1698,6 +1794,7 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
         info->residual = res;
         info->dchi = dchi;
         info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        info->stagnated = stagnated ? 1 : 0;
     }
     if (!converged || !cg_ok) {
         c->cols.erase({iq, atom});
@@ -1709,8 +1806,45 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
     return HP_OK;
 }
 
-extern "C" hp_status hp_hubbard(hp_ctx* c, double* chi0_out, double* chi_out, double* hub_out) {
+// Nearest Hubbard neighbours of another species for the V list: for Hubbard atom s of cell 0, every
+// (l', s') of the q-mesh supercell with a minimum-image distance within d_min + dist_thr of the
+// shortest one (dist_thr = 6e-4 bohr, the paper's default, Appendix B); (chi index, distance) pairs
+static std::vector<std::pair<int, double>> nearest_hubbard(const hp_ctx* c, int s) {
+    const int nh = (int)c->hub_atoms.size();
+    const double n[3] = {(double)c->qmesh[0], (double)c->qmesh[1], (double)c->qmesh[2]};
+    const int ia = c->hub_atoms[s];
+    std::vector<std::pair<int, double>> all;
+    for (int l1 = 0, l = 0; l1 < c->qmesh[0]; ++l1)
+        for (int l2 = 0; l2 < c->qmesh[1]; ++l2)
+            for (int l3 = 0; l3 < c->qmesh[2]; ++l3, ++l) {
+                const int R[3] = {l1, l2, l3};
+                for (int jj = 0; jj < nh; ++jj) {
+                    const int ja = c->hub_atoms[jj];
+                    if (c->atom_species[ja] == c->atom_species[ia]) continue;
+                    double d[3], x[3] = {0, 0, 0};
+                    for (int i = 0; i < 3; ++i) {
+                        d[i] = (c->frac[3 * ja + i] + R[i] - c->frac[3 * ia + i]) / n[i];
+                        d[i] -= std::nearbyint(d[i]);
+                    }
+                    for (int i = 0; i < 3; ++i)
+                        for (int j = 0; j < 3; ++j) x[j] += d[i] * n[i] * c->cell[3 * i + j];
+                    all.push_back({l * nh + jj, std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2])});
+                }
+            }
+    std::vector<std::pair<int, double>> out;
+    if (all.empty()) return out;
+    double dmin = INFINITY;
+    for (auto& p : all) dmin = std::min(dmin, p.second);
+    for (auto& p : all)
+        if (p.second <= dmin + 6e-4) out.push_back(p);
+    std::sort(out.begin(), out.end());
+    return out;
+}
+
+extern "C" hp_status hp_hubbard(hp_ctx* c, double* chi0_out, double* chi_out, double* hub_out, double* U_out,
+                                hp_pairV* V_out, int* nV) {
     if (!c) return HP_EINVAL;
+    if (V_out && !nV) return fail(c, HP_EINVAL, "hp_hubbard: V needs its capacity nV");
     const int nh = (int)c->hub_atoms.size(), nq = c->nq;
     const int n = nh * nq;
     std::vector<double2> cols0((size_t)nq * nh * nh), cols((size_t)nq * nh * nh);
@@ -1735,13 +1869,14 @@ extern "C" hp_status hp_hubbard(hp_ctx* c, double* chi0_out, double* chi_out, do
                 Rl[3 * i + 2] = i3;
             }
     double2* d_cols;
-    double *d_q, *d_R, *d_mats, *d_work;
+    double *d_q, *d_R, *d_mats, *d_work, *d_norms;
     int* d_sing;
     CK(dalloc(c, &d_cols, 2 * cols.size()));
     CK(dalloc(c, &d_q, 3 * nq));
     CK(dalloc(c, &d_R, 3 * nq));
     CK(dalloc(c, &d_mats, (size_t)7 * n * n));
     CK(dalloc(c, &d_work, n));
+    CK(dalloc(c, &d_norms, 4));
     CK(dalloc(c, &d_sing, 2));
     CK(h2d(d_cols, cols0.data(), cols0.size(), c->st));
     CK(h2d(d_cols + cols0.size(), cols.data(), cols.size(), c->st));
@@ -1760,16 +1895,44 @@ extern "C" hp_status hp_hubbard(hp_ctx* c, double* chi0_out, double* chi_out, do
     CK(cudaMemcpyAsync(inv, chi, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, c->st));
     CK(k_invert(inv0, d_work, n, d_sing, c->st));
     CK(k_invert(inv, d_work, n, d_sing + 1, c->st));
+    // 1-norm condition numbers ||A||_1 ||A^-1||_1 of chi_0 and chi
+    CK(k_norm1(chi0, n, d_norms + 0, c->st));
+    CK(k_norm1(inv0, n, d_norms + 1, c->st));
+    CK(k_norm1(chi, n, d_norms + 2, c->st));
+    CK(k_norm1(inv, n, d_norms + 3, c->st));
     CK(k_hub_matrix(inv0, inv, n, kHaToEv, hub, c->st));
     std::vector<double> h((size_t)7 * n * n);
     int sing[2];
+    double nrm[4];
     CK(d2h(h.data(), d_mats, h.size(), c->st));
     CK(d2h(sing, d_sing, 2, c->st));
-    for (void* p : {(void*)d_cols, (void*)d_q, (void*)d_R, (void*)d_mats, (void*)d_work, (void*)d_sing}) dfree(c, p);
-    if (sing[0] || sing[1]) return fail(c, HP_ESINGULAR, "hp_hubbard: chi0 or chi is singular");
+    CK(d2h(nrm, d_norms, 4, c->st));
+    for (void* p : {(void*)d_cols, (void*)d_q, (void*)d_R, (void*)d_mats, (void*)d_work, (void*)d_norms, (void*)d_sing})
+        dfree(c, p);
     if (chi0_out) memcpy(chi0_out, h.data(), sizeof(double) * n * n);
     if (chi_out) memcpy(chi_out, h.data() + (size_t)2 * n * n, sizeof(double) * n * n);
-    if (hub_out) memcpy(hub_out, h.data() + (size_t)6 * n * n, sizeof(double) * n * n);
+    const double cond0 = nrm[0] * nrm[1], cond = nrm[2] * nrm[3];
+    if (sing[0] || sing[1] || !(cond0 <= 1e10) || !(cond <= 1e10)) {
+        char msg[200];
+        snprintf(msg, sizeof(msg), "hp_hubbard: chi0 or chi is singular or ill-conditioned (1-norm condition numbers "
+                 "%.3e, %.3e; bound 1e10)", cond0, cond);
+        return fail(c, HP_ESINGULAR, msg);
+    }
+    const double* hubh = h.data() + (size_t)6 * n * n;
+    if (hub_out) memcpy(hub_out, hubh, sizeof(double) * n * n);
+    if (U_out)
+        for (int s = 0; s < nh; ++s) U_out[s] = hubh[(size_t)s * n + s];
+    if (V_out || nV) {
+        int cnt = 0;
+        const int cap = nV ? *nV : 0;
+        for (int s = 0; s < nh; ++s)
+            for (auto& p : nearest_hubbard(c, s)) {
+                if (V_out && cnt < cap) V_out[cnt] = hp_pairV{s, p.first, p.second, hubh[(size_t)s * n + p.first]};
+                ++cnt;
+            }
+        if (nV) *nV = cnt;
+        if (V_out && cnt > cap) return fail(c, HP_EINVAL, "hp_hubbard: V holds fewer entries than the neighbour pairs");
+    }
     return HP_OK;
 }
 
@@ -1793,7 +1956,9 @@ extern "C" hp_status hp_batch_run(int ncells, hp_ctx* const* cells, double* cons
         hp_status s = HP_OK;
         for (size_t a = 0; a < c->hub_atoms.size() && s == HP_OK; ++a)
             for (int iq = 0; iq < c->nq && s == HP_OK; ++iq) s = hp_response(c, iq, c->hub_atoms[a], nullptr, nullptr, nullptr);
-        if (s == HP_OK) s = hp_hubbard(c, chi0 ? chi0[i] : nullptr, chi ? chi[i] : nullptr, hub ? hub[i] : nullptr);
+        if (s == HP_OK)
+            s = hp_hubbard(c, chi0 ? chi0[i] : nullptr, chi ? chi[i] : nullptr, hub ? hub[i] : nullptr, nullptr, nullptr,
+                           nullptr);
         status[i] = s;
     };
     std::vector<std::thread> th;

@@ -323,7 +323,7 @@ static bool launch_fixed(int n, V* data, int A, int B, const V* tw, int sign, in
     }
 }
 
-cudaError_t fft_plan_create(FftPlan& p, const int N[3]) {
+cudaError_t fft_plan_create(hp_ctx* c, FftPlan& p, const int N[3]) {
     for (int d = 0; d < 3; ++d) {
         p.N[d] = N[d];
         if (!fft_factor(N[d], p.ax[d].rad)) return cudaErrorInvalidValue;
@@ -332,13 +332,13 @@ cudaError_t fft_plan_create(FftPlan& p, const int N[3]) {
             const double a = -2.0 * M_PI * (double)t / (double)N[d];
             tw[t] = cmk(std::cos(a), std::sin(a));
         }
-        cudaError_t e = cudaMalloc(&p.ax[d].d_tw, sizeof(double2) * N[d]);
+        cudaError_t e = dalloc(c, &p.ax[d].d_tw, N[d]);
         if (e != cudaSuccess) return e;
         e = cudaMemcpy(p.ax[d].d_tw, tw.data(), sizeof(double2) * N[d], cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return e;
         std::vector<float2> tw32(N[d]);
         for (int t = 0; t < N[d]; ++t) tw32[t] = cmkf((float)tw[t].x, (float)tw[t].y);
-        e = cudaMalloc(&p.ax[d].d_tw32, sizeof(float2) * N[d]);
+        e = dalloc(c, &p.ax[d].d_tw32, N[d]);
         if (e != cudaSuccess) return e;
         e = cudaMemcpy(p.ax[d].d_tw32, tw32.data(), sizeof(float2) * N[d], cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return e;
@@ -346,10 +346,8 @@ cudaError_t fft_plan_create(FftPlan& p, const int N[3]) {
     return cudaSuccess;
 }
 
-void fft_plan_destroy(FftPlan& p) {
+void fft_plan_destroy(FftPlan& p) {  // the tables themselves are freed with the context's allocations
     for (int d = 0; d < 3; ++d) {
-        if (p.ax[d].d_tw) cudaFree(p.ax[d].d_tw);
-        if (p.ax[d].d_tw32) cudaFree(p.ax[d].d_tw32);
         p.ax[d].d_tw = nullptr;
         p.ax[d].d_tw32 = nullptr;
     }
@@ -433,6 +431,8 @@ void fft_host_lines(const Radices& rad, const std::vector<double2>& tw, int nlin
 }  // namespace hp
 
 extern "C" long long hp_launch_count(void) { return hp::g_launches.load(); }
+
+extern "C" long long hp_alloc_count(void) { return hp::g_allocs.load(); }
 
 extern "C" hp_status hp_selftest_fft_host(int n, int nlines, int sign, const double* in, double* out) {
     if (n < 1 || nlines < 1 || !in || !out || (sign != 1 && sign != -1)) return HP_EINVAL;

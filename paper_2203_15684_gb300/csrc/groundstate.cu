@@ -526,10 +526,15 @@ hp_status hp::nscf_states(hp_ctx* c, const std::vector<const KSphere*>& sph, con
     return HP_OK;
 }
 
-extern "C" hp_status hp_ground_state(hp_ctx* c, double nelec, int nspin, const int* init_moment, hp_gs_info* info) {
+extern "C" hp_status hp_ground_state(hp_ctx* c, double nelec, int nspin, const int* init_moment, double tot_mag,
+                                     hp_gs_info* info) {
     if (!c) return HP_EINVAL;
     auto t0 = std::chrono::steady_clock::now();
     if (nspin != 1 && nspin != 2) return fail(c, HP_EINVAL, "hp_ground_state: nspin must be 1 or 2");
+    if (!std::isfinite(tot_mag) || (nspin == 1 && tot_mag != 0.0))
+        return fail(c, HP_EINVAL, "hp_ground_state: tot_mag must be finite, and 0 for nspin = 1");
+    if (tot_mag != 0.0)
+        return fail(c, HP_ENOTIMPL, "hp_ground_state: only tot_mag = 0 (equal occupied band counts per spin) is built");
     const int nocc = (int)std::lround(nelec / 2.0);
     if (nocc < 1 || std::fabs(nelec - 2.0 * nocc) > 1e-9)
         return fail(c, HP_EINVAL, "hp_ground_state: nelec must be an even positive number");
@@ -874,6 +879,7 @@ extern "C" hp_status hp_selftest_eigh(int n, int nbatch, const double* A, double
     if (cudaMalloc(&dA, sizeof(double2) * nn) != cudaSuccess || cudaMalloc(&dV, sizeof(double2) * nn) != cudaSuccess ||
         cudaMalloc(&dT, sizeof(double2) * nn) != cudaSuccess || cudaMalloc(&dw, sizeof(double) * n * nbatch) != cudaSuccess)
         st = HP_ECUDA;
+    hp::g_allocs.fetch_add(4, std::memory_order_relaxed);
     if (st == HP_OK && cudaMemcpy(dA, A, sizeof(double2) * nn, cudaMemcpyHostToDevice) != cudaSuccess) st = HP_ECUDA;
     if (st == HP_OK) {
         const size_t jsh = (size_t)(n / 2 + 1) * (4 * sizeof(double) + 2 * sizeof(int));

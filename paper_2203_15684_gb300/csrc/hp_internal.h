@@ -78,6 +78,8 @@ __device__ __forceinline__ double f2d_bits(float x) {
 
 // every kernel launch of the library increments this counter (read by hp_launch_count)
 extern std::atomic<long long> g_launches;
+// every device allocation of the library increments this counter (read by hp_alloc_count)
+extern std::atomic<long long> g_allocs;
 #define HP_LAUNCHED() (hp::g_launches.fetch_add(1, std::memory_order_relaxed))
 
 // ------------------------------------------------------------------------------------------------
@@ -102,7 +104,8 @@ struct FftPlan {
 };
 
 bool fft_factor(int n, Radices& out);
-cudaError_t fft_plan_create(FftPlan& p, const int N[3]);
+// twiddle tables are context allocations (freed with the context)
+cudaError_t fft_plan_create(hp_ctx* c, FftPlan& p, const int N[3]);
 void fft_plan_destroy(FftPlan& p);
 // In place, nb grids of N0*N1*N2 complex each, contiguous.  sign +1: sum_G c(G) exp(+iG.r)
 // (to real space), sign -1: sum_r f(r) exp(-iG.r).  Unnormalised both ways.
@@ -207,6 +210,7 @@ cudaError_t k_drho_acc32(const float2* ur, const int* ur_row_of_item, const floa
                          size_t part_elems, cudaStream_t st);
 cudaError_t k_to_f32(const double* a, float* b, long long n, cudaStream_t st);
 cudaError_t k_to_c32(const double2* a, float2* b, long long n, cudaStream_t st);
+cudaError_t k_to_c64(const float2* a, double2* b, long long n, cudaStream_t st);
 cudaError_t k_band_dot(const BandList& L, const SphereSet& S, const double2* X, const double2* Y, int ld,
                        double* out, cudaStream_t st);
 cudaError_t k_band_dot(const BandList& L, const SphereSet& S, const float2* X, const float2* Y, int ld,
@@ -259,6 +263,8 @@ cudaError_t k_chi_assemble(const double2* cols, int nq, int nh, const double* qf
                            double* chi_re, double* chi_im, cudaStream_t st);
 cudaError_t k_invert(double* a, double* work, int n, int* singular, cudaStream_t st);
 cudaError_t k_hub_matrix(const double* inv0, const double* inv, int n, double scale, double* hub, cudaStream_t st);
+// out = max_j sum_i |a_ij| (the matrix 1-norm), one CTA
+cudaError_t k_norm1(const double* a, int n, double* out, cudaStream_t st);
 cudaError_t k_add_real(const double* a, const double* b, double* out, int n, cudaStream_t st);
 cudaError_t k_sum_reduce(const double* partial, int nparts, double* out, cudaStream_t st);
 
@@ -461,12 +467,36 @@ struct hp_ctx {
 
 namespace hp {
 
+// device memory of a context: the registered allocator (hp_options.dev_alloc) or cudaMalloc
+inline cudaError_t dev_malloc(hp_ctx* c, void** p, size_t bytes) {
+    *p = nullptr;
+    g_allocs.fetch_add(1, std::memory_order_relaxed);
+    if (c->opt.dev_alloc) {
+        *p = c->opt.dev_alloc(bytes, c->opt.alloc_user);
+        return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+inline void dev_free_raw(hp_ctx* c, void* p) {
+    if (!p) return;
+    if (c->opt.dev_alloc) {
+        if (c->opt.dev_free) c->opt.dev_free(p, c->opt.alloc_user);
+    } else {
+        cudaFree(p);
+    }
+}
+
 template <class T>
 cudaError_t dalloc(hp_ctx* c, T** p, size_t n) {
     *p = nullptr;
     if (n == 0) n = 1;
-    cudaError_t e = cudaMalloc((void**)p, sizeof(T) * n);
-    if (e == cudaSuccess) c->owned.push_back((void*)*p);
+    void* q = nullptr;
+    cudaError_t e = dev_malloc(c, &q, sizeof(T) * n);
+    if (e == cudaSuccess) {
+        *p = (T*)q;
+        c->owned.push_back(q);
+    }
     return e;
 }
 

@@ -295,6 +295,17 @@ cudaError_t k_to_c32(const double2* a, float2* b, long long n, cudaStream_t st) 
     return cudaGetLastError();
 }
 
+__global__ void to_f64_kernel(const float* __restrict__ a, double* __restrict__ b, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        b[i] = (double)a[i];
+}
+
+cudaError_t k_to_c64(const float2* a, double2* b, long long n, cudaStream_t st) {
+    to_f64_kernel<<<std::min(cdiv(2 * n, 256), 4096), 256, 0, st>>>((const float*)a, (double*)b, 2 * n);
+    HP_LAUNCHED();
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------------------------------------
 // segmented projector contractions over one or two projector families (rows 0 .. n0-1 from the
 // first, n0 .. n0+n1-1 from the second):
@@ -1706,6 +1717,29 @@ cudaError_t k_hub_matrix(const double* inv0, const double* inv, int n, double sc
     return cudaGetLastError();
 }
 
+__global__ void norm1_kernel(const double* __restrict__ a, int n, double* __restrict__ out) {
+    __shared__ double red[256];
+    double best = 0.0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        double col = 0.0;
+        for (int i = 0; i < n; ++i) col += fabs(a[(long long)i * n + j]);
+        best = fmax(best, col);
+    }
+    red[threadIdx.x] = best;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
+}
+
+cudaError_t k_norm1(const double* a, int n, double* out, cudaStream_t st) {
+    norm1_kernel<<<1, 256, 0, st>>>(a, n, out);
+    HP_LAUNCHED();
+    return cudaGetLastError();
+}
+
 __global__ void add_real_kernel(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ out, int n) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = a[i] + b[i];
@@ -1734,6 +1768,24 @@ __global__ void convert_selftest_kernel(const double* __restrict__ in, long long
 }
 }  // namespace
 
+extern "C" hp_status hp_selftest_xc(int n, int nspin, const double* rho, double* vxc, double* fxc) {
+    if (n < 1 || (nspin != 1 && nspin != 2) || !rho || !vxc || !fxc) return HP_EINVAL;
+    const int nf = nspin == 1 ? 1 : 3;
+    double *d_rho = nullptr, *d_v = nullptr, *d_f = nullptr;
+    cudaError_t e = cudaMalloc(&d_rho, sizeof(double) * (size_t)nspin * n);
+    if (e == cudaSuccess) e = cudaMalloc(&d_v, sizeof(double) * (size_t)nspin * n);
+    if (e == cudaSuccess) e = cudaMalloc(&d_f, sizeof(double) * (size_t)nf * n);
+    if (e == cudaSuccess) hp::g_allocs.fetch_add(3, std::memory_order_relaxed);
+    if (e == cudaSuccess) e = cudaMemcpy(d_rho, rho, sizeof(double) * (size_t)nspin * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = hp::k_xc(d_rho, nspin, n, d_v, d_f, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(vxc, d_v, sizeof(double) * (size_t)nspin * n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(fxc, d_f, sizeof(double) * (size_t)nf * n, cudaMemcpyDeviceToHost);
+    cudaFree(d_rho);
+    cudaFree(d_v);
+    cudaFree(d_f);
+    return e == cudaSuccess ? HP_OK : HP_ECUDA;
+}
+
 extern "C" hp_status hp_selftest_convert(long long n, const double* in, float* f, double* back, float* f_ref,
                                          double* back_ref) {
     if (n < 1 || !in || !f || !back || !f_ref || !back_ref) return HP_EINVAL;
@@ -1745,6 +1797,7 @@ extern "C" hp_status hp_selftest_convert(long long n, const double* in, float* f
     if (e == cudaSuccess) e = cudaMalloc(&d_back_ref, n8);
     if (e == cudaSuccess) e = cudaMalloc(&d_f, n4);
     if (e == cudaSuccess) e = cudaMalloc(&d_f_ref, n4);
+    if (e == cudaSuccess) hp::g_allocs.fetch_add(5, std::memory_order_relaxed);
     if (e == cudaSuccess) e = cudaMemcpy(d_in, in, n8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
         convert_selftest_kernel<<<(int)std::min<long long>((n + 255) / 256, 4096), 256>>>(d_in, n, d_f, d_back, d_f_ref,

@@ -50,6 +50,16 @@ extern "C" hp_status hp_apply_h_noalloc(hp_ctx* c, int ik, int spin, int nb, con
     if (!c->have_gs) return fail(c, HP_ESTATE, "hp_apply_h_noalloc: no ground state (potential) yet");
     if (ik < 0 || ik >= c->nk || spin < 0 || spin >= c->nspin || nb < 1 || !psi_dev || !out_dev)
         return fail(c, HP_EINVAL, "hp_apply_h_noalloc: bad arguments");
+    // the context's buffers (potential, projectors, sphere tables) live on the device current at
+    // hp_setup; the scratch array is looked up on the current device, so both must be the same
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return fail(c, HP_ECUDA, "hp_apply_h_noalloc: cudaGetDevice failed");
+    if (dev != c->device) {
+        char msg[160];
+        snprintf(msg, sizeof(msg), "hp_apply_h_noalloc: current device %d is not the context's device %d", dev,
+                 c->device);
+        return fail(c, HP_EINVAL, msg);
+    }
     cudaStream_t st = stream ? (cudaStream_t)stream : c->st;
     const int ld = c->ld, nr = c->nr;
     constexpr int kPS = 128;

@@ -4,6 +4,12 @@
 
 tiny_config0.json: the two-atom cube at its full size (20 Ry, FFT 20^3, k 2x2x2, q 1x1x1):
 oracle ground state (gap, eigenvalues at k = Gamma), chi_0, chi and U of the H atom.
+
+medium_config1_column.json (``python tests/golden/make_golden.py medium``, a few CPU hours): the
+medium rocksalt workload at its full size (35 Ry, FFT 36^3, k 4x4x4, q 2x2x2, nspin = 2): the
+oracle's ground state (every occupied eigenvalue, the gap, the Hubbard occupations) and one
+declared (q, J) column, q = (1/2, 0, 0) and J = the first H atom: Delta_q n^0 and Delta_q n of every
+Hubbard atom, both spins, element by element.
 """
 
 import json
@@ -34,8 +40,32 @@ def tiny_config0():
                 note="oracle: SCF tol 1e-12, CG 1e-13, response SCF 1e-12")
 
 
+def _cplx(a):
+    a = np.asarray(a)
+    return [a.real.tolist(), a.imag.tolist()]
+
+
+def medium_config1_column(iq=4, J=0):
+    w = W.medium()
+    m = Model(w)
+    gs = G.scf(m, tol=1e-12, verbose=True)
+    r = R.solve_column(m, gs, iq, J, tol_cg=1e-12, scf_tol=1e-11, conv_chi=1e-12, verbose=True)
+    occ = gs.occupations()
+    return dict(workload="medium", iq=iq, qfrac=m.qpts[iq].tolist(), J=J, hub_atoms=list(m.hub_atoms),
+                gap=gs.gap(), eps=gs.eps[:, :, : m.nocc].tolist(), gs_iterations=gs.iterations,
+                gs_residual=gs.residual, occupations={str(a): occ[a].tolist() for a in m.hub_atoms},
+                dn0={str(a): _cplx(r["dn0"][a]) for a in m.hub_atoms},
+                dn={str(a): _cplx(r["dn"][a]) for a in m.hub_atoms},
+                response_iterations=r["iterations"], cg_iterations=r["cg_iterations"],
+                note="oracle: ground-state SCF tol 1e-12; response CG 1e-12 per band, SCF 1e-11, "
+                     "response traces 1e-12")
+
+
 if __name__ == "__main__":
-    out = tiny_config0()
-    with open(os.path.join(HERE, "tiny_config0.json"), "w") as f:
+    if len(sys.argv) > 1 and sys.argv[1] == "medium":
+        name, out = "medium_config1_column.json", medium_config1_column()
+    else:
+        name, out = "tiny_config0.json", tiny_config0()
+    with open(os.path.join(HERE, name), "w") as f:
         json.dump(out, f, indent=1)
-    print(out)
+    print("wrote", name)

@@ -110,10 +110,19 @@ def test_hubbard_matrix_tiny_q():
     chi0_ref = HB.assemble_chi(m, c0).real
     chi_ref = HB.assemble_chi(m, c).real
     hub_ref = HB.hubbard_matrix(chi0_ref, chi_ref)
-    chi0, chi, hub = ctx.hubbard()
+    r = ctx.hubbard_parameters()
+    chi0, chi, hub = r["chi0"], r["chi"], r["hub"]
     assert np.abs(chi0 - chi0_ref).max() < 1e-8 * np.abs(chi0_ref).max()
     assert np.abs(chi - chi_ref).max() < 1e-8 * np.abs(chi_ref).max()
     assert np.abs(hub - hub_ref).max() < 1e-8 * np.abs(hub_ref).max()
+    # U per Hubbard atom and the nearest-neighbour V list (reading c17), against the oracle's shell
+    nh = len(m.hub_atoms)
+    assert np.abs(r["U"] - np.diag(hub_ref)[:nh]).max() < 1e-8 * np.abs(hub_ref).max()
+    expect = [(s, j) for s in range(nh) for j in HB.neighbours(m, s)]
+    assert [(s, j) for s, j, _, _ in r["V"]] == expect
+    for s, j, dist, v in r["V"]:
+        assert abs(v - hub_ref[s, j]) < 1e-8 * np.abs(hub_ref).max()
+        assert 0 < dist < 8.0
 
 
 def test_response_spin_polarised():

@@ -8,6 +8,7 @@ import pytest
 
 import workloads as W
 from oracle import fd, groundstate as G, hubbard as HB, response as R, sos
+from oracle.hamiltonian import dense_h
 from oracle.model import Model
 
 
@@ -184,3 +185,41 @@ def test_off_mesh_branch_equals_mapped_states(monkeypatch):
         scale = max(np.abs(np.asarray(v)).max() for v in a.values())
         for atom in a:
             assert np.abs(np.asarray(a[atom]) - np.asarray(b[atom])).max() < 1e-8 * scale
+
+
+def test_neighbours_rocksalt_shell_of_six():
+    """Reading c17: in the rocksalt cell every metal (H) has six ligand (L) neighbours tied at a/2
+    and every ligand six metals; on the 2x2x2 q mesh the six are distinct atoms of the supercell
+    (+-x, +-y, +-z).  A shell rule that kept one of a tied set, or took the wrong species, fails."""
+    m = Model(W.medium())
+    a = 8.4
+    R = m.supercell_R()
+    nh = len(m.hub_atoms)
+    n = np.array(m.qmesh, dtype=float)
+    for si, ia in enumerate(m.hub_atoms):
+        nb = HB.neighbours(m, si)
+        assert len(nb) == 6 and len(set(nb)) == 6
+        for j in nb:
+            l, sj = divmod(j, nh)
+            ja = m.hub_atoms[sj]
+            assert m.atom_species[ja] != m.atom_species[ia]
+            d = (m.frac[ja] + R[l] - m.frac[ia]) / n
+            d -= np.round(d)
+            assert abs(np.linalg.norm(d * n * a) - a / 2) < 1e-12
+
+
+def test_sternheimer_operator_equals_dense_matrix():
+    """The Sternheimer operator through the FFT route equals the dense aliased H plus alpha Cq Cq^H
+    minus the shift, on random vectors at a k+q point of the q = (1/2, 0, 0) column."""
+    w = W.tiny_q(ecut=8.0, grid=(12, 12, 12), kmesh=(2, 2, 2), qmesh=(2, 1, 1))
+    m = Model(w)
+    rng = np.random.default_rng(3)
+    vr = m.vloc_r() + 0.2 * rng.standard_normal(m.nr)
+    kdq = m.kdata(m.kpts[3] + m.qpts[1])
+    Cq = np.linalg.qr(rng.standard_normal((kdq.npw, 5)) + 1j * rng.standard_normal((kdq.npw, 5)))[0]
+    X = rng.standard_normal((kdq.npw, 4)) + 1j * rng.standard_normal((kdq.npw, 4))
+    eps = np.array([-0.7, -0.5, -0.2, 0.1])
+    got = R.sternheimer_operator(m, kdq, vr, Cq, 1.3, eps, X)
+    Hd = dense_h(m, kdq, vr) + 1.3 * (Cq @ Cq.conj().T)
+    ref = np.stack([(Hd - e * np.eye(kdq.npw)) @ X[:, j] for j, e in enumerate(eps)], axis=1)
+    assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()

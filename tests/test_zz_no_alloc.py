@@ -39,19 +39,43 @@ def _rows(ctx, ik, X):
     return out
 
 
+def _noalloc(ctx, ik, X):
+    """One allocation-free call on fresh device rows; returns (result, device allocations made by
+    the library during the call)."""
+    nb = X.shape[0]
+    xd = torch.from_numpy(_rows(ctx, ik, X).view(np.float64)).cuda()
+    yd = torch.full_like(xd, float("nan"))
+    torch.cuda.synchronize()
+    a0 = P.alloc_count()
+    ctx.apply_h_noalloc(ik, 0, nb, xd.data_ptr(), yd.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    made = P.alloc_count() - a0
+    return yd.cpu().numpy().view(np.complex128), made
+
+
 @pytest.mark.parametrize("ik", [0, 5])
 def test_noalloc_matches_allocating_entry_point_twice(ctx, ik):
     npw = len(ctx.sphere(ik))
     for call, nb in enumerate((37, 11)):
         X = W.random_coefficients(1000 * ik + call, (nb, npw))
         ref = ctx.apply_h(ik, 0, X)
-        xd = torch.from_numpy(_rows(ctx, ik, X).view(np.float64)).cuda()
-        yd = torch.full_like(xd, float("nan"))
-        torch.cuda.synchronize()
-        ctx.apply_h_noalloc(ik, 0, nb, xd.data_ptr(), yd.data_ptr(), torch.cuda.current_stream().cuda_stream)
-        got = yd.cpu().numpy().view(np.complex128)
+        got, made = _noalloc(ctx, ik, X)
+        assert made == 0                   # the defining property: no device allocation at call time
         assert np.all(got[:, npw:] == 0)
         assert np.abs(got[:, :npw] - ref).max() < 1e-11 * np.abs(ref).max()
+
+
+def test_noalloc_several_grid_chunks(ctx):
+    """600 bands on the 20^3 grid: the fixed scratch holds about 490 FFT grids after the band list
+    and projections, so the local part runs in two chunks, the second one partial (offsets c0 > 0
+    into the band list for the scatter, the potential and the gather)."""
+    ik = 3
+    npw = len(ctx.sphere(ik))
+    X = W.random_coefficients(4242, (600, npw))
+    ref = ctx.apply_h(ik, 0, X)
+    got, made = _noalloc(ctx, ik, X)
+    assert made == 0
+    assert np.all(got[:, npw:] == 0)
+    assert np.abs(got[:, :npw] - ref).max() < 1e-11 * np.abs(ref).max()
 
 
 def test_noalloc_rejects_batches_beyond_the_fixed_scratch(ctx):
