@@ -1,21 +1,37 @@
 #!/usr/bin/env python3
 """Benchmark of the DFPT Hubbard-parameter hot path on GB300.
 
-Workload (--workload): "medium" (default), the rocksalt-like cell (8.4 bohr cube, 4 H + 4 L,
-40 electrons, collinear nspin = 2 with an antiferromagnetic start, 35 Ry, FFT 36^3, k 4x4x4,
-q 2x2x2); "precision", the same cell at 50 Ry (FFT 45^3).  The ground state is computed on the GPU
-before timing.  One step = one (q, J) self-consistent Sternheimer response
-(the per-q set-up a1 and a3-a10): every (spin, k, band) system of that pair, to the FP64
-tolerances the parity tests use.  The 64 (q, J) pairs of the full chi matrix are independent and
-alike, so the full-matrix wall time is reported as steps-per-matrix x time per step.  The headline
-is the mixed-precision form (FP32 FFTs, grid work and projections; FP64 vectors, CG scalars,
-mixing and inversion); the FP64 form is timed on the same ground state and pairs for comparison.
+Workloads (--workload):
+  precision (default)  the rocksalt-like cube (8.4 bohr, 4 H + 4 L, 40 electrons, collinear nspin = 2
+                       with an antiferromagnetic start) at 50 Ry, FFT 45^3, k 4x4x4, q 2x2x2: the
+                       mixed-precision form's workload;
+  medium               the same cell at 35 Ry, FFT 36^3;
+  batch                the batching form (cells per hour over a batch of cells).
+The H species' projector strength is D = -4.0 Ha in every workload (the insulating reading of the
+model; +1.5 Ha leaves the cells metallic).  Ground states are computed on the GPU before timing.
 
-Metric: H.psi/s (single-band applications of the Sternheimer operator, summed over ranks).
+One step = one (q, J) self-consistent Sternheimer response (the per-q set-up a1 and a3-a10): every
+(spin, k, band) system of that pair, in the mixed-precision form (FP32 FFTs, grid work and
+projections; FP64 step lengths, norms, mixing and inversion).  value = H.psi/s over the K timed
+steps (single-band applications of the Sternheimer operator, summed over ranks).
+
+Beside the timed steps, on the same ground state and GPU:
+  * the full chi matrix in the mixed form, measured: every (q, J) pair and hp_hubbard, wall time
+    from a ready ground state to U and V in host memory (chi_matrix.mixed_s);
+  * the FP64 form on --fp64-steps pairs (H.psi/s and seconds per pair), and with --fp64-full the
+    whole FP64 chi matrix, measured, with max |U_mixed - U_FP64| and |V_mixed - V_FP64| in meV;
+  * with --companion medium (the default for the precision workload): the 35 Ry cell's ground state
+    and full mixed chi matrix, measured, and the declared oracle column of that cell (q = (1/2,0,0),
+    J = the first H; stored by the oracle under tests/golden/) against this run's FP64 and mixed
+    responses, element by element.
+e2e: the same response through the C ABI with the ground state copied in from pinned host memory
+and Delta n copied out, every step.  cpu_baseline: the oracle's Sternheimer operator on the host
+cores, one thread and one process per core.
+
 N > 1 (torchrun): the (q, J) pairs are sharded round-robin over ranks (weak scaling, no collective
 on the data path); timing is the max over ranks between barriers.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload medium|precision]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload ...]
 """
 
 from __future__ import annotations
@@ -35,31 +51,39 @@ sys.path.insert(0, ROOT)
 
 METRIC = "full χ-matrix wall time & H·ψ/s, mixed vs FP64 on 1 GB300 at |ΔU|≤1 meV"
 UNIT = "Hpsi/s"
+_CELL = "rocksalt cube a=8.4 bohr, 4 H + 4 L (H projector D=-4.0 Ha), 40 electrons, nspin=2 (AFM start), "
 WORKLOADS = {
-    "medium": "medium: rocksalt cube a=8.4 bohr, 4 H + 4 L, 40 electrons, nspin=2 (AFM start), "
-              "ecutwfc 35 Ry (npw<=2103), FFT 36^3, k 4x4x4, q 2x2x2",
-    "precision": "precision: the medium cell at ecutwfc 50 Ry (npw<=3575), FFT 45^3, k 4x4x4, q 2x2x2, "
-                 "nspin=2 (AFM start)",
-    "batch": "batch: 6 small insulating cells of uneven sizes (two-atom cube at 8/10/20 Ry, q meshes of 1-8 "
-             "points, rocksalt cell at 6 Ry with nspin=2), mixed form",
+    "precision": "precision (config 2): " + _CELL + "ecutwfc 50 Ry (npw<=3575), FFT 45^3, k 4x4x4, q 2x2x2",
+    "medium": "medium (config 1): " + _CELL + "ecutwfc 35 Ry (npw<=2103), FFT 36^3, k 4x4x4, q 2x2x2",
+    "batch": "batch: small insulating cells of uneven sizes, mixed form",
 }
+STEP = ("one (q, J) self-consistent Sternheimer response (set-up a1, a3-a10) over every (spin, k, band) system of "
+        "the pair, mixed form")
+GOLDEN_MEDIUM = os.path.join(ROOT, "tests", "golden", "medium_config1_column.json")
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
-    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--fp64-steps", type=int, default=2)
     p.add_argument("--fp64-warmup", type=int, default=1)
+    p.add_argument("--fp64-full", action="store_true", help="also measure the whole FP64 chi matrix (minutes)")
+    p.add_argument("--no-chi-matrix", action="store_true", help="skip the measured full mixed chi matrix")
+    p.add_argument("--companion", default=None, choices=["none", "medium"],
+                   help="second workload measured beside the headline (default: medium for precision)")
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--e2e-steps", type=int, default=2)
-    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--band-batch", type=int, default=0, help="grids per FFT batch (0 = automatic)")
-    p.add_argument("--workload", default="medium", choices=sorted(WORKLOADS))
+    p.add_argument("--workload", default="precision", choices=sorted(WORKLOADS))
     p.add_argument("--cg-adapt", type=float, default=None,
                    help="CG threshold factor for outer iterations after the first (library default if omitted)")
-    return p.parse_args()
+    a = p.parse_args()
+    if a.companion is None:
+        a.companion = "medium" if a.workload == "precision" else "none"
+    return a
 
 
 # ------------------------------------------------------------------------------------------------
@@ -117,27 +141,27 @@ class ClockSampler:
 # ------------------------------------------------------------------------------------------------
 # oracle timing (CPU baseline and the reference arm)
 # ------------------------------------------------------------------------------------------------
-def _oracle_sample(seconds, workload="medium"):
-    """The oracle's Sternheimer operator (H + alpha P_v - eps) applied to blocks of 20 bands on the
-    workload's spheres and grid, with the oracle's own starting-density potential, for about
-    ``seconds``; returns (H.psi count, elapsed)."""
+def _oracle_sample(seconds, workload="precision", seed=2203):
+    """The oracle's Sternheimer operator (H_k+q + alpha O_k+q - eps, Eq. LRKSeq_lp) applied to blocks of
+    nocc bands on the workload's k spheres and grid, with the oracle's own starting-density potential
+    and seeded orthonormal occupied states, for about ``seconds``; returns (H.psi count, elapsed)."""
     import numpy as np
 
     import workloads as W
     from oracle import groundstate as G
-    from oracle.hamiltonian import apply_h
     from oracle.model import Model
+    from oracle.response import sternheimer_operator
 
     w = getattr(W, workload)()
     m = Model(w)
     vr = m.vloc_r() + G.hxc_potential(m, G.initial_density(m))[0]
-    rng = np.random.default_rng(2203)
-    n, t0, ik = 0, time.perf_counter(), 0
+    rng = np.random.default_rng(seed)
+    n, t0, ik = 0, time.perf_counter(), seed % len(m.kpts)
     while True:
         kd = m.kdata(m.kpts[ik % len(m.kpts)])
         U = np.linalg.qr(rng.standard_normal((kd.npw, m.nocc)) + 1j * rng.standard_normal((kd.npw, m.nocc)))[0]
         X = rng.standard_normal((kd.npw, m.nocc)) + 1j * rng.standard_normal((kd.npw, m.nocc))
-        Y = apply_h(m, kd, vr, X) + 2.0 * (U @ (U.conj().T @ X)) - X * 0.5
+        Y = sternheimer_operator(m, kd, vr, U, 2.0, np.full(m.nocc, 0.5), X)
         n += X.shape[1]
         ik += 1
         el = time.perf_counter() - t0
@@ -145,42 +169,86 @@ def _oracle_sample(seconds, workload="medium"):
             return n, el, float(np.abs(Y).max())
 
 
-def run_oracle_subprocess(seconds, workload="medium"):
+def _oracle_procs(seconds, workload, nproc):
+    """nproc one-thread oracle processes at once (different k points); -> (total H.psi, max elapsed)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = ("import json,sys; sys.path.insert(0, %r); import bench; n, el, _ = bench._oracle_sample(%f, %r); "
-            "print(json.dumps(dict(n=n, el=el)))" % (ROOT, seconds, workload))
-    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    return d["n"], d["el"]
+    procs = []
+    for i in range(nproc):
+        code = ("import json,sys; sys.path.insert(0, %r); import bench; n, el, _ = bench._oracle_sample(%f, %r, %d); "
+                "print(json.dumps(dict(n=n, el=el)))" % (ROOT, seconds, workload, 2203 + i))
+        procs.append(subprocess.Popen([sys.executable, "-c", code], env=env, stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True))
+    n, el = 0, 0.0
+    for p in procs:
+        out, _ = p.communicate(timeout=900)
+        d = json.loads(out.strip().splitlines()[-1])
+        n += d["n"]
+        el = max(el, d["el"])
+    return n, el
 
 
-def cpu_baseline(seconds, workload="medium"):
-    n, el = run_oracle_subprocess(seconds, workload)
-    return {"value": n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "oracle Sternheimer operator (H + alpha P_v - eps) on %d single-band vectors of the %s "
-                      "workload (20-band blocks cycling over its 64 k spheres), %.1f s, 1 thread" % (n, workload, el)}
+def host_cpu():
+    """(model name, logical cores) of the host, read at run time."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None and os.path.exists("/proc/cpuinfo"):
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                model = line.split(":", 1)[1].strip()
+                break
+    return model or "unknown", os.cpu_count() or 1
+
+
+def cpu_baseline(seconds, workload="precision"):
+    model, ncores = host_cpu()
+    n1, el1 = _oracle_procs(seconds, workload, 1)
+    nall, elall = _oracle_procs(seconds, workload, ncores)
+    return {"value": nall / elall, "unit": UNIT, "cores": ncores, "kind": "oracle", "cpu_model": model,
+            "one_thread": {"value": n1 / el1, "cores": 1},
+            "sample": "the oracle's Sternheimer operator (numpy FP64) on blocks of 20 bands cycling over the %s "
+                      "workload's k spheres: %d one-thread processes at once for %.1f s (%d H.psi), and one process "
+                      "alone (%d H.psi in %.1f s)" % (workload, ncores, elall, nall, n1, el1)}
+
+
+def static_config(workload, world=1):
+    return {"workload": WORKLOADS[workload], "step": STEP,
+            "l2": "inputs larger than L2 (response working set of several GB)",
+            "parallelism": "(q, J) pairs round-robin over %d rank(s)" % world}
 
 
 def reference_arm(args, rank):
+    """The oracle as it stands, timed on the host cores (one process per core) on this arm's workload
+    and metric; each step is a bounded sample of the workload."""
     if rank != 0:
         return
-    vals = []
-    n_tot, el_tot = 0, 0.0
+    if args.workload == "batch":
+        print(json.dumps({"impl": "reference", "unavailable": "the batch workload has no oracle arm"}))
+        return
+    model, ncores = host_cpu()
+    per = 4.0
     for _ in range(args.warmup):
-        run_oracle_subprocess(2.0, args.workload)
+        _oracle_procs(0.5, args.workload, ncores)
+    n_tot, el_tot = 0, 0.0
     for _ in range(args.steps):
-        n, el = run_oracle_subprocess(5.0, args.workload)
-        vals.append(n / el)
+        n, el = _oracle_procs(per, args.workload, ncores)
         n_tot += n
         el_tot += el
     value = n_tot / el_tot
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * el_tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload], "step": "about 5 s of the oracle's Sternheimer operator on the "
-                                                          "workload's spheres (1 thread)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "%d H.psi in %.1f s over %d steps" % (n_tot, el_tot, args.steps)},
+            "config": static_config(args.workload, args.gpus),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": ncores, "kind": "oracle", "cpu_model": model,
+                             "sample": "each step: %d one-thread oracle processes applying the Sternheimer operator for "
+                                       "about %.0f s; %d H.psi in %.1f s over %d steps"
+                                       % (ncores, per, n_tot, el_tot, args.steps)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -231,6 +299,16 @@ def reduce_over_ranks(elapsed, units, dist, device):
     dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
     dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
     return float(tmax[0]), float(t[1])
+
+
+def tensor_peak():
+    """Dense TF32 tensor peak for the contractions: the measured bf16 burst peak x the nominal
+    TF32/BF16 ratio (1.1 / 2.25)."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["bf16_tflops"]) * 1.1 / 2.25, "measured bf16 burst (MEASURED_PEAKS.json) x 1.1/2.25 (TF32)"
+    return 1900.0 * 1.1 / 2.25, "fallback 1.9 PFLOP/s bf16 x 1.1/2.25 (TF32)"
 
 
 def measured_peaks():
@@ -297,11 +375,106 @@ def batch_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def _traces(dn, nh):
+    import numpy as np
+
+    return np.array([np.trace(dn[a].sum(0)) for a in range(nh)])
+
+
+class Engine:
+    """One workload's context and ground state on this rank's GPU, and the timed pieces run on it."""
+
+    def __init__(self, P, W, name, stream, args, rank, world):
+        import torch
+
+        self.P, self.torch, self.name, self.stream = P, torch, name, stream
+        self.w = getattr(W, name)()
+        opts = dict(cuda_stream=stream.cuda_stream, band_batch=args.band_batch)
+        if args.cg_adapt is not None:
+            opts["cg_adapt"] = args.cg_adapt
+        self.ctx = P.Context.from_workload(self.w, **opts)
+        t0 = time.perf_counter()
+        self.gs = self.ctx.ground_state(self.w["nelec"], self.w["nspin"], self.w["moments"])
+        torch.cuda.synchronize()
+        self.gs_seconds = time.perf_counter() - t0
+        self.atoms, _ = self.ctx.hubbard_atoms()
+        self.sizes = self.ctx.query_sizes()
+        self.pairs = [(iq, int(J)) for J in self.atoms for iq in range(self.sizes["nq"])]
+        self.mine = shard_pairs(self.pairs, rank, world)
+
+    def event_time(self, fn):
+        """fn() between CUDA events on the context's stream; -> (result, seconds)."""
+        torch = self.torch
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(self.stream)
+        out = fn()
+        e1.record(self.stream)
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1) / 1000.0
+
+    def chi_matrix(self, precision):
+        """Every (q, J) response and hp_hubbard from the ready ground state: -> dict with the measured
+        wall time, H.psi, U (eV) and the V list."""
+        self.ctx.set_precision(precision)
+
+        def run():
+            hpsi = 0
+            for iq, J in self.pairs:
+                _, _, info = self.ctx.response(iq, J)
+                hpsi += info["hpsi"]
+            return hpsi, self.ctx.hubbard_parameters()
+
+        (hpsi, hp), el = self.event_time(run)
+        return {"seconds": el, "hpsi": hpsi, "hpsi_per_s": hpsi / el, "pairs": len(self.pairs),
+                "U_eV": [float(u) for u in hp["U"]], "V": [(int(a), int(b), float(d), float(v)) for a, b, d, v in hp["V"]]}
+
+
+def uv_error_mev(a, b):
+    """max |U_a - U_b| and max |V_a - V_b| over the pairs, in meV."""
+    du = max(abs(x - y) for x, y in zip(a["U_eV"], b["U_eV"])) * 1000.0
+    dv = max(abs(x[3] - y[3]) for x, y in zip(a["V"], b["V"])) * 1000.0 if a["V"] else None
+    return du, dv
+
+
+def golden_check(eng):
+    """The oracle's stored column of the medium cell (tests/golden/) against this GPU's FP64 and mixed
+    responses of the same (q, J) on its own ground state: max |Delta n_GPU - Delta n_oracle| /
+    max |Delta n_oracle| for Delta n^0 and Delta n, and the ground-state eigenvalues."""
+    import numpy as np
+
+    if not os.path.exists(GOLDEN_MEDIUM):
+        return None
+    g = json.load(open(GOLDEN_MEDIUM))
+    iq, J = int(g["iq"]), int(g["J"])
+    hub = [int(a) for a in g["hub_atoms"]]
+    mm = eng.sizes["mmax"]
+
+    def pad(d):
+        out = np.zeros((len(hub), eng.sizes["nspin"], mm, mm), dtype=complex)
+        for i, a in enumerate(hub):
+            re, im = d[str(a)]
+            x = np.array(re) + 1j * np.array(im)
+            out[i, :, : x.shape[1], : x.shape[2]] = x
+        return out
+
+    r0, r1 = pad(g["dn0"]), pad(g["dn"])
+    eps, _, _ = eng.ctx.get_ground_state()
+    out = {"column": {"qfrac": g["qfrac"], "J": J},
+           "eps_max_abs_diff_ha": float(np.abs(eps - np.array(g["eps"])).max())}
+    for prec, tag in ((0, "fp64"), (1, "mixed")):
+        eng.ctx.set_precision(prec)
+        dn0, dn, _ = eng.ctx.response(iq, J)
+        out[tag] = {"dn0_rel_err": float(np.abs(dn0 - r0).max() / np.abs(r0).max()),
+                    "dn_rel_err": float(np.abs(dn - r1).max() / np.abs(r1).max())}
+    return out
+
+
 def main():
     args = parse()
     if args.workload == "batch":
         if args.impl == "reference":
-            print(json.dumps({"impl": "reference", "unavailable": "the batch mode has no reference arm"}))
+            print(json.dumps({"impl": "reference", "unavailable": "the batch workload has no oracle arm"}))
             return
         batch_arm(args)
         return
@@ -323,18 +496,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     stream = torch.cuda.current_stream()
-    w = getattr(W, args.workload)()
-    opts = dict(cuda_stream=stream.cuda_stream, band_batch=args.band_batch)
-    if args.cg_adapt is not None:
-        opts["cg_adapt"] = args.cg_adapt
-    ctx = P.Context.from_workload(w, **opts)
-    t0 = time.perf_counter()
-    gs = ctx.ground_state(w["nelec"], w["nspin"], w["moments"])
-    gs_seconds = time.perf_counter() - t0
-    atoms, _ = ctx.hubbard_atoms()
-    s = ctx.query_sizes()
-    pairs = [(iq, int(J)) for J in atoms for iq in range(s["nq"])]
-    mine = shard_pairs(pairs, rank, world)
+    eng = Engine(P, W, args.workload, stream, args, rank, world)
+    ctx, mine, nh = eng.ctx, eng.mine, len(eng.atoms)
 
     def barrier():
         if dist is not None:
@@ -348,7 +511,7 @@ def main():
         for _ in range(warmup):
             iq, J = mine[k % len(mine)]
             _, dn, _ = ctx.response(iq, J)
-            traces[(iq, J)] = np.array([np.trace(dn[a].sum(0)) for a in range(len(atoms))])
+            traces[(iq, J)] = _traces(dn, nh)
             k += 1
         barrier()
         torch.cuda.synchronize()
@@ -363,10 +526,8 @@ def main():
         hpsi, iters = 0, []
         for _ in range(steps):
             iq, J = mine[k % len(mine)]
-            torch.cuda.nvtx.range_push("timed_step")
             _, dn, info = ctx.response(iq, J)
-            torch.cuda.nvtx.range_pop()
-            traces[(iq, J)] = np.array([np.trace(dn[a].sum(0)) for a in range(len(atoms))])
+            traces[(iq, J)] = _traces(dn, nh)
             hpsi += info["hpsi"]
             iters.append(info["iterations"])
             k += 1
@@ -381,12 +542,8 @@ def main():
         out["ms_per_step"] = 1000.0 * out["elapsed"] / steps if steps else None
         return out
 
-    # FP64 form (comparison) then the mixed form (headline), on the same ground state and pairs
-    f64 = leg(0, 0, args.fp64_warmup, args.fp64_steps)
+    # the headline: mixed form, K timed (q, J) responses
     mix = leg(1, 0, args.warmup, args.steps, profile=True, clocks=ClockSampler(torch.cuda.current_device()))
-    common = [p for p in f64["traces"] if p in mix["traces"]]
-    chi_rel = max(float(np.abs(mix["traces"][p] - f64["traces"][p]).max() / np.abs(f64["traces"][p]).max())
-                  for p in common) if common else None
 
     # end to end through the C ABI (mixed form): ground state from pinned host memory, response,
     # Delta n back to the host, every step
@@ -395,20 +552,45 @@ def main():
     host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in (vhxc, rho, eps)]
     psi_h = torch.from_numpy(psi.view(np.float64)).pin_memory().numpy().view(np.complex128)
     h2d = sum(a.nbytes for a in host) + psi_h.nbytes
-    d2h = 2 * s["nhub_atoms"] * s["nspin"] * s["mmax"] ** 2 * 16
+    d2h = 2 * eng.sizes["nhub_atoms"] * eng.sizes["nspin"] * eng.sizes["mmax"] ** 2 * 16
     barrier()
     torch.cuda.synchronize()
     te = time.perf_counter()
     hpsi_e, k = 0, mix["k"]
     for _ in range(args.e2e_steps):
         iq, J = mine[k % len(mine)]
-        ctx.set_ground_state_packed(w["nspin"], w["nelec"], host[0], host[1], host[2], psi_h)
+        ctx.set_ground_state_packed(eng.w["nspin"], eng.w["nelec"], host[0], host[1], host[2], psi_h)
         _, _, info = ctx.response(iq, J)
         hpsi_e += info["hpsi"]
         k += 1
     torch.cuda.synchronize()
     e2e_el = max(time.perf_counter() - te, 1e-9)
     barrier()
+
+    # FP64 form on the same ground state and pairs (comparison), the measured chi matrices
+    f64 = leg(0, 0, args.fp64_warmup, args.fp64_steps)
+    common = [p for p in f64["traces"] if p in mix["traces"]]
+    chi_rel = max(float(np.abs(mix["traces"][p] - f64["traces"][p]).max() / np.abs(f64["traces"][p]).max())
+                  for p in common) if common else None
+    chi = {"pairs_per_matrix": len(eng.pairs)}
+    if rank == 0 and world == 1 and not args.no_chi_matrix:
+        chi["mixed"] = eng.chi_matrix(1)
+        if args.fp64_full:
+            chi["fp64"] = eng.chi_matrix(0)
+            chi["u_err_mev_mixed_vs_fp64"], chi["v_err_mev_mixed_vs_fp64"] = uv_error_mev(chi["mixed"], chi["fp64"])
+            chi["speedup_mixed_vs_fp64"] = chi["fp64"]["seconds"] / chi["mixed"]["seconds"]
+    companion = None
+    if rank == 0 and world == 1 and args.companion != "none":
+        del ctx, eng.ctx
+        eng2 = Engine(P, W, args.companion, stream, args, 0, 1)
+        companion = {"workload": WORKLOADS[args.companion], "ground_state_s": eng2.gs_seconds, "gap_ha": eng2.gs["gap"]}
+        companion["chi_matrix"] = {"mixed": eng2.chi_matrix(1)}
+        if args.fp64_full:
+            companion["chi_matrix"]["fp64"] = eng2.chi_matrix(0)
+            u, v = uv_error_mev(companion["chi_matrix"]["mixed"], companion["chi_matrix"]["fp64"])
+            companion["chi_matrix"]["u_err_mev_mixed_vs_fp64"], companion["chi_matrix"]["v_err_mev_mixed_vs_fp64"] = u, v
+        if args.companion == "medium":
+            companion["oracle_column"] = golden_check(eng2)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -430,41 +612,39 @@ def main():
                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (nominal flops: 5 n log2 n "
                                    "per transformed line, 8 per complex multiply-add)",
                     "hbm_achieved_gbs": achieved, "hbm_peak_gbs": peak, "hbm_frac": achieved / peak}
+    elif bound == "tensor":
+        tpeak = tensor_peak()
+        roofline = {"bound": "tensor", "achieved": tflops, "peak": tpeak[0], "unit": "TFLOP/s",
+                    "frac": tflops / tpeak[0], "peak_source": tpeak[1],
+                    "hbm_achieved_gbs": achieved, "hbm_peak_gbs": peak, "hbm_frac": achieved / peak}
     else:
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                     "peak_source": peak_src, "achieved_tflops": tflops}
     roofline.update({"traffic": ncu_traffic(fam, alg, args.workload), "kernel": FAMILY_KERNELS[fam][0],
                      "launches": p["launches"], "avg_launch_ms": avg_s * 1000.0, "algorithmic_bytes_per_launch": alg,
                      "share_of_step": p["ms"] / 1000.0 / mix["elapsed"]})
-    roofline.update({
-                "families": {f: {"share_of_step": round(q["ms"] / 1000.0 / mix["elapsed"], 4),
-                                 "launches": q["launches"], "bound": FAMILY_BOUND[f],
-                                 "gbs": round(q["bytes"] / q["ms"] * 1e-6, 1) if q["ms"] else None,
-                                 "tflops": round(q["flops"] / q["ms"] * 1e-9, 3) if q["ms"] else None,
-                                 "traffic_per_launch": (ncu_traffic(f, q["bytes"] / q["launches"], args.workload)
-                                                        if q["launches"] else None)}
-                             for f, q in prof.items()}})
+    roofline["families"] = {f: {"share_of_step": round(q["ms"] / 1000.0 / mix["elapsed"], 4),
+                                "launches": q["launches"], "bound": FAMILY_BOUND[f],
+                                "gbs": round(q["bytes"] / q["ms"] * 1e-6, 1) if q["ms"] else None,
+                                "tflops": round(q["flops"] / q["ms"] * 1e-9, 3) if q["ms"] else None,
+                                "traffic_per_launch": (ncu_traffic(f, q["bytes"] / q["launches"], args.workload)
+                                                       if q["launches"] else None)}
+                            for f, q in prof.items()}
     line = {"metric": METRIC, "value": mix["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": mix["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64 (mixed: FP32 grids and projections, FP64 vectors and scalars)",
-            "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload],
-                       "step": "one (q, J) self-consistent Sternheimer response, %d band systems"
-                               % (s["nspin"] * s["nk"] * s["nocc"]),
-                       "pairs_per_chi_matrix": len(pairs),
-                       "chi_matrix_s": mix["ms_per_step"] * len(pairs) / 1000.0 / world,
-                       "outer_iterations_per_step": mix["iters"],
-                       "fp64": {"hpsi_per_s": f64["value"], "ms_per_step": f64["ms_per_step"],
-                                "chi_matrix_s": (f64["ms_per_step"] * len(pairs) / 1000.0 / world
-                                                 if f64["ms_per_step"] else None),
-                                "steps": args.fp64_steps, "warmup": args.fp64_warmup,
-                                "outer_iterations_per_step": f64["iters"], "gpu_launches": f64["launches"]},
-                       "chi_matrix_speedup_mixed_vs_fp64": (f64["ms_per_step"] / mix["ms_per_step"]
-                                                            if f64["ms_per_step"] else None),
-                       "chi_max_rel_diff_mixed_vs_fp64": chi_rel,
-                       "ground_state_s": gs_seconds, "gap_ha": gs["gap"],
-                       "l2": "inputs larger than L2 (response working set about 1.7 GB mixed, 2.6 GB FP64)",
-                       "parallelism": "(q, J) pairs round-robin over %d rank(s)" % world},
+            "vs_baseline": None, "dtype": "f32+f64 (mixed: FP32 grids and projections, FP64 step lengths, norms, "
+                                      "mixing and chi)",
+            "data": "synthetic", "config": static_config(args.workload, world),
+            "outer_iterations_per_step": mix["iters"],
+            "chi_matrix": chi,
+            "fp64": {"hpsi_per_s": f64["value"], "ms_per_pair": f64["ms_per_step"], "steps": args.fp64_steps,
+                     "warmup": args.fp64_warmup, "outer_iterations_per_step": f64["iters"],
+                     "gpu_launches": f64["launches"],
+                     "speedup_mixed_vs_fp64_per_pair": (f64["ms_per_step"] / mix["ms_per_step"]
+                                                        if f64["ms_per_step"] else None),
+                     "chi_column_max_rel_diff_mixed_vs_fp64": chi_rel},
+            "ground_state_s": eng.gs_seconds, "gap_ha": eng.gs["gap"],
+            "companion": companion,
             "clocks": mix["clocks"],
             "e2e": {"value": hpsi_e / e2e_el, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": mix["launches"], "roofline": roofline}

@@ -142,9 +142,10 @@ typedef struct {
     double residual;        /* final rms of dV_out - dV_in */
     double dchi;            /* final change of the response traces */
     double seconds;
-    int stagnated;          /* mixed form: 1 when the SCF stopped because its residual had not fallen for
-                             * three iterations while below 1e-5 of the response potential (the FP32
-                             * noise floor) rather than on the mixed_floor test; 0 otherwise */
+    int stagnated;          /* mixed form: 1 when the SCF stopped on the FP32 noise floor rather than on
+                             * the mixed_floor test: the residual is below 1e-5 of the response
+                             * potential and its last three iterations came no lower than 0.8 of the
+                             * best one before them; 0 otherwise */
 } hp_resp_info;
 
 /* One inter-site pair of hp_hubbard's V list: Hubbard atom s of the primitive cell (index into the
@@ -361,6 +362,17 @@ hp_status hp_selftest_eigh(int n, int nbatch, const double* A, double* w, double
  * response's Delta V_xc = sum_s' f_ss' Delta rho_s' (Sec. 2.3, the response Hxc potential).
  * Allocates its own device buffers.  Errors: HP_EINVAL, HP_ECUDA. */
 hp_status hp_selftest_xc(int n, int nspin, const double* rho, double* vxc, double* fxc);
+
+/* Device self-test of the tensor-core building block of the projector contractions (no counterpart
+ * in the paper): D[m][n] = sum_k A[m][k] B[n][k] for FP32 row-major A (M x K) and B (N x K) by
+ * tcgen05 kind::tf32 MMAs with the three-product TF32 split, FP32 accumulation in TMEM.
+ * 1 <= M <= 128, 16 <= N <= 128 with N % 16 == 0, K a multiple of 32.  lbo_swap = 1 exchanges the
+ * leading- and stride-byte-offset fields of the operand descriptors (the data layout is unchanged;
+ * every address stays inside the staged tiles), for checking which reading the hardware follows.
+ * Every device-side wait gives up after timeout_s (HP_ETIMEOUT).  Allocates its own device buffers.
+ * Errors: HP_EINVAL, HP_ECUDA, HP_ETIMEOUT. */
+hp_status hp_selftest_tc(int M, int N, int K, const float* A, const float* B, float* D, int lbo_swap,
+                         double timeout_s);
 
 /* Device self-test of the integer-operation FP64 <-> FP32 conversions used in the FP32 form's hot
  * loops (no counterpart in the paper).  For n host values in[i]: f[i] = FP64 -> FP32 rounded to

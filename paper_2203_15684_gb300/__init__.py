@@ -81,7 +81,8 @@ SYMBOLS = ["hp_default_options", "hp_setup", "hp_query_sizes", "hp_sphere", "hp_
            "hp_set_ground_state", "hp_get_ground_state", "hp_apply_h", "hp_response", "hp_hubbard", "hp_last_error",
            "hp_destroy", "hp_selftest_fft_host", "hp_selftest_eigh", "hp_get_wavefunctions", "hp_profile_begin",
            "hp_profile_end", "hp_launch_count", "hp_apply_h_noalloc", "hp_set_precision", "hp_selftest_convert",
-           "hp_batch_run", "hp_alloc_count", "hp_sphere_kq", "hp_apply_sternheimer", "hp_selftest_xc"]
+           "hp_batch_run", "hp_alloc_count", "hp_sphere_kq", "hp_apply_sternheimer", "hp_selftest_xc",
+           "hp_selftest_tc"]
 
 
 def lib():
@@ -125,6 +126,7 @@ def lib():
     L.hp_sphere_kq.argtypes = [V, I, I, P(I), P(I)]
     L.hp_apply_sternheimer.argtypes = [V, I, I, I, I, P(D), P(D), P(D)]
     L.hp_selftest_xc.argtypes = [I, I, P(D), P(D), P(D)]
+    L.hp_selftest_tc.argtypes = [I, I, I, P(C.c_float), P(C.c_float), P(C.c_float), I, D]
     for n in SYMBOLS:
         f = getattr(L, n)
         if n in ("hp_launch_count", "hp_alloc_count"):
@@ -227,6 +229,21 @@ def selftest_xc(rho):
     if st != HP_OK:
         raise HPError(st, "hp_selftest_xc")
     return v, f
+
+
+def selftest_tc(A, B, lbo_swap=0, timeout_s=2.0):
+    """D = A B^T on the tensor cores (tcgen05 kind::tf32, three-product TF32 split): A (M, K), B (N, K)
+    float32 -> D (M, N) float32."""
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    B = np.ascontiguousarray(B, dtype=np.float32)
+    M, K = A.shape
+    N = B.shape[0]
+    D = np.zeros((M, N), dtype=np.float32)
+    fp = lambda a: a.ctypes.data_as(C.POINTER(C.c_float))
+    st = lib().hp_selftest_tc(M, N, K, fp(A), fp(B), fp(D), int(lbo_swap), float(timeout_s))
+    if st != HP_OK:
+        raise HPError(st, "hp_selftest_tc")
+    return D
 
 
 class TorchAllocator:

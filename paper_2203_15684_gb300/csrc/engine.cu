@@ -597,6 +597,7 @@ static hp_status setup_impl(hp_ctx* c, const double cell[9], int nspecies, const
     if (c->nproj > kPStride || c->nhub > kPStride) return fail(c, HP_EINVAL, "hp_setup: more than 128 projector rows");
     if (c->hub_atoms.empty()) return fail(c, HP_EINVAL, "hp_setup: no Hubbard species");
     // device data
+    tc_set_timeout(c->opt.wait_timeout_s);
     c->fused = fused_supported(c->N) && !getenv("HP_NO_FUSED");
     c->fused_reg = !getenv("HP_FUSED_SMEM");  // HP_FUSED_SMEM: shared-memory line FFTs instead
     // rows of one combined projection (at most the buffer's 128; HP_PROJ_ROWS lowers it)
@@ -1401,6 +1402,8 @@ extern "C" hp_status hp_apply_sternheimer(hp_ctx* c, int iq, int ik, int spin, i
     dfree(c, dX64);
     dfree(c, dX);
     dfree(c, dY);
+    if (s == HP_OK && tc_enabled() && tc_take_error(c->st))
+        return fail(c, HP_ETIMEOUT, "hp_apply_sternheimer: a tensor-core contraction gave up on a bounded wait");
     return s;
 }
 
@@ -1569,7 +1572,11 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
             CK(d2h(rr.data(), c->d_rr, rows, c->st));
             list_clear(La);
             for (int i = 0; i < rows; ++i) {
-                if (!std::isfinite(rr[i])) return fail(c, HP_ENUMERIC, "hp_response: non-finite CG residual");
+                if (!std::isfinite(rr[i])) {
+                    if (tc_enabled() && tc_take_error(c->st))
+                        return fail(c, HP_ETIMEOUT, "hp_response: a tensor-core contraction gave up on a bounded wait");
+                    return fail(c, HP_ENUMERIC, "hp_response: non-finite CG residual");
+                }
                 if (rr[i] > tolb[i]) list_add(La, Lall.row[i], Lall.k[i], Lall.spin[i], Lall.shift[i]);
             }
             if (La.row.empty()) break;
@@ -1717,12 +1724,14 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
             converged = true;
             break;
         }
-        // mixed form: a residual that has stopped falling for three iterations below 1e-5 of the
-        // response potential sits on the FP32 noise floor; the iteration has done what it can
+        // mixed form: a residual below 1e-5 of the response potential whose last three iterations
+        // came no lower than 0.8 of the best one before them sits on the FP32 noise floor; the
+        // iteration has done what it can
         if (mixed && it >= 6 && res < 1e-5 * vrms) {
             const size_t n = res_hist.size();
             const double lo = std::min(res_hist[n - 1], std::min(res_hist[n - 2], res_hist[n - 3]));
-            if (lo > 0.5 * res_hist[n - 4] && dchi < 1e-5 * tmax) {
+            const double best = *std::min_element(res_hist.begin(), res_hist.end() - 3);
+            if (lo > 0.8 * best && dchi < 1e-5 * tmax) {
                 converged = true;
                 stagnated = true;
                 break;
@@ -1780,6 +1789,8 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
                            c->st));
     }
     CK(cudaStreamSynchronize(c->st));
+    if (tc_enabled() && tc_take_error(c->st))
+        return fail(c, HP_ETIMEOUT, "hp_response: a tensor-core contraction gave up on a bounded wait");
     RespCols& rc = c->cols[{iq, atom}];
     rc.dn0 = dn0;
     rc.dn = dn;

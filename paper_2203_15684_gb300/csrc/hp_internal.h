@@ -176,6 +176,35 @@ struct ProjMat {            // a family of projector matrices: base + s*stride_s
     double scale2 = 1.0;    // expansion weight of the second family's rows
 };
 
+// device view of a ProjMat (families in FP64 or in their FP32 copies)
+struct ProjDev {
+    const void* a0;
+    const void* a1;
+    long long s0_s, s0_k, s1_s, s1_k;
+    int n0, r0, n1, r1;
+    const int* kmap;
+};
+
+#if defined(__CUDACC__)
+template <class AT>
+__device__ __forceinline__ const AT* proj_row(const ProjDev& d, int s, int mk, int p, int ld) {
+    if (p < d.n0) return (const AT*)d.a0 + s * d.s0_s + mk * d.s0_k + (long long)(d.r0 + p) * ld;
+    return (const AT*)d.a1 + s * d.s1_s + mk * d.s1_k + (long long)(d.r1 + p - d.n0) * ld;
+}
+#endif
+
+// tc.cu: the FP32 projections and expansions on the tensor cores (tcgen05 kind::tf32, three-product
+// TF32 split, FP32 accumulation in TMEM); FP32 families and FP32 band vectors only
+bool tc_enabled();
+void tc_set_timeout(double seconds);
+// partial sums part[ks][item][p] of the projection over the ksplit plane-wave splits of each segment
+cudaError_t tc_proj(const ProjDev& d, const BandList& L, const SphereSet& S, const float2* X, int ld, int ksplit,
+                    double2* part, cudaStream_t st);
+cudaError_t tc_expand(const ProjDev& d, const BandList& L, const SphereSet& S, const double2* P, const double* pscale,
+                      double alpha, double scale2, float2* Y, int ld, cudaStream_t st);
+// 1 when a tensor-core kernel gave up on a bounded wait since the last call (synchronises the stream)
+int tc_take_error(cudaStream_t st);
+
 // kernels.cu
 cudaError_t k_scatter(const SphereSet& S, const BandList& L, int c0, int nc, const double2* X, int ldx,
                       double2* grid, int nr, cudaStream_t st);

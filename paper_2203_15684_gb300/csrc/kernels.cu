@@ -318,19 +318,6 @@ cudaError_t k_to_c64(const float2* a, double2* b, long long n, cudaStream_t st) 
 constexpr int kPStride = 128;
 constexpr int TG = 32;
 
-struct ProjDev {
-    const void* a0;
-    const void* a1;
-    long long s0_s, s0_k, s1_s, s1_k;
-    int n0, r0, n1, r1;
-    const int* kmap;
-};
-
-template <class AT>
-__device__ __forceinline__ const AT* proj_row(const ProjDev& d, int s, int mk, int p, int ld) {
-    if (p < d.n0) return (const AT*)d.a0 + s * d.s0_s + mk * d.s0_k + (long long)(d.r0 + p) * ld;
-    return (const AT*)d.a1 + s * d.s1_s + mk * d.s1_k + (long long)(d.r1 + p - d.n0) * ld;
-}
 
 template <class V>
 __device__ __forceinline__ V load_as(const double2& x) {
@@ -553,14 +540,20 @@ static cudaError_t proj_t(const BandList& L, const SphereSet& S, const ProjMat& 
     const bool use32 = fp32 && fam32(A);
     const ProjDev d = proj_dev(A, use32);
     const ProfMark pm = prof_start(st);
-    if (!fp32)
-        proj_launch<double, double2, XT>(npt, nbi, g, st, d, ld, X, L, S, ksplit, scratch);
-    else if (use32)
-        proj_launch<float, float2, XT>(npt, nbi, g, st, d, ld, X, L, S, ksplit, scratch);
-    else
-        proj_launch<float, double2, XT>(npt, nbi, g, st, d, ld, X, L, S, ksplit, scratch);
-    HP_LAUNCHED();
-    cudaError_t e = cudaGetLastError();
+    const bool tc = use32 && std::is_same<XT, float2>::value && tc_enabled();
+    cudaError_t e = cudaSuccess;
+    if (tc) {
+        e = tc_proj(d, L, S, reinterpret_cast<const float2*>(X), ld, ksplit, scratch, st);
+    } else {
+        if (!fp32)
+            proj_launch<double, double2, XT>(npt, nbi, g, st, d, ld, X, L, S, ksplit, scratch);
+        else if (use32)
+            proj_launch<float, float2, XT>(npt, nbi, g, st, d, ld, X, L, S, ksplit, scratch);
+        else
+            proj_launch<float, double2, XT>(npt, nbi, g, st, d, ld, X, L, S, ksplit, scratch);
+        HP_LAUNCHED();
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) return e;
     proj_reduce_kernel<<<cdiv((long long)L.nb * nrow, 256), 256, 0, st>>>(scratch, ksplit, L.nb, nrow, P);
     HP_LAUNCHED();
@@ -704,13 +697,18 @@ static cudaError_t expand_t(const BandList& L, const SphereSet& S, const ProjMat
     const ProjDev d = proj_dev(A, use32);
     const ProfMark pm = prof_start(st);
     const int ms = max_seg(L);
-    if (ms <= 4) expand_launch<4>(fp32, use32, g, st, d, ld, P, pscale, alpha, A.scale2, Y, L, S);
-    else if (ms <= 8) expand_launch<8>(fp32, use32, g, st, d, ld, P, pscale, alpha, A.scale2, Y, L, S);
-    else if (ms <= 12) expand_launch<12>(fp32, use32, g, st, d, ld, P, pscale, alpha, A.scale2, Y, L, S);
-    else if (ms <= 16 || !fp32) expand_launch<16>(fp32, use32, g, st, d, ld, P, pscale, alpha, A.scale2, Y, L, S);
-    else if (ms <= 20) expand_launch<20>(fp32, use32, g, st, d, ld, P, pscale, alpha, A.scale2, Y, L, S);
-    else expand_launch<24>(fp32, use32, g, st, d, ld, P, pscale, alpha, A.scale2, Y, L, S);
-    HP_LAUNCHED();
+    if (use32 && std::is_same<YT, float2>::value && tc_enabled()) {
+        const cudaError_t e = tc_expand(d, L, S, P, pscale, alpha, A.scale2, reinterpret_cast<float2*>(Y), ld, st);
+        if (e != cudaSuccess) return e;
+    } else {
+        if (ms <= 4) expand_launch<4>(fp32, use32, g, st, d, ld, P, pscale, alpha, A.scale2, Y, L, S);
+        else if (ms <= 8) expand_launch<8>(fp32, use32, g, st, d, ld, P, pscale, alpha, A.scale2, Y, L, S);
+        else if (ms <= 12) expand_launch<12>(fp32, use32, g, st, d, ld, P, pscale, alpha, A.scale2, Y, L, S);
+        else if (ms <= 16 || !fp32) expand_launch<16>(fp32, use32, g, st, d, ld, P, pscale, alpha, A.scale2, Y, L, S);
+        else if (ms <= 20) expand_launch<20>(fp32, use32, g, st, d, ld, P, pscale, alpha, A.scale2, Y, L, S);
+        else expand_launch<24>(fp32, use32, g, st, d, ld, P, pscale, alpha, A.scale2, Y, L, S);
+        HP_LAUNCHED();
+    }
     if (prof_on() && L.k.size() >= (size_t)L.nb && L.seg_k.size() >= (size_t)L.nseg) {
         // band vectors read and written, coefficients read, projector rows once per segment
         const double ab = use32 ? 8.0 : 16.0;
