@@ -113,6 +113,10 @@ typedef struct {
     void* (*dev_alloc)(size_t bytes, void* user);
     void (*dev_free)(void* ptr, void* user);
     void* alloc_user;
+    int hub_ortho;          /* Hubbard projectors (Sec. 2.2): 0 = non-orthogonalised atomic orbitals
+                             * (default); 1 = Loewdin ortho-atomic orbitals (Eq. OAO_def): at every k
+                             * (and k+q) phi~_b = sum_a phi_a (O^-1/2)_ab with O_ab = <phi_a|phi_b> over
+                             * every Hubbard orbital of every atom that carries one */
 } hp_options;
 
 /* Fills *opt with the defaults listed above. */
@@ -366,12 +370,13 @@ hp_status hp_selftest_xc(int n, int nspin, const double* rho, double* vxc, doubl
 /* Device self-test of the tensor-core building block of the projector contractions (no counterpart
  * in the paper): D[m][n] = sum_k A[m][k] B[n][k] for FP32 row-major A (M x K) and B (N x K) by
  * tcgen05 kind::tf32 MMAs with the three-product TF32 split, FP32 accumulation in TMEM.
- * 1 <= M <= 128, 16 <= N <= 128 with N % 16 == 0, K a multiple of 32.  lbo_swap = 1 exchanges the
+ * 1 <= M <= 128, 16 <= N <= 128 with N % 16 == 0, K a multiple of 32.  mode bits: 1 exchanges the
  * leading- and stride-byte-offset fields of the operand descriptors (the data layout is unchanged;
- * every address stays inside the staged tiles), for checking which reading the hardware follows.
- * Every device-side wait gives up after timeout_s (HP_ETIMEOUT).  Allocates its own device buffers.
- * Errors: HP_EINVAL, HP_ECUDA, HP_ETIMEOUT. */
-hp_status hp_selftest_tc(int M, int N, int K, const float* A, const float* B, float* D, int lbo_swap,
+ * every address stays inside the staged tiles), for checking which reading the hardware follows;
+ * 2 adds the fourth product a_lo b_lo; 4 drains the TMEM accumulator into FP64 registers after every
+ * 32 values of K.  Every device-side wait gives up after timeout_s (HP_ETIMEOUT).  Allocates its own
+ * device buffers.  Errors: HP_EINVAL, HP_ECUDA, HP_ETIMEOUT. */
+hp_status hp_selftest_tc(int M, int N, int K, const float* A, const float* B, float* D, int mode,
                          double timeout_s);
 
 /* Device self-test of the integer-operation FP64 <-> FP32 conversions used in the FP32 form's hot

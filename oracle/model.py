@@ -73,6 +73,16 @@ def good_fft_size(n):
         m += 1
 
 
+def lowdin_orthonormalize(phi):
+    """Loewdin ortho-atomic orbitals (Sec. 2.2, Eq. OAO_def) from the rows of ``phi`` (orbitals x plane
+    waves at one k): O_ab = <phi_a|phi_b>, phi~_b = sum_a phi_a (O^-1/2)_ab, with O^-1/2 from the
+    eigen-decomposition of the Hermitian O.  Every orbital of every atom in the set takes part."""
+    O = phi.conj() @ phi.T
+    w, V = np.linalg.eigh(O)
+    Sinv = (V * (w ** -0.5)[None, :]) @ V.conj().T
+    return Sinv.T @ phi
+
+
 class KData:
     """Per-k (or per-(k+q)) basis data: sphere, kinetic energies, grid map, projectors."""
 
@@ -90,6 +100,8 @@ class KData:
             raise ValueError("FFT grid too small to hold the wavefunction sphere")
         self.beta = model.projectors(self.K)          # (nproj, npw)
         self.phi = model.hubbard_orbitals(self.K)     # (nhub, npw)
+        if model.ortho_atomic:
+            self.phi = lowdin_orthonormalize(self.phi)
 
 
 class Model:
@@ -116,6 +128,12 @@ class Model:
         self.kpts = self.mesh_points(self.kmesh)
         self.qpts = self.mesh_points(self.qmesh)
         self.moments = w.get("moments")
+        # Hubbard projectors (Sec. 2.2): non-orthogonalised atomic orbitals, or Loewdin ortho-atomic
+        # orbitals orthogonalised over every orbital of every atom that carries one (Eq. OAO_def)
+        proj = w.get("hubbard_projectors", "atomic")
+        if proj not in ("atomic", "ortho-atomic"):
+            raise ValueError("hubbard_projectors must be 'atomic' or 'ortho-atomic'")
+        self.ortho_atomic = proj == "ortho-atomic"
         # separable projectors: one (l_proj) channel per atom, 2l+1 components
         self.proj_atom, self.proj_l, self.proj_m, self.proj_D = [], [], [], []
         for ia, s in enumerate(self.atom_species):

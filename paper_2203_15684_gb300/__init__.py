@@ -46,7 +46,7 @@ class Options(C.Structure):
                 ("gs_tol", C.c_double), ("gs_maxiter", C.c_int), ("fft_grid", C.c_int * 3), ("band_batch", C.c_int),
                 ("cuda_stream", C.c_void_p), ("cg_adapt", C.c_double), ("mixed_floor", C.c_double),
                 ("wait_timeout_s", C.c_double), ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN),
-                ("alloc_user", C.c_void_p)]
+                ("alloc_user", C.c_void_p), ("hub_ortho", C.c_int)]
 
 
 class Sizes(C.Structure):
@@ -231,16 +231,17 @@ def selftest_xc(rho):
     return v, f
 
 
-def selftest_tc(A, B, lbo_swap=0, timeout_s=2.0):
-    """D = A B^T on the tensor cores (tcgen05 kind::tf32, three-product TF32 split): A (M, K), B (N, K)
-    float32 -> D (M, N) float32."""
+def selftest_tc(A, B, lbo_swap=0, timeout_s=2.0, four=False, drain=False):
+    """D = A B^T on the tensor cores (tcgen05 kind::tf32, three-product TF32 split; four: also a_lo b_lo;
+    drain: accumulator drained to FP64 every 32 values of K): A (M, K), B (N, K) float32 -> D (M, N)."""
     A = np.ascontiguousarray(A, dtype=np.float32)
     B = np.ascontiguousarray(B, dtype=np.float32)
     M, K = A.shape
     N = B.shape[0]
     D = np.zeros((M, N), dtype=np.float32)
     fp = lambda a: a.ctypes.data_as(C.POINTER(C.c_float))
-    st = lib().hp_selftest_tc(M, N, K, fp(A), fp(B), fp(D), int(lbo_swap), float(timeout_s))
+    mode = (1 if lbo_swap else 0) | (2 if four else 0) | (4 if drain else 0)
+    st = lib().hp_selftest_tc(M, N, K, fp(A), fp(B), fp(D), mode, float(timeout_s))
     if st != HP_OK:
         raise HPError(st, "hp_selftest_tc")
     return D
@@ -311,6 +312,7 @@ class Context:
     @classmethod
     def from_workload(cls, w, torch_alloc=None, **opts):
         opts.setdefault("fft_grid", w.get("grid"))
+        opts.setdefault("hub_ortho", 1 if w.get("hubbard_projectors", "atomic") == "ortho-atomic" else 0)
         return cls(w["cell"], w["species"], w["atoms"], w["ecutwfc"], w["kmesh"], w["qmesh"], default_options(**opts),
                    torch_alloc=torch_alloc)
 

@@ -463,6 +463,7 @@ extern "C" void hp_default_options(hp_options* o) {
     o->dev_alloc = nullptr;
     o->dev_free = nullptr;
     o->alloc_user = nullptr;
+    o->hub_ortho = 0;
 }
 
 extern "C" const char* hp_last_error(const hp_ctx* c) { return c ? c->err.c_str() : "null context"; }
@@ -485,6 +486,8 @@ static hp_status setup_impl(hp_ctx* c, const double cell[9], int nspecies, const
     for (int i = 0; i < 3; ++i) {
         if (kmesh[i] < 1 || qmesh[i] < 1) return fail(c, HP_EINVAL, "hp_setup: mesh sizes must be >= 1");
     }
+    if (c->opt.hub_ortho != 0 && c->opt.hub_ortho != 1)
+        return fail(c, HP_EINVAL, "hp_setup: hub_ortho must be 0 (atomic) or 1 (ortho-atomic)");
     if (c->opt.nmix < 0 || c->opt.nmix > 8 || !(c->opt.cg_tol > 0) || c->opt.niter_max < 1 || c->opt.cg_maxiter < 1 ||
         !(c->opt.mixed_floor >= 0) || !(c->opt.wait_timeout_s > 0))
         return fail(c, HP_EINVAL, "hp_setup: options out of range (0 <= nmix <= 8, tolerances > 0, wait_timeout_s > 0)");
@@ -684,6 +687,10 @@ static hp_status setup_impl(hp_ctx* c, const double cell[9], int nspecies, const
         CK(cudaStreamSynchronize(c->st));
         dfree(c, d_mil);
         dfree(c, d_kc);
+    }
+    if (c->opt.hub_ortho) {  // Loewdin ortho-atomic Hubbard projectors at every k of the mesh
+        st = ortho_hubbard_rows(c, c->kset, c->nk, c->d_phi_k);
+        if (st != HP_OK) return st;
     }
     return HP_OK;
 }
@@ -1132,6 +1139,7 @@ hp_status build_qfam(hp_ctx* c, int iq, const std::vector<const KSphere*>& sph, 
     }
     hp_status s = family_rows(c, kc, mil, c->qc.set, false, F.beta);
     if (s == HP_OK) s = family_rows(c, kc, mil, c->qc.set, true, F.phi);
+    if (s == HP_OK && c->opt.hub_ortho) s = ortho_hubbard_rows(c, c->qc.set, nk, F.phi);
     if (s != HP_OK) return s;
     // occupied states: rows of k' on the mesh, non-self-consistent states off it
     std::vector<int> off;

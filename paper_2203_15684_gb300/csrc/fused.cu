@@ -334,7 +334,8 @@ __global__ void __launch_bounds__(kColRegThreads) col_fwd_reg_kernel(
 }
 
 // plane transforms with one thread per line: P (band, z) planes per CTA, each [y][x] in shared
-// memory with row stride N0 + 1.  The columns with one grid x form one run of consecutive column
+// memory with an odd row stride (N0, or N0 + 1 for even N0: 8-byte rows of different y then fall in
+// different bank pairs).  The columns with one grid x form one run of consecutive column
 // indices and consecutive y (mod N1), given per (k, x) by xtab = (first column, count, first y), so
 // the y-line threads read and write their column values straight from and to the column buffers:
 //   op 0: y-inverse (columns -> smem) | x: inverse, * V, forward | y-forward (smem -> columns)
@@ -343,7 +344,7 @@ __global__ void __launch_bounds__(kColRegThreads) col_fwd_reg_kernel(
 template <class V, int N0, int N1>
 struct PlaneCfg {
     static constexpr int L = N0 > N1 ? N0 : N1;
-    static constexpr int LD = N0 + 1;
+    static constexpr int LD = (N0 % 2) ? N0 : N0 + 1;
     static constexpr int kSmemMax = 227 * 1024;
     static constexpr int per_plane = N1 * LD * (int)sizeof(V);
     static constexpr int P0 = 256 / L > 0 ? 256 / L : 1;
@@ -352,10 +353,10 @@ struct PlaneCfg {
     static constexpr bool ok = N0 <= reg_nmax<V>() && N1 <= reg_nmax<V>() && P * per_plane <= kSmemMax;
     // resident CTAs per SM asked of the compiler (register budget 65536 / (NT * MINB) per thread):
     // three for the inverse-only form of FP32 lines up to 36 points, which fits 80 registers
-    // without spilling, two for the forms that also hold the forward transform
+    // without spilling, two for the other FP32 forms up to 45 points (128 registers, no spills)
     template <int OP>
     static constexpr int minb() {
-        return (sizeof(V) == 8 && L <= 36) ? (OP == 1 && 3 * P * per_plane <= 228 * 1024 ? 3 : 2) : 1;
+        return (sizeof(V) == 8 && L <= 45) ? (OP == 1 && L <= 36 && 3 * P * per_plane <= 228 * 1024 ? 3 : 2) : 1;
     }
 };
 
@@ -856,9 +857,9 @@ static cudaError_t plane_dispatch(int n0, int n1, const FusedArgs& a) {
 // ------------------------------------------------------------------------------------------------
 constexpr int kDrhoGroup = 32;
 
-// two resident CTAs per SM asked of the compiler for lines up to 36 points (no spills there)
+// two resident CTAs per SM asked of the compiler for lines up to 45 points
 template <int N0, int N1>
-constexpr int drho_minb() { return (N0 <= 36 && N1 <= 36) ? 2 : 1; }
+constexpr int drho_minb() { return (N0 <= 45 && N1 <= 45) ? 2 : 1; }
 
 template <int N0, int N1>
 __global__ void __launch_bounds__(PlaneCfg<float2, N0, N1>::NT, drho_minb<N0, N1>()) drho_plane_kernel(

@@ -406,6 +406,77 @@ hp_status cheb_filter(hp_ctx* c, const EigSpace& E, BandList& L, GsWork& W, doub
 
 }  // namespace
 
+// Pout[c0 + b][a] = sum_j V[g][a][j] w_j^-1/2 conj(V[g][b][j]) = (O^-1/2)_ab for O = V diag(w) V^H
+__global__ void lowdin_sym_kernel(const double2* __restrict__ V, const double* __restrict__ w,
+                                  const int* __restrict__ seg_start, int n, double2* __restrict__ Pout,
+                                  int* __restrict__ bad) {
+    const int g = blockIdx.x;
+    const int c0 = seg_start[g];
+    const double2* Vg = V + (long long)g * n * n;
+    const double* wg = w + (long long)g * n;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int a = e / n, b = e % n;
+        double2 s = cmk(0.0, 0.0);
+        for (int j = 0; j < n; ++j) {
+            const double ww = wg[j];
+            if (!(ww > 1e-28)) {
+                *bad = 1;
+                continue;
+            }
+            s = cadd(s, cscale(cmulc(Vg[(long long)b * n + j], Vg[(long long)a * n + j]), 1.0 / sqrt(ww)));
+        }
+        Pout[(long long)(c0 + b) * kPS + a] = s;
+    }
+}
+
+hp_status hp::ortho_hubbard_rows(hp_ctx* c, const SphereSet& S, int nk, double2* phi) {
+    const int n = c->nhub, ld = c->ld;
+    if (n == 0 || nk == 0) return HP_OK;
+    const int rows = nk * n;
+    double2 *Pb = nullptr, *Mb = nullptr, *Vb = nullptr, *Tmp = nullptr, *out = nullptr;
+    double* w = nullptr;
+    int* bad = nullptr;
+    CK(dalloc(c, &Pb, (size_t)rows * kPS));
+    CK(dalloc(c, &Mb, (size_t)nk * n * n));
+    CK(dalloc(c, &Vb, (size_t)nk * n * n));
+    CK(dalloc(c, &Tmp, (size_t)nk * n * n));
+    CK(dalloc(c, &w, (size_t)nk * n));
+    CK(dalloc(c, &out, (size_t)rows * ld));
+    CK(dalloc(c, &bad, 1));
+    auto release = [&]() {
+        for (void* p : {(void*)Pb, (void*)Mb, (void*)Vb, (void*)Tmp, (void*)w, (void*)out, (void*)bad}) dfree(c, p);
+    };
+    BandList& L = c->L3;
+    list_clear(L);
+    for (int k = 0; k < nk; ++k)
+        for (int m = 0; m < n; ++m) list_add(L, k * n + m, k, 0, 0.0);
+    hp_status st = upload_list(c, L);
+    if (st != HP_OK) return st;
+    // O_ab = <phi_a|phi_b>: the projection of every row on the family, packed per k as M[k][a][b]
+    ProjMat fam{phi, 0, (long long)n * ld, n, 0, nullptr};
+    if ((st = project(c, S, L, fam, phi, Pb)) != HP_OK) return st;
+    pack_seg_kernel<<<nk, 256, 0, c->st>>>(Pb, L.d_seg_start, n, Mb);
+    HP_LAUNCHED();
+    CK(cudaGetLastError());
+    const size_t jsh = (size_t)(n / 2 + 1) * (4 * sizeof(double) + 2 * sizeof(int));
+    jacobi_kernel<<<nk, 256, jsh, c->st>>>(Mb, Vb, w, Tmp, n, 40);
+    HP_LAUNCHED();
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync(bad, 0, sizeof(int), c->st));
+    lowdin_sym_kernel<<<nk, 256, 0, c->st>>>(Vb, w, L.d_seg_start, n, Pb, bad);
+    HP_LAUNCHED();
+    CK(cudaGetLastError());
+    // phi~_b = sum_a phi_a (O^-1/2)_ab
+    CK(cudaMemsetAsync(out, 0, sizeof(double2) * (size_t)rows * ld, c->st));
+    CK(k_expand(L, S, fam, Pb, nullptr, 1.0, out, ld, c->st));
+    CK(cudaMemcpyAsync(phi, out, sizeof(double2) * (size_t)rows * ld, cudaMemcpyDeviceToDevice, c->st));
+    int hbad = 0;
+    CK(d2h(&hbad, bad, 1, c->st));
+    release();
+    if (hbad) return fail(c, HP_ENUMERIC, "ortho-atomic projectors: the Hubbard orbitals are linearly dependent");
+    return HP_OK;
+}
+
 // Non-self-consistent occupied states at k points off the k mesh (k + q): Chebyshev-filtered
 // subspace iteration with the ground-state potential V_eff held fixed, nocc + extra bands, until the
 // occupied residuals ||(H - eps) u|| are below 1e-11.  out: [nspin][nkq][nocc][ld]; eps_occ:

@@ -392,6 +392,9 @@ hp_status project(hp_ctx* c, const SphereSet& S, const BandList& L, const ProjMa
 hp_status apply_nonlocal(hp_ctx* c, const SphereSet& S, const BandList& L, const double2* X, double2* Y, double2* P,
                          const int* kmap, bool fp32 = false);
 void invalidate_response(hp_ctx* c);
+// Loewdin ortho-atomic Hubbard rows (Eq. OAO_def) in place: for each of the nk spheres of S,
+// phi_b <- sum_a phi_a (O^-1/2)_ab with O_ab = <phi_a|phi_b> over the nhub rows (groundstate.cu)
+hp_status ortho_hubbard_rows(hp_ctx* c, const SphereSet& S, int nk, double2* phi);
 // occupied states at k points off the k mesh with the ground-state potential fixed (groundstate.cu)
 hp_status nscf_states(hp_ctx* c, const std::vector<const KSphere*>& sph, const SphereSet& S, const double2* beta,
                       double2* out, std::vector<double>& eps_occ);

@@ -235,6 +235,15 @@ def batch_cells(ncells=16, seed=BATCH_SEED):
     return cells
 
 
+def with_projectors(w, kind):
+    """A copy of workload ``w`` with its Hubbard projector kind: "atomic" (non-orthogonalised atomic
+    orbitals, the default) or "ortho-atomic" (Loewdin orthogonalised, Sec. 2.2)."""
+    out = copy.deepcopy(w)
+    out["hubbard_projectors"] = kind
+    out["name"] = w["name"] + ("_oao" if kind == "ortho-atomic" else "")
+    return out
+
+
 CONFIGS = {"tiny": tiny, "medium": medium, "precision": precision, "olivine": olivine}
 
 
