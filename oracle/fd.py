@@ -27,9 +27,13 @@ def fd_column(model, J, lam=2e-3, gs0=None, tol=1e-12, bare=False):
         gs0 = scf(model, tol=tol)
     frozen = gs0.vhxc if bare else None
 
+    # a Hubbard-corrected ground state keeps its Hubbard potential fixed: the linear-response problem
+    # has no response of the Hubbard potential (Sec. 2.3)
+    hub = gs0.hub_occ
+
     def d(h):
-        plus = scf(model, tol=tol, perturb=(J, +h), frozen_vhxc=frozen, vstart=gs0.vhxc)
-        minus = scf(model, tol=tol, perturb=(J, -h), frozen_vhxc=frozen, vstart=gs0.vhxc)
+        plus = scf(model, tol=tol, perturb=(J, +h), frozen_vhxc=frozen, vstart=gs0.vhxc, frozen_hub=hub)
+        minus = scf(model, tol=tol, perturb=(J, -h), frozen_vhxc=frozen, vstart=gs0.vhxc, frozen_hub=hub)
         return (_traces(plus) - _traces(minus)) / (2.0 * h)
 
     return (4.0 * d(lam / 2.0) - d(lam)) / 3.0

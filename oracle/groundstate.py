@@ -23,7 +23,7 @@ import math
 import numpy as np
 import scipy.linalg
 
-from . import xc
+from . import dftu, xc
 from .hamiltonian import apply_h, dense_h, hartree_r, to_grid
 from .mixing import Broyden
 
@@ -68,9 +68,10 @@ def eigensolve(model, kd, vr, nbnd, extra=None):
 
 
 class GroundState:
-    """Converged ground state: eigenpairs at the k mesh, densities and potentials."""
+    """Converged ground state: eigenpairs at the k mesh, densities and potentials; with a Hubbard
+    correction (DFT+U+V) also the occupation matrices its Hubbard potential is built from."""
 
-    def __init__(self, model, vloc, vhxc, rho, eps, C, kds, iterations, residual):
+    def __init__(self, model, vloc, vhxc, rho, eps, C, kds, iterations, residual, hub_occ=None):
         self.model = model
         self.vloc = vloc
         self.vhxc = vhxc
@@ -80,9 +81,20 @@ class GroundState:
         self.kds = kds
         self.iterations = iterations
         self.residual = residual
+        self.hub_occ = hub_occ    # occupations of V_Hub (dftu.occupations), None without a correction
 
     def vr(self, s):
         return self.vloc + self.vhxc[s]
+
+    def hub_w(self, kd, s):
+        """W of the ground state's Hubbard potential at k point ``kd`` (None without a correction)."""
+        if self.hub_occ is None:
+            return None
+        return dftu.w_matrix(self.model, kd, self.hub_occ, s)
+
+    def hub_dense(self, kd, s):
+        W = self.hub_w(kd, s)
+        return None if W is None else dftu.dense(self.model, kd, W)
 
     @property
     def nocc(self):
@@ -125,14 +137,42 @@ def density(model, C_all, kds):
     return rho * f / (len(kds) * model.omega)
 
 
+def _pack(occ):
+    onsite, pocc = occ
+    parts = [onsite[a].reshape(-1) for a in sorted(onsite)] + [p.reshape(-1) for p in pocc]
+    z = np.concatenate(parts) if parts else np.zeros(0, dtype=complex)
+    return np.concatenate([z.real, z.imag])
+
+
+def _unpack(x, like):
+    onsite, pocc = like
+    n = len(x) // 2
+    z = x[:n] + 1j * x[n:]
+    out_on, out_p, o = {}, [], 0
+    for a in sorted(onsite):
+        sz = onsite[a].size
+        out_on[a] = z[o:o + sz].reshape(onsite[a].shape)
+        o += sz
+    for p in pocc:
+        out_p.append(z[o:o + p.size].reshape(p.shape))
+        o += p.size
+    return out_on, out_p
+
+
 def scf(model, tol=1e-11, maxiter=300, nextra=4, alpha=0.3, nmix=6, perturb=None, frozen_vhxc=None,
-        vstart=None, verbose=False):
+        vstart=None, frozen_hub=None, verbose=False):
     """Fixed-occupation SCF.
 
     perturb: optional (atom J, lambda): adds lambda sum_m |phi^J_m><phi^J_m| to H (Sec. 2.3, the
     perturbing potential of Eq. chi).  frozen_vhxc: if given, V_Hxc is held at this value and one
     non-self-consistent diagonalisation is done (bare response, chi_0).  vstart: optional starting
-    V_Hxc (nspin, nr) instead of the one of the starting density."""
+    V_Hxc (nspin, nr) instead of the one of the starting density.
+
+    With Hubbard parameters in the workload (DFT+U+V, Sec. 2.1) H carries the Hubbard potential of
+    Eq. Hub_pot_0 built from the occupation matrices, which are mixed together with V_Hxc (one
+    modified Broyden vector) and converged to ``tol`` as well.  frozen_hub: occupation matrices to
+    hold the Hubbard potential at (the response of the Hubbard potential is not part of the
+    linear-response problem, Sec. 2.3)."""
     kds = [model.kdata(k) for k in model.kpts]
     vloc = model.vloc_r()
     nbnd = model.nocc + nextra
@@ -143,12 +183,17 @@ def scf(model, tol=1e-11, maxiter=300, nextra=4, alpha=0.3, nmix=6, perturb=None
         for ik, kd in enumerate(kds):
             ph = kd.phi[sl]
             extras[ik] = lam * (ph.T @ ph.conj())
+    hub = dftu.active(model)
     if frozen_vhxc is not None:
         vin = frozen_vhxc.copy()
     elif vstart is not None:
         vin = vstart.copy()
     else:
         vin = hxc_potential(model, initial_density(model))
+    occ_in = None
+    if hub:
+        occ_in = frozen_hub if frozen_hub is not None else dftu.occupations(
+            model, [[np.zeros((kd.npw, model.nocc)) for kd in kds] for _ in range(model.nspin)], kds)
     mixer = Broyden(alpha=alpha, nmix=nmix)
     res = np.inf
     it = 0
@@ -157,20 +202,34 @@ def scf(model, tol=1e-11, maxiter=300, nextra=4, alpha=0.3, nmix=6, perturb=None
         C = [[None] * len(kds) for _ in range(model.nspin)]
         for s in range(model.nspin):
             for ik, kd in enumerate(kds):
-                e, v = eigensolve(model, kd, vloc + vin[s], nbnd, extras[ik])
+                extra = extras[ik]
+                if hub:
+                    h = dftu.dense(model, kd, dftu.w_matrix(model, kd, occ_in, s))
+                    extra = h if extra is None else extra + h
+                e, v = eigensolve(model, kd, vloc + vin[s], nbnd, extra)
                 eps[s, ik] = e
                 C[s][ik] = v
         rho = density(model, C, kds)
         if frozen_vhxc is not None:
-            return GroundState(model, vloc, vin, rho, eps, C, kds, it, 0.0)
+            return GroundState(model, vloc, vin, rho, eps, C, kds, it, 0.0, occ_in)
         vout = hxc_potential(model, rho)
         F = vout - vin
         res = math.sqrt(float(np.mean(F * F)))
+        x, f = vin.reshape(-1), F.reshape(-1)
+        res_n = 0.0
+        if hub and frozen_hub is None:
+            occ_out = dftu.occupations(model, C, kds)
+            xn, fn = _pack(occ_in), _pack(occ_out) - _pack(occ_in)
+            res_n = float(np.abs(fn).max()) if len(fn) else 0.0
+            x, f = np.concatenate([x, xn]), np.concatenate([f, fn])
         if verbose:
-            print("scf", it, res)
-        if res < tol:
-            return GroundState(model, vloc, vin, rho, eps, C, kds, it, res)
-        vin = mixer.step(vin.reshape(-1), F.reshape(-1)).reshape(vin.shape)
+            print("scf", it, res, res_n)
+        if res < tol and res_n < tol:
+            return GroundState(model, vloc, vin, rho, eps, C, kds, it, res, occ_in)
+        x = mixer.step(x, f)
+        vin = x[: vin.size].reshape(vin.shape)
+        if hub and frozen_hub is None:
+            occ_in = _unpack(x[vin.size:], occ_in)
     raise RuntimeError("ground-state SCF did not converge (residual %.3e)" % res)
 
 
@@ -190,7 +249,7 @@ def kq_states(model, gs, ik, iq):
             Cs.append(gs.C[s][kp][rows, : model.nocc])
             es.append(gs.eps[s, kp, : model.nocc])
         else:
-            e, v = eigensolve(model, kdq, gs.vr(s), model.nocc)
+            e, v = eigensolve(model, kdq, gs.vr(s), model.nocc, gs.hub_dense(kdq, s))
             Cs.append(v)
             es.append(e)
     return kdq, Cs, np.array(es)

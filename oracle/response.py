@@ -31,18 +31,21 @@ import math
 
 import numpy as np
 
-from . import xc
+from . import dftu, xc
 from .groundstate import kq_states
 from .hamiltonian import apply_h, from_grid, hartree_r, to_grid
 from .mixing import Broyden
 
 
-def sternheimer_operator(model, kdq, vr, Cq, alpha, eps_v, X):
+def sternheimer_operator(model, kdq, vr, Cq, alpha, eps_v, X, W=None):
     """Left-hand side of Eq. LRKSeq_lp on the columns of X (npw_k+q, nb):
     (H_k+q + alpha O_k+q - eps_v) X with O_k+q = Cq Cq^H the projector on the occupied states at
     k+q (Eq. proj_v, Cq (npw_k+q, nocc)), ``vr`` the spin's local potential on the grid and eps_v
-    one shift per column."""
+    one shift per column.  W: the ground state's Hubbard potential at k+q (DFT+U+V, Eq. Hub_pot_0),
+    part of H_k+q; its response is not (Sec. 2.3)."""
     HX = apply_h(model, kdq, vr, X)
+    if W is not None:
+        HX = HX + dftu.apply(model, kdq, W, X)
     return HX + alpha * (Cq @ (Cq.conj().T @ X)) - X * np.asarray(eps_v)[None, :]
 
 
@@ -72,7 +75,8 @@ class ResponseContext:
     def apply_A(self, s, ik, X, eps_v):
         """(H_k+q + alpha O_k+q - eps_v) X for the columns of X (per-column eps_v)."""
         kdq, Cq, _ = self.kq[ik]
-        return sternheimer_operator(self.model, kdq, self.gs.vr(s), Cq[s], self.alpha, eps_v, X)
+        return sternheimer_operator(self.model, kdq, self.gs.vr(s), Cq[s], self.alpha, eps_v, X,
+                                    self.gs.hub_w(kdq, s))
 
     def dv_times_u(self, s, ik, dv):
         """Delta V_Hxc,q(r) u_k(r), taken to the k+q sphere."""

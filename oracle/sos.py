@@ -33,6 +33,9 @@ def bare_column(model, gs, iq, J):
             kd = gs.kds[ik]
             kdq, _, _ = kq_states(model, gs, ik, iq)
             H = dense_h(model, kdq, gs.vr(s))
+            hub = gs.hub_dense(kdq, s)  # DFT+U+V ground state: its Hubbard potential is part of H
+            if hub is not None:
+                H = H + hub
             e_all, v_all = scipy.linalg.eigh(H)
             ec, Vc = e_all[no:], v_all[:, no:]
             U = gs.C[s][ik][:, :no]
