@@ -159,6 +159,8 @@ typedef struct {
     int s, jchi;
     double dist;
     double V;
+    int j;                  /* the neighbour's Hubbard-atom index (primitive cell) ... */
+    int R[3];               /* ... displaced by the lattice vector R (crystal units) */
 } hp_pairV;
 
 /* ------------------------------------------------------------------------------------------ */
@@ -216,6 +218,13 @@ hp_status hp_ground_state(hp_ctx* ctx, double nelec, int nspin, const int* init_
 hp_status hp_set_ground_state(hp_ctx* ctx, int nspin, double nelec, const double* vhxc,
                               const double* rho, const double* eps, const double* psi);
 
+/* Lowest nlev (1 .. 100) eigenvalues (Ha, ascending) of the bare Hamiltonian T + V_loc + V_NL (no
+ * Hxc potential, no Hubbard term) at the first point of the k mesh (k = 0 for the Gamma-centred
+ * meshes).  No counterpart in the paper: it serves the electron-count rule of the batch of
+ * synthetic cells (the occupied band count is chosen at the largest gap of this spectrum).
+ * Errors: HP_EINVAL, HP_ENOTCONV, HP_ECUDA. */
+hp_status hp_bare_levels(hp_ctx* ctx, int nlev, double* eps);
+
 /* Reads back the ground state: any pointer may be NULL.  eps: nspin x nk x nocc; rho, vhxc:
  * nspin x nr.  Errors: HP_ESTATE before a ground state. */
 hp_status hp_get_ground_state(const hp_ctx* ctx, double* eps, double* rho, double* vhxc);
@@ -236,7 +245,7 @@ hp_status hp_get_ground_state(const hp_ctx* ctx, double* eps, double* rho, doubl
  * caller.  The current device must be the context's device (the one current at hp_setup) and the
  * stream must belong to it.  Errors: HP_EINVAL (bad arguments, another device current, or nb too
  * large for the fixed scratch on this grid: call it on fewer bands), HP_ESTATE (no ground state),
- * HP_ECUDA. */
+ * HP_ENOTIMPL (a Hubbard-corrected ground state, hp_set_hubbard), HP_ECUDA. */
 hp_status hp_apply_h_noalloc(hp_ctx* ctx, int ik, int spin, int nb, const double* psi_dev, double* out_dev,
                              void* stream);
 
@@ -246,7 +255,8 @@ hp_status hp_apply_h_noalloc(hp_ctx* ctx, int ik, int spin, int nb, const double
 hp_status hp_get_wavefunctions(const hp_ctx* ctx, double* psi);
 
 /* Kohn-Sham operator at mesh point ik and spin s applied to nb host vectors (npw_k complex each,
- * hp_sphere order): out = H psi with H = T + V_loc + V_Hxc,s + V_NL (needs a ground state). */
+ * hp_sphere order): out = H psi with H = T + V_loc + V_Hxc,s + V_NL, plus the Hubbard potential of a
+ * DFT+U+V ground state (hp_set_hubbard); needs a ground state. */
 hp_status hp_apply_h(hp_ctx* ctx, int ik, int spin, int nb, const double* psi, double* out);
 
 /* Wavefunction sphere at k+q for mesh point ik and q point iq, in the coefficient order the
@@ -272,6 +282,22 @@ hp_status hp_apply_sternheimer(hp_ctx* ctx, int iq, int ik, int spin, int nb, co
  * the context for hp_hubbard.  Errors: HP_ESTATE (no ground state), HP_ENOGAP, HP_EINVAL,
  * HP_ENOTCONV (partial data written), HP_ENUMERIC. */
 hp_status hp_response(hp_ctx* ctx, int iq, int atom, double* dn0, double* dn, hp_resp_info* info);
+
+/* Hubbard-corrected ground state (DFT+U+V, Sec. 2.1; the self-consistent U/V cycle of Sec. 5.2
+ * runs ground state -> response -> hp_hubbard -> hp_set_hubbard -> ground state ...).  U: on-site
+ * U per Hubbard atom in eV (nhub_atoms entries, NULL for none); V[0 .. nV): inter-site pairs
+ * (s = atom, j = neighbour, R = its lattice vector, V in eV; s, j index the Hubbard atoms; jchi and
+ * dist are ignored), as hp_hubbard returns them.  The Hubbard potential of Eq. Hub_pot_0,
+ *   V_Hub = sum_I U^I sum (delta/2 - n^I) |phi^I_m1><phi^I_m2|
+ *         - sum_(s,j,R) V sum n^{s j(R)}_m1m2 |phi^s_m1><phi^j_m2 shifted by R|,
+ * with the occupation matrices of Eq. occ_matrix_0 (1/N_k per cell) and the star sum over the
+ * listed pairs (list a pair in both directions), is added to H in hp_ground_state (its occupation
+ * matrices converged together with V_Hxc), in the states at k+q and in the Sternheimer operator;
+ * its response is not part of the linear response (Sec. 2.3).  hp_set_ground_state takes the
+ * occupation matrices from the imported occupied states.  All zero or nV = 0 with U = NULL: no
+ * correction.  Takes effect at the next hp_ground_state or hp_set_ground_state; discards the
+ * current ground state.  Errors: HP_EINVAL (an index out of range). */
+hp_status hp_set_hubbard(hp_ctx* ctx, const double* U, int nV, const hp_pairV* V);
 
 /* Post-processing (a11): the q-sum with phases (Eq. occ_matrix_response_lp_1) into chi_0 and chi
  * (Eq. chi), their inverses and U, V (Eqs. U_def, V_def).

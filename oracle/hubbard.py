@@ -70,3 +70,34 @@ def neighbours(model, s_index, dist_thr=6e-4):
         return []
     dmin = min(d for d, _ in dists)
     return sorted(j for d, j in dists if d <= dmin + dist_thr)
+
+
+def neighbour_pairs(model, s_index, dist_thr=6e-4):
+    """The neighbours of ``neighbours`` as (chi index, Hubbard index j, lattice vector R of the
+    neighbour in primitive cells): atom j displaced by R sits at the shortest distance from atom s."""
+    R = model.supercell_R()
+    nh = len(model.hub_atoms)
+    n = np.array(model.qmesh, dtype=float)
+    ia = model.hub_atoms[s_index]
+    out = []
+    for jchi in neighbours(model, s_index, dist_thr):
+        l, jj = divmod(jchi, nh)
+        ja = model.hub_atoms[jj]
+        d = (model.frac[ja] + R[l] - model.frac[ia]) / n
+        w = np.round(d)
+        out.append((jchi, jj, tuple(int(x) for x in (R[l] - w * n))))
+    return out
+
+
+def cycle_step(model_factory, U_in, pairs_in, solve):
+    """One step of the self-consistent U/V cycle (Sec. 2.1 with Sec. 5.2's workflow): the ground
+    state with the Hubbard potential of (U_in, pairs_in), every (q, J) response, chi_0 and chi,
+    then U_out (per Hubbard atom) and the nearest-neighbour pairs with V_out.  ``model_factory``
+    maps (U, pairs) to a Model; ``solve(model)`` returns (chi0, chi) assembled as assemble_chi does."""
+    m = model_factory(U_in, pairs_in)
+    chi0, chi = solve(m)
+    hub = hubbard_matrix(chi0, chi)
+    nh = len(m.hub_atoms)
+    U_out = [float(hub[s, s]) for s in range(nh)]
+    pairs_out = [(s, jj, Rv, float(hub[s, jchi])) for s in range(nh) for jchi, jj, Rv in neighbour_pairs(m, s)]
+    return U_out, pairs_out, hub

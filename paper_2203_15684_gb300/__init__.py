@@ -65,7 +65,8 @@ class RespInfo(C.Structure):
 
 
 class PairV(C.Structure):
-    _fields_ = [("s", C.c_int), ("jchi", C.c_int), ("dist", C.c_double), ("V", C.c_double)]
+    _fields_ = [("s", C.c_int), ("jchi", C.c_int), ("dist", C.c_double), ("V", C.c_double), ("j", C.c_int),
+                ("R", C.c_int * 3)]
 
 
 class KernelStats(C.Structure):
@@ -82,7 +83,7 @@ SYMBOLS = ["hp_default_options", "hp_setup", "hp_query_sizes", "hp_sphere", "hp_
            "hp_destroy", "hp_selftest_fft_host", "hp_selftest_eigh", "hp_get_wavefunctions", "hp_profile_begin",
            "hp_profile_end", "hp_launch_count", "hp_apply_h_noalloc", "hp_set_precision", "hp_selftest_convert",
            "hp_batch_run", "hp_alloc_count", "hp_sphere_kq", "hp_apply_sternheimer", "hp_selftest_xc",
-           "hp_selftest_tc"]
+           "hp_selftest_tc", "hp_set_hubbard", "hp_bare_levels"]
 
 
 def lib():
@@ -127,6 +128,8 @@ def lib():
     L.hp_apply_sternheimer.argtypes = [V, I, I, I, I, P(D), P(D), P(D)]
     L.hp_selftest_xc.argtypes = [I, I, P(D), P(D), P(D)]
     L.hp_selftest_tc.argtypes = [I, I, I, P(C.c_float), P(C.c_float), P(C.c_float), I, D]
+    L.hp_set_hubbard.argtypes = [V, P(D), I, P(PairV)]
+    L.hp_bare_levels.argtypes = [V, I, P(D)]
     for n in SYMBOLS:
         f = getattr(L, n)
         if n in ("hp_launch_count", "hp_alloc_count"):
@@ -451,7 +454,29 @@ class Context:
         pairs = (PairV * max(1, cap.value))()
         self._check(lib().hp_hubbard(self._ptr, None, None, None, None, pairs, C.byref(cap)), "hp_hubbard")
         V = [(p.s, p.jchi, p.dist, p.V) for p in pairs[: cap.value]]
-        return dict(chi0=chi0, chi=chi, hub=hub, U=U, V=V)
+        Vpairs = [(p.s, p.j, tuple(p.R), p.V) for p in pairs[: cap.value]]
+        return dict(chi0=chi0, chi=chi, hub=hub, U=U, V=V, pairs=Vpairs)
+
+    def set_hubbard(self, U=None, pairs=()):
+        """DFT+U+V ground state (hp_set_hubbard): U (eV per Hubbard atom, or None) and pairs
+        [(s, j, (R1, R2, R3), V_eV)] of Hubbard-atom indices, as hubbard_parameters()["pairs"]."""
+        nh = self.query_sizes()["nhub_atoms"]
+        u = None
+        if U is not None:
+            u_a = np.ascontiguousarray(U, dtype=np.float64).reshape(nh)
+            u = _dptr(u_a)
+        arr = (PairV * max(1, len(pairs)))()
+        for i, (s_, j, R, v) in enumerate(pairs):
+            arr[i].s, arr[i].j, arr[i].V = int(s_), int(j), float(v)
+            for d in range(3):
+                arr[i].R[d] = int(R[d])
+        self._check(lib().hp_set_hubbard(self._ptr, u, len(pairs), arr), "hp_set_hubbard")
+
+    def bare_levels(self, nlev):
+        """Lowest nlev eigenvalues of T + V_loc + V_NL at k = 0 (hp_bare_levels)."""
+        e = np.zeros(int(nlev))
+        self._check(lib().hp_bare_levels(self._ptr, int(nlev), _dptr(e)), "hp_bare_levels")
+        return e
 
     def sphere_kq(self, iq, ik):
         """Miller indices (npw, 3) of the k+q sphere in the response's coefficient order."""
@@ -470,6 +495,19 @@ class Context:
                                                _dptr(x.view(np.float64)), _dptr(out.view(np.float64))),
                     "hp_apply_sternheimer")
         return out
+
+
+def batch_electron_count(ctx, w):
+    """Occupied bands of a synthetic batch cell (nspin = 1): the band count b in
+    [n_H + n_L, 5 n_H + 3 n_L] with the largest gap eps_b - eps_(b-1) of the bare Hamiltonian's
+    spectrum at k = 0 (computed by the library); returns nelec = 2 b."""
+    kinds = [int(s) for s, _ in w["atoms"]]
+    nH = sum(1 for k in kinds if k == 0)
+    nL = len(kinds) - nH
+    lo, hi = nH + nL, 5 * nH + 3 * nL
+    e = ctx.bare_levels(hi + 1)
+    b = max(range(lo, hi + 1), key=lambda n: e[n] - e[n - 1])
+    return 2.0 * b
 
 
 def batch_run(contexts):

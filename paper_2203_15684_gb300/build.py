@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhpgb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["fft.cu", "kernels.cu", "engine.cu", "groundstate.cu", "noalloc.cu", "fused.cu", "profile.cu", "tc.cu"]
+SOURCES = ["fft.cu", "kernels.cu", "engine.cu", "groundstate.cu", "noalloc.cu", "fused.cu", "profile.cu", "tc.cu", "hubbard.cu"]
 
 
 def nvcc():

@@ -822,6 +822,25 @@ extern "C" hp_status hp_set_ground_state(hp_ctx* c, int nspin, double nelec, con
                               cudaMemcpyHostToDevice));
             }
     CK(cudaStreamSynchronize(c->st));
+    if (c->hub_on) {  // DFT+U+V: the Hubbard potential from the occupation matrices of the imported states
+        for (void* p : {(void*)c->d_hub_occ, (void*)c->d_hubW}) dfree(c, p);
+        CK(dalloc(c, &c->d_hub_occ, hub_occ_len(c, nspin)));
+        CK(dalloc(c, &c->d_hubW, (size_t)nspin * c->nk * c->nhub * c->nhub));
+        BandList& L = c->L3;
+        list_clear(L);
+        for (int sp = 0; sp < nspin; ++sp)
+            for (int k = 0; k < c->nk; ++k)
+                for (int v = 0; v < nocc; ++v) list_add(L, (sp * c->nk + k) * nocc + v, k, sp, 0.0);
+        if ((s = upload_list(c, L)) != HP_OK) return s;
+        double2* P;
+        CK(dalloc(c, &P, (size_t)L.nb * kPStride));
+        ProjMat F{c->d_phi_k, 0, (long long)c->nhub * c->ld, c->nhub, 0, nullptr};
+        if ((s = project(c, c->kset, L, F, c->d_psi, P)) != HP_OK) return s;
+        if ((s = hub_occupations(c, P, nspin, c->nk, nocc, c->d_kfrac, c->d_hub_occ)) != HP_OK) return s;
+        if ((s = hub_build_w(c, c->d_hub_occ, nspin, c->nk, c->d_kfrac, c->d_hubW)) != HP_OK) return s;
+        CK(cudaStreamSynchronize(c->st));
+        dfree(c, P);
+    }
     c->have_gs = true;
     return HP_OK;
 }
@@ -880,6 +899,7 @@ extern "C" hp_status hp_apply_h(hp_ctx* c, int ik, int spin, int nb, const doubl
     hp_status s = upload_list(c, L);
     if (s == HP_OK) s = apply_local(c, c->kset, L, dX, dY, c->d_veff);
     if (s == HP_OK) s = apply_nonlocal(c, c->kset, L, dX, dY, dP, nullptr);
+    if (s == HP_OK && c->hub_on && c->d_hubW) s = hub_apply(c, c->kset, L, c->d_phi_k, nullptr, c->d_hubW, dX, dY, false, false, dP);
     if (s == HP_OK) {
         cudaError_t e = d2h(h.data(), dY, h.size(), c->st);
         if (e != cudaSuccess) s = cuda_fail(c, e, "hp_apply_h copy-out");
@@ -1074,13 +1094,17 @@ hp_status prepare_resp(hp_ctx* c) {
 }
 
 
-void free_sphereset(hp_ctx* c, SphereSet& S) {
+}  // namespace
+
+void hp::free_sphereset(hp_ctx* c, SphereSet& S) {
     for (void* p : {(void*)S.d_npw, (void*)S.d_idx, (void*)S.d_g2, (void*)S.d_prec, (void*)S.d_prec32, (void*)S.d_kin32,
                     (void*)S.d_iz, (void*)S.d_ncol, (void*)S.d_col_start, (void*)S.d_col_len, (void*)S.d_col_xy,
                     (void*)S.d_xtab})
         dfree(c, p);
     S = SphereSet();
 }
+
+namespace {
 
 // projector (nrow0 = nproj) or Hubbard rows (nhub) at the given k points: kc [nk][3] Cartesian,
 // Miller indices [nk][ld][3] of the sphere set S
@@ -1141,6 +1165,21 @@ hp_status build_qfam(hp_ctx* c, int iq, const std::vector<const KSphere*>& sph, 
     if (s == HP_OK) s = family_rows(c, kc, mil, c->qc.set, true, F.phi);
     if (s == HP_OK && c->opt.hub_ortho) s = ortho_hubbard_rows(c, c->qc.set, nk, F.phi);
     if (s != HP_OK) return s;
+    if (c->hub_on) {  // W of the ground state's Hubbard potential at every k+q of this q
+        std::vector<double> kf(3 * nk);
+        for (int ik = 0; ik < nk; ++ik) {
+            const int ki[3] = {ik / (c->kmesh[1] * c->kmesh[2]), (ik / c->kmesh[2]) % c->kmesh[1], ik % c->kmesh[2]};
+            for (int d = 0; d < 3; ++d) kf[3 * ik + d] = (double)ki[d] / c->kmesh[d] + (double)qi[d] / c->qmesh[d];
+        }
+        double* d_kf;
+        CK(dalloc(c, &d_kf, kf.size()));
+        CK(h2d(d_kf, kf.data(), kf.size(), c->st));
+        dfree(c, F.hubW);
+        CK(dalloc(c, &F.hubW, (size_t)nspin * nk * c->nhub * c->nhub));
+        if ((s = hub_build_w(c, c->d_hub_occ, nspin, nk, d_kf, F.hubW)) != HP_OK) return s;
+        CK(cudaStreamSynchronize(c->st));
+        dfree(c, d_kf);
+    }
     // occupied states: rows of k' on the mesh, non-self-consistent states off it
     std::vector<int> off;
     for (int ik = 0; ik < nk; ++ik) {
@@ -1169,13 +1208,27 @@ hp_status build_qfam(hp_ctx* c, int iq, const std::vector<const KSphere*>& sph, 
         s = upload_sphereset(c, so, nullptr, So);
         c->fused = fused_before;  // the off-mesh set is not used by the fused transforms
         if (s != HP_OK) return s;
-        double2 *beta_o = nullptr, *psi_o = nullptr;
+        double2 *beta_o = nullptr, *psi_o = nullptr, *phi_o = nullptr, *w_o = nullptr;
         CK(dalloc(c, &beta_o, (size_t)noff * std::max(1, c->nproj) * ld));
         CK(dalloc(c, &psi_o, (size_t)nspin * noff * nocc * ld));
         s = family_rows(c, kco, milo, So, false, beta_o);
+        if (s == HP_OK && c->hub_on) {  // Hubbard rows and W of the off-mesh points, packed like beta_o
+            const size_t nn = (size_t)c->nhub * c->nhub;
+            CK(dalloc(c, &phi_o, (size_t)noff * c->nhub * ld));
+            CK(dalloc(c, &w_o, (size_t)nspin * noff * nn));
+            for (int j = 0; j < noff; ++j) {
+                CK(cudaMemcpyAsync(phi_o + (size_t)j * c->nhub * ld, F.phi + (size_t)off[j] * c->nhub * ld,
+                                   sizeof(double2) * c->nhub * ld, cudaMemcpyDeviceToDevice, c->st));
+                for (int sp = 0; sp < nspin; ++sp)
+                    CK(cudaMemcpyAsync(w_o + ((size_t)sp * noff + j) * nn, F.hubW + ((size_t)sp * nk + off[j]) * nn,
+                                       sizeof(double2) * nn, cudaMemcpyDeviceToDevice, c->st));
+            }
+        }
         std::vector<double> eps_o;
-        if (s == HP_OK) s = nscf_states(c, so, So, beta_o, psi_o, eps_o);
+        if (s == HP_OK) s = nscf_states(c, so, So, beta_o, phi_o, w_o, psi_o, eps_o);
         if (s != HP_OK) return s;
+        dfree(c, phi_o);
+        dfree(c, w_o);
         for (int j = 0; j < noff; ++j)
             for (int sp = 0; sp < nspin; ++sp)
                 CK(cudaMemcpyAsync(F.psi + ((size_t)sp * nk + off[j]) * nocc * ld,
@@ -1274,6 +1327,15 @@ void fam_psi_kq(const hp_ctx* c, const double2** base, const float2** base32, lo
     }
 }
 
+// Y += V_Hub X at k+q (DFT+U+V ground states; the Hubbard potential is fixed in the response)
+hp_status hub_term_kq(hp_ctx* c, const BandList& L, const double2* X, double2* Y) {
+    if (!c->hub_on || !c->d_hubW) return HP_OK;
+    const bool fp32 = c->opt.precision == HP_PRECISION_MIXED;
+    const ProjMat F = fam_phi_kq(c, c->nhub, 0);
+    const double2* W = c->qc.off ? c->qfam[c->qc.iq].hubW : c->d_hubW;
+    return hub_apply(c, c->qc.set, L, F.base, F.kmap, W, X, Y, c->vec32, fp32, c->d_Pbuf);
+}
+
 // Y = A X = (H_k+q + alpha O_k+q - eps_v) X on the items of L
 hp_status apply_sternheimer(hp_ctx* c, const BandList& L, const double2* X, double2* Y) {
     const SphereSet& S = c->qc.set;
@@ -1305,7 +1367,7 @@ hp_status apply_sternheimer(hp_ctx* c, const BandList& L, const double2* X, doub
                 CK(k_expand(L, S, F, c->d_Pbuf, w, al, Y, c->ld, c->st, fp32));
             }
         }
-        return HP_OK;
+        return hub_term_kq(c, L, X, Y);
     }
     if (c->vec32) {
         s = project(c, S, L, A, (const float2*)X, c->d_Pbuf, fp32);
@@ -1316,7 +1378,7 @@ hp_status apply_sternheimer(hp_ctx* c, const BandList& L, const double2* X, doub
         if (s != HP_OK) return s;
         CK(k_expand(L, S, A, c->d_Pbuf, c->d_projD, 1.0, Y, c->ld, c->st, fp32));
     }
-    return HP_OK;
+    return hub_term_kq(c, L, X, Y);
 }
 
 double dev_dot(hp_ctx* c, const double2* a, const double2* b, long long n, cudaError_t* err) {
@@ -1828,11 +1890,17 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
 // Nearest Hubbard neighbours of another species for the V list: for Hubbard atom s of cell 0, every
 // (l', s') of the q-mesh supercell with a minimum-image distance within d_min + dist_thr of the
 // shortest one (dist_thr = 6e-4 bohr, the paper's default, Appendix B); (chi index, distance) pairs
-static std::vector<std::pair<int, double>> nearest_hubbard(const hp_ctx* c, int s) {
+struct Neighbour {
+    int jchi, j;
+    double dist;
+    int R[3];
+};
+
+static std::vector<Neighbour> nearest_hubbard(const hp_ctx* c, int s) {
     const int nh = (int)c->hub_atoms.size();
     const double n[3] = {(double)c->qmesh[0], (double)c->qmesh[1], (double)c->qmesh[2]};
     const int ia = c->hub_atoms[s];
-    std::vector<std::pair<int, double>> all;
+    std::vector<Neighbour> all;
     for (int l1 = 0, l = 0; l1 < c->qmesh[0]; ++l1)
         for (int l2 = 0; l2 < c->qmesh[1]; ++l2)
             for (int l3 = 0; l3 < c->qmesh[2]; ++l3, ++l) {
@@ -1841,22 +1909,26 @@ static std::vector<std::pair<int, double>> nearest_hubbard(const hp_ctx* c, int 
                     const int ja = c->hub_atoms[jj];
                     if (c->atom_species[ja] == c->atom_species[ia]) continue;
                     double d[3], x[3] = {0, 0, 0};
+                    Neighbour nb{l * nh + jj, jj, 0.0, {0, 0, 0}};
                     for (int i = 0; i < 3; ++i) {
                         d[i] = (c->frac[3 * ja + i] + R[i] - c->frac[3 * ia + i]) / n[i];
-                        d[i] -= std::nearbyint(d[i]);
+                        const double w = std::nearbyint(d[i]);
+                        d[i] -= w;
+                        nb.R[i] = R[i] - (int)w * c->qmesh[i];  // the neighbour's lattice vector, primitive cells
                     }
                     for (int i = 0; i < 3; ++i)
                         for (int j = 0; j < 3; ++j) x[j] += d[i] * n[i] * c->cell[3 * i + j];
-                    all.push_back({l * nh + jj, std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2])});
+                    nb.dist = std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+                    all.push_back(nb);
                 }
             }
-    std::vector<std::pair<int, double>> out;
+    std::vector<Neighbour> out;
     if (all.empty()) return out;
     double dmin = INFINITY;
-    for (auto& p : all) dmin = std::min(dmin, p.second);
+    for (auto& p : all) dmin = std::min(dmin, p.dist);
     for (auto& p : all)
-        if (p.second <= dmin + 6e-4) out.push_back(p);
-    std::sort(out.begin(), out.end());
+        if (p.dist <= dmin + 6e-4) out.push_back(p);
+    std::sort(out.begin(), out.end(), [](const Neighbour& a, const Neighbour& b) { return a.jchi < b.jchi; });
     return out;
 }
 
@@ -1946,7 +2018,8 @@ extern "C" hp_status hp_hubbard(hp_ctx* c, double* chi0_out, double* chi_out, do
         const int cap = nV ? *nV : 0;
         for (int s = 0; s < nh; ++s)
             for (auto& p : nearest_hubbard(c, s)) {
-                if (V_out && cnt < cap) V_out[cnt] = hp_pairV{s, p.first, p.second, hubh[(size_t)s * n + p.first]};
+                if (V_out && cnt < cap)
+                    V_out[cnt] = hp_pairV{s, p.jchi, p.dist, hubh[(size_t)s * n + p.jchi], p.j, {p.R[0], p.R[1], p.R[2]}};
                 ++cnt;
             }
         if (nV) *nV = cnt;

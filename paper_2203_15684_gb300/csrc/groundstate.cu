@@ -271,6 +271,8 @@ struct EigSpace {
     const SphereSet* S;
     int nk, nbnd;
     const double2* beta;  // [nk][nproj][ld]
+    const double2* phi = nullptr;   // DFT+U+V: Hubbard rows [nk][nhub][ld] ...
+    const double2* hubW = nullptr;  // ... and W [nspin][nk][nhub][nhub]; null without a correction
 };
 
 struct GsWork {
@@ -284,11 +286,14 @@ struct GsWork {
 // Y = (H - shift) X for the list (shift taken from the list), including the nonlocal part
 hp_status apply_h_shift(hp_ctx* c, const EigSpace& E, const BandList& L, const double2* X, double2* Y, double2* P) {
     hp_status s = apply_local(c, *E.S, L, X, Y, c->d_veff);
-    if (s != HP_OK || c->nproj == 0) return s;
-    ProjMat B{E.beta, 0, (long long)c->nproj * c->ld, c->nproj, 0, nullptr};
-    s = project(c, *E.S, L, B, X, P);
     if (s != HP_OK) return s;
-    CK(k_expand(L, *E.S, B, P, c->d_projD, 1.0, Y, c->ld, c->st));
+    if (c->nproj > 0) {
+        ProjMat B{E.beta, 0, (long long)c->nproj * c->ld, c->nproj, 0, nullptr};
+        s = project(c, *E.S, L, B, X, P);
+        if (s != HP_OK) return s;
+        CK(k_expand(L, *E.S, B, P, c->d_projD, 1.0, Y, c->ld, c->st));
+    }
+    if (E.hubW) return hub_apply(c, *E.S, L, E.phi, nullptr, E.hubW, X, Y, false, false, P);
     return HP_OK;
 }
 
@@ -482,7 +487,7 @@ hp_status hp::ortho_hubbard_rows(hp_ctx* c, const SphereSet& S, int nk, double2*
 // occupied residuals ||(H - eps) u|| are below 1e-11.  out: [nspin][nkq][nocc][ld]; eps_occ:
 // [nspin][nkq][nocc].
 hp_status hp::nscf_states(hp_ctx* c, const std::vector<const KSphere*>& sph, const SphereSet& S, const double2* beta,
-                          double2* out, std::vector<double>& eps_occ) {
+                          const double2* phi, const double2* hubW, double2* out, std::vector<double>& eps_occ) {
     const int nspin = c->nspin, nocc = c->nocc, ld = c->ld, nr = c->nr;
     const int nkq = (int)sph.size();
     int npw_min = ld;
@@ -492,7 +497,7 @@ hp_status hp::nscf_states(hp_ctx* c, const std::vector<const KSphere*>& sph, con
     const int rows = nspin * nkq * nbnd;
     const long long nvec = (long long)rows * ld;
     const long long ndv = (long long)nspin * nr;
-    const EigSpace E{&S, nkq, nbnd, beta};
+    const EigSpace E{&S, nkq, nbnd, beta, phi, hubW};
     GsWork W;
     CK(dalloc(c, &W.X, nvec));
     CK(dalloc(c, &W.Y0, nvec));
@@ -629,7 +634,18 @@ extern "C" hp_status hp_ground_state(hp_ctx* c, double nelec, int nspin, const i
     CK(dalloc(c, &c->d_rho, ndv));
     CK(dalloc(c, &c->d_veff, ndv));
     CK(dalloc(c, &c->d_psi, nvec));
-    const EigSpace E{&c->kset, nk, nbnd, c->d_beta_k};
+    // DFT+U+V: the occupation matrices of the Hubbard potential ride at the end of the mixed vector
+    const bool hub = c->hub_on;
+    const long long nho = hub ? hub_occ_len(c, nspin) : 0;
+    const long long ndvx = ndv + nho;
+    for (void* p : {(void*)c->d_hub_occ, (void*)c->d_hubW}) dfree(c, p);
+    c->d_hub_occ = nullptr;
+    c->d_hubW = nullptr;
+    if (hub) {
+        CK(dalloc(c, &c->d_hub_occ, nho));
+        CK(dalloc(c, &c->d_hubW, (size_t)nspin * nk * c->nhub * c->nhub));
+    }
+    const EigSpace E{&c->kset, nk, nbnd, c->d_beta_k, hub ? c->d_phi_k : nullptr, hub ? c->d_hubW : nullptr};
     GsWork W;
     CK(dalloc(c, &W.X, nvec));
     CK(dalloc(c, &W.Y0, nvec));
@@ -683,17 +699,18 @@ extern "C" hp_status hp_ground_state(hp_ctx* c, double nelec, int nspin, const i
     if (!c->d_partial) CK(dalloc(c, &c->d_partial, 1024));
     double2 *vin, *vout, *dvh, *xprev, *fprev;
     double* vxc;
-    CK(dalloc(c, &vin, ndv));
-    CK(dalloc(c, &vout, ndv));
+    CK(dalloc(c, &vin, ndvx));
+    CK(dalloc(c, &vout, ndvx));
     CK(dalloc(c, &dvh, nr));
-    CK(dalloc(c, &xprev, ndv));
-    CK(dalloc(c, &fprev, ndv));
+    CK(dalloc(c, &xprev, ndvx));
+    CK(dalloc(c, &fprev, ndvx));
     CK(dalloc(c, &vxc, ndv));
+    if (hub) CK(cudaMemsetAsync(vin + ndv, 0, sizeof(double2) * nho, c->st));  // start: empty occupations
     const int nmix = 6;
     std::vector<double2*> hdx(nmix), hdf(nmix);
     for (int i = 0; i < nmix; ++i) {
-        CK(dalloc(c, &hdx[i], ndv));
-        CK(dalloc(c, &hdf[i], ndv));
+        CK(dalloc(c, &hdx[i], ndvx));
+        CK(dalloc(c, &hdf[i], ndvx));
     }
     double2** dptrs;
     CK(dalloc(c, &dptrs, 2 * (nmix + 1)));
@@ -759,6 +776,7 @@ extern "C" hp_status hp_ground_state(hp_ctx* c, double nelec, int nspin, const i
         veff_kernel<<<cdiv_(nr, 256), 256, 0, c->st>>>(c->d_vloc, vin, nspin, nr, c->d_veff, c->d_vhxc);
         HP_LAUNCHED();
         CK(cudaGetLastError());
+        if (hub && (st = hub_build_w(c, vin + ndv, nspin, nk, c->d_kfrac, c->d_hubW)) != HP_OK) return st;
         vec_max_kernel<<<1, 256, 0, c->st>>>(c->d_veff, ndv, c->d_small + 100);
         HP_LAUNCHED();
         CK(cudaGetLastError());
@@ -791,14 +809,23 @@ extern "C" hp_status hp_ground_state(hp_ctx* c, double nelec, int nspin, const i
                 CK(fft3d(c->fft, c->d_grid, nc, +1, c->st));
                 CK(k_density_acc(c->d_grid, nc, nr, Lo, c0, wrho, nspin, c->d_rho, c->st));
             }
+            if (hub) {  // occupation matrices of the occupied states, at the end of the output vector
+                ProjMat F{c->d_phi_k, 0, (long long)c->nhub * ld, c->nhub, 0, nullptr};
+                if ((st = project(c, c->kset, Lo, F, W.X, W.Pb)) != HP_OK) return st;
+                if ((st = hub_occupations(c, W.Pb, nspin, nk, nocc, c->d_kfrac, vout + ndv)) != HP_OK) return st;
+            }
         }
         if ((st = hxc(vout)) != HP_OK) return st;
-        CK(k_vec_sub(vout, vout, vin, ndv, c->st));  // residual F
-        double ff = 0.0;
+        CK(k_vec_sub(vout, vout, vin, ndvx, c->st));  // residual F
+        double ff = 0.0, fn = 0.0;
         CK(k_vec_dot(vout, vout, ndv, c->d_small, c->d_partial, c->st));
         CK(d2h(&ff, c->d_small, 1, c->st));
-        if (!std::isfinite(ff)) return fail(c, HP_ENUMERIC, "hp_ground_state: non-finite residual");
-        res = std::sqrt(ff / (double)ndv);
+        if (hub) {
+            CK(k_vec_dot(vout + ndv, vout + ndv, nho, c->d_small, c->d_partial, c->st));
+            CK(d2h(&fn, c->d_small, 1, c->st));
+        }
+        if (!std::isfinite(ff) || !std::isfinite(fn)) return fail(c, HP_ENUMERIC, "hp_ground_state: non-finite residual");
+        res = std::max(std::sqrt(ff / (double)ndv), hub ? std::sqrt(fn / (double)nho) : 0.0);
         if (verbose)
             fprintf(stderr, "hp_ground_state: it %d res %.3e vmax %.3f b %.3f top %.4f occ %.6f\n", it, res, vmax, b,
                     aseg.empty() ? 0.0 : *std::max_element(ritz.begin(), ritz.end()), ritz[nocc - 1]);
@@ -819,23 +846,23 @@ extern "C" hp_status hp_ground_state(hp_ctx* c, double nelec, int nspin, const i
                 hdf[nmix - 1] = t0f;
                 --nhist;
             }
-            CK(k_vec_sub(hdf[nhist], vout, fprev, ndv, c->st));
-            CK(k_vec_sub(hdx[nhist], vin, xprev, ndv, c->st));
+            CK(k_vec_sub(hdf[nhist], vout, fprev, ndvx, c->st));
+            CK(k_vec_sub(hdx[nhist], vin, xprev, ndvx, c->st));
             double nn = 0.0;
-            CK(k_vec_dot(hdf[nhist], hdf[nhist], ndv, c->d_small, c->d_partial, c->st));
+            CK(k_vec_dot(hdf[nhist], hdf[nhist], ndvx, c->d_small, c->d_partial, c->st));
             CK(d2h(&nn, c->d_small, 1, c->st));
             if (nn > 0) {
-                CK(k_vec_scale_copy(hdf[nhist], hdf[nhist], 1.0 / std::sqrt(nn), ndv, c->st));
-                CK(k_vec_scale_copy(hdx[nhist], hdx[nhist], 1.0 / std::sqrt(nn), ndv, c->st));
+                CK(k_vec_scale_copy(hdf[nhist], hdf[nhist], 1.0 / std::sqrt(nn), ndvx, c->st));
+                CK(k_vec_scale_copy(hdx[nhist], hdx[nhist], 1.0 / std::sqrt(nn), ndvx, c->st));
                 ++nhist;
             }
         }
-        CK(cudaMemcpyAsync(xprev, vin, sizeof(double2) * ndv, cudaMemcpyDeviceToDevice, c->st));
-        CK(cudaMemcpyAsync(fprev, vout, sizeof(double2) * ndv, cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemcpyAsync(xprev, vin, sizeof(double2) * ndvx, cudaMemcpyDeviceToDevice, c->st));
+        CK(cudaMemcpyAsync(fprev, vout, sizeof(double2) * ndvx, cudaMemcpyDeviceToDevice, c->st));
         const int m = nhist;
         for (int i = 0; i < m; ++i)
             for (int j = 0; j <= m; ++j)
-                CK(k_vec_dot(hdf[i], j < m ? hdf[j] : vout, ndv, c->d_small + 16 + i * (m + 1) + j, c->d_partial, c->st));
+                CK(k_vec_dot(hdf[i], j < m ? hdf[j] : vout, ndvx, c->d_small + 16 + i * (m + 1) + j, c->d_partial, c->st));
         CK(k_broyden_coef(c->d_small + 16, m, m + 1, 0.01, c->d_small + 8, c->st));
         std::vector<const double2*> ptrs(2 * (nmix + 1), nullptr);
         for (int i = 0; i < m; ++i) {
@@ -844,12 +871,13 @@ extern "C" hp_status hp_ground_state(hp_ctx* c, double nelec, int nspin, const i
         }
         CK(h2d((const double2**)dptrs, ptrs.data(), ptrs.size(), c->st));
         CK(k_broyden_apply(vin, vout, (const double2* const*)dptrs, (const double2* const*)(dptrs + nmix + 1),
-                           c->d_small + 8, m, 0.3, ndv, c->st));
+                           c->d_small + 8, m, 0.3, ndvx, c->st));
     }
     // polish: extra filter passes at the final potential until the occupied residuals are small
     veff_kernel<<<cdiv_(nr, 256), 256, 0, c->st>>>(c->d_vloc, vin, nspin, nr, c->d_veff, c->d_vhxc);
     HP_LAUNCHED();
     CK(cudaGetLastError());
+    if (hub && (st = hub_build_w(c, vin + ndv, nspin, nk, c->d_kfrac, c->d_hubW)) != HP_OK) return st;
     double rmax = INFINITY;
     for (int pass = 0; pass < 30; ++pass) {
         vec_max_kernel<<<1, 256, 0, c->st>>>(c->d_veff, ndv, c->d_small + 100);
@@ -904,6 +932,12 @@ extern "C" hp_status hp_ground_state(hp_ctx* c, double nelec, int nspin, const i
             CK(fft3d(c->fft, c->d_grid, nc, +1, c->st));
             CK(k_density_acc(c->d_grid, nc, nr, Lo, c0, wrho, nspin, c->d_rho, c->st));
         }
+        if (hub) {  // the occupations (and W) the response's Hamiltonian uses: those of the final states
+            ProjMat F{c->d_phi_k, 0, (long long)c->nhub * ld, c->nhub, 0, nullptr};
+            if ((st = project(c, c->kset, Lo, F, c->d_psi, W.Pb)) != HP_OK) return st;
+            if ((st = hub_occupations(c, W.Pb, nspin, nk, nocc, c->d_kfrac, c->d_hub_occ)) != HP_OK) return st;
+            if ((st = hub_build_w(c, c->d_hub_occ, nspin, nk, c->d_kfrac, c->d_hubW)) != HP_OK) return st;
+        }
     }
     CK(cudaStreamSynchronize(c->st));
     c->eps = ritz;
@@ -938,6 +972,39 @@ extern "C" hp_status hp_ground_state(hp_ctx* c, double nelec, int nspin, const i
     }
     if (!converged || rmax > 1e-9) return fail(c, HP_ENOTCONV, "hp_ground_state: SCF or eigenvector residual cap reached");
     if (!(gap > 1e-4)) return fail(c, HP_ENOGAP, "hp_ground_state: no gap at the fixed band count");
+    return HP_OK;
+}
+
+// Lowest levels of the bare Hamiltonian T + V_loc + V_NL (no Hxc, no Hubbard term) at the first k
+// point of the mesh (Gamma for the Gamma-centred meshes), by the non-self-consistent eigensolver.
+extern "C" hp_status hp_bare_levels(hp_ctx* c, int nlev, double* eps) {
+    if (!c) return HP_EINVAL;
+    if (nlev < 1 || nlev > 100 || !eps) return fail(c, HP_EINVAL, "hp_bare_levels: 1 <= nlev <= 100 and eps given");
+    if (c->ks[0].npw < nlev + 6) return fail(c, HP_EINVAL, "hp_bare_levels: fewer plane waves than levels");
+    const int nspin0 = c->nspin, nocc0 = c->nocc;
+    double* veff0 = c->d_veff;
+    const bool hub0 = c->hub_on;
+    c->nspin = 1;
+    c->nocc = nlev;
+    c->d_veff = c->d_vloc;
+    c->hub_on = false;
+    SphereSet S0;
+    std::vector<const KSphere*> sph{&c->ks[0]};
+    const bool fused0 = c->fused;
+    hp_status st = upload_sphereset(c, sph, nullptr, S0);
+    c->fused = fused0;
+    double2* psi = nullptr;
+    std::vector<double> lev;
+    if (st == HP_OK && dalloc(c, &psi, (size_t)nlev * c->ld) != cudaSuccess) st = fail(c, HP_ENOMEM, "hp_bare_levels");
+    if (st == HP_OK) st = nscf_states(c, sph, S0, c->d_beta_k, nullptr, nullptr, psi, lev);
+    c->nspin = nspin0;
+    c->nocc = nocc0;
+    c->d_veff = veff0;
+    c->hub_on = hub0;
+    dfree(c, psi);
+    free_sphereset(c, S0);
+    if (st != HP_OK) return st;
+    for (int i = 0; i < nlev; ++i) eps[i] = lev[i];
     return HP_OK;
 }
 

@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <array>
 #include <atomic>
 #include <cstdint>
 #include <map>
@@ -320,6 +321,13 @@ struct QFam {
     bool built = false;
     double2 *psi = nullptr, *beta = nullptr, *phi = nullptr;  // [nspin][nk][nocc][ld], [nk][nproj][ld], [nk][nhub][ld]
     float2 *psi32 = nullptr, *beta32 = nullptr, *phi32 = nullptr;
+    double2* hubW = nullptr;       // DFT+U+V: W of the Hubbard potential at each k+q, [nspin][nk][nhub][nhub]
+};
+
+// DFT+U+V (hubbard.cu): parameters on the device and the Hubbard potential in the projection basis
+struct HubPair {
+    int i, j, R[3];                // Hubbard-atom indices and the lattice vector of j
+    double V;                      // Ha
 };
 
 struct QCache {                    // per-q data: the k+q sphere set and the k map of the families
@@ -382,6 +390,10 @@ hp_status upload_list(hp_ctx* c, BandList& L);
 void list_clear(BandList& L);
 void list_add(BandList& L, int row, int k, int spin, double shift);
 hp_status ensure_grid(hp_ctx* c, int want);
+// sphere sets (engine.cu): spheres of the given k points, Miller indices shifted by -shift[k]
+hp_status upload_sphereset(hp_ctx* c, const std::vector<const KSphere*>& sph,
+                           const std::vector<std::array<int, 3>>* shift, SphereSet& S);
+void free_sphereset(hp_ctx* c, SphereSet& S);
 int band_batch(const hp_ctx* c, int nb);
 hp_status apply_local(hp_ctx* c, const SphereSet& S, const BandList& L, const double2* X, double2* Y,
                       const double* veff, bool fp32 = false);
@@ -395,9 +407,24 @@ void invalidate_response(hp_ctx* c);
 // Loewdin ortho-atomic Hubbard rows (Eq. OAO_def) in place: for each of the nk spheres of S,
 // phi_b <- sum_a phi_a (O^-1/2)_ab with O_ab = <phi_a|phi_b> over the nhub rows (groundstate.cu)
 hp_status ortho_hubbard_rows(hp_ctx* c, const SphereSet& S, int nk, double2* phi);
-// occupied states at k points off the k mesh with the ground-state potential fixed (groundstate.cu)
+// occupied states at k points off the k mesh with the ground-state potential fixed (groundstate.cu);
+// phi / hubW: Hubbard rows and W at those k points (DFT+U+V ground states), else null
 hp_status nscf_states(hp_ctx* c, const std::vector<const KSphere*>& sph, const SphereSet& S, const double2* beta,
-                      double2* out, std::vector<double>& eps_occ);
+                      const double2* phi, const double2* hubW, double2* out, std::vector<double>& eps_occ);
+// DFT+U+V (hubbard.cu).  The occupation vector holds, as complex numbers, the on-site matrices
+// [nspin][nhub][nhub] (blocks of one atom used) then the pair matrices [npairs][nspin][5][5].
+int hub_occ_len(const hp_ctx* c, int nspin);
+hp_status hub_upload(hp_ctx* c);
+// occupation vector from the projections P[item][p] (stride 128) of the occupied states, items in
+// (spin, k, band) order with nocc bands per (spin, k); kfrac_dev [nk][3]
+hp_status hub_occupations(hp_ctx* c, const double2* P, int nspin, int nk, int nocc, const double* kfrac_dev,
+                          double2* occ);
+// W [nspin][nkf][nhub][nhub] at nkf k points (fractional coordinates kfrac_dev [nkf][3])
+hp_status hub_build_w(hp_ctx* c, const double2* occ, int nspin, int nkf, const double* kfrac_dev, double2* W);
+// Y += V_Hub X on the list items: projection on the Hubbard rows phi (family of the list's spheres,
+// optional kmap), W of the item's (spin, k) (same kmap), expansion; P: projection scratch (items x 128)
+hp_status hub_apply(hp_ctx* c, const SphereSet& S, const BandList& L, const double2* phi, const int* kmap,
+                    const double2* W, const void* X, void* Y, bool vec32, bool fp32, double2* P);
 
 }  // namespace hp
 
@@ -495,6 +522,18 @@ struct hp_ctx {
     size_t scratch_elems = 0;
     hp::BandList L1, L2, L3;           // reusable band lists
     std::vector<void*> owned;          // device allocations freed in hp_destroy
+    // DFT+U+V ground state (hp_set_hubbard)
+    std::vector<double> hubU;          // [nhub_atoms] Ha
+    std::vector<hp::HubPair> hubV;
+    bool hub_on = false;
+    double* d_hubU = nullptr;          // [nhub_atoms]
+    int* d_hub_pair_int = nullptr;     // [npairs][5] i, j, R
+    double* d_hub_pairV = nullptr;     // [npairs]
+    int* d_hub_row_atom = nullptr;     // [nhub] Hubbard-atom index of each Hubbard row
+    int* d_hub_off = nullptr;          // [nhub_atoms] first row, then [nhub_atoms] m dimension
+    double* d_kfrac = nullptr;         // [nk][3] the k mesh, crystal coordinates
+    double2* d_hub_occ = nullptr;      // occupation vector of the ground state's Hubbard potential
+    double2* d_hubW = nullptr;         // [nspin][nk][nhub][nhub] W at the k mesh
 };
 
 namespace hp {

@@ -48,6 +48,7 @@ extern "C" hp_status hp_apply_h_noalloc(hp_ctx* c, int ik, int spin, int nb, con
     using namespace hp;
     if (!c) return HP_EINVAL;
     if (!c->have_gs) return fail(c, HP_ESTATE, "hp_apply_h_noalloc: no ground state (potential) yet");
+    if (c->hub_on) return fail(c, HP_ENOTIMPL, "hp_apply_h_noalloc: no Hubbard-corrected (DFT+U+V) operator");
     if (ik < 0 || ik >= c->nk || spin < 0 || spin >= c->nspin || nb < 1 || !psi_dev || !out_dev)
         return fail(c, HP_EINVAL, "hp_apply_h_noalloc: bad arguments");
     // the context's buffers (potential, projectors, sphere tables) live on the device current at

@@ -49,3 +49,38 @@ def test_batch_equals_cells_alone(precision):
     for (a0, a1, a2), (b0, b1, b2) in zip(alone, batch):
         for a, b in ((a0, b0), (a1, b1), (a2, b2)):
             assert np.abs(a - b).max() <= 1e-12 * max(1.0, np.abs(a).max())
+
+
+def test_seeded_cells_electron_rule_and_batch():
+    """Two cells of the seeded batch (config 3): the library's bare spectrum at k = 0 equals the
+    oracle's dense diagonalisation of T + V_loc + V_NL (1e-9 Ha); the electron-count rule (largest
+    gap among band counts n_H + n_L .. 5 n_H + 3 n_L) gives a ground state with a gap; the two cells
+    at once equal the cells alone (mixed form)."""
+    from oracle.groundstate import eigensolve
+    from oracle.model import Model
+
+    cells = [c for c in W.batch_cells() if c["name"] in ("batch03", "batch07")]
+    ready, alone = [], []
+    for w in cells:
+        stream = torch.cuda.Stream()
+        ctx = P.Context.from_workload(w, cuda_stream=stream.cuda_stream, precision=1)
+        nH = sum(1 for s, _ in w["atoms"] if s == 0)
+        n = 5 * nH + 3 * (len(w["atoms"]) - nH) + 1
+        lev = ctx.bare_levels(n)
+        m = Model(w)
+        ref, _ = eigensolve(m, m.kdata(m.kpts[0]), m.vloc_r(), n)
+        assert np.abs(lev - ref).max() < 1e-9
+        nelec = P.batch_electron_count(ctx, w)
+        assert nelec % 2 == 0 and 2 * (len(w["atoms"])) <= nelec <= 2 * (n - 1)
+        gs = ctx.ground_state(nelec, 1)
+        assert gs["gap"] > 1e-4
+        atoms, _ = ctx.hubbard_atoms()
+        for J in atoms:
+            for iq in range(ctx.query_sizes()["nq"]):
+                ctx.response(iq, int(J))
+        alone.append(ctx.hubbard())
+        ready.append((ctx, stream))
+    batch = P.batch_run([c for c, _ in ready])
+    for (a0, a1, a2), (b0, b1, b2) in zip(alone, batch):
+        for a, b in ((a0, b0), (a1, b1), (a2, b2)):
+            assert np.abs(a - b).max() <= 1e-12 * max(1.0, np.abs(a).max())
