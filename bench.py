@@ -218,6 +218,56 @@ def cpu_baseline(seconds, workload="precision"):
                       "alone (%d H.psi in %.1f s)" % (workload, ncores, elall, nall, n1, el1)}
 
 
+def _oracle_config0():
+    """The oracle's full chi of the tiny workload (config 0: ground state, then the one (q, J) column and
+    U); returns (ground-state seconds, chi seconds from the ready ground state, U in eV)."""
+    import numpy as np
+
+    import workloads as W
+    from oracle import groundstate as G, hubbard as HB, response as R
+    from oracle.model import Model
+
+    m = Model(W.tiny())
+    t0 = time.perf_counter()
+    gs = G.scf(m, tol=1e-12)
+    t1 = time.perf_counter()
+    r = R.solve_column(m, gs, 0, m.hub_atoms[0])
+    c0 = HB.trace_column(m, r["dn0"]).real
+    c = HB.trace_column(m, r["dn"]).real
+    U = HB.hubbard_matrix(np.array([[c0[0]]]), np.array([[c[0]]]))[0, 0]
+    return t1 - t0, time.perf_counter() - t1, float(U)
+
+
+def oracle_config0_chi(ncores):
+    """Oracle chi time for config 0 in a subprocess with all host cores available to its BLAS."""
+    env = dict(os.environ, OMP_NUM_THREADS=str(ncores), OPENBLAS_NUM_THREADS=str(ncores))
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; g, c, u = bench._oracle_config0(); "
+            "print(json.dumps(dict(gs=g, chi=c, U=u)))" % ROOT)
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=1200)
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def gpu_config0_chi(P, W, stream):
+    """The library's full chi of config 0 (FP64 and mixed) from its own ground state: seconds and U."""
+    import torch
+
+    w = W.tiny()
+    out = {}
+    ctx = P.Context.from_workload(w, cuda_stream=stream.cuda_stream)
+    ctx.ground_state(w["nelec"], w["nspin"])
+    atoms, _ = ctx.hubbard_atoms()
+    for prec, tag in ((0, "fp64"), (1, "mixed")):
+        ctx.set_precision(prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.response(0, int(atoms[0]))
+        hp = ctx.hubbard_parameters()
+        torch.cuda.synchronize()
+        out[tag] = {"chi_s": time.perf_counter() - t0, "U_eV": float(hp["U"][0])}
+    ctx.destroy()
+    return out
+
+
 def static_config(workload, world=1):
     return {"workload": WORKLOADS[workload], "step": STEP,
             "l2": "inputs larger than L2 (response working set of several GB)",
@@ -537,7 +587,9 @@ def main():
         hpsi, iters = 0, []
         for _ in range(steps):
             iq, J = mine[k % len(mine)]
+            torch.cuda.nvtx.range_push("timed_step")  # lets a profiler select the timed launches
             _, dn, info = ctx.response(iq, J)
+            torch.cuda.nvtx.range_pop()
             traces[(iq, J)] = _traces(dn, nh)
             hpsi += info["hpsi"]
             iters.append(info["iterations"])
@@ -661,6 +713,14 @@ def main():
             "gpu_launches": mix["launches"], "roofline": roofline}
     if args.cpu_seconds > 0:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, args.workload)
+        # config 0 end to end: the oracle's chi time on the host cores against this GPU's
+        ref0 = oracle_config0_chi(line["cpu_baseline"]["cores"])
+        gpu0 = gpu_config0_chi(P, W, stream)
+        line["cpu_baseline"]["config0_chi"] = {
+            "workload": "tiny (config 0): two-atom cube a=8 bohr, 20 Ry, FFT 20^3, k 2x2x2, q 1x1x1",
+            "oracle_chi_s": ref0["chi"], "oracle_ground_state_s": ref0["gs"], "oracle_U_eV": ref0["U"],
+            "gpu": gpu0, "u_err_mev_fp64_vs_oracle": 1000.0 * abs(gpu0["fp64"]["U_eV"] - ref0["U"]),
+            "u_err_mev_mixed_vs_oracle": 1000.0 * abs(gpu0["mixed"]["U_eV"] - ref0["U"])}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

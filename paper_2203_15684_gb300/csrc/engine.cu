@@ -196,6 +196,19 @@ hp_status upload_sphereset(hp_ctx* c, const std::vector<const KSphere*>& sph, co
             t[1] += 1;
         }
     S.contig = contig;
+    {
+        const int m0 = (N0 - 1) / 4, m1 = (N1 - 1) / 4;
+        bool prun = true;
+        for (int k = 0; k < nk && prun; ++k)
+            for (int j = 0; j < ncol[k]; ++j) {
+                const int x = cxy[k][j] / N1, y = cxy[k][j] % N1;
+                if (!((x <= m0 || x >= N0 - m0) && (y <= m1 || y >= N1 - m1))) {
+                    prun = false;
+                    break;
+                }
+            }
+        S.lines_prunable = prun;
+    }
     if (S.d_xtab && S.xtab_n0 != N0) {
         dfree(c, S.d_xtab);
         S.d_xtab = nullptr;

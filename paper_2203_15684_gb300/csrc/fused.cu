@@ -11,6 +11,7 @@
 // Real-space band grids use the plane-major layout [z][y][x] so that a plane is contiguous.
 // HBM traffic per band drops from ~6 full-grid round trips to two compact column buffers.
 #include <cmath>
+#include <cstdlib>
 #include <mutex>
 #include <type_traits>
 #include <vector>
@@ -409,7 +410,16 @@ __device__ __forceinline__ void mul_row(const E* __restrict__ p, V (&a)[N]) {
     }
 }
 
-template <class V, int N0, int N1, int OP>
+// PR (pruned lines): every grid column of the spheres has x and y indices within m of 0 (mod N) with
+// m = (N - 1) / 4 (the alias-free grid's sphere), so the lines along x and y carry their nonzero
+// inputs, and need their outputs, only there.  The other positions enter the register FFTs as literal
+// zeros or are never stored, and the compiler drops the arithmetic that feeds nothing.
+template <int N, bool PR>
+__device__ __forceinline__ constexpr bool live(int i) {
+    return !PR || i <= (N - 1) / 4 || i >= N - (N - 1) / 4;
+}
+
+template <class V, int N0, int N1, int OP, bool PR>
 __global__ void __launch_bounds__(PlaneCfg<V, N0, N1>::NT, PlaneCfg<V, N0, N1>::template minb<OP>()) plane_reg_kernel(
     const V* __restrict__ colin, V* __restrict__ colout, int ncmax, const int* __restrict__ kk,
     const int* __restrict__ spin, int c0, int nc, const int* __restrict__ xtab, int N2,
@@ -428,7 +438,7 @@ __global__ void __launch_bounds__(PlaneCfg<V, N0, N1>::NT, PlaneCfg<V, N0, N1>::
         if (tid < P * N0) {
             const int p = tid / N0, x = tid % N0;
             const long long q = q0 + p;
-            if (q < npairs) {
+            if (q < npairs && (!PR || live<N0, PR>(x))) {
                 const int k = kk[c0 + (int)(q / N2)];
                 const int* t = xtab + ((long long)k * N0 + x) * 3;
                 const int j0 = t[0], cnt = t[1], y0 = t[2];
@@ -438,7 +448,7 @@ __global__ void __launch_bounds__(PlaneCfg<V, N0, N1>::NT, PlaneCfg<V, N0, N1>::
                 for (int y = 0; y < N1; ++y) {
                     int i = y - y0;
                     if (i < 0) i += N1;
-                    a[y] = i < cnt ? src[i] : cpack<V>(0.0, 0.0);
+                    a[y] = (live<N1, PR>(y) && i < cnt) ? src[i] : cpack<V>(0.0, 0.0);
                 }
                 if (cnt > 0) rfft<V, N1, +1>(a);
                 V* col = S + p * PS + x;
@@ -461,13 +471,14 @@ __global__ void __launch_bounds__(PlaneCfg<V, N0, N1>::NT, PlaneCfg<V, N0, N1>::
                 mul_row<V, V, N0>(dvt + ((long long)spin[c0 + c] * N2 + z) * NP + y * N0, a);
             } else {
 #pragma unroll
-                for (int x = 0; x < N0; ++x) a[x] = rowp[x];
+                for (int x = 0; x < N0; ++x) a[x] = live<N0, PR>(x) ? rowp[x] : cpack<V>(0.0, 0.0);
                 rfft<V, N0, +1>(a);
             }
             if (OP == 0) mul_row<V, T, N0>(vt + ((long long)spin[c0 + c] * N2 + z) * NP + y * N0, a);
             if (OP != 1) rfft<V, N0, -1>(a);
 #pragma unroll
-            for (int x = 0; x < N0; ++x) rowp[x] = a[x];
+            for (int x = 0; x < N0; ++x)
+                if (OP == 1 || live<N0, PR>(x)) rowp[x] = a[x];
         }
     }
     __syncthreads();
@@ -500,7 +511,7 @@ __global__ void __launch_bounds__(PlaneCfg<V, N0, N1>::NT, PlaneCfg<V, N0, N1>::
                 for (int y = 0; y < N1; ++y) {
                     int i = y - y0;
                     if (i < 0) i += N1;
-                    if (i < cnt) dst[i] = cscale(a[y], sc);
+                    if (live<N1, PR>(y) && i < cnt) dst[i] = cscale(a[y], sc);
                 }
             }
         }
@@ -749,6 +760,22 @@ static cudaError_t col_launch(bool inv, const FusedArgs& a) {
     return cudaGetLastError();
 }
 
+template <class V, int N0, int N1, int OP, bool PR>
+static cudaError_t plane_reg_go(const FusedArgs& a, size_t smem, int grid) {
+    using Cfg = PlaneCfg<V, N0, N1>;
+    using T = typename Scalar<V>::type;
+    const SphereSet& S = *a.S;
+    const BandList& L = *a.L;
+    // set once per kernel (a function-local static is initialised once, also with several host threads)
+    static const cudaError_t attr = cudaFuncSetAttribute(plane_reg_kernel<V, N0, N1, OP, PR>,
+                                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (attr != cudaSuccess) return attr;
+    plane_reg_kernel<V, N0, N1, OP, PR><<<grid, Cfg::NT, smem, a.st>>>(
+        (const V*)a.colA, (V*)a.colB, S.ncmax, L.d_k, L.d_spin, a.c0, a.nc, S.d_xtab, a.N2, (const T*)a.vt,
+        (const V*)a.ur, L.d_row, (const V*)a.dvt, (V*)a.out, a.inv_n);
+    return cudaSuccess;
+}
+
 template <class V, int N0, int N1, int OP>
 static cudaError_t plane_reg_launch(const FusedArgs& a) {
     using Cfg = PlaneCfg<V, N0, N1>;
@@ -758,16 +785,18 @@ static cudaError_t plane_reg_launch(const FusedArgs& a) {
     cudaError_t e = regfft_init();
     if (e != cudaSuccess) return e;
     const size_t smem = (size_t)Cfg::P * Cfg::per_plane;
-    // set once per kernel (a function-local static is initialised once, also with several host threads)
-    static const cudaError_t attr =
-        cudaFuncSetAttribute(plane_reg_kernel<V, N0, N1, OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (attr != cudaSuccess) return attr;
     const long long npairs = (long long)a.nc * a.N2;
     const int grid = cdivf(npairs, Cfg::P);
     const ProfMark pm = prof_start(a.st);
-    plane_reg_kernel<V, N0, N1, OP><<<grid, Cfg::NT, smem, a.st>>>(
-        (const V*)a.colA, (V*)a.colB, S.ncmax, L.d_k, L.d_spin, a.c0, a.nc, S.d_xtab, a.N2, (const T*)a.vt,
-        (const V*)a.ur, L.d_row, (const V*)a.dvt, (V*)a.out, a.inv_n);
+    // pruned lines for the FP32 production grids (36 and more points) when the spheres allow them
+    constexpr bool kPrunable = sizeof(V) == 8 && N0 >= 36 && N1 >= 36;
+    if constexpr (kPrunable) {
+        if (S.lines_prunable && !getenv("HP_NO_PRUNE")) e = plane_reg_go<V, N0, N1, OP, true>(a, smem, grid);
+        else e = plane_reg_go<V, N0, N1, OP, false>(a, smem, grid);
+    } else {
+        e = plane_reg_go<V, N0, N1, OP, false>(a, smem, grid);
+    }
+    if (e != cudaSuccess) return e;
     HP_LAUNCHED();
     if (prof_on() && L.k.size() >= (size_t)(a.c0 + a.nc) && L.spin.size() >= (size_t)(a.c0 + a.nc) && !S.ncol.empty()) {
         const double nr = (double)N0 * N1 * a.N2;
