@@ -197,9 +197,9 @@ hp_status upload_sphereset(hp_ctx* c, const std::vector<const KSphere*>& sph, co
         }
     S.contig = contig;
     {
-        const int m0 = (N0 - 1) / 4, m1 = (N1 - 1) / 4;
+        const int m0 = (N0 - 1) / 4, m1 = (N1 - 1) / 4, m2 = (N2 - 1) / 4;
         bool prun = true;
-        for (int k = 0; k < nk && prun; ++k)
+        for (int k = 0; k < nk && prun; ++k) {
             for (int j = 0; j < ncol[k]; ++j) {
                 const int x = cxy[k][j] / N1, y = cxy[k][j] % N1;
                 if (!((x <= m0 || x >= N0 - m0) && (y <= m1 || y >= N1 - m1))) {
@@ -207,6 +207,11 @@ hp_status upload_sphereset(hp_ctx* c, const std::vector<const KSphere*>& sph, co
                     break;
                 }
             }
+            for (int i = 0; i < S.npw[k] && prun; ++i) {
+                const int z = iz[(size_t)k * ld + i];
+                if (!(z <= m2 || z >= N2 - m2)) prun = false;
+            }
+        }
         S.lines_prunable = prun;
     }
     if (S.d_xtab && S.xtab_n0 != N0) {

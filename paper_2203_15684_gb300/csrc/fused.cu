@@ -269,11 +269,20 @@ static cudaError_t regfft_init() {
     return err;
 }
 
+// PR (pruned lines): every sphere point has x, y and z grid indices within m of 0 (mod N) with
+// m = (N - 1) / 4 (the sphere of an alias-free grid), so the lines along x, y and z carry their nonzero
+// inputs, and need their outputs, only there.  The other positions enter the register FFTs as literal
+// zeros or are never stored, and the compiler drops the arithmetic that feeds nothing.
+template <int N, bool PR>
+__device__ __forceinline__ constexpr bool live(int i) {
+    return !PR || i <= (N - 1) / 4 || i >= N - (N - 1) / 4;
+}
+
 // column transforms with one thread per (band, column): the column's sphere points are one run of
 // consecutive z (wrapping at N2), so every register index is a compile-time z.
 constexpr int kColRegThreads = 128;
 
-template <class V, int N2, class VT>
+template <class V, int N2, class VT, bool PR>
 __global__ void __launch_bounds__(kColRegThreads) col_inv_reg_kernel(
     const VT* __restrict__ X, int ld, const int* __restrict__ row, const int* __restrict__ kk, int c0,
     const int* __restrict__ ncol, const int* __restrict__ col_start, const int* __restrict__ col_len,
@@ -290,7 +299,7 @@ __global__ void __launch_bounds__(kColRegThreads) col_inv_reg_kernel(
     for (int z = 0; z < N2; ++z) {
         int p = z - z0;
         if (p < 0) p += N2;
-        a[z] = p < len ? from_vec<V>(x[p]) : cpack<V>(0.0, 0.0);
+        a[z] = (live<N2, PR>(z) && p < len) ? from_vec<V>(x[p]) : cpack<V>(0.0, 0.0);
     }
     rfft<V, N2, +1>(a);
     V* dst = colbuf + (long long)c * N2 * ncmax + j;
@@ -298,7 +307,7 @@ __global__ void __launch_bounds__(kColRegThreads) col_inv_reg_kernel(
     for (int z = 0; z < N2; ++z) dst[(long long)z * ncmax] = a[z];
 }
 
-template <class V, int N2, class VT>
+template <class V, int N2, class VT, bool PR>
 __global__ void __launch_bounds__(kColRegThreads) col_fwd_reg_kernel(
     const V* __restrict__ colbuf, int ncmax, const int* __restrict__ row, const int* __restrict__ kk, int c0,
     const int* __restrict__ npw, const int* __restrict__ ncol, const int* __restrict__ col_start,
@@ -326,7 +335,7 @@ __global__ void __launch_bounds__(kColRegThreads) col_fwd_reg_kernel(
     for (int z = 0; z < N2; ++z) {
         int p = z - z0;
         if (p < 0) p += N2;
-        if (p < len) {
+        if (live<N2, PR>(z) && p < len) {
             const bool k32 = sizeof(VT) == 8;
             fwd_store<V>(Y, X, ro + st + p, a[z], mode, (mode == 0 && !k32) ? g2[ko + p] : 0.0,
                          (mode == 0 && k32) ? kin32[ko + p] : 0.f, sh, sh32, scale);
@@ -408,15 +417,6 @@ __device__ __forceinline__ void mul_row(const E* __restrict__ p, V (&a)[N]) {
         if constexpr (sizeof(E) == sizeof(V)) a[i] = cmul(a[i], p[i]);
         else a[i] = cscale(a[i], p[i]);
     }
-}
-
-// PR (pruned lines): every grid column of the spheres has x and y indices within m of 0 (mod N) with
-// m = (N - 1) / 4 (the alias-free grid's sphere), so the lines along x and y carry their nonzero
-// inputs, and need their outputs, only there.  The other positions enter the register FFTs as literal
-// zeros or are never stored, and the compiler drops the arithmetic that feeds nothing.
-template <int N, bool PR>
-__device__ __forceinline__ constexpr bool live(int i) {
-    return !PR || i <= (N - 1) / 4 || i >= N - (N - 1) / 4;
 }
 
 template <class V, int N0, int N1, int OP, bool PR>
@@ -707,14 +707,25 @@ static void col_kernels(bool inv, bool reg, dim3 g, const FusedArgs& a) {
     const BandList& L = *a.L;
     const VT* X = (const VT*)a.X;
     VT* Y = (VT*)a.Y;
+    // pruned z lines for the FP32 production grids (36 and more points) when the spheres allow them
+    constexpr bool kPrunable = sizeof(V) == 8 && N2 >= 36;
+    const bool pr = kPrunable && S.lines_prunable && !getenv("HP_NO_PRUNE");
     if (reg && inv) {
-        col_inv_reg_kernel<V, N2, VT><<<g, kColRegThreads, 0, a.st>>>(X, S.ld, L.d_row, L.d_k, a.c0, S.d_ncol,
-                                                                      S.d_col_start, S.d_col_len, S.d_iz, S.ncmax,
-                                                                      (V*)a.colA);
+        if (pr)
+            col_inv_reg_kernel<V, N2, VT, kPrunable><<<g, kColRegThreads, 0, a.st>>>(
+                X, S.ld, L.d_row, L.d_k, a.c0, S.d_ncol, S.d_col_start, S.d_col_len, S.d_iz, S.ncmax, (V*)a.colA);
+        else
+            col_inv_reg_kernel<V, N2, VT, false><<<g, kColRegThreads, 0, a.st>>>(
+                X, S.ld, L.d_row, L.d_k, a.c0, S.d_ncol, S.d_col_start, S.d_col_len, S.d_iz, S.ncmax, (V*)a.colA);
     } else if (reg) {
-        col_fwd_reg_kernel<V, N2, VT><<<g, kColRegThreads, 0, a.st>>>(
-            (const V*)a.colB, S.ncmax, L.d_row, L.d_k, a.c0, S.d_npw, S.d_ncol, S.d_col_start, S.d_col_len, S.d_iz,
-            S.d_g2, S.d_kin32, L.d_shift, X, Y, S.ld, a.mode, a.scale);
+        if (pr)
+            col_fwd_reg_kernel<V, N2, VT, kPrunable><<<g, kColRegThreads, 0, a.st>>>(
+                (const V*)a.colB, S.ncmax, L.d_row, L.d_k, a.c0, S.d_npw, S.d_ncol, S.d_col_start, S.d_col_len,
+                S.d_iz, S.d_g2, S.d_kin32, L.d_shift, X, Y, S.ld, a.mode, a.scale);
+        else
+            col_fwd_reg_kernel<V, N2, VT, false><<<g, kColRegThreads, 0, a.st>>>(
+                (const V*)a.colB, S.ncmax, L.d_row, L.d_k, a.c0, S.d_npw, S.d_ncol, S.d_col_start, S.d_col_len,
+                S.d_iz, S.d_g2, S.d_kin32, L.d_shift, X, Y, S.ld, a.mode, a.scale);
     } else if (inv) {
         col_inv_kernel<V, N2, VT><<<g, kColThreads, 0, a.st>>>(X, S.ld, L.d_row, L.d_k, a.c0, S.d_ncol, S.d_col_start,
                                                                S.d_col_len, S.d_iz, S.ncmax, (V*)a.colA,
@@ -890,7 +901,7 @@ constexpr int kDrhoGroup = 32;
 template <int N0, int N1>
 constexpr int drho_minb() { return (N0 <= 45 && N1 <= 45) ? 2 : 1; }
 
-template <int N0, int N1>
+template <int N0, int N1, bool PR>
 __global__ void __launch_bounds__(PlaneCfg<float2, N0, N1>::NT, drho_minb<N0, N1>()) drho_plane_kernel(
     const float2* __restrict__ colin, int ncmax, const int* __restrict__ kk, const int* __restrict__ spin,
     const int* __restrict__ ur_row, int c0, int nc, const int* __restrict__ xtab, int N2,
@@ -913,7 +924,7 @@ __global__ void __launch_bounds__(PlaneCfg<float2, N0, N1>::NT, drho_minb<N0, N1
         if (tid < P * N0) {
             const int p = tid / N0, x = tid % N0;
             const int c = r0 + p;
-            if (c < b1) {
+            if (c < b1 && live<N0, PR>(x)) {
                 const int k = kk[c0 + c];
                 const int* t = xtab + ((long long)k * N0 + x) * 3;
                 const int j0 = t[0], cnt = t[1], y0 = t[2];
@@ -923,7 +934,7 @@ __global__ void __launch_bounds__(PlaneCfg<float2, N0, N1>::NT, drho_minb<N0, N1
                 for (int y = 0; y < N1; ++y) {
                     int i = y - y0;
                     if (i < 0) i += N1;
-                    a[y] = i < cnt ? src[i] : cmkf(0.f, 0.f);
+                    a[y] = (live<N1, PR>(y) && i < cnt) ? src[i] : cmkf(0.f, 0.f);
                 }
                 if (cnt > 0) rfft<V, N1, +1>(a);
                 V* col = S + p * PS + x;
@@ -940,7 +951,7 @@ __global__ void __launch_bounds__(PlaneCfg<float2, N0, N1>::NT, drho_minb<N0, N1
                 V* rowp = S + p * PS + y * LD;
                 V a[N0];
 #pragma unroll
-                for (int x = 0; x < N0; ++x) a[x] = rowp[x];
+                for (int x = 0; x < N0; ++x) a[x] = live<N0, PR>(x) ? rowp[x] : cmkf(0.f, 0.f);
                 rfft<V, N0, +1>(a);
                 const V* u = ur + ((long long)ur_row[c0 + c] * N2 + z) * NP + y * N0;
 #pragma unroll
@@ -991,12 +1002,24 @@ static cudaError_t drho_plane_launch(const FusedArgs& a, double2* part, int grou
         if (e != cudaSuccess) return e;
         const size_t smem = ((size_t)Cfg::P * N1 * Cfg::LD + 2 * (size_t)N0 * N1) * sizeof(float2);
         static const cudaError_t attr =
-            cudaFuncSetAttribute(drho_plane_kernel<N0, N1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(drho_plane_kernel<N0, N1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (attr != cudaSuccess) return attr;
         dim3 g(a.N2, (a.nc + kDrhoGroup - 1) / kDrhoGroup);
-        drho_plane_kernel<N0, N1><<<g, Cfg::NT, smem, a.st>>>((const float2*)a.colA, S.ncmax, L.d_k, L.d_spin, L.d_row,
-                                                               a.c0, a.nc, S.d_xtab, a.N2, (const float2*)a.ur, part,
-                                                               group0);
+        if constexpr (N0 >= 36 && N1 >= 36) {
+            if (S.lines_prunable && !getenv("HP_NO_PRUNE")) {
+                static const cudaError_t attr_p = cudaFuncSetAttribute(
+                    drho_plane_kernel<N0, N1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (attr_p != cudaSuccess) return attr_p;
+                drho_plane_kernel<N0, N1, true><<<g, Cfg::NT, smem, a.st>>>(
+                    (const float2*)a.colA, S.ncmax, L.d_k, L.d_spin, L.d_row, a.c0, a.nc, S.d_xtab, a.N2,
+                    (const float2*)a.ur, part, group0);
+                HP_LAUNCHED();
+                return cudaGetLastError();
+            }
+        }
+        drho_plane_kernel<N0, N1, false><<<g, Cfg::NT, smem, a.st>>>((const float2*)a.colA, S.ncmax, L.d_k, L.d_spin,
+                                                                      L.d_row, a.c0, a.nc, S.d_xtab, a.N2,
+                                                                      (const float2*)a.ur, part, group0);
         HP_LAUNCHED();
         return cudaGetLastError();
     }

@@ -146,8 +146,8 @@ struct SphereSet {          // device arrays, nk spheres of at most ld points
     int* d_xtab = nullptr;
     int xtab_n0 = 0;
     bool contig = false;        // every column is one run of consecutive z (mod N2)
-    // every column's x and y lie within (N - 1) / 4 of 0 (mod N0, N1): the plane transforms may prune
-    // their lines to those positions
+    // every sphere point's x, y and z grid indices lie within (N - 1) / 4 of 0 (mod N): the column and
+    // plane transforms may prune their lines to those positions
     bool lines_prunable = false;
 };
 
