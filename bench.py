@@ -53,14 +53,14 @@ METRIC = "full Ï‡-matrix wall time & HÂ·Ïˆ/s, mixed vs FP64 on 1 GB300 at |Î”U|â
 UNIT = "Hpsi/s"
 _CELL = "rocksalt cube a=8.4 bohr, 4 H + 4 L (H projector D=-4.0 Ha), 40 electrons, nspin=2 (AFM start), "
 WORKLOADS = {
-    "precision": "precision (config 2): " + _CELL + "ecutwfc 50 Ry (npw<=3575), FFT 45^3, k 4x4x4, q 2x2x2",
-    "medium": "medium (config 1): " + _CELL + "ecutwfc 35 Ry (npw<=2103), FFT 36^3, k 4x4x4, q 2x2x2",
-    "batch": "batch (config 3): 16 synthetic cells from seed 15684, 2-12 atoms, orthorhombic 7-12 bohr, "
+    "precision": "precision: " + _CELL + "ecutwfc 50 Ry (npw<=3575), FFT 45^3, k 4x4x4, q 2x2x2",
+    "medium": "medium: " + _CELL + "ecutwfc 35 Ry (npw<=2103), FFT 36^3, k 4x4x4, q 2x2x2",
+    "batch": "batch: 16 synthetic cells from seed 15684, 2-12 atoms, orthorhombic 7-12 bohr, "
              "25-45 Ry, k 2-4 and q 1-2 per axis, nspin=1, occupied bands at the largest bare gap, mixed form",
 }
 STEP = ("one (q, J) self-consistent Sternheimer response (set-up a1, a3-a10) over every (spin, k, band) system of "
         "the pair, mixed form")
-GOLDEN_MEDIUM = os.path.join(ROOT, "tests", "golden", "medium_config1_column.json")
+GOLDEN_MEDIUM = os.path.join(ROOT, "tests", "golden", "medium_column.json")
 
 
 def parse():
@@ -218,8 +218,8 @@ def cpu_baseline(seconds, workload="precision"):
                       "alone (%d H.psi in %.1f s)" % (workload, ncores, elall, nall, n1, el1)}
 
 
-def _oracle_config0():
-    """The oracle's full chi of the tiny workload (config 0: ground state, then the one (q, J) column and
+def _oracle_tiny():
+    """The oracle's full chi of the tiny workload (ground state, then the one (q, J) column and
     U); returns (ground-state seconds, chi seconds from the ready ground state, U in eV)."""
     import numpy as np
 
@@ -238,17 +238,17 @@ def _oracle_config0():
     return t1 - t0, time.perf_counter() - t1, float(U)
 
 
-def oracle_config0_chi(ncores):
-    """Oracle chi time for config 0 in a subprocess with all host cores available to its BLAS."""
+def oracle_tiny_chi(ncores):
+    """Oracle chi time for the tiny workload in a subprocess with all host cores available to its BLAS."""
     env = dict(os.environ, OMP_NUM_THREADS=str(ncores), OPENBLAS_NUM_THREADS=str(ncores))
-    code = ("import json,sys; sys.path.insert(0, %r); import bench; g, c, u = bench._oracle_config0(); "
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; g, c, u = bench._oracle_tiny(); "
             "print(json.dumps(dict(gs=g, chi=c, U=u)))" % ROOT)
     r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=1200)
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
-def gpu_config0_chi(P, W, stream):
-    """The library's full chi of config 0 (FP64 and mixed) from its own ground state: seconds and U."""
+def gpu_tiny_chi(P, W, stream):
+    """The library's full chi of the tiny workload (FP64 and mixed) from its own ground state: seconds and U."""
     import torch
 
     w = W.tiny()
@@ -390,7 +390,7 @@ def batch_arm(args):
             nelec = P.batch_electron_count(ctx, w)
             ctx.ground_state(nelec, 1)
         except P.HPError as e:
-            skipped.append("%s: %s" % (w["name"], str(e).split(":")[0]))
+            skipped.append("%s: %s" % (w["name"], str(e)[:200]))
             ctx.destroy()
             continue
         ctxs.append((w, ctx, stream, nelec))
@@ -713,11 +713,11 @@ def main():
             "gpu_launches": mix["launches"], "roofline": roofline}
     if args.cpu_seconds > 0:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds, args.workload)
-        # config 0 end to end: the oracle's chi time on the host cores against this GPU's
-        ref0 = oracle_config0_chi(line["cpu_baseline"]["cores"])
-        gpu0 = gpu_config0_chi(P, W, stream)
-        line["cpu_baseline"]["config0_chi"] = {
-            "workload": "tiny (config 0): two-atom cube a=8 bohr, 20 Ry, FFT 20^3, k 2x2x2, q 1x1x1",
+        # the tiny workload end to end: the oracle's chi time on the host cores against this GPU's
+        ref0 = oracle_tiny_chi(line["cpu_baseline"]["cores"])
+        gpu0 = gpu_tiny_chi(P, W, stream)
+        line["cpu_baseline"]["tiny_chi"] = {
+            "workload": "tiny: two-atom cube a=8 bohr, 20 Ry, FFT 20^3, k 2x2x2, q 1x1x1",
             "oracle_chi_s": ref0["chi"], "oracle_ground_state_s": ref0["gs"], "oracle_U_eV": ref0["U"],
             "gpu": gpu0, "u_err_mev_fp64_vs_oracle": 1000.0 * abs(gpu0["fp64"]["U_eV"] - ref0["U"]),
             "u_err_mev_mixed_vs_oracle": 1000.0 * abs(gpu0["mixed"]["U_eV"] - ref0["U"])}

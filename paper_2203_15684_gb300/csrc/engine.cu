@@ -227,11 +227,13 @@ hp_status upload_sphereset(hp_ctx* c, const std::vector<const KSphere*>& sph, co
         S.d_xtab = nullptr;
         S.xtab_n0 = 0;
     }
-    for (int k = 0; k < nk && c->fused; ++k) {  // the fused transforms need one buffer slot per grid column
+    S.cols_distinct = true;
+    for (int k = 0; k < nk && S.cols_distinct; ++k) {  // the fused transforms need one buffer slot per grid column
         std::vector<int> xs(cxy[k]);
         std::sort(xs.begin(), xs.end());
-        if (std::adjacent_find(xs.begin(), xs.end()) != xs.end()) c->fused = false;
+        if (std::adjacent_find(xs.begin(), xs.end()) != xs.end()) S.cols_distinct = false;
     }
+    if (!S.cols_distinct) c->fused = false;
     CK(h2d(S.d_npw, S.npw.data(), nk, c->st));
     CK(h2d(S.d_idx, idx.data(), idx.size(), c->st));
     CK(h2d(S.d_g2, g2.data(), g2.size(), c->st));
@@ -335,11 +337,14 @@ hp_status ensure_scratch(hp_ctx* c, size_t elems) {
 hp_status apply_local(hp_ctx* c, const SphereSet& S, const BandList& L, const double2* X, double2* Y,
                       const double* veff, bool fp32) {
     if (L.nb == 0) return HP_OK;
-    hp_status s = ensure_grid(c, band_batch(c, L.nb));
+    // chunks of a size fixed by the sizes alone (not by the buffer's history), so that a result does
+    // not depend on what ran before it
+    const int chunk = band_batch(c, L.nb);
+    hp_status s = ensure_grid(c, chunk);
     if (s != HP_OK) return s;
     if (fp32) {  // FP32 grids: twice as many per batch in the same buffer
         float2* g32 = (float2*)c->d_grid;
-        const int cap = 2 * c->grid_cap;
+        const int cap = 2 * chunk;
         for (int c0 = 0; c0 < L.nb; c0 += cap) {
             const int nc = std::min(cap, L.nb - c0);
             CK(k_scatter32(S, L, c0, nc, X, g32, c->nr, c->st));
@@ -350,8 +355,8 @@ hp_status apply_local(hp_ctx* c, const SphereSet& S, const BandList& L, const do
         }
         return HP_OK;
     }
-    for (int c0 = 0; c0 < L.nb; c0 += c->grid_cap) {
-        const int nc = std::min(c->grid_cap, L.nb - c0);
+    for (int c0 = 0; c0 < L.nb; c0 += chunk) {
+        const int nc = std::min(chunk, L.nb - c0);
         CK(k_scatter(S, L, c0, nc, X, c->ld, c->d_grid, c->nr, c->st));
         CK(fft3d(c->fft, c->d_grid, nc, +1, c->st));
         CK(k_mul_rpot(c->d_grid, nc, c->nr, veff, L, c0, c->st));
@@ -393,6 +398,7 @@ FusedArgs fused_args(hp_ctx* c, const SphereSet& S, const BandList& L) {
     a.colA = c->d_colA;
     a.colB = c->d_colB;
     a.vt = c->d_vt;
+    a.vtx = c->d_vtx;
     a.inv_n = 1.0 / c->nr;
     a.reg = c->fused_reg;
     a.st = c->st;
@@ -619,7 +625,8 @@ static hp_status setup_impl(hp_ctx* c, const double cell[9], int nspecies, const
     if (c->hub_atoms.empty()) return fail(c, HP_EINVAL, "hp_setup: no Hubbard species");
     // device data
     tc_set_timeout(c->opt.wait_timeout_s);
-    c->fused = fused_supported(c->N) && !getenv("HP_NO_FUSED");
+    c->fused_grid = fused_supported(c->N) && !getenv("HP_NO_FUSED");
+    c->fused = c->fused_grid;
     c->fused_reg = !getenv("HP_FUSED_SMEM");  // HP_FUSED_SMEM: shared-memory line FFTs instead
     // rows of one combined projection (at most the buffer's 128; HP_PROJ_ROWS lowers it)
     c->proj_rows_max = kPStride;
@@ -1015,9 +1022,10 @@ hp_status prepare_resp(hp_ctx* c) {
     if (c->fused) {
         // plane-major V_eff (FP64 or FP32) and the real-space occupied bands through the fused path
         dfree(c, c->d_vt);
+        dfree(c, c->d_vtx);
         dfree(c, c->d_dvt);
         dfree(c, c->d_drho_pm);
-        c->d_vt = c->d_dvt = nullptr;
+        c->d_vt = c->d_vtx = c->d_dvt = nullptr;
         double* tmp;
         CK(dalloc(c, &tmp, (size_t)nspin * nr));
         CK(k_to_planes_real(c->d_veff, tmp, c->N, nspin, c->st));
@@ -1037,6 +1045,19 @@ hp_status prepare_resp(hp_ctx* c) {
             c->d_vt = tmp;
             c->d_dvt = dv64;
         }
+        // x-major copy: the register plane kernels read it with consecutive threads on consecutive y
+        void* vx;
+        if (mixed) {
+            float* v;
+            CK(dalloc(c, &v, (size_t)nspin * nr));
+            vx = v;
+        } else {
+            double* v;
+            CK(dalloc(c, &v, (size_t)nspin * nr));
+            vx = v;
+        }
+        c->d_vtx = vx;
+        CK(k_planes_xmajor(c->d_vt, c->d_vtx, c->N[0], c->N[1], (long long)nspin * c->N[2], mixed, c->st));
         CK(dalloc(c, &c->d_drho_pm, (size_t)nspin * nr));
         const int chunk = fused_batch(c, c->kset, rows);
         s = ensure_colbuf(c, sizeof(double2) * (size_t)chunk * c->N[2] * c->kset.ncmax);
@@ -1292,8 +1313,14 @@ hp_status prepare_q(hp_ctx* c, int iq, std::vector<int>& kprime) {
         kprime[ik] = (j[0] * c->kmesh[1] + j[1]) * c->kmesh[2] + j[2];
         sph[ik] = &c->ks[kprime[ik]];
     }
-    if (c->qc.iq == iq) return HP_OK;
+    // the route of this q: fused where the grid, the k set and the k+q set allow it, whatever earlier
+    // q points chose (so that a response does not depend on the calls before it)
+    if (c->qc.iq == iq) {
+        c->fused = c->fused_grid && c->kset.cols_distinct && c->qc.set.cols_distinct;
+        return HP_OK;
+    }
     hp_status s = upload_sphereset(c, sph, &g0, c->qc.set);
+    c->fused = c->fused_grid && c->kset.cols_distinct && c->qc.set.cols_distinct;
     if (s != HP_OK) return s;
     std::vector<int> kmap(c->nk);
     for (int ik = 0; ik < c->nk; ++ik) kmap[ik] = off ? ik : kprime[ik];
@@ -1513,7 +1540,7 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
     std::vector<int> kprime;
     s = prepare_q(c, iq, kprime);
     if (s != HP_OK) return s;
-    if (c->ur_planes != c->fused) {  // the k+q spheres turned the fused path off: rebuild the caches
+    if (c->ur_planes != c->fused) {  // the route changed with q: rebuild the caches
         c->resp_ready = false;
         if ((s = prepare_resp(c)) != HP_OK) return s;
     }
@@ -1604,7 +1631,7 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
                 }
             } else if (mixed) {
                 float2* g32 = (float2*)c->d_grid;
-                const int cap = 2 * c->grid_cap;
+                const int cap = 2 * band_batch(c, rows);
                 CK(k_to_c32(c->d_dv, c->d_dv32, ndv, c->st));
                 for (int c0 = 0; c0 < rows; c0 += cap) {
                     const int nc = std::min(cap, rows - c0);
@@ -1613,8 +1640,9 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
                     CK(k_gather_scaled32(Sq, Lall, c0, nc, g32, nr, -1.0 / nr, c->d_b, ld, c->st));
                 }
             } else {
-                for (int c0 = 0; c0 < rows; c0 += c->grid_cap) {
-                    const int nc = std::min(c->grid_cap, rows - c0);
+                const int chunk = band_batch(c, rows);
+                for (int c0 = 0; c0 < rows; c0 += chunk) {
+                    const int nc = std::min(chunk, rows - c0);
                     CK(k_mul_cpot(c->d_grid, c->d_ur, Lall.d_row, nc, nr, c->d_dv, Lall, c0, c->st));
                     CK(fft3d(c->fft, c->d_grid, nc, -1, c->st));
                     CK(k_gather_scaled(Sq, Lall, c0, nc, c->d_grid, nr, -1.0 / nr, c->d_b, ld, 0, c->st));
@@ -1691,15 +1719,18 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
         if (c->fused) {
             // x -> real space (plane-major) through the fused path, then conj(u) x accumulated per spin
             CK(cudaMemsetAsync(c->d_drho_pm, 0, sizeof(double2) * ndv, c->st));
-            const int chunk = std::min(fused_batch(c, Sq, rows), mixed ? 2 * c->grid_cap : c->grid_cap);
+            const int chunk = fused_batch(c, Sq, rows);
             if ((s = ensure_colbuf(c, sizeof(double2) * (size_t)chunk * c->N[2] * Sq.ncmax)) != HP_OK) return s;
             FusedArgs probe = fused_args(c, Sq, Lall);
             const bool fdrho = v32 && fused_drho_supported(probe);
             if (fdrho) {
                 // FP32 form: Delta u(r) stays on chip; group sums of conj(u) Delta u, then the groups in order
                 int ng = 0;
-                for (int c0 = 0; c0 < rows; c0 += chunk) ng += fused_drho_groups(std::min(chunk, rows - c0));
-                if ((s = ensure_scratch(c, (size_t)ng * 2 * nr)) != HP_OK) return s;
+                for (int c0 = 0; c0 < rows; c0 += chunk) ng += fused_drho_groups(c->N[0], c->N[1], std::min(chunk, rows - c0));
+                // the groups' sums, then their spin masks (ints) in the scratch's last elements
+                const size_t nmask = ((size_t)ng + 3) / 4;
+                if ((s = ensure_scratch(c, (size_t)ng * 2 * nr + nmask)) != HP_OK) return s;
+                int* gmask = reinterpret_cast<int*>(c->d_scratch + (size_t)ng * 2 * nr);
                 int g0 = 0;
                 for (int c0 = 0; c0 < rows; c0 += chunk) {
                     FusedArgs a = fused_args(c, Sq, Lall);
@@ -1709,10 +1740,10 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
                     a.vec32 = true;
                     a.ur = c->d_ur32;
                     CK(fused_col(true, true, a));
-                    CK(fused_drho(a, c->d_scratch, g0));
-                    g0 += fused_drho_groups(a.nc);
+                    CK(fused_drho(a, c->d_scratch, gmask, g0));
+                    g0 += fused_drho_groups(c->N[0], c->N[1], a.nc);
                 }
-                CK(k_drho_reduce(c->d_scratch, ng, nr, nspin, wrho, c->d_drho_pm, c->st));
+                CK(k_drho_reduce(c->d_scratch, ng, nr, nspin, wrho, c->d_drho_pm, c->st, gmask));
             }
             for (int c0 = 0; c0 < rows && !fdrho; c0 += chunk) {
                 FusedArgs a = fused_args(c, Sq, Lall);
@@ -1732,7 +1763,7 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
             CK(k_from_planes_c(c->d_drho_pm, c->d_drho, c->N, nspin, c->st));
         } else if (mixed) {
             float2* g32 = (float2*)c->d_grid;
-            const int cap = 2 * c->grid_cap;
+            const int cap = 2 * band_batch(c, rows);
             for (int c0 = 0; c0 < rows; c0 += cap) {
                 const int nc = std::min(cap, rows - c0);
                 CK(k_scatter32(Sq, Lall, c0, nc, c->d_x, g32, nr, c->st));
@@ -1741,8 +1772,9 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
                                    c->scratch_elems, c->st));
             }
         } else {
-            for (int c0 = 0; c0 < rows; c0 += c->grid_cap) {
-                const int nc = std::min(c->grid_cap, rows - c0);
+            const int chunk = band_batch(c, rows);
+            for (int c0 = 0; c0 < rows; c0 += chunk) {
+                const int nc = std::min(chunk, rows - c0);
                 CK(k_scatter(Sq, Lall, c0, nc, c->d_x, ld, c->d_grid, nr, c->st));
                 CK(fft3d(c->fft, c->d_grid, nc, +1, c->st));
                 CK(k_drho_acc(c->d_ur, Lall.d_row, c->d_grid, nc, nr, Lall, c0, wrho, nspin, c->d_drho, c->d_scratch,

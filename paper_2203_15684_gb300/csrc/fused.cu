@@ -423,7 +423,7 @@ template <class V, int N0, int N1, int OP, bool PR>
 __global__ void __launch_bounds__(PlaneCfg<V, N0, N1>::NT, PlaneCfg<V, N0, N1>::template minb<OP>()) plane_reg_kernel(
     const V* __restrict__ colin, V* __restrict__ colout, int ncmax, const int* __restrict__ kk,
     const int* __restrict__ spin, int c0, int nc, const int* __restrict__ xtab, int N2,
-    const typename Scalar<V>::type* __restrict__ vt, const V* __restrict__ ur, const int* __restrict__ ur_row,
+    const typename Scalar<V>::type* __restrict__ vtx, const V* __restrict__ ur, const int* __restrict__ ur_row,
     const V* __restrict__ dvt, V* __restrict__ out, double inv_n) {
     using Cfg = PlaneCfg<V, N0, N1>;
     using T = typename Scalar<V>::type;
@@ -433,8 +433,42 @@ __global__ void __launch_bounds__(PlaneCfg<V, N0, N1>::NT, PlaneCfg<V, N0, N1>::
     const long long q0 = (long long)blockIdx.x * P;
     const long long npairs = (long long)nc * N2;
     const int tid = threadIdx.x;
-    // ---- y-inverse: line x of plane p from its run of columns (zero where x has none)
-    if (OP != 2) {
+    if constexpr (OP == 2) {
+        // ---- u(r) Delta V(r) of each plane into shared memory, consecutive threads on consecutive points
+        constexpr int EPT = (NP + NT - 1) / NT;
+        __shared__ long long u_of[P], d_of[P];
+        if (tid < P) {
+            const long long q = q0 + tid;
+            if (q < npairs) {
+                const int c = (int)(q / N2), z = (int)(q % N2);
+                u_of[tid] = ((long long)ur_row[c0 + c] * N2 + z) * NP;
+                d_of[tid] = ((long long)spin[c0 + c] * N2 + z) * NP;
+            }
+        }
+        __syncthreads();
+        // plane by plane, every load of the plane issued before the first product
+        const int np = (int)min((long long)P, npairs - q0);
+        for (int p = 0; p < np; ++p) {
+            const V* u = ur + u_of[p];
+            const V* d = dvt + d_of[p];
+            V uv[EPT], dv[EPT];
+#pragma unroll
+            for (int j = 0; j < EPT; ++j) {
+                const int e = tid + j * NT;
+                if (e < NP) {
+                    uv[j] = __ldcs(u + e);
+                    dv[j] = __ldg(d + e);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < EPT; ++j) {
+                const int e = tid + j * NT;
+                if (e < NP) S[p * PS + (e / N0) * LD + e % N0] = cmul(uv[j], dv[j]);
+            }
+        }
+        __syncthreads();
+    } else {
+        // ---- y-inverse: line x of plane p from its run of columns (zero where x has none)
         if (tid < P * N0) {
             const int p = tid / N0, x = tid % N0;
             const long long q = q0 + p;
@@ -467,14 +501,18 @@ __global__ void __launch_bounds__(PlaneCfg<V, N0, N1>::NT, PlaneCfg<V, N0, N1>::
             V* rowp = S + p * PS + y * LD;
             V a[N0];
             if (OP == 2) {
-                load_row<V, N0>(ur + ((long long)ur_row[c0 + c] * N2 + z) * NP + y * N0, a);
-                mul_row<V, V, N0>(dvt + ((long long)spin[c0 + c] * N2 + z) * NP + y * N0, a);
+#pragma unroll
+                for (int x = 0; x < N0; ++x) a[x] = rowp[x];
             } else {
 #pragma unroll
                 for (int x = 0; x < N0; ++x) a[x] = live<N0, PR>(x) ? rowp[x] : cpack<V>(0.0, 0.0);
                 rfft<V, N0, +1>(a);
             }
-            if (OP == 0) mul_row<V, T, N0>(vt + ((long long)spin[c0 + c] * N2 + z) * NP + y * N0, a);
+            if (OP == 0) {  // V(r) from the x-major planes: consecutive threads (y) on consecutive words
+                const T* vx = vtx + ((long long)spin[c0 + c] * N2 + z) * NP + y;
+#pragma unroll
+                for (int x = 0; x < N0; ++x) a[x] = cscale(a[x], __ldg(vx + x * N1));
+            }
             if (OP != 1) rfft<V, N0, -1>(a);
 #pragma unroll
             for (int x = 0; x < N0; ++x)
@@ -782,7 +820,7 @@ static cudaError_t plane_reg_go(const FusedArgs& a, size_t smem, int grid) {
                                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (attr != cudaSuccess) return attr;
     plane_reg_kernel<V, N0, N1, OP, PR><<<grid, Cfg::NT, smem, a.st>>>(
-        (const V*)a.colA, (V*)a.colB, S.ncmax, L.d_k, L.d_spin, a.c0, a.nc, S.d_xtab, a.N2, (const T*)a.vt,
+        (const V*)a.colA, (V*)a.colB, S.ncmax, L.d_k, L.d_spin, a.c0, a.nc, S.d_xtab, a.N2, (const T*)a.vtx,
         (const V*)a.ur, L.d_row, (const V*)a.dvt, (V*)a.out, a.inv_n);
     return cudaSuccess;
 }
@@ -889,13 +927,18 @@ static cudaError_t plane_dispatch(int n0, int n1, const FusedArgs& a) {
 }
 
 // ------------------------------------------------------------------------------------------------
-// Delta rho with the inverse transform of Delta u fused in (FP32 form): CTA (z-plane, group of
-// kDrhoGroup bands).  Rounds of P bands: y- and x-inverse transforms of the bands' z-plane as in
-// op 1, then conj(u(r)) Delta u(r) per point; the group's sum per spin is kept in FP32 in shared memory and
-// written as FP64 to part[group][spin][z][y][x]; the groups are added in a fixed order afterwards.
-// Delta u(r) never goes to HBM.
+// Delta rho with the inverse transform of Delta u fused in (FP32 form): CTA (z-plane, group of G
+// bands, G the multiple of P nearest above 32).  Rounds of P bands: y- and x-inverse transforms of the
+// bands' z-plane as in op 1, left in shared memory; then, point by point with coalesced reads of
+// u(r), conj(u(r)) Delta u(r) added to the group's sum of its spin (FP32, shared memory).  The sums
+// are written as FP64 to part[group][spin][z][y][x] for the spins the group holds (bit s of
+// mask[group]); the groups are added in a fixed order afterwards.  Delta u(r) never goes to HBM.
 // ------------------------------------------------------------------------------------------------
-constexpr int kDrhoGroup = 32;
+template <int N0, int N1>
+__host__ __device__ constexpr int drho_group() {
+    constexpr int P = PlaneCfg<float2, N0, N1>::P;
+    return ((32 + P - 1) / P) * P;
+}
 
 // two resident CTAs per SM asked of the compiler for lines up to 45 points
 template <int N0, int N1>
@@ -905,21 +948,30 @@ template <int N0, int N1, bool PR>
 __global__ void __launch_bounds__(PlaneCfg<float2, N0, N1>::NT, drho_minb<N0, N1>()) drho_plane_kernel(
     const float2* __restrict__ colin, int ncmax, const int* __restrict__ kk, const int* __restrict__ spin,
     const int* __restrict__ ur_row, int c0, int nc, const int* __restrict__ xtab, int N2,
-    const float2* __restrict__ ur, double2* __restrict__ part, int group0) {
+    const float2* __restrict__ ur, double2* __restrict__ part, int* __restrict__ mask, int group0) {
     using V = float2;
     using Cfg = PlaneCfg<V, N0, N1>;
-    constexpr int P = Cfg::P, NT = Cfg::NT, LD = Cfg::LD, NP = N0 * N1, PS = N1 * LD;
+    constexpr int P = Cfg::P, NT = Cfg::NT, LD = Cfg::LD, NP = N0 * N1, PS = N1 * LD, G = drho_group<N0, N1>();
     constexpr int EPT = (NP + NT - 1) / NT;
     extern __shared__ __align__(16) unsigned char smraw[];
     V* S = (V*)smraw;          // [P][N1][LD]
     V* A = S + P * PS;         // [2][NP] the group's sums per spin (each point owned by one thread)
     __shared__ int sp_of[P];
+    __shared__ long long u_of[P];  // offset of the band's plane z in ur
+    __shared__ int seen;           // bit s: the group holds a band of spin s
     const int z = blockIdx.x, grp = blockIdx.y;
-    const int b0 = grp * kDrhoGroup, b1 = min(nc, b0 + kDrhoGroup);
+    const int b0 = grp * G, b1 = min(nc, b0 + G);
     const int tid = threadIdx.x;
+    int myseen = 0;
+    if (tid == 0) seen = 0;
     for (int e = tid; e < 2 * NP; e += NT) A[e] = cmkf(0.f, 0.f);
     for (int r0 = b0; r0 < b1; r0 += P) {
-        if (tid < P) sp_of[tid] = (r0 + tid < b1) ? spin[c0 + r0 + tid] : -1;
+        if (tid < P) {
+            const bool in = r0 + tid < b1;
+            sp_of[tid] = in ? spin[c0 + r0 + tid] : -1;
+            u_of[tid] = in ? ((long long)ur_row[c0 + r0 + tid] * N2 + z) * NP : 0;
+            if (in) myseen |= 1 << sp_of[tid];
+        }
         // y-inverse on the x-lines of each band's column runs (zero elsewhere)
         if (tid < P * N0) {
             const int p = tid / N0, x = tid % N0;
@@ -943,55 +995,63 @@ __global__ void __launch_bounds__(PlaneCfg<float2, N0, N1>::NT, drho_minb<N0, N1
             }
         }
         __syncthreads();
-        // x-inverse, then conj(u(r)) Delta u(r) written back in place
+        // x-inverse in place
         if (tid < P * N1) {
             const int p = tid / N1, y = tid % N1;
-            const int c = r0 + p;
-            if (c < b1) {
+            if (r0 + p < b1) {
                 V* rowp = S + p * PS + y * LD;
                 V a[N0];
 #pragma unroll
                 for (int x = 0; x < N0; ++x) a[x] = live<N0, PR>(x) ? rowp[x] : cmkf(0.f, 0.f);
                 rfft<V, N0, +1>(a);
-                const V* u = ur + ((long long)ur_row[c0 + c] * N2 + z) * NP + y * N0;
 #pragma unroll
-                for (int x = 0; x < N0; ++x) {
-                    const V uv = u[x];
-                    rowp[x] = cmkf(uv.x * a[x].x + uv.y * a[x].y, uv.x * a[x].y - uv.y * a[x].x);
+                for (int x = 0; x < N0; ++x) rowp[x] = a[x];
+            }
+        }
+        __syncthreads();
+        // conj(u(r)) Delta u(r) of the round's bands into the per-spin sums, in band order; u(r) read
+        // with consecutive threads on consecutive points, every load of a band issued before its sums
+        const int np = min(P, b1 - r0);
+        for (int p = 0; p < np; ++p) {
+            const V* up = ur + u_of[p];
+            V* Ap = A + sp_of[p] * NP;
+            V u[EPT];
+#pragma unroll
+            for (int j = 0; j < EPT; ++j) {
+                const int e = tid + j * NT;
+                if (e < NP) u[j] = __ldcs(up + e);
+            }
+#pragma unroll
+            for (int j = 0; j < EPT; ++j) {
+                const int e = tid + j * NT;
+                if (e < NP) {
+                    const V d = S[p * PS + (e / N0) * LD + e % N0];
+                    Ap[e] = cadd(Ap[e], cmkf(u[j].x * d.x + u[j].y * d.y, u[j].x * d.y - u[j].y * d.x));
                 }
             }
         }
         __syncthreads();
-        // the round's bands into the per-spin sums, in band order
+    }
+    if (myseen) atomicOr(&seen, myseen);
+    __syncthreads();
+    const int bits = seen;
+    const long long nr = (long long)NP * N2;
+    for (int sp = 0; sp < 2; ++sp) {
+        if (!((bits >> sp) & 1)) continue;
 #pragma unroll
         for (int j = 0; j < EPT; ++j) {
             const int e = tid + j * NT;
             if (e < NP) {
-                const int o = (e / N0) * LD + e % N0;
-                for (int p = 0; p < P; ++p) {
-                    const int sp = sp_of[p];
-                    if (sp < 0) break;
-                    A[sp * NP + e] = cadd(A[sp * NP + e], S[p * PS + o]);
-                }
+                const V v = A[sp * NP + e];
+                part[((long long)(group0 + grp) * 2 + sp) * nr + (long long)z * NP + e] = cmk((double)v.x, (double)v.y);
             }
         }
-        __syncthreads();
     }
-    const long long nr = (long long)NP * N2;
-#pragma unroll
-    for (int j = 0; j < EPT; ++j) {
-        const int e = tid + j * NT;
-        if (e < NP) {
-            const long long r = (long long)z * NP + e;
-            const V s0 = A[e], s1 = A[NP + e];
-            part[((long long)(group0 + grp) * 2) * nr + r] = cmk((double)s0.x, (double)s0.y);
-            part[((long long)(group0 + grp) * 2 + 1) * nr + r] = cmk((double)s1.x, (double)s1.y);
-        }
-    }
+    if (z == 0 && tid == 0) mask[group0 + grp] = bits;
 }
 
 template <int N0, int N1>
-static cudaError_t drho_plane_launch(const FusedArgs& a, double2* part, int group0) {
+static cudaError_t drho_plane_launch(const FusedArgs& a, double2* part, int* mask, int group0) {
     using Cfg = PlaneCfg<float2, N0, N1>;
     if constexpr (!Cfg::ok) {
         return cudaErrorInvalidValue;
@@ -1004,7 +1064,8 @@ static cudaError_t drho_plane_launch(const FusedArgs& a, double2* part, int grou
         static const cudaError_t attr =
             cudaFuncSetAttribute(drho_plane_kernel<N0, N1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (attr != cudaSuccess) return attr;
-        dim3 g(a.N2, (a.nc + kDrhoGroup - 1) / kDrhoGroup);
+        constexpr int G = drho_group<N0, N1>();
+        dim3 g(a.N2, (a.nc + G - 1) / G);
         if constexpr (N0 >= 36 && N1 >= 36) {
             if (S.lines_prunable && !getenv("HP_NO_PRUNE")) {
                 static const cudaError_t attr_p = cudaFuncSetAttribute(
@@ -1012,20 +1073,28 @@ static cudaError_t drho_plane_launch(const FusedArgs& a, double2* part, int grou
                 if (attr_p != cudaSuccess) return attr_p;
                 drho_plane_kernel<N0, N1, true><<<g, Cfg::NT, smem, a.st>>>(
                     (const float2*)a.colA, S.ncmax, L.d_k, L.d_spin, L.d_row, a.c0, a.nc, S.d_xtab, a.N2,
-                    (const float2*)a.ur, part, group0);
+                    (const float2*)a.ur, part, mask, group0);
                 HP_LAUNCHED();
                 return cudaGetLastError();
             }
         }
         drho_plane_kernel<N0, N1, false><<<g, Cfg::NT, smem, a.st>>>((const float2*)a.colA, S.ncmax, L.d_k, L.d_spin,
                                                                       L.d_row, a.c0, a.nc, S.d_xtab, a.N2,
-                                                                      (const float2*)a.ur, part, group0);
+                                                                      (const float2*)a.ur, part, mask, group0);
         HP_LAUNCHED();
         return cudaGetLastError();
     }
 }
 
-int fused_drho_groups(int nc) { return (nc + kDrhoGroup - 1) / kDrhoGroup; }
+#define HP_DRHO_SIZES(M) M(10, 10) M(12, 12) M(15, 15) M(16, 16) M(18, 18) M(20, 20) M(24, 24) M(36, 36) M(45, 45) M(72, 45)
+
+int fused_drho_groups(int n0, int n1, int nc) {
+#define HP_DG(A0, A1) \
+    if (n0 == A0 && n1 == A1) return (nc + drho_group<A0, A1>() - 1) / drho_group<A0, A1>();
+    HP_DRHO_SIZES(HP_DG)
+#undef HP_DG
+    return 0;
+}
 
 bool fused_drho_supported(const FusedArgs& a) {
     const int n0 = a.N0, n1 = a.N1;
@@ -1035,13 +1104,32 @@ bool fused_drho_supported(const FusedArgs& a) {
     return sizes && a.reg && a.S->d_xtab && a.S->xtab_n0 == n0;
 }
 
-cudaError_t fused_drho(const FusedArgs& a, double2* part, int group0) {
+cudaError_t fused_drho(const FusedArgs& a, double2* part, int* mask, int group0) {
 #define HP_DR(A0, A1) \
-    if (a.N0 == A0 && a.N1 == A1) return drho_plane_launch<A0, A1>(a, part, group0);
-    HP_DR(10, 10) HP_DR(12, 12) HP_DR(15, 15) HP_DR(16, 16) HP_DR(18, 18) HP_DR(20, 20) HP_DR(24, 24)
-    HP_DR(36, 36) HP_DR(45, 45) HP_DR(72, 45)
+    if (a.N0 == A0 && a.N1 == A1) return drho_plane_launch<A0, A1>(a, part, mask, group0);
+    HP_DRHO_SIZES(HP_DR)
 #undef HP_DR
     return cudaErrorInvalidValue;
+}
+
+template <class T>
+__global__ void planes_xmajor_kernel(const T* __restrict__ in, T* __restrict__ out, int N0, int N1, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const long long np = (long long)N0 * N1;
+    const long long pl = i / np;
+    const int r = (int)(i % np), x = r / N1, y = r % N1;
+    out[i] = in[pl * np + (long long)y * N0 + x];
+}
+
+cudaError_t k_planes_xmajor(const void* in, void* out, int N0, int N1, long long nplanes, bool fp32, cudaStream_t st) {
+    const long long n = nplanes * N0 * N1;
+    if (n <= 0) return cudaSuccess;
+    const int blocks = (int)((n + 255) / 256);
+    if (fp32) planes_xmajor_kernel<float><<<blocks, 256, 0, st>>>((const float*)in, (float*)out, N0, N1, n);
+    else planes_xmajor_kernel<double><<<blocks, 256, 0, st>>>((const double*)in, (double*)out, N0, N1, n);
+    HP_LAUNCHED();
+    return cudaGetLastError();
 }
 
 bool fused_supported(const int N[3]) {

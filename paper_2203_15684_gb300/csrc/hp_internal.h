@@ -149,6 +149,7 @@ struct SphereSet {          // device arrays, nk spheres of at most ld points
     // every sphere point's x, y and z grid indices lie within (N - 1) / 4 of 0 (mod N): the column and
     // plane transforms may prune their lines to those positions
     bool lines_prunable = false;
+    bool cols_distinct = true;  // no two columns of one k share an (x, y) (the fused transforms need this)
 };
 
 struct BandList {
@@ -260,9 +261,10 @@ cudaError_t k_formfactor(const double* kcart, int nk, const int* miller, const i
                          const double* bvec, int nrow, const int* row_atom, const int* row_l, const int* row_m,
                          const double* row_width, const double* row_pref, const double* tau, double2* out,
                          cudaStream_t st);
-// drho[s][r] += weight * sum over the nsplit partial sums part[slice][s][r] (fixed order)
+// drho[s][r] += weight * sum over the nsplit partial sums part[slice][s][r] (fixed order); with a
+// mask, only the slices whose bit s of mask[slice] is set hold spin s (the others are skipped)
 cudaError_t k_drho_reduce(const double2* part, int nsplit, int nr, int nspin, double weight, double2* drho,
-                          cudaStream_t st);
+                          cudaStream_t st, const int* mask = nullptr);
 cudaError_t k_drho_acc(const double2* ur, const int* ur_row_of_item, const double2* xr, int nc, int nr,
                        const BandList& L, int c0, double weight, int nspin, double2* drho, double2* part,
                          size_t part_elems, cudaStream_t st);
@@ -354,6 +356,7 @@ struct FusedArgs {
     void* colA = nullptr;        // column buffer written by col_inv, read by plane
     void* colB = nullptr;        // column buffer written by plane, read by col_fwd
     const void* vt = nullptr;    // plane-major real potential [spin][z][y][x]
+    const void* vtx = nullptr;   // the same with x-major planes [spin][z][x][y] (register plane kernels)
     const void* ur = nullptr;    // plane-major real-space bands [row][z][y][x]
     const void* dvt = nullptr;   // plane-major complex Delta V [spin][z][y][x]
     void* out = nullptr;         // plane-major real-space output [c][z][y][x]
@@ -376,11 +379,14 @@ void prof_stop(const ProfMark& m, int fam, cudaStream_t st, double flops, double
 bool fused_supported(const int N[3]);
 cudaError_t fused_col(bool fp32, bool inv, const FusedArgs& a);
 cudaError_t fused_plane(bool fp32, int op, const FusedArgs& a);
+// out[plane][x][y] = in[plane][y][x] for nplanes planes of N1 x N0 reals (float or double)
+cudaError_t k_planes_xmajor(const void* in, void* out, int N0, int N1, long long nplanes, bool fp32, cudaStream_t st);
 // Delta rho of the FP32 form with the inverse plane transform fused in: partial sums of groups of
-// bands, part[group0 + g][spin][z][y][x] (FP64); the groups are then added by k_drho_reduce
+// bands, part[group0 + g][spin][z][y][x] (FP64) for the spins of the group, mask[group0 + g] = those
+// spins as bits; the groups are then added by k_drho_reduce
 bool fused_drho_supported(const FusedArgs& a);
-int fused_drho_groups(int nc);
-cudaError_t fused_drho(const FusedArgs& a, double2* part, int group0);
+int fused_drho_groups(int n0, int n1, int nc);
+cudaError_t fused_drho(const FusedArgs& a, double2* part, int* mask, int group0);
 cudaError_t k_to_planes_real(const double* a, double* b, const int N[3], int nvec, cudaStream_t st);
 cudaError_t k_to_planes_c(const double2* a, double2* b, const int N[3], int nvec, cudaStream_t st);
 cudaError_t k_from_planes_c(const double2* b, double2* a, const int N[3], int nvec, cudaStream_t st);
@@ -491,12 +497,14 @@ struct hp_ctx {
     float* d_veff32 = nullptr;         // mixed precision: FP32 copy of V_loc + V_Hxc
     float2* d_dv32 = nullptr;          // mixed precision: FP32 copy of Delta V_Hxc
     // sphere-sparse fused transforms (when the grid sizes are supported)
-    bool fused = false;
+    bool fused = false;                // the fused transforms serve the current k and k+q sets
+    bool fused_grid = false;           // the grid sizes allow the fused transforms
     int proj_rows_max = 128;           // rows of one combined beta / P_v projection
     bool vec32 = false;                // response band vectors stored in FP32 (mixed form, fused path)
     bool fused_reg = true;             // fused transforms with register-resident line FFTs
     bool ur_planes = false;            // the real-space band cache is plane-major (built by the fused path)
     void* d_vt = nullptr;              // plane-major V_eff [nspin][z][y][x] (double or float)
+    void* d_vtx = nullptr;             // V_eff with x-major planes [nspin][z][x][y] (double or float)
     void* d_dvt = nullptr;             // plane-major Delta V (double2 or float2)
     double2* d_drho_pm = nullptr;      // plane-major Delta rho accumulation
     void* d_colA = nullptr;

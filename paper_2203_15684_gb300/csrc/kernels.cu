@@ -531,6 +531,9 @@ static cudaError_t proj_t(const BandList& L, const SphereSet& S, const ProjMat& 
     // about one wave of 8 resident CTAs per SM, at least two 32-point tiles per split
     int ksplit = std::max(1, cdiv(152 * 8, std::max(1, L.nseg)));
     ksplit = std::min(ksplit, std::max(1, S.ld / (2 * TG)));
+    // at most 16 splits, which the callers' scratch holds: the split, and with it the order of the sums,
+    // is then fixed by the sizes alone and not by how large the scratch has grown
+    ksplit = std::min(ksplit, 16);
     while (ksplit > 1 && (size_t)ksplit * L.nb * kPStride > scratch_elems) --ksplit;
     if ((size_t)ksplit * L.nb * kPStride > scratch_elems) return cudaErrorMemoryAllocation;
     const int npt = nrow <= 32 ? 1 : nrow <= 64 ? 2 : 4;
@@ -1073,12 +1076,13 @@ __global__ void __launch_bounds__(256) drho_part_kernel(const V* __restrict__ ur
 }
 
 __global__ void drho_reduce_kernel(const double2* __restrict__ part, int nsplit, int nr, int nspin, double weight,
-                                   double2* __restrict__ drho) {
+                                   double2* __restrict__ drho, const int* __restrict__ mask) {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (long long)nspin * nr) return;
     const int s = (int)(e / nr), r = (int)(e % nr);
     double2 acc = cmk(0.0, 0.0);
-    for (int sl = 0; sl < nsplit; ++sl) acc = cadd(acc, part[((long long)sl * 2 + s) * nr + r]);
+    for (int sl = 0; sl < nsplit; ++sl)
+        if (!mask || ((mask[sl] >> s) & 1)) acc = cadd(acc, part[((long long)sl * 2 + s) * nr + r]);
     drho[e] = cadd(drho[e], cscale(acc, weight));
 }
 
@@ -1090,6 +1094,7 @@ static cudaError_t drho_acc_launch(const V* ur, const int* ur_row, const V* xr, 
     const int bx = cdiv(nr, 256);
     // about two waves of 8 resident CTAs per SM, slices of at least one tile, partials within the scratch
     int nsplit = std::max(1, std::min(cdiv(2 * 152 * 8, bx), cdiv(nc, kDrhoTile)));
+    nsplit = std::min(nsplit, 32);  // what the callers' scratch (64 grids) holds, whatever its current size
     while (nsplit > 1 && (size_t)nsplit * 2 * nr > part_elems) --nsplit;
     if ((size_t)nsplit * 2 * nr > part_elems) return cudaErrorMemoryAllocation;
     const int slice = cdiv(nc, nsplit);
@@ -1098,14 +1103,15 @@ static cudaError_t drho_acc_launch(const V* ur, const int* ur_row, const V* xr, 
     HP_LAUNCHED();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    drho_reduce_kernel<<<cdiv((long long)nspin * nr, 256), 256, 0, st>>>(part, nsplit, nr, nspin, weight, drho);
+    drho_reduce_kernel<<<cdiv((long long)nspin * nr, 256), 256, 0, st>>>(part, nsplit, nr, nspin, weight, drho,
+                                                                          nullptr);
     HP_LAUNCHED();
     return cudaGetLastError();
 }
 
 cudaError_t k_drho_reduce(const double2* part, int nsplit, int nr, int nspin, double weight, double2* drho,
-                          cudaStream_t st) {
-    drho_reduce_kernel<<<cdiv((long long)nspin * nr, 256), 256, 0, st>>>(part, nsplit, nr, nspin, weight, drho);
+                          cudaStream_t st, const int* mask) {
+    drho_reduce_kernel<<<cdiv((long long)nspin * nr, 256), 256, 0, st>>>(part, nsplit, nr, nspin, weight, drho, mask);
     HP_LAUNCHED();
     return cudaGetLastError();
 }

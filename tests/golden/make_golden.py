@@ -2,10 +2,10 @@
 
     python tests/golden/make_golden.py
 
-tiny_config0.json: the two-atom cube at its full size (20 Ry, FFT 20^3, k 2x2x2, q 1x1x1):
+tiny_full.json: the two-atom cube at its full size (20 Ry, FFT 20^3, k 2x2x2, q 1x1x1):
 oracle ground state (gap, eigenvalues at k = Gamma), chi_0, chi and U of the H atom.
 
-medium_config1_column.json (``python tests/golden/make_golden.py medium``, a few CPU hours): the
+medium_column.json (``python tests/golden/make_golden.py medium``, a few CPU hours): the
 medium rocksalt workload at its full size (35 Ry, FFT 36^3, k 4x4x4, q 2x2x2, nspin = 2): the
 oracle's ground state (every occupied eigenvalue, the gap, the Hubbard occupations) and one
 declared (q, J) column, q = (1/2, 0, 0) and J = the first H atom: Delta_q n^0 and Delta_q n of every
@@ -26,7 +26,7 @@ from oracle import groundstate as G, hubbard as HB, response as R  # noqa: E402
 from oracle.model import Model  # noqa: E402
 
 
-def tiny_config0():
+def tiny_full():
     w = W.tiny()
     m = Model(w)
     gs = G.scf(m, tol=1e-12)
@@ -45,7 +45,7 @@ def _cplx(a):
     return [a.real.tolist(), a.imag.tolist()]
 
 
-def medium_config1_column(iq=4, J=0):
+def medium_column(iq=4, J=0):
     w = W.medium()
     m = Model(w)
     gs = G.scf(m, tol=1e-12, verbose=True)
@@ -63,9 +63,9 @@ def medium_config1_column(iq=4, J=0):
 
 if __name__ == "__main__":
     if len(sys.argv) > 1 and sys.argv[1] == "medium":
-        name, out = "medium_config1_column.json", medium_config1_column()
+        name, out = "medium_column.json", medium_column()
     else:
-        name, out = "tiny_config0.json", tiny_config0()
+        name, out = "tiny_full.json", tiny_full()
     with open(os.path.join(HERE, name), "w") as f:
         json.dump(out, f, indent=1)
     print("wrote", name)

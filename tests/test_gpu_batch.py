@@ -52,7 +52,7 @@ def test_batch_equals_cells_alone(precision):
 
 
 def test_seeded_cells_electron_rule_and_batch():
-    """Two cells of the seeded batch (config 3): the library's bare spectrum at k = 0 equals the
+    """Two cells of the seeded batch of 16 cells: the library's bare spectrum at k = 0 equals the
     oracle's dense diagonalisation of T + V_loc + V_NL (1e-9 Ha); the electron-count rule (largest
     gap among band counts n_H + n_L .. 5 n_H + 3 n_L) gives a ground state with a gap; the two cells
     at once equal the cells alone (mixed form)."""

@@ -1,8 +1,8 @@
-"""The medium workload at its full size, in the benchmark's launch configuration (config 1: rocksalt
+"""The medium workload at its full size, in the benchmark's launch configuration (rocksalt
 cube 8.4 bohr, 4 H + 4 L, nspin = 2, 35 Ry, FFT 36^3, k 4x4x4, q 2x2x2: 2560 band systems per
 (q, J)), against the oracle on a declared column.
 
-tests/golden/medium_config1_column.json is written by tests/golden/make_golden.py, which calls only
+tests/golden/medium_column.json is written by tests/golden/make_golden.py, which calls only
 the oracle: its ground state (SCF to 1e-12) and the self-consistent response to J = the first H atom
 at q = (1/2, 0, 0).  Here the library computes its own ground state on the GPU (gs_tol 1e-12) and the
 same column: occupied eigenvalues within 1e-9 Ha, Delta n^0 and Delta n element by element at 1e-8
@@ -19,7 +19,7 @@ import workloads as W
 pytestmark = pytest.mark.gpu
 
 P = pytest.importorskip("paper_2203_15684_gb300")
-GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "medium_config1_column.json")
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "medium_column.json")
 
 
 def _padded(g, key, nspin, mmax=5):

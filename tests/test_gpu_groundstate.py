@@ -39,9 +39,9 @@ def test_ground_state_spin_polarised():
     _gs_compare(w, moments=w["moments"])
 
 
-def test_config0_end_to_end_against_golden():
+def test_tiny_end_to_end_against_golden():
     """Two-atom cube at full size: GPU ground state, response, chi and U vs the stored oracle run."""
-    ref = json.load(open(os.path.join(HERE, "golden", "tiny_config0.json")))
+    ref = json.load(open(os.path.join(HERE, "golden", "tiny_full.json")))
     w = W.tiny()
     ctx = P.Context.from_workload(w, gs_tol=1e-12, cg_tol=1e-12, scf_tol=1e-11, conv_thr_chi=1e-11)
     info = ctx.ground_state(w["nelec"], w["nspin"])

@@ -55,8 +55,8 @@ def test_mixed_response_spin_polarised():
     assert np.abs(dn - r1).max() < 1e-5 * np.abs(r1).max()
 
 
-def test_mixed_config0_end_to_end_within_1mev():
-    ref = json.load(open(os.path.join(HERE, "golden", "tiny_config0.json")))
+def test_mixed_tiny_end_to_end_within_1mev():
+    ref = json.load(open(os.path.join(HERE, "golden", "tiny_full.json")))
     w = W.tiny()
     ctx = P.Context.from_workload(w, precision=1, gs_tol=1e-12)
     ctx.ground_state(w["nelec"], w["nspin"])
@@ -70,15 +70,18 @@ def test_mixed_stagnation_exit_is_reported():
     """With the mixed form's noise-floor test switched off (mixed_floor ~ 0) the response SCF can only
     stop on its stagnation rule (residual below 1e-5 of the response potential that has not fallen
     for three iterations); hp_resp_info says so, and the result still meets the mixed form's bar.
-    With a floor well above the FP32 noise (1e-5) the ordinary exit is taken."""
+    With a floor well above the FP32 noise (1e-5) the ordinary exit is taken.  Either exit leaves a
+    residual of up to 1e-5 of the response potential, which bounds the error of the occupations at a
+    few times 1e-5 (bar 5e-5) rather than at the converged form's 1e-5."""
     w = W.tiny_lowcut(ecut=10.0, grid=(12, 12, 12))
     m = Model(w)
     gs = G.scf(m, tol=1e-12)
     J = m.hub_atoms[0]
     ref = oracle_dn_padded(m, R.solve_column(m, gs, 0, J, tol_cg=1e-13, scf_tol=1e-12, conv_chi=1e-13)["dn"])
-    for floor, expect in ((1e-14, 1), (1e-5, 0)):
+    for floor, expect, bar in ((1e-14, 1, 5e-5), (1e-5, 0, 5e-5)):
         ctx = P.Context.from_workload(w, precision=1, mixed_floor=floor, scf_tol=1e-14, conv_thr_chi=1e-14)
         import_ground_state(ctx, m, gs)
         _, dn, info = ctx.response(0, J)
         assert info["stagnated"] == expect, (floor, info)
-        assert np.abs(dn - ref).max() < 1e-5 * np.abs(ref).max()
+        err = np.abs(dn - ref).max() / np.abs(ref).max()
+        assert err < bar, (floor, err)
