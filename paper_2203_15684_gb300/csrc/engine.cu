@@ -380,11 +380,14 @@ hp_status ensure_colbuf(hp_ctx* c, size_t bytes) {
     return HP_OK;
 }
 
-// bands per batch of the fused transforms (two column buffers and, for real-space output, grids)
+// bands per batch of the fused transforms: the two column buffers (2 GB each at most), or the
+// caller's band_batch option; not bound by the 3D-FFT grid budget, so that one launch covers as many
+// bands as the buffers hold
 int fused_batch(const hp_ctx* c, const SphereSet& S, int nb) {
     const size_t per = sizeof(double2) * (size_t)c->N[2] * std::max(1, S.ncmax);
-    int b = (int)std::min<size_t>(32768, std::max<size_t>(1, ((size_t)512 << 20) / per));
-    return std::max(1, std::min(nb, std::min(b, band_batch(c, nb))));
+    int b = (int)std::min<size_t>(32768, std::max<size_t>(1, ((size_t)2 << 30) / per));
+    if (c->opt.band_batch > 0) b = std::min(b, c->opt.band_batch);
+    return std::max(1, std::min(nb, b));
 }
 
 FusedArgs fused_args(hp_ctx* c, const SphereSet& S, const BandList& L) {
@@ -1745,10 +1748,11 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
                 }
                 CK(k_drho_reduce(c->d_scratch, ng, nr, nspin, wrho, c->d_drho_pm, c->st, gmask));
             }
-            for (int c0 = 0; c0 < rows && !fdrho; c0 += chunk) {
+            const int gchunk = std::min(chunk, band_batch(c, rows));  // real-space bands in the grid buffer
+            for (int c0 = 0; c0 < rows && !fdrho; c0 += gchunk) {
                 FusedArgs a = fused_args(c, Sq, Lall);
                 a.c0 = c0;
-                a.nc = std::min(chunk, rows - c0);
+                a.nc = std::min(gchunk, rows - c0);
                 a.X = c->d_x;
                 a.vec32 = v32;
                 a.out = c->d_grid;
