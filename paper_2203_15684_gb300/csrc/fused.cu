@@ -37,6 +37,11 @@ template <> struct FactorF<24> { using type = Radices_<4, 2, 3>; };
 template <> struct FactorF<36> { using type = Radices_<4, 3, 3>; };
 template <> struct FactorF<45> { using type = Radices_<3, 3, 5>; };
 template <> struct FactorF<72> { using type = Radices_<4, 2, 3, 3>; };
+// factors of the prime-factor (Good-Thomas) register FFTs below
+template <> struct FactorF<4> { using type = Radices_<4>; };
+template <> struct FactorF<5> { using type = Radices_<5>; };
+template <> struct FactorF<8> { using type = Radices_<4, 2>; };
+template <> struct FactorF<9> { using type = Radices_<3, 3>; };
 
 template <class V>
 __device__ __forceinline__ void bfly(V* v, int R, int s) {
@@ -193,8 +198,12 @@ template <> struct TwOff<24> { static constexpr int v = 91; };
 template <> struct TwOff<36> { static constexpr int v = 115; };
 template <> struct TwOff<45> { static constexpr int v = 151; };
 template <> struct TwOff<72> { static constexpr int v = 196; };
-constexpr int kTwTotal = 268;
-constexpr int kTwSizes[] = {10, 12, 15, 16, 18, 20, 24, 36, 45, 72};
+template <> struct TwOff<4> { static constexpr int v = 268; };
+template <> struct TwOff<5> { static constexpr int v = 272; };
+template <> struct TwOff<8> { static constexpr int v = 277; };
+template <> struct TwOff<9> { static constexpr int v = 285; };
+constexpr int kTwTotal = 294;
+constexpr int kTwSizes[] = {10, 12, 15, 16, 18, 20, 24, 36, 45, 72, 4, 5, 8, 9};
 __constant__ float2 c_tw32[kTwTotal];
 __constant__ double2 c_tw64[kTwTotal];
 
@@ -239,9 +248,56 @@ __device__ __forceinline__ void rfft_(Radices_<R...>, V (&a)[N]) {
     rstages<V, N, SIGN, 1, R...>(a);
 }
 
+// Lengths N = N1 N2 with coprime N1, N2 run as a prime-factor (Good-Thomas) FFT: input n =
+// (N2 n1 + N1 n2) mod N, N2 transforms of length N1 over n1, N1 transforms of length N2 over n2, and
+// output k = (N2 [N2^-1 mod N1] k1 + N1 [N1^-1 mod N2] k2) mod N, with no twiddle factors between
+// the two sets of transforms (W_N^(nk) = W_N1^(n1 k1) W_N2^(n2 k2) for these index maps).
+template <int N>
+struct PfaF {
+    static constexpr int n1 = 0, n2 = 0;
+};
+template <> struct PfaF<36> { static constexpr int n1 = 4, n2 = 9; };
+template <> struct PfaF<45> { static constexpr int n1 = 9, n2 = 5; };
+template <> struct PfaF<72> { static constexpr int n1 = 8, n2 = 9; };
+
+__host__ __device__ constexpr int inv_mod(int a, int m) {
+    for (int x = 1; x < m; ++x)
+        if ((a * x) % m == 1) return x;
+    return 1;
+}
+
+template <class V, int N, int SIGN>
+__device__ __forceinline__ void rfft(V (&a)[N]);
+
+template <class V, int N1, int N2, int SIGN>
+__device__ __forceinline__ void rfft_pfa(V (&a)[N1 * N2]) {
+    constexpr int N = N1 * N2;
+    constexpr int A = inv_mod(N2 % N1, N1), B = inv_mod(N1 % N2, N2);
+    V y[N];  // y[k1 N2 + n2]
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) {
+        V t[N1];
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) t[n1] = a[(N2 * n1 + N1 * n2) % N];
+        rfft<V, N1, SIGN>(t);
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) y[k1 * N2 + n2] = t[k1];
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) {
+        V t[N2];
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) t[n2] = y[k1 * N2 + n2];
+        rfft<V, N2, SIGN>(t);
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) a[(N2 * A * k1 + N1 * B * k2) % N] = t[k2];
+    }
+}
+
 template <class V, int N, int SIGN>
 __device__ __forceinline__ void rfft(V (&a)[N]) {
-    rfft_<V, N, SIGN>(typename FactorF<N>::type{}, a);
+    if constexpr (PfaF<N>::n1 > 0) rfft_pfa<V, PfaF<N>::n1, PfaF<N>::n2, SIGN>(a);
+    else rfft_<V, N, SIGN>(typename FactorF<N>::type{}, a);
 }
 
 // line lengths a thread can hold: 72 complex FP32 or 36 complex FP64 values
