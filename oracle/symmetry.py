@@ -1,0 +1,169 @@
+"""Oracle symmetry reductions of the response calculation: which Hubbard atoms are perturbed, how the
+columns of the atoms that are not perturbed are rebuilt, and which q points are computed (Sec. 2.4
+"Symmetry"; Sec. 3.2, the linear-response step and its post-processing; the hp.x input table of
+Appendix B: find_atpert, docc_thr, dist_thr, skip_equivalence_q).
+
+Test infrastructure only (see the package docstring).
+
+Perturbed atoms (find_atpert):
+  1  Hubbard atoms of one species whose ground-state occupations Tr n^I (summed over spin, Eq.
+     occ_matrix_0) differ by less than docc_thr (5e-5) form a class, whatever the sign of their
+     moments; one atom per class, the first in atom order, is perturbed.
+  2  one atom per species.
+  4  every Hubbard atom.
+  (3, classes from the space group, is not built.)
+
+Column reconstruction (post-processing): the real-space response column of a Hubbard atom J that was
+not perturbed, chi_{(l,s),(0,J)} = (1/N_q) sum_q exp(i q.R_l) Delta^J_q n^s (Eqs. chi and
+occ_matrix_response_lp_1), is taken from its class representative J': the entry for (l, s) is the
+entry (l', s') of J' with the species of s, the distance of (l, s) from J (minimum image in the
+supercell of the q mesh) within dist_thr (6e-4 bohr), and the spin orientation of s relative to J.
+The orientation of an atom is the sign of Tr n^up - Tr n^down where that difference exceeds
+docc_thr, else 0.  The first such (l', s') in index order is taken.  The full matrix then follows
+from the lattice periodicity of the supercell: chi_{(l,s),(l'',J)} = chi_{(l - l'' mod n, s),(0,J)}.
+
+Time reversal (the +-q of the small group of q): for a ground state with real potentials and real
+Hubbard orbitals the response to exp(-i q.R) is the complex conjugate of the response to exp(i q.R),
+Delta_{-q} n = conj(Delta_q n); of each pair {q, -q + G} of the q mesh the first in mesh order is
+computed.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+
+def spin_traces(model, gs):
+    """{atom: [Tr n^{I sigma} for sigma]} of the ground state (nspin = 1: one channel)."""
+    return {ia: [float(np.trace(n[s]).real) for s in range(n.shape[0])] for ia, n in gs.occupations().items()}
+
+
+def total_traces(model, gs):
+    """{atom: Tr n^I summed over spin (twice the channel for nspin = 1)}."""
+    f = 2.0 if model.nspin == 1 else 1.0
+    return {ia: f * sum(t) for ia, t in spin_traces(model, gs).items()}
+
+
+def perturbed_atoms(model, gs, find_atpert=1, docc_thr=5e-5):
+    """(atoms to perturb in atom order, {Hubbard atom: its class representative})."""
+    if find_atpert not in (1, 2, 4):
+        raise ValueError("find_atpert must be 1, 2 or 4")
+    tr = total_traces(model, gs)
+    rep = {}
+    for ia in model.hub_atoms:
+        sp = model.atom_species[ia]
+        r = ia
+        for ja in model.hub_atoms:
+            if ja >= ia:
+                break
+            if rep[ja] != ja or model.atom_species[ja] != sp:
+                continue
+            if find_atpert == 4:
+                continue
+            if find_atpert == 2 or (find_atpert == 1 and abs(tr[ja] - tr[ia]) < docc_thr):
+                r = ja
+                break
+        rep[ia] = r
+    return [ia for ia in model.hub_atoms if rep[ia] == ia], rep
+
+
+def orientations(model, gs, docc_thr=5e-5):
+    """{atom: +1 / -1 / 0}: sign of the Hubbard manifold's moment where it exceeds docc_thr."""
+    out = {}
+    for ia, t in spin_traces(model, gs).items():
+        d = t[0] - t[1] if len(t) == 2 else 0.0
+        out[ia] = 0 if abs(d) <= docc_thr else (1 if d > 0 else -1)
+    return out
+
+
+def realspace_column(model, qcols):
+    """qcols[iq] = trace vector over Hubbard atoms of one perturbed atom J.  Returns the column
+    (0, J) of the supercell matrix, index l * N_H + s, as assemble_chi orders it."""
+    R = model.supercell_R()
+    nh = len(model.hub_atoms)
+    nq = len(model.qpts)
+    col = np.zeros(len(R) * nh, dtype=complex)
+    for iq, q in enumerate(model.qpts):
+        for l in range(len(R)):
+            col[l * nh:(l + 1) * nh] += np.exp(2j * np.pi * np.dot(q, R[l])) * qcols[iq] / nq
+    return col
+
+
+def _distance(model, ia, ja, Rl):
+    """Minimum-image distance in the supercell from atom ia of cell 0 to atom ja of cell Rl."""
+    n = np.array(model.qmesh, dtype=float)
+    d = (model.frac[ja] + Rl - model.frac[ia]) / n
+    d -= np.round(d)
+    return float(np.linalg.norm(d @ (model.cell * n[:, None])))
+
+
+def reconstruct_columns(model, cols, rep, orient, dist_thr=6e-4):
+    """cols = {J: real-space column} for the perturbed atoms; returns the columns of every Hubbard
+    atom, those of the others rebuilt from their representatives."""
+    R = model.supercell_R()
+    nh = len(model.hub_atoms)
+    out = dict(cols)
+    for J in model.hub_atoms:
+        if J in out:
+            continue
+        Jp = rep[J]
+        src = cols[Jp]
+        col = np.zeros_like(src)
+        for l in range(len(R)):
+            for s, ia in enumerate(model.hub_atoms):
+                d = _distance(model, J, ia, R[l])
+                o = orient[ia] * orient[J]
+                hit = None
+                for lp in range(len(R)):
+                    for sp, ib in enumerate(model.hub_atoms):
+                        if model.atom_species[ib] != model.atom_species[ia]:
+                            continue
+                        if orient[ib] * orient[Jp] != o:
+                            continue
+                        if abs(_distance(model, Jp, ib, R[lp]) - d) <= dist_thr:
+                            hit = lp * nh + sp
+                            break
+                    if hit is not None:
+                        break
+                if hit is None:
+                    raise ValueError("no atom of the representative's column matches (%d, %d) of atom %d" % (l, s, J))
+                col[l * nh + s] = src[hit]
+        out[J] = col
+    return out
+
+
+def chi_from_columns(model, cols):
+    """The supercell matrix from the real-space columns (0, J) of every Hubbard atom, by the lattice
+    periodicity of the supercell."""
+    R = model.supercell_R()
+    nh = len(model.hub_atoms)
+    n = np.array(model.qmesh, dtype=int)
+    index = {tuple(int(x) for x in r): l for l, r in enumerate(R)}
+    chi = np.zeros((len(R) * nh, len(R) * nh), dtype=complex)
+    for jj, J in enumerate(model.hub_atoms):
+        for lp, rp in enumerate(R):
+            for l, r in enumerate(R):
+                d = index[tuple(int(x) for x in np.mod(np.array(r, dtype=int) - np.array(rp, dtype=int), n))]
+                chi[l * nh:(l + 1) * nh, lp * nh + jj] = cols[J][d * nh:(d + 1) * nh]
+    return chi
+
+
+def minus_q(model, iq):
+    """Index of -q (mod G) in the q mesh."""
+    n = np.array(model.qmesh, dtype=int)
+    i = np.rint(np.array(model.qpts[iq]) * n).astype(int)
+    j = np.mod(-i, n)
+    for jq, q in enumerate(model.qpts):
+        if np.array_equal(np.rint(np.array(q) * n).astype(int), j):
+            return jq
+    raise ValueError("-q is not on the mesh")
+
+
+def irreducible_q(model):
+    """(q indices to compute, partner[iq] = the computed q whose response gives iq: itself, or the
+    first of the pair {q, -q} whose conjugate it is)."""
+    partner = []
+    for iq in range(len(model.qpts)):
+        jq = minus_q(model, iq)
+        partner.append(min(iq, jq))
+    return sorted(set(partner)), partner
