@@ -16,11 +16,14 @@ Perturbed atoms (find_atpert):
 Column reconstruction (post-processing): the real-space response column of a Hubbard atom J that was
 not perturbed, chi_{(l,s),(0,J)} = (1/N_q) sum_q exp(i q.R_l) Delta^J_q n^s (Eqs. chi and
 occ_matrix_response_lp_1), is taken from its class representative J': the entry for (l, s) is the
-entry (l', s') of J' with the species of s, the distance of (l, s) from J (minimum image in the
-supercell of the q mesh) within dist_thr (6e-4 bohr), and the spin orientation of s relative to J.
-The orientation of an atom is the sign of Tr n^up - Tr n^down where that difference exceeds
-docc_thr, else 0.  The first such (l', s') in index order is taken.  The full matrix then follows
-from the lattice periodicity of the supercell: chi_{(l,s),(l'',J)} = chi_{(l - l'' mod n, s),(0,J)}.
+entry (l', s') of J' with the species of s and the spin orientation of s relative to J whose
+separation from J' matches that of (l, s) from J within dist_thr (6e-4 bohr): first as a vector
+modulo the supercell of the q mesh (exact for atoms that are images under a lattice translation,
+whatever the shape of the supercell), else, where no atom matches the vector, as the minimum-image
+distance.  The orientation of an atom is the sign of Tr n^up - Tr n^down where that difference
+exceeds docc_thr, else 0.  The first matching (l', s') in index order is taken.  The full matrix then
+follows from the lattice periodicity of the supercell: chi_{(l,s),(l'',J)} = chi_{(l - l'' mod n,
+s),(0,J)}.
 
 Time reversal (the +-q of the small group of q): for a ground state with real potentials and real
 Hubbard orbitals the response to exp(-i q.R) is the complex conjugate of the response to exp(i q.R),
@@ -89,12 +92,16 @@ def realspace_column(model, qcols):
     return col
 
 
-def _distance(model, ia, ja, Rl):
-    """Minimum-image distance in the supercell from atom ia of cell 0 to atom ja of cell Rl."""
+def _separation(model, ia, ja, Rl):
+    """Separation of atom ja of cell Rl from atom ia of cell 0, in supercell fractional coordinates."""
+    return (model.frac[ja] + np.asarray(Rl, dtype=float) - model.frac[ia]) / np.array(model.qmesh, dtype=float)
+
+
+def _length(model, f):
+    """Length (bohr) of the supercell fractional vector f taken to its minimum image."""
     n = np.array(model.qmesh, dtype=float)
-    d = (model.frac[ja] + Rl - model.frac[ia]) / n
-    d -= np.round(d)
-    return float(np.linalg.norm(d @ (model.cell * n[:, None])))
+    f = f - np.round(f)
+    return float(np.linalg.norm(f @ (model.cell * n[:, None])))
 
 
 def reconstruct_columns(model, cols, rep, orient, dist_thr=6e-4):
@@ -111,20 +118,15 @@ def reconstruct_columns(model, cols, rep, orient, dist_thr=6e-4):
         col = np.zeros_like(src)
         for l in range(len(R)):
             for s, ia in enumerate(model.hub_atoms):
-                d = _distance(model, J, ia, R[l])
+                v = _separation(model, J, ia, R[l])
+                d = _length(model, v)
                 o = orient[ia] * orient[J]
-                hit = None
-                for lp in range(len(R)):
-                    for sp, ib in enumerate(model.hub_atoms):
-                        if model.atom_species[ib] != model.atom_species[ia]:
-                            continue
-                        if orient[ib] * orient[Jp] != o:
-                            continue
-                        if abs(_distance(model, Jp, ib, R[lp]) - d) <= dist_thr:
-                            hit = lp * nh + sp
-                            break
-                    if hit is not None:
-                        break
+                cands = [(lp * nh + sp, _separation(model, Jp, ib, R[lp]))
+                         for lp in range(len(R)) for sp, ib in enumerate(model.hub_atoms)
+                         if model.atom_species[ib] == model.atom_species[ia] and orient[ib] * orient[Jp] == o]
+                hit = next((i for i, vp in cands if _length(model, vp - v) <= dist_thr), None)
+                if hit is None:
+                    hit = next((i for i, vp in cands if abs(_length(model, vp) - d) <= dist_thr), None)
                 if hit is None:
                     raise ValueError("no atom of the representative's column matches (%d, %d) of atom %d" % (l, s, J))
                 col[l * nh + s] = src[hit]

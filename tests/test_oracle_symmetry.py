@@ -81,6 +81,23 @@ def test_rebuilt_columns_equal_computed_ones(rocksalt):
             S.reconstruct_columns(m, rs, rep, orient, dist_thr=-1.0)
 
 
+def test_rebuilt_columns_in_an_elongated_supercell():
+    """On a 2 x 1 x 1 q mesh the supercell is no longer cubic: atoms at one distance from a site are
+    not all equivalent, and the distance alone picks a wrong entry (1.5 % off here); the separation
+    vector finds the translation image.  Gamma-only k (the L orbitals carry no occupation there), the
+    H columns."""
+    w = W.medium_small(ecut=6.0, grid=(16, 16, 16), kmesh=(1, 1, 1), qmesh=(2, 1, 1))
+    m = Model(w)
+    gs = G.scf(m, tol=1e-11)
+    tr = {J: [H.trace_column(m, R.solve_column(m, gs, iq, J, **TOL)["dn"]) for iq in range(2)] for J in (0, 1)}
+    _, rep = S.perturbed_atoms(m, gs, 1)
+    orient = S.orientations(m, gs)
+    rs = {0: S.realspace_column(m, tr[0]), 4: np.zeros(len(m.supercell_R()) * len(m.hub_atoms), dtype=complex)}
+    direct = S.realspace_column(m, tr[1])
+    got = S.reconstruct_columns(m, rs, rep, orient)[1]
+    assert np.abs(got - direct).max() < 1e-8 * np.abs(direct).max()
+
+
 def test_columns_to_matrix_matches_q_sum():
     """chi from the real-space columns (lattice periodicity of the supercell) equals the q-summed
     assembly, on a 3 x 1 x 1 q mesh with random columns (index conventions only)."""
