@@ -309,10 +309,43 @@ hp_status hp_set_hubbard(hp_ctx* ctx, const double* U, int nV, const hp_pairV* V
  * within d_min + 6e-4 bohr of it (the paper's dist_thr default, Appendix B); *nV is the capacity
  * of V on input and the number of pairs on output (all pairs are counted even when they do not fit;
  * HP_EINVAL then).  Any output pointer may be NULL (nV with V).  Needs every (q, J) column
- * (HP_ESTATE otherwise).  chi0 and chi are written even when one of them is singular or has a
+ * (HP_ESTATE otherwise), where a missing (q, J) is taken from (-q, J) by conjugation and the
+ * columns of an atom that was not perturbed are rebuilt from its class (hp_perturbed_atoms).  chi0 and chi are written even when one of them is singular or has a
  * 1-norm condition number above 1e10; U, V and hub are then not written and the call returns
  * HP_ESINGULAR. */
 hp_status hp_hubbard(hp_ctx* ctx, double* chi0, double* chi, double* hub, double* U, hp_pairV* V, int* nV);
+
+/* Symmetry reductions (Sec. 2.4 "Symmetry"; Sec. 3.2, the linear-response step and its
+ * post-processing; the hp.x inputs find_atpert, docc_thr, dist_thr and skip_equivalence_q).
+ *
+ * hp_perturbed_atoms: after a ground state, sorts the Hubbard atoms into classes and keeps them in
+ * the context.  find_atpert 1: atoms of one species whose spin-summed occupations Tr n^I (Eq.
+ * occ_matrix_0 with the active Hubbard projectors; twice the channel for nspin = 1) differ by less
+ * than docc_thr (the paper's default 5e-5) form a class, whatever the sign of their moments;
+ * 2: one class per species; 4: every atom alone (this clears the classes).  The first atom of each
+ * class in atom order represents it.  Writes *npert and atoms[0 .. *npert) (the representatives,
+ * atom indices; capacity nhub_atoms), rep[i] (the representative of the i-th Hubbard atom in
+ * hp_hubbard_atoms order; may be NULL) and trace[2 i + s] (Tr n^{I s}, s < nspin; may be NULL).
+ * With classes kept, hp_hubbard rebuilds the columns of every atom that does not represent its class
+ * (whether or not its responses were computed): the entry
+ * of cell l, atom s of the real-space column (0, J), chi_{(l,s),(0,J)} = (1/N_q) sum_q
+ * exp(i q.R_l) Delta^J_q n^s, is the entry (l', s') of the representative's column with the species
+ * of s and the spin orientation of s relative to J (orientation: the sign of Tr n^up - Tr n^down
+ * where that exceeds docc_thr, else 0) whose separation from J' matches that of (l, s) from J within
+ * dist_thr bohr (the paper's default 6e-4): as a vector modulo the q-mesh supercell, else, where no
+ * atom matches the vector, as the minimum-image distance; the first such (l', s') in index order.
+ * Errors: HP_ESTATE without a ground state; HP_EINVAL for another find_atpert, docc_thr <= 0,
+ * dist_thr < 0 or a NULL npert/atoms.  A new ground state clears the classes. */
+hp_status hp_perturbed_atoms(hp_ctx* ctx, int find_atpert, double docc_thr, double dist_thr, int* npert, int* atoms,
+                             int* rep, double* trace);
+
+/* hp_irreducible_q: the q points to compute under time reversal (of the small group of q only the
+ * +-q pairs; the ground states here have real potentials and real Hubbard orbitals, so
+ * Delta_{-q} n = conj(Delta_q n)): of each pair {q, -q + G} of the q mesh the first in mesh order.
+ * Writes *nirr and iq[0 .. *nirr) (capacity nq), and partner[iq] for every q of the mesh (itself, or
+ * the computed q whose conjugate response it takes; may be NULL).  hp_hubbard fills a missing (q, J)
+ * column from (-q, J) this way.  Errors: HP_EINVAL for a NULL ctx, nirr or iq. */
+hp_status hp_irreducible_q(const hp_ctx* ctx, int* nirr, int* iq, int* partner);
 
 /* Several independent cells at once (the batching form; the paper's code runs one system per job,
  * so there is no counterpart there).  For every context cells[0 .. ncells-1], each set up with its

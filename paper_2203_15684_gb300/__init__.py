@@ -83,7 +83,7 @@ SYMBOLS = ["hp_default_options", "hp_setup", "hp_query_sizes", "hp_sphere", "hp_
            "hp_destroy", "hp_selftest_fft_host", "hp_selftest_eigh", "hp_get_wavefunctions", "hp_profile_begin",
            "hp_profile_end", "hp_launch_count", "hp_apply_h_noalloc", "hp_set_precision", "hp_selftest_convert",
            "hp_batch_run", "hp_alloc_count", "hp_sphere_kq", "hp_apply_sternheimer", "hp_selftest_xc",
-           "hp_selftest_tc", "hp_set_hubbard", "hp_bare_levels"]
+           "hp_selftest_tc", "hp_set_hubbard", "hp_bare_levels", "hp_perturbed_atoms", "hp_irreducible_q"]
 
 
 def lib():
@@ -130,6 +130,8 @@ def lib():
     L.hp_selftest_tc.argtypes = [I, I, I, P(C.c_float), P(C.c_float), P(C.c_float), I, D]
     L.hp_set_hubbard.argtypes = [V, P(D), I, P(PairV)]
     L.hp_bare_levels.argtypes = [V, I, P(D)]
+    L.hp_perturbed_atoms.argtypes = [V, I, D, D, P(I), P(I), P(I), P(D)]
+    L.hp_irreducible_q.argtypes = [V, P(I), P(I), P(I)]
     for n in SYMBOLS:
         f = getattr(L, n)
         if n in ("hp_launch_count", "hp_alloc_count"):
@@ -477,6 +479,28 @@ class Context:
         e = np.zeros(int(nlev))
         self._check(lib().hp_bare_levels(self._ptr, int(nlev), _dptr(e)), "hp_bare_levels")
         return e
+
+    def perturbed_atoms(self, find_atpert=1, docc_thr=5e-5, dist_thr=6e-4):
+        """(atoms to perturb, representative atom of each Hubbard atom, Tr n^{I s} (nhub_atoms, 2));
+        the classes stay in the context for hubbard()'s column reconstruction."""
+        nh = self.query_sizes()["nhub_atoms"]
+        npert = C.c_int()
+        atoms = np.zeros(nh, dtype=np.int32)
+        rep = np.zeros(nh, dtype=np.int32)
+        tr = np.zeros((nh, 2))
+        self._check(lib().hp_perturbed_atoms(self._ptr, int(find_atpert), float(docc_thr), float(dist_thr),
+                                             C.byref(npert), _iptr(atoms), _iptr(rep), _dptr(tr)),
+                    "hp_perturbed_atoms")
+        return [int(a) for a in atoms[:npert.value]], [int(r) for r in rep], tr
+
+    def irreducible_q(self):
+        """(q indices to compute under time reversal, partner q of every q)."""
+        nq = self.query_sizes()["nq"]
+        n = C.c_int()
+        iq = np.zeros(nq, dtype=np.int32)
+        partner = np.zeros(nq, dtype=np.int32)
+        self._check(lib().hp_irreducible_q(self._ptr, C.byref(n), _iptr(iq), _iptr(partner)), "hp_irreducible_q")
+        return [int(x) for x in iq[:n.value]], [int(x) for x in partner]
 
     def sphere_kq(self, iq, ik):
         """Miller indices (npw, 3) of the k+q sphere in the response's coefficient order."""

@@ -812,6 +812,8 @@ void hp::invalidate_response(hp_ctx* c) {
     c->resp_ready = false;
     c->qc.iq = -1;
     c->cols.clear();
+    c->hub_rep.clear();  // the classes follow the ground state's occupations
+    c->hub_orient.clear();
     for (QFam& F : c->qfam) F.built = false;  // the states at k+q follow the ground state
 }
 
@@ -1986,6 +1988,204 @@ static std::vector<Neighbour> nearest_hubbard(const hp_ctx* c, int s) {
     return out;
 }
 
+// ------------------------------------------------------------------------------------------------
+// symmetry reductions: classes of Hubbard atoms, time-reversal q pairs, rebuilt columns
+// ------------------------------------------------------------------------------------------------
+// index of -q (mod G) in the q mesh
+static int minus_q(const hp_ctx* c, int iq) {
+    const int n0 = c->qmesh[0], n1 = c->qmesh[1], n2 = c->qmesh[2];
+    const int i0 = iq / (n1 * n2), i1 = (iq / n2) % n1, i2 = iq % n2;
+    return (((n0 - i0) % n0) * n1 + (n1 - i1) % n1) * n2 + (n2 - i2) % n2;
+}
+
+extern "C" hp_status hp_irreducible_q(const hp_ctx* c, int* nirr, int* iq_out, int* partner) {
+    if (!c || !nirr || !iq_out) return HP_EINVAL;
+    int m = 0;
+    for (int iq = 0; iq < c->nq; ++iq) {
+        const int p = std::min(iq, minus_q(c, iq));
+        if (partner) partner[iq] = p;
+        if (p == iq) iq_out[m++] = iq;
+    }
+    *nirr = m;
+    return HP_OK;
+}
+
+// separation of Hubbard atom b of cell (l1, l2, l3) from Hubbard atom a of cell 0, in fractional
+// coordinates of the q-mesh supercell
+static void supercell_separation(const hp_ctx* c, int a, int b, const int R[3], double f[3]) {
+    const int ia = c->hub_atoms[a], ja = c->hub_atoms[b];
+    for (int i = 0; i < 3; ++i) f[i] = (c->frac[3 * ja + i] + R[i] - c->frac[3 * ia + i]) / c->qmesh[i];
+}
+
+// length (bohr) of a supercell fractional vector taken to its minimum image
+static double supercell_length(const hp_ctx* c, const double f[3]) {
+    double x[3] = {0, 0, 0};
+    for (int i = 0; i < 3; ++i) {
+        const double d = f[i] - std::nearbyint(f[i]);
+        for (int j = 0; j < 3; ++j) x[j] += d * c->qmesh[i] * c->cell[3 * i + j];
+    }
+    return std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+}
+
+extern "C" hp_status hp_perturbed_atoms(hp_ctx* c, int find_atpert, double docc_thr, double dist_thr, int* npert,
+                                        int* atoms, int* rep, double* trace) {
+    if (!c) return HP_EINVAL;
+    if (!c->have_gs) return fail(c, HP_ESTATE, "hp_perturbed_atoms: no ground state");
+    if ((find_atpert != 1 && find_atpert != 2 && find_atpert != 4) || !(docc_thr > 0) || !(dist_thr >= 0) || !npert ||
+        !atoms)
+        return fail(c, HP_EINVAL, "hp_perturbed_atoms: find_atpert 1, 2 or 4, docc_thr > 0, dist_thr >= 0, outputs given");
+    const int nh = (int)c->hub_atoms.size(), nspin = c->nspin, nk = c->nk, nocc = c->nocc;
+    // Tr n^{I s} = (1/N_k) sum_k sum_v sum_m |<phi^I_m,k|u_vk>|^2 (Eq. occ_matrix_0)
+    BandList& L = c->L3;
+    list_clear(L);
+    for (int sp = 0; sp < nspin; ++sp)
+        for (int k = 0; k < nk; ++k)
+            for (int v = 0; v < nocc; ++v) list_add(L, (sp * nk + k) * c->nbnd + v, k, sp, 0.0);
+    hp_status s = upload_list(c, L);
+    if (s != HP_OK) return s;
+    double2* P;
+    CK(dalloc(c, &P, (size_t)L.nb * kPStride));
+    ProjMat F{c->d_phi_k, 0, (long long)c->nhub * c->ld, c->nhub, 0, nullptr};
+    s = project(c, c->kset, L, F, c->d_psi, P);
+    std::vector<double2> h((size_t)L.nb * kPStride);
+    if (s == HP_OK) {
+        cudaError_t e = d2h(h.data(), P, h.size(), c->st);
+        if (e != cudaSuccess) s = cuda_fail(c, e, "hp_perturbed_atoms");
+    }
+    dfree(c, P);
+    if (s != HP_OK) return s;
+    std::vector<double> tr((size_t)nh * 2, 0.0);
+    for (int b = 0; b < L.nb; ++b)
+        for (int a = 0; a < nh; ++a)
+            for (int m = 0; m < c->hub_mdim[a]; ++m) {
+                const double2 p = h[(size_t)b * kPStride + c->hub_off[a] + m];
+                tr[2 * a + L.spin[b]] += (p.x * p.x + p.y * p.y) / nk;
+            }
+    const double f = nspin == 1 ? 2.0 : 1.0;
+    std::vector<int> rp(nh);
+    for (int a = 0; a < nh; ++a) {
+        rp[a] = a;
+        if (find_atpert == 4) continue;
+        const double ta = f * (tr[2 * a] + tr[2 * a + 1]);
+        for (int b = 0; b < a; ++b) {
+            if (rp[b] != b || c->atom_species[c->hub_atoms[b]] != c->atom_species[c->hub_atoms[a]]) continue;
+            const double tb = f * (tr[2 * b] + tr[2 * b + 1]);
+            if (find_atpert == 2 || std::fabs(ta - tb) < docc_thr) {
+                rp[a] = b;
+                break;
+            }
+        }
+    }
+    int m = 0;
+    for (int a = 0; a < nh; ++a) {
+        if (rp[a] == a) atoms[m++] = c->hub_atoms[a];
+        if (rep) rep[a] = c->hub_atoms[rp[a]];
+        if (trace)
+            for (int sp = 0; sp < nspin; ++sp) trace[2 * a + sp] = tr[2 * a + sp];
+    }
+    *npert = m;
+    c->hub_rep.clear();
+    c->hub_orient.clear();
+    if (find_atpert != 4) {
+        c->hub_rep = rp;
+        c->hub_orient.assign(nh, 0);
+        for (int a = 0; a < nh; ++a) {
+            const double d = nspin == 2 ? tr[2 * a] - tr[2 * a + 1] : 0.0;
+            c->hub_orient[a] = std::fabs(d) <= docc_thr ? 0 : (d > 0 ? 1 : -1);
+        }
+        c->dist_thr = dist_thr;
+    }
+    return HP_OK;
+}
+
+// cell l of the q-mesh supercell as integer coordinates
+static void cell_of(const hp_ctx* c, int l, int R[3]) {
+    R[0] = l / (c->qmesh[1] * c->qmesh[2]);
+    R[1] = (l / c->qmesh[2]) % c->qmesh[1];
+    R[2] = l % c->qmesh[2];
+}
+
+// Column (q, J) traces of every q for Hubbard atom jj, rebuilt from its class representative: the
+// representative's real-space column chi_{(l,s),(0,J')} = (1/N_q) sum_q exp(2 pi i q.R_l) x_q[s],
+// the distance rule, and back to q: x_q[s] = sum_l exp(-2 pi i q.R_l) chi_{(l,s),(0,J)}.
+// cols: [q][J][s] complex, the representative's entries filled.
+static hp_status rebuild_atom(hp_ctx* c, int jj, std::vector<double2>& cols) {
+    const int nh = (int)c->hub_atoms.size(), nq = c->nq;
+    const int jr = c->hub_rep[jj];
+    const double PI2 = 6.28318530717958647692;
+    auto phase = [&](int iq, int l) {
+        int Q[3], R[3];
+        cell_of(c, iq, Q);
+        cell_of(c, l, R);
+        double d = 0.0;
+        for (int i = 0; i < 3; ++i) d += (double)Q[i] / c->qmesh[i] * R[i];
+        return PI2 * d;
+    };
+    std::vector<double2> rs((size_t)nq * nh, cmk(0.0, 0.0));  // representative, real space [l][s]
+    for (int l = 0; l < nq; ++l)
+        for (int s = 0; s < nh; ++s) {
+            double re = 0.0, im = 0.0;
+            for (int iq = 0; iq < nq; ++iq) {
+                const double2 x = cols[((size_t)iq * nh + jr) * nh + s];
+                const double a = phase(iq, l);
+                re += std::cos(a) * x.x - std::sin(a) * x.y;
+                im += std::cos(a) * x.y + std::sin(a) * x.x;
+            }
+            rs[(size_t)l * nh + s] = cmk(re / nq, im / nq);
+        }
+    // the entry of (l, s) is that of the first (l', s') of the species of s and the orientation of s
+    // relative to J whose separation from J' matches: as a vector modulo the supercell (translation
+    // images), else as a minimum-image distance
+    std::vector<double2> rj((size_t)nq * nh);
+    for (int l = 0; l < nq; ++l)
+        for (int s = 0; s < nh; ++s) {
+            int R[3];
+            cell_of(c, l, R);
+            double v[3];
+            supercell_separation(c, jj, s, R, v);
+            const double d = supercell_length(c, v);
+            const int o = c->hub_orient[s] * c->hub_orient[jj];
+            int hit = -1;
+            for (int pass = 0; pass < 2 && hit < 0; ++pass)
+                for (int lp = 0; lp < nq && hit < 0; ++lp) {
+                    int Rp[3];
+                    cell_of(c, lp, Rp);
+                    for (int sp = 0; sp < nh; ++sp) {
+                        if (c->atom_species[c->hub_atoms[sp]] != c->atom_species[c->hub_atoms[s]]) continue;
+                        if (c->hub_orient[sp] * c->hub_orient[jr] != o) continue;
+                        double vp[3];
+                        supercell_separation(c, jr, sp, Rp, vp);
+                        const double dv[3] = {vp[0] - v[0], vp[1] - v[1], vp[2] - v[2]};
+                        const bool match = pass == 0 ? supercell_length(c, dv) <= c->dist_thr
+                                                     : std::fabs(supercell_length(c, vp) - d) <= c->dist_thr;
+                        if (match) {
+                            hit = lp * nh + sp;
+                            break;
+                        }
+                    }
+                }
+            if (hit < 0) {
+                char msg[200];
+                snprintf(msg, sizeof(msg), "hp_hubbard: no entry of atom %d's column matches cell %d, atom %d of atom %d's",
+                         c->hub_atoms[jr], l, c->hub_atoms[s], c->hub_atoms[jj]);
+                return fail(c, HP_ESTATE, msg);
+            }
+            rj[(size_t)l * nh + s] = rs[hit];
+        }
+    for (int iq = 0; iq < nq; ++iq)
+        for (int s = 0; s < nh; ++s) {
+            double re = 0.0, im = 0.0;
+            for (int l = 0; l < nq; ++l) {
+                const double2 x = rj[(size_t)l * nh + s];
+                const double a = -phase(iq, l);
+                re += std::cos(a) * x.x - std::sin(a) * x.y;
+                im += std::cos(a) * x.y + std::sin(a) * x.x;
+            }
+            cols[((size_t)iq * nh + jj) * nh + s] = cmk(re, im);
+        }
+    return HP_OK;
+}
+
 extern "C" hp_status hp_hubbard(hp_ctx* c, double* chi0_out, double* chi_out, double* hub_out, double* U_out,
                                 hp_pairV* V_out, int* nV) {
     if (!c) return HP_EINVAL;
@@ -1993,15 +2193,37 @@ extern "C" hp_status hp_hubbard(hp_ctx* c, double* chi0_out, double* chi_out, do
     const int nh = (int)c->hub_atoms.size(), nq = c->nq;
     const int n = nh * nq;
     std::vector<double2> cols0((size_t)nq * nh * nh), cols((size_t)nq * nh * nh);
+    std::vector<char> have((size_t)nq * nh, 0);
     for (int iq = 0; iq < nq; ++iq)
         for (int jj = 0; jj < nh; ++jj) {
+            // the column itself, else the conjugate of (-q, J) (time reversal)
             auto it = c->cols.find({iq, c->hub_atoms[jj]});
-            if (it == c->cols.end()) return fail(c, HP_ESTATE, "hp_hubbard: a (q, J) response is missing");
+            double cj = 1.0;
+            if (it == c->cols.end()) {
+                it = c->cols.find({minus_q(c, iq), c->hub_atoms[jj]});
+                cj = -1.0;
+            }
+            if (it == c->cols.end()) continue;
+            have[(size_t)iq * nh + jj] = 1;
             for (int s = 0; s < nh; ++s) {
-                cols0[((size_t)iq * nh + jj) * nh + s] = cmk(it->second.tr0[2 * s], it->second.tr0[2 * s + 1]);
-                cols[((size_t)iq * nh + jj) * nh + s] = cmk(it->second.tr[2 * s], it->second.tr[2 * s + 1]);
+                cols0[((size_t)iq * nh + jj) * nh + s] = cmk(it->second.tr0[2 * s], cj * it->second.tr0[2 * s + 1]);
+                cols[((size_t)iq * nh + jj) * nh + s] = cmk(it->second.tr[2 * s], cj * it->second.tr[2 * s + 1]);
             }
         }
+    auto complete = [&](int jj) {
+        for (int iq = 0; iq < nq; ++iq)
+            if (!have[(size_t)iq * nh + jj]) return false;
+        return true;
+    };
+    // with classes kept, every atom that does not represent its class takes the rebuilt columns
+    for (int jj = 0; jj < nh; ++jj) {
+        const bool rebuilt = !c->hub_rep.empty() && c->hub_rep[jj] != jj;
+        if (!rebuilt && complete(jj)) continue;
+        if (!rebuilt || !complete(c->hub_rep[jj])) return fail(c, HP_ESTATE, "hp_hubbard: a (q, J) response is missing");
+        hp_status s = rebuild_atom(c, jj, cols0);
+        if (s == HP_OK) s = rebuild_atom(c, jj, cols);
+        if (s != HP_OK) return s;
+    }
     std::vector<double> qf(3 * nq), Rl(3 * nq);
     for (int i1 = 0, i = 0; i1 < c->qmesh[0]; ++i1)
         for (int i2 = 0; i2 < c->qmesh[1]; ++i2)

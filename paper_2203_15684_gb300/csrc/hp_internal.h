@@ -526,6 +526,10 @@ struct hp_ctx {
     double* d_partial = nullptr;
     // results
     std::map<std::pair<int, int>, hp::RespCols> cols;
+    // symmetry classes of the Hubbard atoms (hp_perturbed_atoms; empty: every atom is perturbed)
+    std::vector<int> hub_rep;          // per Hubbard atom: index (in hub_atoms) of its representative
+    std::vector<int> hub_orient;       // per Hubbard atom: +1 / -1 / 0 spin orientation
+    double dist_thr = 6e-4;            // bohr, distance tolerance of the column reconstruction
     // scratch (device)
     double2* d_grid = nullptr;         // grid_cap x nr
     int grid_cap = 0;
