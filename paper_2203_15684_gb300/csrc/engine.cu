@@ -1132,7 +1132,8 @@ hp_status prepare_resp(hp_ctx* c) {
         CK(dalloc(c, &c->d_hist_dx[i], (size_t)nspin * nr));
         CK(dalloc(c, &c->d_hist_df[i], (size_t)nspin * nr));
     }
-    if (!c->d_hist_ptrs) CK(dalloc(c, &c->d_hist_ptrs, 64));
+    if (!c->d_hist_ptrs) CK(dalloc(c, &c->d_hist_ptrs, 32 + 2 * kMaxDots));
+    if (!c->d_partials) CK(dalloc(c, &c->d_partials, (size_t)kMaxDots * 256));
     c->resp_ready = true;
     return HP_OK;
 }
@@ -1896,20 +1897,21 @@ extern "C" hp_status hp_response(hp_ctx* c, int iq, int atom, double* dn0_out, d
         CK(cudaMemcpyAsync(xprev, c->d_dv, sizeof(double2) * ndv, cudaMemcpyDeviceToDevice, c->st));
         CK(cudaMemcpyAsync(fprev, c->d_dvout, sizeof(double2) * ndv, cudaMemcpyDeviceToDevice, c->st));
         const int m = nhist;
-        // overlaps <dF_i|dF_j> and <dF_k|F> into d_small[16 + i*(m+1) + j]
-        for (int i = 0; i < m; ++i) {
-            for (int j = 0; j <= m; ++j) {
-                const double2* bj = (j < m) ? c->d_hist_df[j] : c->d_dvout;
-                CK(k_vec_dot(c->d_hist_df[i], bj, ndv, c->d_small + 16 + i * (m + 1) + j, c->d_partial, c->st));
-            }
-        }
-        CK(k_broyden_coef(c->d_small + 16, m, m + 1, 0.01, c->d_small + 8, c->st));
-        std::vector<const double2*> ptrs(2 * (nmix + 1), nullptr);
+        // overlaps <dF_i|dF_j> and <dF_k|F> into d_small[16 + i*(m+1) + j], in one batched launch;
+        // pointer table: [0, nmix] dX, [nmix + 1, 2 nmix + 1] dF, from 32 the dot operands
+        std::vector<const double2*> ptrs(32 + 2 * kMaxDots, nullptr);
         for (int i = 0; i < m; ++i) {
             ptrs[i] = c->d_hist_dx[i];
             ptrs[nmix + 1 + i] = c->d_hist_df[i];
+            for (int j = 0; j <= m; ++j) {
+                ptrs[32 + i * (m + 1) + j] = c->d_hist_df[i];
+                ptrs[32 + kMaxDots + i * (m + 1) + j] = (j < m) ? c->d_hist_df[j] : c->d_dvout;
+            }
         }
         CK(h2d((const double2**)c->d_hist_ptrs, ptrs.data(), ptrs.size(), c->st));
+        CK(k_vec_dots((const double2* const*)(c->d_hist_ptrs + 32), (const double2* const*)(c->d_hist_ptrs + 32 + kMaxDots),
+                      m * (m + 1), ndv, c->d_small + 16, c->d_partials, c->st));
+        CK(k_broyden_coef(c->d_small + 16, m, m + 1, 0.01, c->d_small + 8, c->st));
         CK(k_broyden_apply(c->d_dv, c->d_dvout, (const double2* const*)c->d_hist_ptrs,
                            (const double2* const*)(c->d_hist_ptrs + nmix + 1), c->d_small + 8, m, c->opt.alpha_mix, ndv,
                            c->st));

@@ -285,6 +285,11 @@ cudaError_t k_dn_blocks(const double2* M, int nspin, int nhub, int nhub_atoms, c
 cudaError_t k_dn_traces(const double2* dn, int nh, int nspin, int mmax, double f, double2* tr, cudaStream_t st);
 cudaError_t k_vec_dot(const double2* a, const double2* b, long long n, double* out, double* partial,
                       cudaStream_t st);
+// out[p] = Re <A[p] | B[p]> for p < npairs (device pointer arrays), each as k_vec_dot computes it;
+// partials: npairs x 256 doubles
+cudaError_t k_vec_dots(const double2* const* A, const double2* const* B, int npairs, long long n, double* out,
+                       double* partials, cudaStream_t st);
+constexpr int kMaxDots = 72;  // nmix (m <= 8) x (m + 1) overlaps of a Broyden step
 cudaError_t k_vec_axpy(double2* y, const double2* x, double a, long long n, cudaStream_t st);
 cudaError_t k_vec_axpy(float2* y, const float2* x, double a, long long n, cudaStream_t st);
 cudaError_t k_vec_sub(double2* out, const double2* a, const double2* b, long long n, cudaStream_t st);
@@ -524,6 +529,7 @@ struct hp_ctx {
     double2** d_hist_ptrs = nullptr;
     double* d_small = nullptr;         // small scalars for reductions / Broyden
     double* d_partial = nullptr;
+    double* d_partials = nullptr;      // kMaxDots x 256 partial sums of the batched dot products
     // results
     std::map<std::pair<int, int>, hp::RespCols> cols;
     // symmetry classes of the Hubbard atoms (hp_perturbed_atoms; empty: every atom is perturbed)

@@ -1475,6 +1475,44 @@ cudaError_t k_vec_dot(const double2* a, const double2* b, long long n, double* o
     return cudaGetLastError();
 }
 
+// npairs dot products Re<A_p|B_p> at once, each with the partition and reduction order of k_vec_dot
+// (so each result equals k_vec_dot's bit for bit): block (b, p) sums the slice b of pair p.
+__global__ void vec_dots_kernel(const double2* const* __restrict__ A, const double2* const* __restrict__ B, long long n,
+                                double* __restrict__ partial) {
+    __shared__ double sh[32];
+    const int p = blockIdx.y;
+    const double2* __restrict__ a = A[p];
+    const double2* __restrict__ b = B[p];
+    double s = 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double2 x = a[i], y = b[i];
+        s += x.x * y.x + x.y * y.y;
+    }
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) partial[(long long)p * gridDim.x + blockIdx.x] = s;
+}
+
+__global__ void sums_reduce_kernel(const double* __restrict__ partial, int nparts, double* __restrict__ out) {
+    __shared__ double sh[32];
+    const double* part = partial + (long long)blockIdx.x * nparts;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += part[i];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+
+cudaError_t k_vec_dots(const double2* const* A, const double2* const* B, int npairs, long long n, double* out,
+                       double* partials, cudaStream_t st) {
+    if (npairs <= 0) return cudaSuccess;
+    vec_dots_kernel<<<dim3(kRedBlocks, npairs), 256, 0, st>>>(A, B, n, partials);
+    HP_LAUNCHED();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    sums_reduce_kernel<<<npairs, 256, 0, st>>>(partials, kRedBlocks, out);
+    HP_LAUNCHED();
+    return cudaGetLastError();
+}
+
 cudaError_t k_sum_reduce(const double* partial, int nparts, double* out, cudaStream_t st) {
     sum_reduce_kernel<<<1, 256, 0, st>>>(partial, nparts, out);
     HP_LAUNCHED();
