@@ -79,6 +79,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--band-batch", type=int, default=0, help="grids per FFT batch (0 = automatic)")
     p.add_argument("--workload", default="precision", choices=sorted(WORKLOADS))
+    p.add_argument("--tc-accuracy", action="store_true",
+                   help="print the tensor-core building block's accuracy table (hp_selftest_tc) and exit")
     p.add_argument("--cg-adapt", type=float, default=None,
                    help="CG threshold factor for outer iterations after the first (library default if omitted)")
     a = p.parse_args()
@@ -382,12 +384,14 @@ def batch_arm(args):
     import paper_2203_15684_gb300 as P
     import workloads as W
 
-    cells, ctxs, skipped = W.batch_cells(), [], []
+    cells, ctxs, skipped, bare_gap = W.batch_cells(), [], [], {}
     for w in cells:
         stream = torch.cuda.Stream()
         ctx = P.Context.from_workload(w, cuda_stream=stream.cuda_stream, precision=1)
+        b, gap = P.batch_band_choice(ctx, w)
+        bare_gap[w["name"]] = gap
+        nelec = 2.0 * b
         try:
-            nelec = P.batch_electron_count(ctx, w)
             ctx.ground_state(nelec, 1)
         except P.HPError as e:
             skipped.append("%s: %s" % (w["name"], str(e)[:200]))
@@ -430,6 +434,7 @@ def batch_arm(args):
             "config": {"workload": WORKLOADS["batch"], "cells": n, "skipped": skipped,
                        "step": "one batch: every (q, J) response and chi/U/V of every cell, ground states before timing",
                        "nelec": {w["name"]: e for w, _, _, e in ctxs},
+                       "bare_gap_ha": bare_gap,
                        "one_after_another_cells_per_hour": n * 3600.0 / ta,
                        "speedup_batch_vs_one_after_another": ta / tb},
             "gpu_launches": P.launch_count() - l0}
@@ -561,8 +566,42 @@ def golden_check(eng):
     return out
 
 
+def tc_accuracy():
+    """Accuracy of the tcgen05 kind::tf32 building block (three-product TF32 split, hp_selftest_tc)
+    on D = A B^T, A (128 x K), B (16 x K) from PCG64 seed K, normal or absolute-normal entries, in four
+    modes (3 or 4 products, with or without draining the TMEM accumulator every 32 values of K):
+    max |D - D_exact| / sqrt(sum_k (a b)^2) and its signed mean, beside the same sum taken
+    sequentially in FP32."""
+    import numpy as np
+
+    import paper_2203_15684_gb300 as P
+
+    out = {}
+    for kind in ("normal", "positive"):
+        for K in (32, 256, 2048):
+            rng = np.random.default_rng(K)
+            A = rng.standard_normal((128, K)).astype(np.float32)
+            B = rng.standard_normal((16, K)).astype(np.float32)
+            if kind == "positive":
+                A, B = np.abs(A), np.abs(B)
+            ref = A.astype(np.float64) @ B.astype(np.float64).T
+            scale = np.sqrt((A.astype(np.float64) ** 2) @ (B.astype(np.float64) ** 2).T)
+            seq = np.cumsum((A[:, None, :] * B[None, :, :]).astype(np.float32), axis=2, dtype=np.float32)[:, :, -1]
+            row = {"fp32_seq": float(np.abs(seq - ref).max() / scale.max()),
+                   "fp32_seq_mean_signed": float(((seq - ref) / scale).mean())}
+            for mode, name in ((0, "3"), (2, "4"), (4, "3drain"), (6, "4drain")):
+                e = (P.selftest_tc(A, B, four=bool(mode & 2), drain=bool(mode & 4)) - ref) / scale
+                row[name] = float(np.abs(e).max())
+                row[name + "_mean_signed"] = float(e.mean())
+            out["%s_K%d" % (kind, K)] = row
+    print(json.dumps(out, indent=1))
+
+
 def main():
     args = parse()
+    if args.tc_accuracy:
+        tc_accuracy()
+        return
     if args.workload == "batch":
         if args.impl == "reference":
             print(json.dumps({"impl": "reference", "unavailable": "the batch workload has no oracle arm"}))

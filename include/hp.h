@@ -219,11 +219,12 @@ hp_status hp_set_ground_state(hp_ctx* ctx, int nspin, double nelec, const double
                               const double* rho, const double* eps, const double* psi);
 
 /* Lowest nlev (1 .. 100) eigenvalues (Ha, ascending) of the bare Hamiltonian T + V_loc + V_NL (no
- * Hxc potential, no Hubbard term) at the first point of the k mesh (k = 0 for the Gamma-centred
+ * Hxc potential, no Hubbard term) at point ik of the k mesh (ik = 0: k = 0 for the Gamma-centred
  * meshes).  No counterpart in the paper: it serves the electron-count rule of the batch of
- * synthetic cells (the occupied band count is chosen at the largest gap of this spectrum).
- * Errors: HP_EINVAL, HP_ENOTCONV, HP_ECUDA. */
-hp_status hp_bare_levels(hp_ctx* ctx, int nlev, double* eps);
+ * synthetic cells (the occupied band count is chosen at the largest gap of this spectrum over the
+ * k mesh).  Errors: HP_EINVAL (ik outside the mesh, nlev outside 1 .. 100 or above the plane-wave
+ * count less 6), HP_ENOTCONV, HP_ECUDA. */
+hp_status hp_bare_levels(hp_ctx* ctx, int ik, int nlev, double* eps);
 
 /* Reads back the ground state: any pointer may be NULL.  eps: nspin x nk x nocc; rho, vhxc:
  * nspin x nr.  Errors: HP_ESTATE before a ground state. */

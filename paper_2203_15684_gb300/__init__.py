@@ -129,7 +129,7 @@ def lib():
     L.hp_selftest_xc.argtypes = [I, I, P(D), P(D), P(D)]
     L.hp_selftest_tc.argtypes = [I, I, I, P(C.c_float), P(C.c_float), P(C.c_float), I, D]
     L.hp_set_hubbard.argtypes = [V, P(D), I, P(PairV)]
-    L.hp_bare_levels.argtypes = [V, I, P(D)]
+    L.hp_bare_levels.argtypes = [V, I, I, P(D)]
     L.hp_perturbed_atoms.argtypes = [V, I, D, D, P(I), P(I), P(I), P(D)]
     L.hp_irreducible_q.argtypes = [V, P(I), P(I), P(I)]
     for n in SYMBOLS:
@@ -474,10 +474,10 @@ class Context:
                 arr[i].R[d] = int(R[d])
         self._check(lib().hp_set_hubbard(self._ptr, u, len(pairs), arr), "hp_set_hubbard")
 
-    def bare_levels(self, nlev):
-        """Lowest nlev eigenvalues of T + V_loc + V_NL at k = 0 (hp_bare_levels)."""
+    def bare_levels(self, nlev, ik=0):
+        """Lowest nlev eigenvalues of T + V_loc + V_NL at mesh point ik (hp_bare_levels)."""
         e = np.zeros(int(nlev))
-        self._check(lib().hp_bare_levels(self._ptr, int(nlev), _dptr(e)), "hp_bare_levels")
+        self._check(lib().hp_bare_levels(self._ptr, int(ik), int(nlev), _dptr(e)), "hp_bare_levels")
         return e
 
     def perturbed_atoms(self, find_atpert=1, docc_thr=5e-5, dist_thr=6e-4):
@@ -521,17 +521,24 @@ class Context:
         return out
 
 
-def batch_electron_count(ctx, w):
-    """Occupied bands of a synthetic batch cell (nspin = 1): the band count b in
-    [n_H + n_L, 5 n_H + 3 n_L] with the largest gap eps_b - eps_(b-1) of the bare Hamiltonian's
-    spectrum at k = 0 (computed by the library); returns nelec = 2 b."""
+def batch_band_choice(ctx, w):
+    """(b, gap): the band count b in [n_H + n_L, 5 n_H + 3 n_L] of a synthetic batch cell (nspin = 1)
+    with the largest gap min_k eps_b(k) - max_k eps_(b-1)(k) of the bare Hamiltonian's spectrum over
+    the k mesh (computed by the library), and that gap in Ha (negative: no band count of the range
+    is gapped)."""
     kinds = [int(s) for s, _ in w["atoms"]]
     nH = sum(1 for k in kinds if k == 0)
     nL = len(kinds) - nH
     lo, hi = nH + nL, 5 * nH + 3 * nL
-    e = ctx.bare_levels(hi + 1)
-    b = max(range(lo, hi + 1), key=lambda n: e[n] - e[n - 1])
-    return 2.0 * b
+    e = np.array([ctx.bare_levels(hi + 1, ik) for ik in range(ctx.query_sizes()["nk"])])
+    gap = {n: float(e[:, n].min() - e[:, n - 1].max()) for n in range(lo, hi + 1)}
+    b = max(gap, key=gap.get)
+    return b, gap[b]
+
+
+def batch_electron_count(ctx, w):
+    """nelec = 2 b for the band count of batch_band_choice."""
+    return 2.0 * batch_band_choice(ctx, w)[0]
 
 
 def batch_run(contexts):

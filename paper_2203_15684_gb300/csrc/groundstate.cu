@@ -977,10 +977,11 @@ extern "C" hp_status hp_ground_state(hp_ctx* c, double nelec, int nspin, const i
 
 // Lowest levels of the bare Hamiltonian T + V_loc + V_NL (no Hxc, no Hubbard term) at the first k
 // point of the mesh (Gamma for the Gamma-centred meshes), by the non-self-consistent eigensolver.
-extern "C" hp_status hp_bare_levels(hp_ctx* c, int nlev, double* eps) {
+extern "C" hp_status hp_bare_levels(hp_ctx* c, int ik, int nlev, double* eps) {
     if (!c) return HP_EINVAL;
-    if (nlev < 1 || nlev > 100 || !eps) return fail(c, HP_EINVAL, "hp_bare_levels: 1 <= nlev <= 100 and eps given");
-    if (c->ks[0].npw < nlev + 6) return fail(c, HP_EINVAL, "hp_bare_levels: fewer plane waves than levels");
+    if (ik < 0 || ik >= c->nk || nlev < 1 || nlev > 100 || !eps)
+        return fail(c, HP_EINVAL, "hp_bare_levels: k index in the mesh, 1 <= nlev <= 100 and eps given");
+    if (c->ks[ik].npw < nlev + 6) return fail(c, HP_EINVAL, "hp_bare_levels: fewer plane waves than levels");
     const int nspin0 = c->nspin, nocc0 = c->nocc;
     double* veff0 = c->d_veff;
     const bool hub0 = c->hub_on;
@@ -989,14 +990,15 @@ extern "C" hp_status hp_bare_levels(hp_ctx* c, int nlev, double* eps) {
     c->d_veff = c->d_vloc;
     c->hub_on = false;
     SphereSet S0;
-    std::vector<const KSphere*> sph{&c->ks[0]};
+    std::vector<const KSphere*> sph{&c->ks[ik]};
     const bool fused0 = c->fused;
     hp_status st = upload_sphereset(c, sph, nullptr, S0);
     c->fused = fused0;
     double2* psi = nullptr;
     std::vector<double> lev;
     if (st == HP_OK && dalloc(c, &psi, (size_t)nlev * c->ld) != cudaSuccess) st = fail(c, HP_ENOMEM, "hp_bare_levels");
-    if (st == HP_OK) st = nscf_states(c, sph, S0, c->d_beta_k, nullptr, nullptr, psi, lev);
+    if (st == HP_OK)
+        st = nscf_states(c, sph, S0, c->d_beta_k + (size_t)ik * std::max(1, c->nproj) * c->ld, nullptr, nullptr, psi, lev);
     c->nspin = nspin0;
     c->nocc = nocc0;
     c->d_veff = veff0;

@@ -52,10 +52,10 @@ def test_batch_equals_cells_alone(precision):
 
 
 def test_seeded_cells_electron_rule_and_batch():
-    """Two cells of the seeded batch of 16 cells: the library's bare spectrum at k = 0 equals the
-    oracle's dense diagonalisation of T + V_loc + V_NL (1e-9 Ha); the electron-count rule (largest
-    gap among band counts n_H + n_L .. 5 n_H + 3 n_L) gives a ground state with a gap; the two cells
-    at once equal the cells alone (mixed form)."""
+    """Two cells of the seeded batch of 16 cells: the library's bare spectrum at the first and the last
+    k point equals the oracle's dense diagonalisation of T + V_loc + V_NL (1e-9 Ha); the electron-count
+    rule (largest gap over the k mesh among band counts n_H + n_L .. 5 n_H + 3 n_L) gives a ground
+    state with a gap; the two cells at once equal the cells alone (mixed form)."""
     from oracle.groundstate import eigensolve
     from oracle.model import Model
 
@@ -66,10 +66,11 @@ def test_seeded_cells_electron_rule_and_batch():
         ctx = P.Context.from_workload(w, cuda_stream=stream.cuda_stream, precision=1)
         nH = sum(1 for s, _ in w["atoms"] if s == 0)
         n = 5 * nH + 3 * (len(w["atoms"]) - nH) + 1
-        lev = ctx.bare_levels(n)
         m = Model(w)
-        ref, _ = eigensolve(m, m.kdata(m.kpts[0]), m.vloc_r(), n)
-        assert np.abs(lev - ref).max() < 1e-9
+        for ik in (0, len(m.kpts) - 1):
+            lev = ctx.bare_levels(n, ik)
+            ref, _ = eigensolve(m, m.kdata(m.kpts[ik]), m.vloc_r(), n)
+            assert np.abs(lev - ref).max() < 1e-9
         nelec = P.batch_electron_count(ctx, w)
         assert nelec % 2 == 0 and 2 * (len(w["atoms"])) <= nelec <= 2 * (n - 1)
         gs = ctx.ground_state(nelec, 1)
