@@ -334,6 +334,16 @@ __device__ __forceinline__ constexpr bool live(int i) {
     return !PR || i <= (N - 1) / 4 || i >= N - (N - 1) / 4;
 }
 
+// The x-lines that a plane's y-transforms run on: all N0, or with pruned lines only the live ones,
+// numbered 0 .. n-1 so that consecutive threads take consecutive live lines and no warp issues for
+// lines that are never computed.
+template <int N0, bool PR>
+struct YLines {
+    static constexpr int m = (N0 - 1) / 4;
+    static constexpr int n = PR ? 2 * m + 1 : N0;
+    __device__ __forceinline__ static int x(int i) { return (!PR || i <= m) ? i : i + N0 - n; }
+};
+
 // column transforms with one thread per (band, column): the column's sphere points are one run of
 // consecutive z (wrapping at N2), so every register index is a compile-time z.
 constexpr int kColRegThreads = 128;
@@ -525,8 +535,8 @@ __global__ void __launch_bounds__(PlaneCfg<V, N0, N1>::NT, PlaneCfg<V, N0, N1>::
         __syncthreads();
     } else {
         // ---- y-inverse: line x of plane p from its run of columns (zero where x has none)
-        if (tid < P * N0) {
-            const int p = tid / N0, x = tid % N0;
+        if (tid < P * YLines<N0, PR>::n) {
+            const int p = tid / YLines<N0, PR>::n, x = YLines<N0, PR>::x(tid % YLines<N0, PR>::n);
             const long long q = q0 + p;
             if (q < npairs && (!PR || live<N0, PR>(x))) {
                 const int k = kk[c0 + (int)(q / N2)];
@@ -586,8 +596,8 @@ __global__ void __launch_bounds__(PlaneCfg<V, N0, N1>::NT, PlaneCfg<V, N0, N1>::
         return;
     }
     // ---- y-forward on the x-lines that hold columns, written straight to the column buffer
-    if (tid < P * N0) {
-        const int p = tid / N0, x = tid % N0;
+    if (tid < P * YLines<N0, PR>::n) {
+        const int p = tid / YLines<N0, PR>::n, x = YLines<N0, PR>::x(tid % YLines<N0, PR>::n);
         const long long q = q0 + p;
         if (q < npairs) {
             const int k = kk[c0 + (int)(q / N2)];
@@ -1029,8 +1039,8 @@ __global__ void __launch_bounds__(PlaneCfg<float2, N0, N1>::NT, drho_minb<N0, N1
             if (in) myseen |= 1 << sp_of[tid];
         }
         // y-inverse on the x-lines of each band's column runs (zero elsewhere)
-        if (tid < P * N0) {
-            const int p = tid / N0, x = tid % N0;
+        if (tid < P * YLines<N0, PR>::n) {
+            const int p = tid / YLines<N0, PR>::n, x = YLines<N0, PR>::x(tid % YLines<N0, PR>::n);
             const int c = r0 + p;
             if (c < b1 && live<N0, PR>(x)) {
                 const int k = kk[c0 + c];
