@@ -352,10 +352,14 @@ template <class V, int N2, class VT, bool PR>
 __global__ void __launch_bounds__(kColRegThreads) col_inv_reg_kernel(
     const VT* __restrict__ X, int ld, const int* __restrict__ row, const int* __restrict__ kk, int c0,
     const int* __restrict__ ncol, const int* __restrict__ col_start, const int* __restrict__ col_len,
-    const int* __restrict__ iz, int ncmax, V* __restrict__ colbuf) {
-    const int c = blockIdx.y;
+    const int* __restrict__ iz, int ncmax, int nc, V* __restrict__ colbuf) {
+    // thread t: band c = t / ncmax of the chunk, column j = t % ncmax (the bands' columns packed, so
+    // that no warp is mostly past the last column of its band)
+    const long long t = (long long)blockIdx.x * kColRegThreads + threadIdx.x;
+    const int c = (int)(t / ncmax);
+    if (c >= nc) return;
+    const int j = (int)(t - (long long)c * ncmax);
     const int k = kk[c0 + c];
-    const int j = blockIdx.x * kColRegThreads + threadIdx.x;
     if (j >= ncol[k]) return;
     const int st = col_start[(long long)k * ncmax + j], len = col_len[(long long)k * ncmax + j];
     const int z0 = iz[(long long)k * ld + st];
@@ -379,13 +383,16 @@ __global__ void __launch_bounds__(kColRegThreads) col_fwd_reg_kernel(
     const int* __restrict__ npw, const int* __restrict__ ncol, const int* __restrict__ col_start,
     const int* __restrict__ col_len, const int* __restrict__ iz, const double* __restrict__ g2,
     const float* __restrict__ kin32, const double* __restrict__ shift, const VT* __restrict__ X,
-    VT* __restrict__ Y, int ld, int mode, double scale) {
-    const int c = blockIdx.y;
+    VT* __restrict__ Y, int ld, int mode, double scale, int nc) {
+    // thread t: band c = t / ncmax of the chunk, column j = t % ncmax (as in col_inv_reg_kernel); the
+    // band's threads also zero its padding beyond npw
+    const long long t = (long long)blockIdx.x * kColRegThreads + threadIdx.x;
+    const int c = (int)(t / ncmax);
+    if (c >= nc) return;
+    const int j = (int)(t - (long long)c * ncmax);
     const int k = kk[c0 + c];
     const long long ro = (long long)row[c0 + c] * ld;
-    if (blockIdx.x == 0)
-        for (int g = npw[k] + threadIdx.x; g < ld; g += kColRegThreads) zero_el(Y[ro + g]);
-    const int j = blockIdx.x * kColRegThreads + threadIdx.x;
+    for (int g = npw[k] + j; g < ld; g += ncmax) zero_el(Y[ro + g]);
     if (j >= ncol[k]) return;
     const int st = col_start[(long long)k * ncmax + j], len = col_len[(long long)k * ncmax + j];
     const int z0 = iz[(long long)k * ld + st];
@@ -814,22 +821,25 @@ static void col_kernels(bool inv, bool reg, dim3 g, const FusedArgs& a) {
     // pruned z lines for the FP32 production grids (36 and more points) when the spheres allow them
     constexpr bool kPrunable = sizeof(V) == 8 && N2 >= 36;
     const bool pr = kPrunable && S.lines_prunable && !getenv("HP_NO_PRUNE");
+    const dim3 gr(cdivf((long long)a.nc * S.ncmax, kColRegThreads));  // register kernels: packed (band, column)
     if (reg && inv) {
         if (pr)
-            col_inv_reg_kernel<V, N2, VT, kPrunable><<<g, kColRegThreads, 0, a.st>>>(
-                X, S.ld, L.d_row, L.d_k, a.c0, S.d_ncol, S.d_col_start, S.d_col_len, S.d_iz, S.ncmax, (V*)a.colA);
+            col_inv_reg_kernel<V, N2, VT, kPrunable><<<gr, kColRegThreads, 0, a.st>>>(
+                X, S.ld, L.d_row, L.d_k, a.c0, S.d_ncol, S.d_col_start, S.d_col_len, S.d_iz, S.ncmax, a.nc,
+                (V*)a.colA);
         else
-            col_inv_reg_kernel<V, N2, VT, false><<<g, kColRegThreads, 0, a.st>>>(
-                X, S.ld, L.d_row, L.d_k, a.c0, S.d_ncol, S.d_col_start, S.d_col_len, S.d_iz, S.ncmax, (V*)a.colA);
+            col_inv_reg_kernel<V, N2, VT, false><<<gr, kColRegThreads, 0, a.st>>>(
+                X, S.ld, L.d_row, L.d_k, a.c0, S.d_ncol, S.d_col_start, S.d_col_len, S.d_iz, S.ncmax, a.nc,
+                (V*)a.colA);
     } else if (reg) {
         if (pr)
-            col_fwd_reg_kernel<V, N2, VT, kPrunable><<<g, kColRegThreads, 0, a.st>>>(
+            col_fwd_reg_kernel<V, N2, VT, kPrunable><<<gr, kColRegThreads, 0, a.st>>>(
                 (const V*)a.colB, S.ncmax, L.d_row, L.d_k, a.c0, S.d_npw, S.d_ncol, S.d_col_start, S.d_col_len,
-                S.d_iz, S.d_g2, S.d_kin32, L.d_shift, X, Y, S.ld, a.mode, a.scale);
+                S.d_iz, S.d_g2, S.d_kin32, L.d_shift, X, Y, S.ld, a.mode, a.scale, a.nc);
         else
-            col_fwd_reg_kernel<V, N2, VT, false><<<g, kColRegThreads, 0, a.st>>>(
+            col_fwd_reg_kernel<V, N2, VT, false><<<gr, kColRegThreads, 0, a.st>>>(
                 (const V*)a.colB, S.ncmax, L.d_row, L.d_k, a.c0, S.d_npw, S.d_ncol, S.d_col_start, S.d_col_len,
-                S.d_iz, S.d_g2, S.d_kin32, L.d_shift, X, Y, S.ld, a.mode, a.scale);
+                S.d_iz, S.d_g2, S.d_kin32, L.d_shift, X, Y, S.ld, a.mode, a.scale, a.nc);
     } else if (inv) {
         col_inv_kernel<V, N2, VT><<<g, kColThreads, 0, a.st>>>(X, S.ld, L.d_row, L.d_k, a.c0, S.d_ncol, S.d_col_start,
                                                                S.d_col_len, S.d_iz, S.ncmax, (V*)a.colA,
