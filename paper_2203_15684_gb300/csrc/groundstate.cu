@@ -802,9 +802,10 @@ extern "C" hp_status hp_ground_state(hp_ctx* c, double nelec, int nspin, const i
                 for (int k = 0; k < nk; ++k)
                     for (int v = 0; v < nocc; ++v) list_add(Lo, (s * nk + k) * nbnd + v, k, s, 0.0);
             if ((st = upload_list(c, Lo)) != HP_OK) return st;
-            if ((st = ensure_grid(c, band_batch(c, Lo.nb))) != HP_OK) return st;
-            for (int c0 = 0; c0 < Lo.nb; c0 += c->grid_cap) {
-                const int nc = std::min(c->grid_cap, Lo.nb - c0);
+            const int gchunk = band_batch(c, Lo.nb);  // fixed by the sizes, not by the buffer's history
+            if ((st = ensure_grid(c, gchunk)) != HP_OK) return st;
+            for (int c0 = 0; c0 < Lo.nb; c0 += gchunk) {
+                const int nc = std::min(gchunk, Lo.nb - c0);
                 CK(k_scatter(c->kset, Lo, c0, nc, W.X, ld, c->d_grid, nr, c->st));
                 CK(fft3d(c->fft, c->d_grid, nc, +1, c->st));
                 CK(k_density_acc(c->d_grid, nc, nr, Lo, c0, wrho, nspin, c->d_rho, c->st));
@@ -926,8 +927,10 @@ extern "C" hp_status hp_ground_state(hp_ctx* c, double nelec, int nspin, const i
             for (int k = 0; k < nk; ++k)
                 for (int v = 0; v < nocc; ++v) list_add(Lo, (s * nk + k) * nbnd + v, k, s, 0.0);
         if ((st = upload_list(c, Lo)) != HP_OK) return st;
-        for (int c0 = 0; c0 < Lo.nb; c0 += c->grid_cap) {
-            const int nc = std::min(c->grid_cap, Lo.nb - c0);
+        const int gchunk = band_batch(c, Lo.nb);
+        if ((st = ensure_grid(c, gchunk)) != HP_OK) return st;
+        for (int c0 = 0; c0 < Lo.nb; c0 += gchunk) {
+            const int nc = std::min(gchunk, Lo.nb - c0);
             CK(k_scatter(c->kset, Lo, c0, nc, c->d_psi, ld, c->d_grid, nr, c->st));
             CK(fft3d(c->fft, c->d_grid, nc, +1, c->st));
             CK(k_density_acc(c->d_grid, nc, nr, Lo, c0, wrho, nspin, c->d_rho, c->st));
