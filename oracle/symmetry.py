@@ -10,8 +10,18 @@ Perturbed atoms (find_atpert):
      occ_matrix_0) differ by less than docc_thr (5e-5) form a class, whatever the sign of their
      moments; one atom per class, the first in atom order, is perturbed.
   2  one atom per species.
+  3  the orbits of the Hubbard atoms under the crystal's space group (below); one atom per orbit, the
+     first in atom order.
   4  every Hubbard atom.
-  (3, classes from the space group, is not built.)
+
+Space group: the operations x -> W x + t on fractional coordinates, W an integer matrix with entries
+in {-1, 0, 1} and determinant +-1 that keeps the lattice metric (W^T G W = G, G = A A^T with the
+lattice vectors as the rows of A), t such that every atom goes onto an atom of its species (within
+1e-5 in fractional coordinates), and the spin orientations of the Hubbard atoms kept up to one global
+sign.  For find_atpert 3 the columns are rebuilt with the operations themselves: an operation g that
+takes J' (cell 0) to J in cell L_J gives chi_{a,(0,J)} = chi_{g^-1(a + L_J),(0,J')}, used when g keeps
+the q-mesh supercell's lattice (W diag(n) = diag(n) M with M integer); the atom of g^-1(a + L_J) and its
+cell follow from its position.
 
 Column reconstruction (post-processing): the real-space response column of a Hubbard atom J that was
 not perturbed, chi_{(l,s),(0,J)} = (1/N_q) sum_q exp(i q.R_l) Delta^J_q n^s (Eqs. chi and
@@ -47,10 +57,56 @@ def total_traces(model, gs):
     return {ia: f * sum(t) for ia, t in spin_traces(model, gs).items()}
 
 
+def space_group(model, orient=None, tol=1e-5):
+    """[(W, t, perm)]: the crystal's operations x -> W x + t (fractional coordinates, column vectors)
+    and the atom each atom goes to; with orient ({Hubbard atom: +1/-1/0}) only the operations that keep
+    the orientations up to one global sign."""
+    import itertools
+
+    A = np.array(model.cell, dtype=float)
+    G = A @ A.T
+    frac = np.array(model.frac, dtype=float)
+    spec = list(model.atom_species)
+    nat = len(frac)
+    ops = []
+    for entries in itertools.product((-1, 0, 1), repeat=9):
+        Wm = np.array(entries, dtype=float).reshape(3, 3)
+        if abs(abs(np.linalg.det(Wm)) - 1.0) > 1e-9:
+            continue
+        if np.abs(Wm.T @ G @ Wm - G).max() > 1e-8 * np.abs(G).max():
+            continue
+        y0 = Wm @ frac[0]
+        for j in range(nat):
+            if spec[j] != spec[0]:
+                continue
+            t = frac[j] - y0
+            perm = []
+            for a in range(nat):
+                y = Wm @ frac[a] + t
+                hit = [b for b in range(nat) if spec[b] == spec[a]
+                       and np.abs((y - frac[b]) - np.round(y - frac[b])).max() < tol]
+                if len(hit) != 1:
+                    break
+                perm.append(hit[0])
+            if len(perm) != nat or len(set(perm)) != nat:
+                continue
+            if orient is not None:
+                if not any(all(orient[perm[a]] == sg * orient[a] for a in model.hub_atoms) for sg in (1, -1)):
+                    continue
+            ops.append((Wm.astype(int), t - np.floor(t), perm))
+    return ops
+
+
 def perturbed_atoms(model, gs, find_atpert=1, docc_thr=5e-5):
     """(atoms to perturb in atom order, {Hubbard atom: its class representative})."""
-    if find_atpert not in (1, 2, 4):
-        raise ValueError("find_atpert must be 1, 2 or 4")
+    if find_atpert not in (1, 2, 3, 4):
+        raise ValueError("find_atpert must be 1, 2, 3 or 4")
+    if find_atpert == 3:
+        ops = space_group(model, orientations(model, gs, docc_thr))
+        rep = {}
+        for ia in model.hub_atoms:  # the first atom of the orbit (the identity is among the operations)
+            rep[ia] = min(perm[ia] for _, _, perm in ops)
+        return [ia for ia in model.hub_atoms if rep[ia] == ia], rep
     tr = total_traces(model, gs)
     rep = {}
     for ia in model.hub_atoms:
@@ -104,17 +160,62 @@ def _length(model, f):
     return float(np.linalg.norm(f @ (model.cell * n[:, None])))
 
 
-def reconstruct_columns(model, cols, rep, orient, dist_thr=6e-4):
+def _supercell_ops(model, ops):
+    """The operations that keep the q-mesh supercell's lattice: W diag(n) = diag(n) M, M integer."""
+    n = np.array(model.qmesh, dtype=float)
+    out = []
+    for Wm, t, perm in ops:
+        M = np.diag(1.0 / n) @ Wm @ np.diag(n)
+        if np.abs(M - np.round(M)).max() < 1e-9:
+            out.append((Wm, t, perm))
+    return out
+
+
+def _rebuild_by_operation(model, src, J, Jp, op):
+    """Column (0, J) from column (0, J') through an operation g with g(J' at cell 0) = J at cell L_J."""
+    Wm, t, _ = op
+    R = model.supercell_R()
+    nh = len(model.hub_atoms)
+    n = np.array(model.qmesh, dtype=int)
+    index = {tuple(int(x) for x in r): l for l, r in enumerate(R)}
+    frac = np.array(model.frac, dtype=float)
+    L_J = np.round(Wm @ frac[Jp] + t - frac[J])
+    Winv = np.linalg.inv(Wm)
+    col = np.zeros_like(src)
+    for l in range(len(R)):
+        for s, ia in enumerate(model.hub_atoms):
+            y = Winv @ (frac[ia] + np.asarray(R[l], dtype=float) + L_J - t)
+            hit = None
+            for sp, ib in enumerate(model.hub_atoms):
+                d = y - frac[ib]
+                if model.atom_species[ib] == model.atom_species[ia] and np.abs(d - np.round(d)).max() < 1e-5:
+                    hit = (sp, np.round(d).astype(int))
+                    break
+            if hit is None:
+                raise ValueError("the operation does not map atom %d of cell %d onto a Hubbard atom" % (ia, l))
+            sp, cell = hit
+            col[l * nh + s] = src[index[tuple(int(x) for x in np.mod(cell, n))] * nh + sp]
+    return col
+
+
+def reconstruct_columns(model, cols, rep, orient, dist_thr=6e-4, ops=None):
     """cols = {J: real-space column} for the perturbed atoms; returns the columns of every Hubbard
-    atom, those of the others rebuilt from their representatives."""
+    atom, those of the others rebuilt from their representatives.  With ops (space_group's, for
+    find_atpert 3) an operation of the supercell that takes the representative onto the atom rebuilds
+    its column; otherwise (or where none does) the separation rule does."""
     R = model.supercell_R()
     nh = len(model.hub_atoms)
     out = dict(cols)
+    sops = _supercell_ops(model, ops) if ops is not None else []
     for J in model.hub_atoms:
         if J in out:
             continue
         Jp = rep[J]
         src = cols[Jp]
+        op = next((o for o in sops if o[2][Jp] == J), None)
+        if op is not None:
+            out[J] = _rebuild_by_operation(model, src, J, Jp, op)
+            continue
         col = np.zeros_like(src)
         for l in range(len(R)):
             for s, ia in enumerate(model.hub_atoms):

@@ -44,6 +44,8 @@ def test_rocksalt_classes(rocksalt):
         assert rep == {0: 0, 1: 0, 2: 0, 3: 0, 4: 4, 5: 4, 6: 4, 7: 4}
     pert, rep = S.perturbed_atoms(m, gs, 4)
     assert pert == list(range(8)) and all(rep[i] == i for i in range(8))
+    pert, rep = S.perturbed_atoms(m, gs, 3)  # the same orbits under the 192 operations
+    assert pert == [0, 4] and rep == {0: 0, 1: 0, 2: 0, 3: 0, 4: 4, 5: 4, 6: 4, 7: 4}
     # the antiferromagnetic start relaxes to zero moments (reading of the medium cell)
     assert set(S.orientations(m, gs).values()) == {0}
 
@@ -58,6 +60,8 @@ def test_displaced_site_is_its_own_class():
     assert rep[1] == 1 and 1 in pert and 0 in pert
     pert2, _ = S.perturbed_atoms(m, gs, 2)
     assert pert2 == [0, 4]
+    _, rep3 = S.perturbed_atoms(m, gs, 3)
+    assert rep3[1] == 1
 
 
 def test_rebuilt_columns_equal_computed_ones(rocksalt):
@@ -95,6 +99,42 @@ def test_rebuilt_columns_in_an_elongated_supercell():
     rs = {0: S.realspace_column(m, tr[0]), 4: np.zeros(len(m.supercell_R()) * len(m.hub_atoms), dtype=complex)}
     direct = S.realspace_column(m, tr[1])
     got = S.reconstruct_columns(m, rs, rep, orient)[1]
+    assert np.abs(got - direct).max() < 1e-8 * np.abs(direct).max()
+
+
+def test_space_group_orders():
+    """The conventional cubic cell of rocksalt has the 48 point operations of m-3m times the 4 fcc
+    centring translations (192); the 2 x 1 x 1 supercell keeps the 16 that leave the x axis on +-x
+    (times 4); the mirror cell has {1, m_xy, m_z, m_xy m_z}; a displaced H site leaves fewer."""
+    m = Model(W.medium_small(ecut=6.0, grid=(16, 16, 16), kmesh=(2, 2, 2), qmesh=(2, 1, 1)))
+    ops = S.space_group(m)
+    assert len(ops) == 192
+    assert len(S._supercell_ops(m, ops)) == 64
+    for Wm, t, perm in ops:  # every operation keeps the metric and maps each species onto itself
+        assert sorted(perm) == list(range(8)) and all(m.atom_species[perm[a]] == m.atom_species[a] for a in range(8))
+    mm = Model(W.mirror())
+    assert len(S.space_group(mm)) == 4
+    w = copy.deepcopy(W.medium_small(ecut=6.0, grid=(16, 16, 16), kmesh=(2, 2, 2), qmesh=(1, 1, 1)))
+    s, p = w["atoms"][1]
+    w["atoms"][1] = (s, (p[0] + 0.03, p[1], p[2]))
+    assert len(S.space_group(Model(w))) < 192
+
+
+def test_mirror_images_by_operation():
+    """find_atpert 3 on the mirror cell puts the two H sites in one orbit; the column of the second,
+    rebuilt from the first through the mirror, equals its computed column on a 2 x 2 x 1 q mesh (the
+    two are images under no translation, so the separation vectors do not match)."""
+    m = Model(W.mirror())
+    gs = G.scf(m, tol=1e-11)
+    pert, rep = S.perturbed_atoms(m, gs, 3)
+    assert pert == [0, 2] and rep == {0: 0, 1: 0, 2: 2}
+    nq = len(m.qpts)
+    tr = {J: [H.trace_column(m, R.solve_column(m, gs, iq, J, **TOL)["dn"]) for iq in range(nq)] for J in (0, 1)}
+    orient = S.orientations(m, gs)
+    ops = S.space_group(m, orient)
+    rs = {0: S.realspace_column(m, tr[0]), 2: np.zeros(len(m.supercell_R()) * len(m.hub_atoms), dtype=complex)}
+    direct = S.realspace_column(m, tr[1])
+    got = S.reconstruct_columns(m, rs, rep, orient, ops=ops)[1]
     assert np.abs(got - direct).max() < 1e-8 * np.abs(direct).max()
 
 

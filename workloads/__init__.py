@@ -139,6 +139,15 @@ def tiny_q(ecut=8.0, grid=(12, 12, 12), kmesh=(2, 2, 2), qmesh=(2, 1, 1)):
     return w
 
 
+def mirror(ecut=8.0, grid=(12, 12, 12), kmesh=(2, 2, 1), qmesh=(2, 2, 1)):
+    """Simple-cubic a = 8 bohr with two H at (0.3, 0, 0) and (0, 0.3, 0) and an L at the body centre;
+    14 electrons (gapped), nspin = 1.  The two H sites are images of each other under the mirror
+    x <-> y and under no lattice translation; the space group has four operations."""
+    return _workload("mirror", _cubic(8.0), [SPECIES_H, SPECIES_L],
+                     [(0, (0.3, 0, 0)), (0, (0, 0.3, 0)), (1, (0.5, 0.5, 0.5))], nelec=14, nspin=1,
+                     ecutwfc=ecut, kmesh=kmesh, qmesh=qmesh, grid=grid)
+
+
 def medium_small(ecut=10.0, grid=(18, 18, 18), kmesh=(2, 2, 2), qmesh=(2, 1, 1)):
     """The medium rocksalt cell (nspin = 2, antiferromagnetic start) at a low cutoff and a coarse
     mesh, small enough for the oracle to finish a full response matrix in a minute."""
