@@ -323,8 +323,11 @@ hp_status hp_hubbard(hp_ctx* ctx, double* chi0, double* chi, double* hub, double
  * the context.  find_atpert 1: atoms of one species whose spin-summed occupations Tr n^I (Eq.
  * occ_matrix_0 with the active Hubbard projectors; twice the channel for nspin = 1) differ by less
  * than docc_thr (the paper's default 5e-5) form a class, whatever the sign of their moments;
- * 2: one class per species; 4: every atom alone (this clears the classes).  The first atom of each
- * class in atom order represents it.  Writes *npert and atoms[0 .. *npert) (the representatives,
+ * 2: one class per species; 3: the orbits under the crystal's space group (the operations
+ * x -> W x + t on fractional coordinates with W an integer matrix of entries -1, 0, 1 and determinant
+ * +-1 that keeps the lattice metric, every atom going onto an atom of its species within 1e-5, and the
+ * Hubbard atoms' spin orientations kept up to one global sign); 4: every atom alone (this clears the
+ * classes).  The first atom of each class in atom order represents it.  Writes *npert and atoms[0 .. *npert) (the representatives,
  * atom indices; capacity nhub_atoms), rep[i] (the representative of the i-th Hubbard atom in
  * hp_hubbard_atoms order; may be NULL) and trace[2 i + s] (Tr n^{I s}, s < nspin; may be NULL).
  * With classes kept, hp_hubbard rebuilds the columns of every atom that does not represent its class
@@ -335,7 +338,10 @@ hp_status hp_hubbard(hp_ctx* ctx, double* chi0, double* chi, double* hub, double
  * where that exceeds docc_thr, else 0) whose separation from J' matches that of (l, s) from J within
  * dist_thr bohr (the paper's default 6e-4): as a vector modulo the q-mesh supercell, else, where no
  * atom matches the vector, as the minimum-image distance; the first such (l', s') in index order.
- * Errors: HP_ESTATE without a ground state; HP_EINVAL for another find_atpert, docc_thr <= 0,
+ * With find_atpert 3 an operation g of the space group that keeps the q-mesh supercell's lattice and
+ * takes J' (cell 0) to J in cell L_J rebuilds the column exactly: chi_{a,(0,J)} =
+ * chi_{g^-1(a + L_J),(0,J')} (the separation rule where no such operation exists).
+ * Errors: HP_ESTATE without a ground state; HP_EINVAL for find_atpert outside 1 .. 4, docc_thr <= 0,
  * dist_thr < 0 or a NULL npert/atoms.  A new ground state clears the classes. */
 hp_status hp_perturbed_atoms(hp_ctx* ctx, int find_atpert, double docc_thr, double dist_thr, int* npert, int* atoms,
                              int* rep, double* trace);

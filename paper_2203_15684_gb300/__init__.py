@@ -481,8 +481,9 @@ class Context:
         return e
 
     def perturbed_atoms(self, find_atpert=1, docc_thr=5e-5, dist_thr=6e-4):
-        """(atoms to perturb, representative atom of each Hubbard atom, Tr n^{I s} (nhub_atoms, 2));
-        the classes stay in the context for hubbard()'s column reconstruction."""
+        """(atoms to perturb, representative atom of each Hubbard atom, Tr n^{I s} (nhub_atoms, 2)) for
+        find_atpert 1 (equal occupations), 2 (species), 3 (space-group orbits) or 4 (all); the classes
+        stay in the context for hubbard()'s column reconstruction."""
         nh = self.query_sizes()["nhub_atoms"]
         npert = C.c_int()
         atoms = np.zeros(nh, dtype=np.int32)

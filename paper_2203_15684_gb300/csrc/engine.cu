@@ -814,6 +814,7 @@ void hp::invalidate_response(hp_ctx* c) {
     c->cols.clear();
     c->hub_rep.clear();  // the classes follow the ground state's occupations
     c->hub_orient.clear();
+    c->sym_ops.clear();
     for (QFam& F : c->qfam) F.built = false;  // the states at k+q follow the ground state
 }
 
@@ -2029,13 +2030,99 @@ static double supercell_length(const hp_ctx* c, const double f[3]) {
     return std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
 }
 
+// The crystal's space group: operations x -> W x + t on fractional coordinates (column vectors), W with
+// entries in {-1, 0, 1} and determinant +-1 keeping the lattice metric (W^T G W = G, G = A A^T, the
+// lattice vectors the rows of A), t taking every atom onto an atom of its species (1e-5 in fractional
+// coordinates), the Hubbard atoms' spin orientations kept up to one global sign.
+static std::vector<hp_ctx::SymOp> space_group(const hp_ctx* c, const std::vector<int>& orient) {
+    const int nat = (int)c->atom_species.size();
+    double G[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            G[3 * i + j] = 0.0;
+            for (int k = 0; k < 3; ++k) G[3 * i + j] += c->cell[3 * i + k] * c->cell[3 * j + k];
+        }
+    double gmax = 0.0;
+    for (double g : G) gmax = std::max(gmax, std::fabs(g));
+    auto frac_close = [](double d) { return std::fabs(d - std::nearbyint(d)) < 1e-5; };
+    std::vector<hp_ctx::SymOp> ops;
+    int W[9];
+    for (int code = 0; code < 19683; ++code) {  // 3^9 matrices with entries in {-1, 0, 1}
+        int r = code;
+        for (int i = 0; i < 9; ++i) {
+            W[i] = r % 3 - 1;
+            r /= 3;
+        }
+        const int det = W[0] * (W[4] * W[8] - W[5] * W[7]) - W[1] * (W[3] * W[8] - W[5] * W[6]) +
+                        W[2] * (W[3] * W[7] - W[4] * W[6]);
+        if (det != 1 && det != -1) continue;
+        bool metric = true;  // (W^T G W)_ij = sum_kl W_ki G_kl W_lj
+        for (int i = 0; i < 3 && metric; ++i)
+            for (int j = 0; j < 3 && metric; ++j) {
+                double v = 0.0;
+                for (int k = 0; k < 3; ++k)
+                    for (int l = 0; l < 3; ++l) v += W[3 * k + i] * G[3 * k + l] * W[3 * l + j];
+                metric = std::fabs(v - G[3 * i + j]) <= 1e-8 * gmax;
+            }
+        if (!metric) continue;
+        auto image = [&](int a, const double t[3], double y[3]) {
+            for (int i = 0; i < 3; ++i) {
+                y[i] = t[i];
+                for (int k = 0; k < 3; ++k) y[i] += W[3 * i + k] * c->frac[3 * a + k];
+            }
+        };
+        const double zero[3] = {0, 0, 0};
+        double y0[3];
+        image(0, zero, y0);
+        for (int j = 0; j < nat; ++j) {
+            if (c->atom_species[j] != c->atom_species[0]) continue;
+            hp_ctx::SymOp op;
+            for (int i = 0; i < 9; ++i) op.W[i] = W[i];
+            for (int i = 0; i < 3; ++i) op.t[i] = c->frac[3 * j + i] - y0[i];
+            bool ok = true;
+            std::vector<char> used(nat, 0);
+            for (int a = 0; a < nat && ok; ++a) {
+                double y[3];
+                image(a, op.t, y);
+                int hit = -1, nhit = 0;
+                for (int b = 0; b < nat; ++b)
+                    if (c->atom_species[b] == c->atom_species[a] && frac_close(y[0] - c->frac[3 * b]) &&
+                        frac_close(y[1] - c->frac[3 * b + 1]) && frac_close(y[2] - c->frac[3 * b + 2])) {
+                        hit = b;
+                        ++nhit;
+                    }
+                ok = nhit == 1 && !used[hit];
+                if (ok) {
+                    used[hit] = 1;
+                    op.perm.push_back(hit);
+                }
+            }
+            if (!ok) continue;
+            bool spin = false;
+            for (int sg = 1; sg >= -1 && !spin; sg -= 2) {
+                spin = true;
+                for (size_t h = 0; h < c->hub_atoms.size() && spin; ++h) {
+                    const int img = op.perm[c->hub_atoms[h]];
+                    int hi = -1;
+                    for (size_t g = 0; g < c->hub_atoms.size(); ++g)
+                        if (c->hub_atoms[g] == img) hi = (int)g;
+                    spin = hi >= 0 && orient[hi] == sg * orient[h];
+                }
+            }
+            if (!spin) continue;
+            for (int i = 0; i < 3; ++i) op.t[i] -= std::floor(op.t[i]);
+            ops.push_back(op);
+        }
+    }
+    return ops;
+}
+
 extern "C" hp_status hp_perturbed_atoms(hp_ctx* c, int find_atpert, double docc_thr, double dist_thr, int* npert,
                                         int* atoms, int* rep, double* trace) {
     if (!c) return HP_EINVAL;
     if (!c->have_gs) return fail(c, HP_ESTATE, "hp_perturbed_atoms: no ground state");
-    if ((find_atpert != 1 && find_atpert != 2 && find_atpert != 4) || !(docc_thr > 0) || !(dist_thr >= 0) || !npert ||
-        !atoms)
-        return fail(c, HP_EINVAL, "hp_perturbed_atoms: find_atpert 1, 2 or 4, docc_thr > 0, dist_thr >= 0, outputs given");
+    if (find_atpert < 1 || find_atpert > 4 || !(docc_thr > 0) || !(dist_thr >= 0) || !npert || !atoms)
+        return fail(c, HP_EINVAL, "hp_perturbed_atoms: find_atpert 1 to 4, docc_thr > 0, dist_thr >= 0, outputs given");
     const int nh = (int)c->hub_atoms.size(), nspin = c->nspin, nk = c->nk, nocc = c->nocc;
     // Tr n^{I s} = (1/N_k) sum_k sum_v sum_m |<phi^I_m,k|u_vk>|^2 (Eq. occ_matrix_0)
     BandList& L = c->L3;
@@ -2064,10 +2151,23 @@ extern "C" hp_status hp_perturbed_atoms(hp_ctx* c, int find_atpert, double docc_
                 tr[2 * a + L.spin[b]] += (p.x * p.x + p.y * p.y) / nk;
             }
     const double f = nspin == 1 ? 2.0 : 1.0;
+    std::vector<int> orient(nh, 0);
+    for (int a = 0; a < nh; ++a) {
+        const double d = nspin == 2 ? tr[2 * a] - tr[2 * a + 1] : 0.0;
+        orient[a] = std::fabs(d) <= docc_thr ? 0 : (d > 0 ? 1 : -1);
+    }
+    std::vector<hp_ctx::SymOp> ops;
+    if (find_atpert == 3) ops = space_group(c, orient);
     std::vector<int> rp(nh);
     for (int a = 0; a < nh; ++a) {
         rp[a] = a;
         if (find_atpert == 4) continue;
+        if (find_atpert == 3) {  // the first atom of the orbit (the identity is among the operations)
+            for (const auto& op : ops)
+                for (int b = 0; b < nh; ++b)
+                    if (c->hub_atoms[b] == op.perm[c->hub_atoms[a]]) rp[a] = std::min(rp[a], b);
+            continue;
+        }
         const double ta = f * (tr[2 * a] + tr[2 * a + 1]);
         for (int b = 0; b < a; ++b) {
             if (rp[b] != b || c->atom_species[c->hub_atoms[b]] != c->atom_species[c->hub_atoms[a]]) continue;
@@ -2088,14 +2188,12 @@ extern "C" hp_status hp_perturbed_atoms(hp_ctx* c, int find_atpert, double docc_
     *npert = m;
     c->hub_rep.clear();
     c->hub_orient.clear();
+    c->sym_ops.clear();
     if (find_atpert != 4) {
         c->hub_rep = rp;
-        c->hub_orient.assign(nh, 0);
-        for (int a = 0; a < nh; ++a) {
-            const double d = nspin == 2 ? tr[2 * a] - tr[2 * a + 1] : 0.0;
-            c->hub_orient[a] = std::fabs(d) <= docc_thr ? 0 : (d > 0 ? 1 : -1);
-        }
+        c->hub_orient = orient;
         c->dist_thr = dist_thr;
+        if (find_atpert == 3) c->sym_ops = ops;
     }
     return HP_OK;
 }
@@ -2135,11 +2233,73 @@ static hp_status rebuild_atom(hp_ctx* c, int jj, std::vector<double2>& cols) {
             }
             rs[(size_t)l * nh + s] = cmk(re / nq, im / nq);
         }
-    // the entry of (l, s) is that of the first (l', s') of the species of s and the orientation of s
-    // relative to J whose separation from J' matches: as a vector modulo the supercell (translation
-    // images), else as a minimum-image distance
     std::vector<double2> rj((size_t)nq * nh);
-    for (int l = 0; l < nq; ++l)
+    // find_atpert 3: an operation g of the q-mesh supercell (W diag(n) = diag(n) M, M integer) that
+    // takes J' (cell 0) to J in cell L_J gives chi_{a,(0,J)} = chi_{g^-1(a + L_J),(0,J')}
+    const hp_ctx::SymOp* use = nullptr;
+    for (const auto& op : c->sym_ops) {
+        if (op.perm[c->hub_atoms[jr]] != c->hub_atoms[jj]) continue;
+        bool keeps = true;
+        for (int i = 0; i < 3 && keeps; ++i)
+            for (int k = 0; k < 3 && keeps; ++k) keeps = (op.W[3 * i + k] * c->qmesh[k]) % c->qmesh[i] == 0;
+        if (keeps) {
+            use = &op;
+            break;
+        }
+    }
+    if (use) {
+        const int* W = use->W;
+        const int det = W[0] * (W[4] * W[8] - W[5] * W[7]) - W[1] * (W[3] * W[8] - W[5] * W[6]) +
+                        W[2] * (W[3] * W[7] - W[4] * W[6]);
+        int Wi[9];  // the inverse of a unimodular integer matrix: adjugate / det
+        Wi[0] = (W[4] * W[8] - W[5] * W[7]) * det;
+        Wi[1] = (W[2] * W[7] - W[1] * W[8]) * det;
+        Wi[2] = (W[1] * W[5] - W[2] * W[4]) * det;
+        Wi[3] = (W[5] * W[6] - W[3] * W[8]) * det;
+        Wi[4] = (W[0] * W[8] - W[2] * W[6]) * det;
+        Wi[5] = (W[2] * W[3] - W[0] * W[5]) * det;
+        Wi[6] = (W[3] * W[7] - W[4] * W[6]) * det;
+        Wi[7] = (W[1] * W[6] - W[0] * W[7]) * det;
+        Wi[8] = (W[0] * W[4] - W[1] * W[3]) * det;
+        const int ir = c->hub_atoms[jr], ij = c->hub_atoms[jj];
+        double LJ[3];
+        for (int i = 0; i < 3; ++i) {
+            double v = use->t[i] - c->frac[3 * ij + i];
+            for (int k = 0; k < 3; ++k) v += W[3 * i + k] * c->frac[3 * ir + k];
+            LJ[i] = std::nearbyint(v);
+        }
+        for (int l = 0; l < nq; ++l)
+            for (int s = 0; s < nh; ++s) {
+                int R[3];
+                cell_of(c, l, R);
+                const int ia = c->hub_atoms[s];
+                double X[3], y[3];
+                for (int i = 0; i < 3; ++i) X[i] = c->frac[3 * ia + i] + R[i] + LJ[i] - use->t[i];
+                for (int i = 0; i < 3; ++i) y[i] = Wi[3 * i] * X[0] + Wi[3 * i + 1] * X[1] + Wi[3 * i + 2] * X[2];
+                int hit = -1;
+                for (int sp = 0; sp < nh && hit < 0; ++sp) {
+                    const int ib = c->hub_atoms[sp];
+                    if (c->atom_species[ib] != c->atom_species[ia]) continue;
+                    bool on = true;
+                    int cell[3];
+                    for (int i = 0; i < 3 && on; ++i) {
+                        const double d = y[i] - c->frac[3 * ib + i];
+                        cell[i] = (int)std::nearbyint(d);
+                        on = std::fabs(d - cell[i]) < 1e-5;
+                    }
+                    if (!on) continue;
+                    int lp = 0;
+                    for (int i = 0; i < 3; ++i) lp = lp * c->qmesh[i] + ((cell[i] % c->qmesh[i]) + c->qmesh[i]) % c->qmesh[i];
+                    hit = lp * nh + sp;
+                }
+                if (hit < 0) return fail(c, HP_ESTATE, "hp_hubbard: a symmetry operation does not map a Hubbard atom onto one");
+                rj[(size_t)l * nh + s] = rs[hit];
+            }
+    }
+    // otherwise the entry of (l, s) is that of the first (l', s') of the species of s and the
+    // orientation of s relative to J whose separation from J' matches: as a vector modulo the supercell
+    // (translation images), else as a minimum-image distance
+    for (int l = 0; l < nq && !use; ++l)
         for (int s = 0; s < nh; ++s) {
             int R[3];
             cell_of(c, l, R);

@@ -536,6 +536,13 @@ struct hp_ctx {
     std::vector<int> hub_rep;          // per Hubbard atom: index (in hub_atoms) of its representative
     std::vector<int> hub_orient;       // per Hubbard atom: +1 / -1 / 0 spin orientation
     double dist_thr = 6e-4;            // bohr, distance tolerance of the column reconstruction
+    // find_atpert 3: the space-group operations x -> W x + t (fractional) and the atom each atom goes to
+    struct SymOp {
+        int W[9];
+        double t[3];
+        std::vector<int> perm;
+    };
+    std::vector<SymOp> sym_ops;
     // scratch (device)
     double2* d_grid = nullptr;         // grid_cap x nr
     int grid_cap = 0;

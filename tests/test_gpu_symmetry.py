@@ -1,6 +1,6 @@
 """Symmetry reductions on the GPU (hp_perturbed_atoms, hp_irreducible_q and the reconstruction in
-hp_hubbard; Sec. 2.4 "Symmetry", Sec. 3.2): the classes and occupations against the oracle, and chi
-from the reduced set of responses against chi from every response.
+hp_hubbard; Sec. 2.4 "Symmetry", Sec. 3.2): the classes (find_atpert 1 to 4) and occupations against
+the oracle, and chi from the reduced set of responses against chi from every response.
 
 The rocksalt cell's four H (and four L) sites are images of each other under fcc translations of the
 cubic cell, so their columns are relabellings of one another (pinned in the oracle tests); a 3 x 1 x 1
@@ -35,7 +35,7 @@ def test_classes_and_traces_match_oracle():
     ctx = P.Context.from_workload(w)
     import_ground_state(ctx, m, gs)
     ref = S.spin_traces(m, gs)
-    for mode in (1, 2, 4):
+    for mode in (1, 2, 3, 4):
         atoms, rep, tr = ctx.perturbed_atoms(mode)
         ref_atoms, ref_rep = S.perturbed_atoms(m, gs, mode)
         assert atoms == ref_atoms
@@ -68,6 +68,28 @@ def test_reduced_atoms_give_the_full_chi(precision):
     red.perturbed_atoms(4)
     with pytest.raises(P.HPError):
         red.hubbard()
+
+
+def test_space_group_orbits_give_the_full_chi():
+    """find_atpert 3 on the mirror cell (its two H sites are images under the mirror x <-> y and under
+    no translation): the library's orbits equal the oracle's, and chi with the second H column rebuilt
+    through the mirror equals chi from both columns (FP64, q mesh 2 x 2 x 1)."""
+    w = W.mirror()
+    m = Model(w)
+    gs = G.scf(m, tol=1e-11)
+    ref_pert, ref_rep = S.perturbed_atoms(m, gs, 3)
+    full = P.Context.from_workload(w)
+    import_ground_state(full, m, gs)
+    atoms, _ = full.hubbard_atoms()
+    c0, c, hub = _chi(full, atoms, range(len(m.qpts)))
+    red = P.Context.from_workload(w)
+    import_ground_state(red, m, gs)
+    pert, rep, _ = red.perturbed_atoms(3)
+    assert pert == ref_pert == [0, 2] and rep == [ref_rep[a] for a in m.hub_atoms]
+    r0, r, rhub = _chi(red, pert, range(len(m.qpts)))
+    assert np.abs(r0 - c0).max() < 1e-9 * np.abs(c0).max()
+    assert np.abs(r - c).max() < 1e-9 * np.abs(c).max()
+    assert np.abs(rhub - hub).max() < 1e-6
 
 
 def test_time_reversal_gives_the_full_chi():
