@@ -39,6 +39,9 @@ Time reversal (the +-q of the small group of q): for a ground state with real po
 Hubbard orbitals the response to exp(-i q.R) is the complex conjugate of the response to exp(i q.R),
 Delta_{-q} n = conj(Delta_q n); of each pair {q, -q + G} of the q mesh the first in mesh order is
 computed.
+
+Star of q (with the space group): an operation of the q-mesh supercell relates the trace columns of
+chi at q and q' = W^-T q (below), so that only one (q, J) pair of each orbit is computed.
 """
 
 from __future__ import annotations
@@ -270,3 +273,89 @@ def irreducible_q(model):
         jq = minus_q(model, iq)
         partner.append(min(iq, jq))
     return sorted(set(partner)), partner
+
+
+# ---- star of q: the (q, J) responses that the space group relates ------------------------------
+#
+# For an operation g: x -> W x + t of the q-mesh supercell, atom a goes to pi(a) with
+# W x_a + t = x_pi(a) + L_a (L_a integer).  The per-q trace columns x_q[J][s] =
+# sum_R exp(-2 pi i q.R) chi_{(s, R), (J, 0)} then obey
+#     x_{q'}[pi(J)][pi(s)] = exp(2 pi i q'.(L_J - L_s)) x_q[J][s],   q' = W^-T q,
+# and time reversal gives x_{-q}[J] = conj(x_q[J]).  A (q, J) pair reached from a computed one by these
+# relations need not be computed.
+
+def _q_index(model, qfrac):
+    n = np.array(model.qmesh, dtype=int)
+    i = np.mod(np.rint(np.asarray(qfrac, dtype=float) * n).astype(int), n)
+    return int((i[0] * n[1] + i[1]) * n[2] + i[2])
+
+
+def _lattice_shifts(model, op):
+    Wm, t, perm = op
+    frac = np.array(model.frac, dtype=float)
+    return {a: np.rint(Wm @ frac[a] + t - frac[perm[a]]) for a in range(len(frac))}
+
+
+def pair_image(model, op, iq, J):
+    """(iq', J') = the image of the pair (q, J) under the operation."""
+    Wm, _, perm = op
+    qp = np.linalg.inv(Wm).T @ np.asarray(model.qpts[iq], dtype=float)
+    return _q_index(model, qp), perm[J]
+
+
+def irreducible_pairs(model, ops, atoms=None, time_reversal=True):
+    """The (iq, J) pairs to compute: the first pair of each orbit under the supercell's operations
+    (and q -> -q), the pairs taken J-major (the Hubbard atoms in order), then q in mesh order."""
+    atoms = list(model.hub_atoms) if atoms is None else atoms
+    sops = _supercell_ops(model, ops)
+    seen, out = set(), []
+    for J in atoms:
+        for iq in range(len(model.qpts)):
+            if (iq, J) in seen:
+                continue
+            out.append((iq, J))
+            stack = [(iq, J)]
+            seen.add((iq, J))
+            while stack:
+                p = stack.pop()
+                imgs = [pair_image(model, op, p[0], p[1]) for op in sops]
+                if time_reversal:
+                    imgs.append((minus_q(model, p[0]), p[1]))
+                for im in imgs:
+                    if im not in seen:
+                        seen.add(im)
+                        stack.append(im)
+    return out
+
+
+def fill_pairs(model, cols, ops, time_reversal=True):
+    """cols = {(iq, J): trace vector over the Hubbard atoms} for the computed pairs; returns the trace
+    vectors of every pair reached from them through the supercell's operations and time reversal."""
+    sops = _supercell_ops(model, ops)
+    hub = list(model.hub_atoms)
+    pos = {a: i for i, a in enumerate(hub)}
+    out = dict(cols)
+    stack = list(cols)
+    while stack:
+        iq, J = stack.pop()
+        x = out[(iq, J)]
+        derived = []
+        for op in sops:
+            iqp, Jp = pair_image(model, op, iq, J)
+            if (iqp, Jp) in out:
+                continue
+            L = _lattice_shifts(model, op)
+            qp = np.asarray(model.qpts[iqp], dtype=float)
+            y = np.zeros_like(x)
+            for s, a in enumerate(hub):
+                y[pos[op[2][a]]] = np.exp(2j * np.pi * np.dot(qp, L[J] - L[a])) * x[s]
+            derived.append(((iqp, Jp), y))
+        if time_reversal:
+            mq = minus_q(model, iq)
+            if (mq, J) not in out:
+                derived.append(((mq, J), x.conj()))
+        for key, y in derived:
+            if key not in out:
+                out[key] = y
+                stack.append(key)
+    return out

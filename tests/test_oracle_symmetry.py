@@ -120,22 +120,74 @@ def test_space_group_orders():
     assert len(S.space_group(Model(w))) < 192
 
 
-def test_mirror_images_by_operation():
+@pytest.fixture(scope="module")
+def mirror():
+    """The mirror cell's ground state and every (q, J) trace column of chi (q mesh 2 x 2 x 1)."""
+    m = Model(W.mirror())
+    gs = G.scf(m, tol=1e-11)
+    cols = {}
+    for iq in range(len(m.qpts)):
+        ctx = R.ResponseContext(m, gs, iq)
+        for J in m.hub_atoms:
+            cols[(iq, J)] = H.trace_column(m, R.solve_column(m, gs, iq, J, ctx=ctx, **TOL)["dn"])
+    return m, gs, cols
+
+
+def test_mirror_images_by_operation(mirror):
     """find_atpert 3 on the mirror cell puts the two H sites in one orbit; the column of the second,
     rebuilt from the first through the mirror, equals its computed column on a 2 x 2 x 1 q mesh (the
     two are images under no translation, so the separation vectors do not match)."""
-    m = Model(W.mirror())
-    gs = G.scf(m, tol=1e-11)
+    m, gs, cols = mirror
     pert, rep = S.perturbed_atoms(m, gs, 3)
     assert pert == [0, 2] and rep == {0: 0, 1: 0, 2: 2}
     nq = len(m.qpts)
-    tr = {J: [H.trace_column(m, R.solve_column(m, gs, iq, J, **TOL)["dn"]) for iq in range(nq)] for J in (0, 1)}
+    tr = {J: [cols[(iq, J)] for iq in range(nq)] for J in (0, 1)}
     orient = S.orientations(m, gs)
     ops = S.space_group(m, orient)
     rs = {0: S.realspace_column(m, tr[0]), 2: np.zeros(len(m.supercell_R()) * len(m.hub_atoms), dtype=complex)}
     direct = S.realspace_column(m, tr[1])
     got = S.reconstruct_columns(m, rs, rep, orient, ops=ops)[1]
     assert np.abs(got - direct).max() < 1e-8 * np.abs(direct).max()
+
+
+def test_star_of_q(mirror):
+    """The (q, J) pairs of the mirror cell reduce to 7 of 12 under its four operations (the mirror
+    takes (1/2, 0, 0) to (0, 1/2, 0) and one H site to the other); the 5 others, derived from the
+    computed 7 with the lattice-shift phases, equal their computed trace columns, and chi follows.
+    The rocksalt cell's 64 pairs on a 2 x 2 x 2 mesh reduce to 8 (one H and one L at the four classes
+    of q)."""
+    m, gs, cols = mirror
+    ops = S.space_group(m, S.orientations(m, gs))
+    irr = S.irreducible_pairs(m, ops)
+    assert len(irr) == 7 and all(p in cols for p in irr)
+    full = S.fill_pairs(m, {p: cols[p] for p in irr}, ops)
+    assert set(full) == set(cols)
+    for p in cols:
+        if p not in irr:
+            assert np.abs(full[p] - cols[p]).max() < 1e-9 * np.abs(cols[p]).max()
+    assert np.abs(H.assemble_chi(m, full) - H.assemble_chi(m, cols)).max() < 1e-9 * np.abs(H.assemble_chi(m, cols)).max()
+    mr = Model(W.medium_small(ecut=6.0, grid=(16, 16, 16), kmesh=(2, 2, 2), qmesh=(2, 2, 2)))
+    assert S.irreducible_pairs(mr, S.space_group(mr)) == [(0, 0), (1, 0), (3, 0), (7, 0), (0, 4), (1, 4), (3, 4), (7, 4)]
+
+
+def test_star_of_q_phases():
+    """The lattice-shift phases at q = (1/3, 0, 0), where they are not +-1: in the Gamma-only rocksalt
+    cell on a 3 x 1 x 1 q mesh the fcc translation (1/2, 1/2, 0) takes H site 1 onto site 0 of the next
+    cell; the column of site 1 derived from that of site 0 equals its computed column (H entries; the L
+    orbitals carry no occupation at Gamma), and so does the q = 2/3 column by time reversal."""
+    m = Model(W.medium_small(ecut=6.0, grid=(16, 16, 16), kmesh=(1, 1, 1), qmesh=(3, 1, 1)))
+    gs = G.scf(m, tol=1e-11)
+    cols = {}
+    for J in (0, 1):
+        for iq in (1, 2):
+            cols[(iq, J)] = H.trace_column(m, R.solve_column(m, gs, iq, J, **TOL)["dn"])
+    ops = S.space_group(m, S.orientations(m, gs))
+    full = S.fill_pairs(m, {(1, 0): cols[(1, 0)]}, ops)
+    hsl = slice(0, 4)
+    for p in ((1, 1), (2, 0), (2, 1)):
+        assert np.abs(full[p][hsl] - cols[p][hsl]).max() < 1e-9 * np.abs(cols[p][hsl]).max()
+    # the phases matter here: without them site 1's column is off
+    assert np.abs(cols[(1, 1)][hsl] - cols[(1, 0)][[1, 0, 3, 2]]).max() > 1e-6 * np.abs(cols[(1, 1)]).max()
 
 
 def test_columns_to_matrix_matches_q_sum():
