@@ -496,21 +496,21 @@ class Engine:
                 "U_eV": [float(u) for u in hp["U"]], "V": [(int(a), int(b), float(d), float(v)) for a, b, d, v in hp["V"]]}
 
 
-    def chi_matrix_reduced(self, precision, full):
-        """The same chi with hp.x's default reductions (Sec. 3.2): find_atpert = 1 (one atom per class
-        of equal occupations, the other columns rebuilt by hp_hubbard) and one q of each time-reversal
-        pair; -> dict as chi_matrix plus the perturbed atoms and |U - U_full|, |V - V_full| in meV."""
+    def chi_matrix_reduced(self, precision, full, find_atpert=1):
+        """The same chi with the symmetry reductions (Sec. 2.4, Sec. 3.2): find_atpert = 1 (hp.x's
+        default: one atom per class of equal occupations, the other columns rebuilt by hp_hubbard) or
+        3 (space-group orbits and the star of q), and time reversal; only hp_irreducible_pairs' (q, J)
+        responses are computed.  -> dict as chi_matrix plus the perturbed atoms and |U - U_full|,
+        |V - V_full| in meV."""
         self.ctx.set_precision(precision)
 
         def run():
-            atoms, _, _ = self.ctx.perturbed_atoms(1)
-            irr, _ = self.ctx.irreducible_q()
+            atoms, _, _ = self.ctx.perturbed_atoms(find_atpert)
             hpsi, n = 0, 0
-            for J in atoms:
-                for iq in irr:
-                    _, _, info = self.ctx.response(iq, J)
-                    hpsi += info["hpsi"]
-                    n += 1
+            for iq, J in self.ctx.irreducible_pairs():
+                _, _, info = self.ctx.response(iq, J)
+                hpsi += info["hpsi"]
+                n += 1
             return hpsi, n, atoms, self.ctx.hubbard_parameters()
 
         try:
@@ -708,6 +708,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_chi_matrix:
         chi["mixed"] = eng.chi_matrix(1)
         chi["mixed_reduced"] = eng.chi_matrix_reduced(1, chi["mixed"])
+        chi["mixed_star"] = eng.chi_matrix_reduced(1, chi["mixed"], find_atpert=3)
         if args.fp64_full:
             chi["fp64"] = eng.chi_matrix(0)
             chi["u_err_mev_mixed_vs_fp64"], chi["v_err_mev_mixed_vs_fp64"] = uv_error_mev(chi["mixed"], chi["fp64"])

@@ -310,8 +310,9 @@ hp_status hp_set_hubbard(hp_ctx* ctx, const double* U, int nV, const hp_pairV* V
  * within d_min + 6e-4 bohr of it (the paper's dist_thr default, Appendix B); *nV is the capacity
  * of V on input and the number of pairs on output (all pairs are counted even when they do not fit;
  * HP_EINVAL then).  Any output pointer may be NULL (nV with V).  Needs every (q, J) column
- * (HP_ESTATE otherwise), where a missing (q, J) is taken from (-q, J) by conjugation and the
- * columns of an atom that was not perturbed are rebuilt from its class (hp_perturbed_atoms).  chi0 and chi are written even when one of them is singular or has a
+ * (HP_ESTATE otherwise), where a missing (q, J) is taken from (-q, J) by conjugation, with
+ * find_atpert 3 from the star of q (hp_irreducible_pairs), and the columns of an atom that was not
+ * perturbed are rebuilt from its class (hp_perturbed_atoms).  chi0 and chi are written even when one of them is singular or has a
  * 1-norm condition number above 1e10; U, V and hub are then not written and the call returns
  * HP_ESINGULAR. */
 hp_status hp_hubbard(hp_ctx* ctx, double* chi0, double* chi, double* hub, double* U, hp_pairV* V, int* nV);
@@ -353,6 +354,16 @@ hp_status hp_perturbed_atoms(hp_ctx* ctx, int find_atpert, double docc_thr, doub
  * the computed q whose conjugate response it takes; may be NULL).  hp_hubbard fills a missing (q, J)
  * column from (-q, J) this way.  Errors: HP_EINVAL for a NULL ctx, nirr or iq. */
 hp_status hp_irreducible_q(const hp_ctx* ctx, int* nirr, int* iq, int* partner);
+
+/* hp_irreducible_pairs: the (q, J) responses to compute under the kept classes (hp_perturbed_atoms)
+ * and, with find_atpert 3, the star of q: an operation x -> W x + t of the space group that keeps the
+ * q-mesh supercell relates the trace columns of chi at q and q' = W^-T q,
+ *   x_{q'}[pi(J)][pi(s)] = exp(2 pi i q'.(L_J - L_s)) x_q[J][s],   W x_a + t = x_pi(a) + L_a,
+ * and time reversal relates q and -q (x_{-q}[J] = conj(x_q[J])).  The first pair of each orbit is
+ * listed, J-major (representative atoms in atom order), then q in mesh order.  Writes *npairs,
+ * iq[0 .. *npairs) and atom[0 .. *npairs) (capacity nq x nhub_atoms).  hp_hubbard derives the other
+ * pairs with these relations.  Errors: HP_EINVAL for a NULL argument. */
+hp_status hp_irreducible_pairs(const hp_ctx* ctx, int* npairs, int* iq, int* atom);
 
 /* Several independent cells at once (the batching form; the paper's code runs one system per job,
  * so there is no counterpart there).  For every context cells[0 .. ncells-1], each set up with its

@@ -83,7 +83,8 @@ SYMBOLS = ["hp_default_options", "hp_setup", "hp_query_sizes", "hp_sphere", "hp_
            "hp_destroy", "hp_selftest_fft_host", "hp_selftest_eigh", "hp_get_wavefunctions", "hp_profile_begin",
            "hp_profile_end", "hp_launch_count", "hp_apply_h_noalloc", "hp_set_precision", "hp_selftest_convert",
            "hp_batch_run", "hp_alloc_count", "hp_sphere_kq", "hp_apply_sternheimer", "hp_selftest_xc",
-           "hp_selftest_tc", "hp_set_hubbard", "hp_bare_levels", "hp_perturbed_atoms", "hp_irreducible_q"]
+           "hp_selftest_tc", "hp_set_hubbard", "hp_bare_levels", "hp_perturbed_atoms", "hp_irreducible_q",
+           "hp_irreducible_pairs"]
 
 
 def lib():
@@ -132,6 +133,7 @@ def lib():
     L.hp_bare_levels.argtypes = [V, I, I, P(D)]
     L.hp_perturbed_atoms.argtypes = [V, I, D, D, P(I), P(I), P(I), P(D)]
     L.hp_irreducible_q.argtypes = [V, P(I), P(I), P(I)]
+    L.hp_irreducible_pairs.argtypes = [V, P(I), P(I), P(I)]
     for n in SYMBOLS:
         f = getattr(L, n)
         if n in ("hp_launch_count", "hp_alloc_count"):
@@ -502,6 +504,17 @@ class Context:
         partner = np.zeros(nq, dtype=np.int32)
         self._check(lib().hp_irreducible_q(self._ptr, C.byref(n), _iptr(iq), _iptr(partner)), "hp_irreducible_q")
         return [int(x) for x in iq[:n.value]], [int(x) for x in partner]
+
+    def irreducible_pairs(self):
+        """[(iq, atom)]: the responses to compute under the kept classes and, with find_atpert 3, the
+        star of q (hp_irreducible_pairs)."""
+        s = self.query_sizes()
+        cap = s["nq"] * s["nhub_atoms"]
+        n = C.c_int()
+        iq = np.zeros(cap, dtype=np.int32)
+        at = np.zeros(cap, dtype=np.int32)
+        self._check(lib().hp_irreducible_pairs(self._ptr, C.byref(n), _iptr(iq), _iptr(at)), "hp_irreducible_pairs")
+        return [(int(a), int(b)) for a, b in zip(iq[:n.value], at[:n.value])]
 
     def sphere_kq(self, iq, ik):
         """Miller indices (npw, 3) of the k+q sphere in the response's coefficient order."""

@@ -2205,6 +2205,172 @@ static void cell_of(const hp_ctx* c, int l, int R[3]) {
     R[2] = l % c->qmesh[2];
 }
 
+// the operation keeps the q-mesh supercell's lattice: W diag(n) = diag(n) M with M integer
+static bool keeps_supercell(const hp_ctx* c, const hp_ctx::SymOp& op) {
+    for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 3; ++k)
+            if ((op.W[3 * i + k] * c->qmesh[k]) % c->qmesh[i] != 0) return false;
+    return true;
+}
+
+// inverse of a unimodular integer matrix: the adjugate times the determinant (+-1)
+static void int_inverse(const int W[9], int Wi[9]) {
+    const int det = W[0] * (W[4] * W[8] - W[5] * W[7]) - W[1] * (W[3] * W[8] - W[5] * W[6]) +
+                    W[2] * (W[3] * W[7] - W[4] * W[6]);
+    Wi[0] = (W[4] * W[8] - W[5] * W[7]) * det;
+    Wi[1] = (W[2] * W[7] - W[1] * W[8]) * det;
+    Wi[2] = (W[1] * W[5] - W[2] * W[4]) * det;
+    Wi[3] = (W[5] * W[6] - W[3] * W[8]) * det;
+    Wi[4] = (W[0] * W[8] - W[2] * W[6]) * det;
+    Wi[5] = (W[2] * W[3] - W[0] * W[5]) * det;
+    Wi[6] = (W[3] * W[7] - W[4] * W[6]) * det;
+    Wi[7] = (W[1] * W[6] - W[0] * W[7]) * det;
+    Wi[8] = (W[0] * W[4] - W[1] * W[3]) * det;
+}
+
+// q' = W^-T q on the q mesh (q = i / n per axis); returns its index
+static int q_image(const hp_ctx* c, const int Wi[9], int iq) {
+    int Q[3];
+    cell_of(c, iq, Q);
+    int out = 0;
+    for (int i = 0; i < 3; ++i) {
+        double v = 0.0;  // (W^-T q)_i = sum_k (W^-1)_ki q_k
+        for (int k = 0; k < 3; ++k) v += Wi[3 * k + i] * (double)Q[k] / c->qmesh[k];
+        const int m = (int)std::nearbyint(v * c->qmesh[i]);
+        out = out * c->qmesh[i] + ((m % c->qmesh[i]) + c->qmesh[i]) % c->qmesh[i];
+    }
+    return out;
+}
+
+// index of a Hubbard atom (atom index) in hub_atoms
+static int hub_index(const hp_ctx* c, int atom) {
+    for (size_t h = 0; h < c->hub_atoms.size(); ++h)
+        if (c->hub_atoms[h] == atom) return (int)h;
+    return -1;
+}
+
+// Star of q: from the known (q, J) trace columns of chi0 and chi, every pair reached through the
+// operations that keep the supercell, x_{q'}[pi(J)][pi(s)] = exp(2 pi i q'.(L_J - L_s)) x_q[J][s] with
+// q' = W^-T q and W x_a + t = x_pi(a) + L_a, and through time reversal, x_{-q}[J] = conj(x_q[J]).
+// cols0, cols: [q][J][s]; have: [q][J].
+static void fill_star(const hp_ctx* c, std::vector<double2>& cols0, std::vector<double2>& cols,
+                      std::vector<char>& have) {
+    const int nh = (int)c->hub_atoms.size(), nq = c->nq;
+    const double PI2 = 6.28318530717958647692;
+    struct Prep {
+        int Wi[9];
+        std::vector<std::array<int, 3>> L;  // per atom
+        std::vector<int> hperm;             // per Hubbard index: the image's Hubbard index
+    };
+    std::vector<Prep> ops;
+    for (const auto& op : c->sym_ops) {
+        if (!keeps_supercell(c, op)) continue;
+        Prep p;
+        int_inverse(op.W, p.Wi);
+        const int nat = (int)op.perm.size();
+        p.L.resize(nat);
+        for (int a = 0; a < nat; ++a)
+            for (int i = 0; i < 3; ++i) {
+                double v = op.t[i] - c->frac[3 * op.perm[a] + i];
+                for (int k = 0; k < 3; ++k) v += op.W[3 * i + k] * c->frac[3 * a + k];
+                p.L[a][i] = (int)std::nearbyint(v);
+            }
+        p.hperm.resize(nh);
+        for (int h = 0; h < nh; ++h) p.hperm[h] = hub_index(c, op.perm[c->hub_atoms[h]]);
+        ops.push_back(std::move(p));
+    }
+    std::vector<int> stack;
+    for (int i = 0; i < nq * nh; ++i)
+        if (have[i]) stack.push_back(i);
+    auto put = [&](int iqp, int Jp, const std::vector<double2>& y0, const std::vector<double2>& y) {
+        const size_t k = (size_t)iqp * nh + Jp;
+        if (have[k]) return;
+        have[k] = 1;
+        for (int s = 0; s < nh; ++s) {
+            cols0[k * nh + s] = y0[s];
+            cols[k * nh + s] = y[s];
+        }
+        stack.push_back((int)k);
+    };
+    std::vector<double2> y0(nh), y(nh);
+    while (!stack.empty()) {
+        const int key = stack.back();
+        stack.pop_back();
+        const int iq = key / nh, J = key % nh;
+        const double2* x0 = &cols0[(size_t)key * nh];
+        const double2* x = &cols[(size_t)key * nh];
+        for (const Prep& p : ops) {
+            const int iqp = q_image(c, p.Wi, iq), Jp = p.hperm[J];
+            if (Jp < 0 || have[(size_t)iqp * nh + Jp]) continue;
+            int Qp[3];
+            cell_of(c, iqp, Qp);
+            bool ok = true;
+            for (int s = 0; s < nh && ok; ++s) {
+                const int sp = p.hperm[s];
+                ok = sp >= 0;
+                if (!ok) break;
+                double a = 0.0;
+                for (int i = 0; i < 3; ++i)
+                    a += (double)Qp[i] / c->qmesh[i] * (p.L[c->hub_atoms[J]][i] - p.L[c->hub_atoms[s]][i]);
+                const double cs = std::cos(PI2 * a), sn = std::sin(PI2 * a);
+                y0[sp] = cmk(cs * x0[s].x - sn * x0[s].y, cs * x0[s].y + sn * x0[s].x);
+                y[sp] = cmk(cs * x[s].x - sn * x[s].y, cs * x[s].y + sn * x[s].x);
+            }
+            if (ok) put(iqp, Jp, y0, y);
+        }
+        const int mq = minus_q(c, iq);
+        for (int s = 0; s < nh; ++s) {
+            y0[s] = cmk(x0[s].x, -x0[s].y);
+            y[s] = cmk(x[s].x, -x[s].y);
+        }
+        put(mq, J, y0, y);
+    }
+}
+
+extern "C" hp_status hp_irreducible_pairs(const hp_ctx* c, int* npairs, int* iq_out, int* atom_out) {
+    if (!c || !npairs || !iq_out || !atom_out) return HP_EINVAL;
+    const int nh = (int)c->hub_atoms.size(), nq = c->nq;
+    std::vector<int> Wis;
+    std::vector<std::vector<int>> hperm;
+    for (const auto& op : c->sym_ops) {
+        if (!keeps_supercell(c, op)) continue;
+        int Wi[9];
+        int_inverse(op.W, Wi);
+        Wis.insert(Wis.end(), Wi, Wi + 9);
+        std::vector<int> hp(nh);
+        for (int h = 0; h < nh; ++h) hp[h] = hub_index(c, op.perm[c->hub_atoms[h]]);
+        hperm.push_back(hp);
+    }
+    std::vector<char> seen((size_t)nq * nh, 0);
+    int n = 0;
+    for (int J = 0; J < nh; ++J) {
+        if (!c->hub_rep.empty() && c->hub_rep[J] != J) continue;
+        for (int iq = 0; iq < nq; ++iq) {
+            if (seen[(size_t)iq * nh + J]) continue;
+            iq_out[n] = iq;
+            atom_out[n] = c->hub_atoms[J];
+            ++n;
+            std::vector<int> stack{iq * nh + J};
+            seen[(size_t)iq * nh + J] = 1;
+            while (!stack.empty()) {
+                const int key = stack.back();
+                stack.pop_back();
+                const int q0 = key / nh, j0 = key % nh;
+                std::vector<int> imgs{minus_q(c, q0) * nh + j0};
+                for (size_t o = 0; o < hperm.size(); ++o)
+                    if (hperm[o][j0] >= 0) imgs.push_back(q_image(c, &Wis[9 * o], q0) * nh + hperm[o][j0]);
+                for (int im : imgs)
+                    if (!seen[im]) {
+                        seen[im] = 1;
+                        stack.push_back(im);
+                    }
+            }
+        }
+    }
+    *npairs = n;
+    return HP_OK;
+}
+
 // Column (q, J) traces of every q for Hubbard atom jj, rebuilt from its class representative: the
 // representative's real-space column chi_{(l,s),(0,J')} = (1/N_q) sum_q exp(2 pi i q.R_l) x_q[s],
 // the distance rule, and back to q: x_q[s] = sum_l exp(-2 pi i q.R_l) chi_{(l,s),(0,J)}.
@@ -2237,30 +2403,15 @@ static hp_status rebuild_atom(hp_ctx* c, int jj, std::vector<double2>& cols) {
     // find_atpert 3: an operation g of the q-mesh supercell (W diag(n) = diag(n) M, M integer) that
     // takes J' (cell 0) to J in cell L_J gives chi_{a,(0,J)} = chi_{g^-1(a + L_J),(0,J')}
     const hp_ctx::SymOp* use = nullptr;
-    for (const auto& op : c->sym_ops) {
-        if (op.perm[c->hub_atoms[jr]] != c->hub_atoms[jj]) continue;
-        bool keeps = true;
-        for (int i = 0; i < 3 && keeps; ++i)
-            for (int k = 0; k < 3 && keeps; ++k) keeps = (op.W[3 * i + k] * c->qmesh[k]) % c->qmesh[i] == 0;
-        if (keeps) {
+    for (const auto& op : c->sym_ops)
+        if (op.perm[c->hub_atoms[jr]] == c->hub_atoms[jj] && keeps_supercell(c, op)) {
             use = &op;
             break;
         }
-    }
     if (use) {
         const int* W = use->W;
-        const int det = W[0] * (W[4] * W[8] - W[5] * W[7]) - W[1] * (W[3] * W[8] - W[5] * W[6]) +
-                        W[2] * (W[3] * W[7] - W[4] * W[6]);
-        int Wi[9];  // the inverse of a unimodular integer matrix: adjugate / det
-        Wi[0] = (W[4] * W[8] - W[5] * W[7]) * det;
-        Wi[1] = (W[2] * W[7] - W[1] * W[8]) * det;
-        Wi[2] = (W[1] * W[5] - W[2] * W[4]) * det;
-        Wi[3] = (W[5] * W[6] - W[3] * W[8]) * det;
-        Wi[4] = (W[0] * W[8] - W[2] * W[6]) * det;
-        Wi[5] = (W[2] * W[3] - W[0] * W[5]) * det;
-        Wi[6] = (W[3] * W[7] - W[4] * W[6]) * det;
-        Wi[7] = (W[1] * W[6] - W[0] * W[7]) * det;
-        Wi[8] = (W[0] * W[4] - W[1] * W[3]) * det;
+        int Wi[9];
+        int_inverse(W, Wi);
         const int ir = c->hub_atoms[jr], ij = c->hub_atoms[jj];
         double LJ[3];
         for (int i = 0; i < 3; ++i) {
@@ -2358,6 +2509,8 @@ extern "C" hp_status hp_hubbard(hp_ctx* c, double* chi0_out, double* chi_out, do
     std::vector<char> have((size_t)nq * nh, 0);
     for (int iq = 0; iq < nq; ++iq)
         for (int jj = 0; jj < nh; ++jj) {
+            // with classes kept only the representatives' columns are taken as computed
+            if (!c->hub_rep.empty() && c->hub_rep[jj] != jj) continue;
             // the column itself, else the conjugate of (-q, J) (time reversal)
             auto it = c->cols.find({iq, c->hub_atoms[jj]});
             double cj = 1.0;
@@ -2377,10 +2530,13 @@ extern "C" hp_status hp_hubbard(hp_ctx* c, double* chi0_out, double* chi_out, do
             if (!have[(size_t)iq * nh + jj]) return false;
         return true;
     };
-    // with classes kept, every atom that does not represent its class takes the rebuilt columns
+    // find_atpert 3: every pair the space group and time reversal reach from the computed ones
+    if (!c->sym_ops.empty()) fill_star(c, cols0, cols, have);
+    // with classes kept, every atom that does not represent its class (and that the star of q has not
+    // completed) takes the rebuilt columns
     for (int jj = 0; jj < nh; ++jj) {
         const bool rebuilt = !c->hub_rep.empty() && c->hub_rep[jj] != jj;
-        if (!rebuilt && complete(jj)) continue;
+        if (complete(jj)) continue;
         if (!rebuilt || !complete(c->hub_rep[jj])) return fail(c, HP_ESTATE, "hp_hubbard: a (q, J) response is missing");
         hp_status s = rebuild_atom(c, jj, cols0);
         if (s == HP_OK) s = rebuild_atom(c, jj, cols);
