@@ -713,6 +713,15 @@ def main():
             chi["fp64"] = eng.chi_matrix(0)
             chi["u_err_mev_mixed_vs_fp64"], chi["v_err_mev_mixed_vs_fp64"] = uv_error_mev(chi["mixed"], chi["fp64"])
             chi["speedup_mixed_vs_fp64"] = chi["fp64"]["seconds"] / chi["mixed"]["seconds"]
+        elif args.fp64_steps > 0:
+            # the FP64 matrix through the star of q (its reconstruction is exact), and the mixed form's
+            # error on every U and V against it
+            chi["fp64_star"] = eng.chi_matrix_reduced(0, chi["mixed"], find_atpert=3)
+            if "U_eV" in chi["fp64_star"]:
+                chi["u_err_mev_mixed_vs_fp64"], chi["v_err_mev_mixed_vs_fp64"] = uv_error_mev(chi["mixed"], chi["fp64_star"])
+                chi["u_err_mev_mixed_star_vs_fp64"], chi["v_err_mev_mixed_star_vs_fp64"] = uv_error_mev(
+                    chi["mixed_star"], chi["fp64_star"])
+            eng.ctx.set_precision(1)
     companion = None
     if rank == 0 and world == 1 and args.companion != "none":
         del ctx, eng.ctx
